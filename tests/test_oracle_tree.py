@@ -1,0 +1,87 @@
+"""Pins for oracle/tree.py (Sec. 2.2, Algorithm 1, Appendix two-scale relations)."""
+import numpy as np
+import pytest
+
+from oracle import basis, tree as T
+from tests.closed_forms import legendre_scaled
+
+
+def test_projection_exact_for_polynomials():
+    k, j, a = 5, 2, (1, 3, 2)
+    rng = np.random.default_rng(0)
+    coef = rng.standard_normal((k, k, k))
+    # f(x) = sum coef_i phi^j_{i,a}(x) evaluated at the box's GL nodes
+    xs = T.box_nodes(k, j, a)
+    P = [legendre_scaled(k, xs[d] * 2 ** j - a[d]) for d in range(3)]
+    vals = np.einsum("ijk,ia,jb,kc->abc", coef, P[0], P[1], P[2]) * 2 ** (1.5 * j)
+    s = T.project_values(k, j, vals.ravel())
+    assert np.allclose(s, coef, atol=1e-12)
+    pts = np.random.default_rng(1).uniform(0, 1, (20, 3)) / 2 ** j + np.array(a) / 2 ** j
+    v2 = T.eval_block(k, j, a, s, pts)
+    Q = [legendre_scaled(k, pts[:, d] * 2 ** j - a[d]) for d in range(3)]
+    ref = np.einsum("ijk,in,jn,kn->n", coef, Q[0], Q[1], Q[2]) * 2 ** (1.5 * j)
+    assert np.allclose(v2, ref, atol=1e-10)
+
+
+def small_density():
+    return T.Density([50.0, -20.0], [60.0, 200.0], [[0.4, 0.55, 0.5], [0.62, 0.4, 0.47]])
+
+
+@pytest.mark.parametrize("k", [3, 6])
+def test_compress_reconstruct_round_trip_and_parseval(k):
+    tr, _ = T.build_tree(small_density(), k, 1e-5, 4, init_level=1)
+    ref = {key: n.s.copy() for key, n in tr.items() if n.leaf}
+    T.compress(tr, k)
+    leaf2 = sum((s ** 2).sum() for s in ref.values())
+    parseval = (tr[(0, 0, 0, 0)].s ** 2).sum() + sum(n.dnorm ** 2 for n in tr.values() if not n.leaf)
+    assert abs(parseval - leaf2) <= 1e-13 * leaf2
+    for key, n in tr.items():
+        if n.leaf:
+            n.s = np.zeros_like(n.s)
+    T.reconstruct(tr, k)
+    depth = T.levels(tr)
+    err = np.sqrt(sum(((tr[key].s - s) ** 2).sum() for key, s in ref.items()))
+    assert err <= 1e-14 * depth * np.sqrt(leaf2)
+
+
+def test_internal_scaling_blocks_are_projections():
+    """After compress, an internal block equals the direct projection of the
+    leaves' piecewise polynomial onto the coarser box (Sec. 2.2.1)."""
+    k = 4
+    tr, _ = T.build_tree(small_density(), k, 1e-4, 3, uniform_level=2)
+    T.compress(tr, k)
+    key = (1, 1, 0, 1)
+    # project the level-2 piecewise polynomial onto box (1, (1,0,1)) with a fine rule
+    g, w = basis.gl01(k)
+    s = np.zeros((k, k, k))
+    for child in T.children(key):
+        xs = T.box_nodes(k, 2, child[1:])
+        pts = T.grid(xs)
+        vals = T.eval_block(k, 2, child[1:], tr[child].s, pts)
+        u = [xs[d] * 2 - key[1 + d] for d in range(3)]
+        P = [basis.phi(k, u[d]) * w / 4 for d in range(3)]     # child width 1/4
+        s += np.einsum("ia,jb,kc,abc->ijk", P[0], P[1], P[2], vals.reshape(k, k, k)) * 2 ** 1.5
+    assert np.allclose(tr[key].s, s, atol=1e-12)
+
+
+def test_algorithm1_linf_bound():
+    k, eps = 6, 1e-5
+    dens = small_density()
+    tr, hit = T.build_tree(dens, k, eps, 6, init_level=1)
+    assert not hit
+    tol = eps * dens.scale()
+    rng = np.random.default_rng(2)
+    worst = 0.0
+    for key, n in tr.items():
+        if not n.leaf:
+            continue
+        j, a = key[0], key[1:]
+        pts = (rng.uniform(0, 1, (30, 3)) + np.array(a)) / 2 ** j
+        worst = max(worst, np.abs(dens(pts) - T.eval_block(k, j, a, n.s, pts)).max())
+    assert worst <= 20 * tol
+
+
+def test_uniform_tree_shape():
+    tr, _ = T.build_tree(small_density(), 3, 1e-3, 5, uniform_level=3)
+    assert len(tr) == 1 + 8 + 64 + 512
+    assert sum(n.leaf for n in tr.values()) == 512
