@@ -1,0 +1,309 @@
+"""Benchmark of the adaptive ns-form apply (one JSON line on rank 0).
+
+A step is one pass of the hot path over the resident input tree of the
+3-D Poisson workload (k = 8, eps = 1e-6, adaptive tree to depth 7, 64 unit-mass
+Gaussians): compress (redundant tree) -> apply_ns (screen, Step-2 refinement,
+separated apply) -> reconstruct (eq. g_assemble, compress, truncation).  The
+operator tables and the input tree are built before timing (inputs resident in
+HBM).  The metric is block-applies/s: items of the plain FP64 screen per
+second of device time (CUDA events on the library's stream), with output
+coeffs/s and the speedup over the plain FP64 GPU path beside it.
+
+--impl reference runs the FP64 CPU oracle (the reference implementation of
+this method in this repository) on a bounded sample of the same workload.
+Under torchrun each rank runs an independent replica (the workload does not
+shard); the value is the units of all ranks over the slowest rank's time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "block-applies/s at eps, 3D Poisson k=8 (plain-FP64 screen item count)"
+UNIT = "block-applies/s"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# SIMT peaks from unit counts and the maximum SM clock (2070 MHz, 152 SMs):
+# FP32: 128 lanes/SM x 2 flop; FP64: the nominal 1.25 TFLOP/s of the part.
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_TFLOPS = 1.25
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+ORACLE_SAMPLE_SRC = r"""
+import json, os, sys, time
+sys.path.insert(0, ROOT)
+import numpy as np
+from oracle import apply as OA, operator as OO, tree as OT
+from paper_0706_0747_gb300 import workloads as W
+cfg, d = W.poisson_k8()
+dens = OT.Density(d.coef, d.expo, d.centers, d.r2coef)
+tree, _ = OT.build_tree(dens, cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
+OT.compress(tree, cfg.k)
+op = OO.Operator(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
+keys = sorted(tree.keys())
+budget = BUDGET
+steps = STEPS
+out = []
+rng = np.random.default_rng(7)
+for s in range(steps):
+    order = rng.permutation(len(keys))
+    st = {}
+    t0 = time.perf_counter()
+    done, items = 0, 0
+    for start in range(0, len(order), 16):
+        sample = [keys[i] for i in order[start:start + 16]]
+        st = {}
+        OA.apply_ns(op, tree, stats=st, nodes=sample)
+        items += st["n_items"]
+        done += len(sample)
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    out.append({"items": items, "nodes": done, "seconds": dt})
+print("ORACLE_JSON " + json.dumps({"steps": out, "n_nodes": len(keys)}))
+"""
+
+
+def run_oracle_sample(budget_s, steps):
+    src = ORACLE_SAMPLE_SRC.replace("ROOT", repr(ROOT)).replace("BUDGET", str(budget_s)).replace(
+        "STEPS", str(steps))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", src], capture_output=True, text=True, env=env)
+    for line in r.stdout.splitlines():
+        if line.startswith("ORACLE_JSON "):
+            return json.loads(line[len("ORACLE_JSON "):])
+    raise RuntimeError("oracle sample failed:\n" + r.stdout[-2000:] + r.stderr[-2000:])
+
+
+def cpu_baseline(budget_s=15.0):
+    res = run_oracle_sample(budget_s, 1)
+    s = res["steps"][0]
+    return {"value": s["items"] / s["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{s['nodes']} of {res['n_nodes']} output nodes (random order), "
+                       f"{s['items']} items in {s['seconds']:.1f} s; tree build, compress and "
+                       "operator tables untimed; single thread")}
+
+
+# ---------------------------------------------------------------- GPU arm
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32", "tc"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        res = run_oracle_sample(10.0, args.steps + args.warmup)
+        steps = res["steps"][args.warmup:]
+        items = sum(s["items"] for s in steps)
+        secs = sum(s["seconds"] for s in steps)
+        value = items / secs
+        sample = (f"per step: a random subset of the {res['n_nodes']} output nodes applied for about 10 s "
+                  "(tree build, compress and operator tables untimed); single thread")
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / len(steps),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": "poisson_k8_eps1e-6_adaptive7"},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import numpy as np
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_0706_0747_gb300 import mra, workloads as W
+
+    cfg, dens = W.poisson_k8()
+    stream = torch.cuda.current_stream()
+    op = mra.make_operator(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
+    tree, hit = mra.build_tree(dens, cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
+    k, n = cfg.k, tree.n
+    avail = ["fp64", "fp32"]
+    prec = args.precision if args.precision != "auto" else avail[-1]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(p):
+        mra.compress(tree)
+        g, st = mra.apply_ns(op, tree, precision=p)
+        rem = mra.reconstruct(g, mode="assemble", truncate=True, eps=cfg.eps)
+        n_out = g.n
+        g.free()
+        return st, n_out
+
+    def timed(p, K, W_):
+        for _ in range(W_):
+            step(p)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        tot_ms, ms_apply, stats = 0.0, [], None
+        l0 = mra.kernel_launches()
+        for _ in range(K):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats, n_out = step(p)
+            e1.record(stream)
+            e1.synchronize()
+            tot_ms += e0.elapsed_time(e1)
+            ms_apply.append(stats["ms_apply"])
+        launches = mra.kernel_launches() - l0
+        torch.cuda.synchronize()
+        if ws > 1:
+            t = torch.tensor([tot_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot_ms = float(t.item())
+            dist.barrier()
+        return tot_ms, ms_apply, stats, n_out, launches
+
+    # plain FP64 GPU path (the speedup's denominator)
+    clk = Clocks(local)
+    K, Wu = args.steps, max(3, args.warmup)
+    try:
+        clk.start()
+        ms64, ap64, st64, nout, l64 = timed("fp64", K, Wu)
+        if prec != "fp64":
+            ms, apl, st, nout, launches = timed(prec, K, Wu)
+        else:
+            ms, apl, st, launches = ms64, ap64, st64, l64
+    finally:
+        clocks = clk.stop()
+    items_plain = st64["n_items"]
+    value = ws * items_plain * K / (ms / 1e3)
+    value64 = ws * items_plain * K / (ms64 / 1e3)
+    coeffs = ws * nout * k ** 3 * K / (ms / 1e3)
+
+    # e2e through the C ABI with host buffers (import -> hot path -> export)
+    coords, leaf, blocks, _ = tree.export()
+    h2d = coords.nbytes + leaf.nbytes + blocks.nbytes
+    e2e_times, d2h = [], 0
+    for it in range(Wu + K):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t_in = mra.tree_import(k, coords, leaf, blocks)
+        mra.compress(t_in)
+        g, _ = mra.apply_ns(op, t_in, precision=prec)
+        mra.reconstruct(g, mode="assemble", truncate=True, eps=cfg.eps)
+        oc, ol, ob, od = g.export()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        d2h = oc.nbytes + ol.nbytes + ob.nbytes + od.nbytes
+        g.free()
+        t_in.free()
+        if it >= Wu:
+            e2e_times.append(dt)
+    e2e_val = ws * items_plain * len(e2e_times) / sum(e2e_times)
+
+    pk, pk_kind = peaks()
+    flops_item = 6 * k ** 4
+    ms_apply = statistics.median(apl)
+    achieved = items_plain * flops_item / (ms_apply / 1e3) / 1e12
+    if prec == "tc":
+        peak, bound = pk["bf16_tflops_sustained"], "tensor"
+    elif prec == "fp32":
+        peak, bound = FP32_SIMT_TFLOPS, "alu"
+    else:
+        peak, bound = FP64_TFLOPS, "alu"
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": f"apply ({prec})", "peak_source": pk_kind if bound == "tensor" else
+            "unit counts x 2070 MHz" if prec == "fp32" else "nominal FP64 rate of the part",
+            "flops_per_item": flops_item}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wu,
+                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32", "tc": "f16x2-split/f32acc"}[prec],
+                "data": "synthetic",
+                "config": {"workload": cfg.name, "k": k, "eps": cfg.eps, "M": op.info().M, "tree_nodes": n,
+                           "depth_hit": bool(hit), "precision": prec, "l2": "flushed (256 MB write) between steps",
+                           "inputs": "64 unit-mass Gaussians, log10 a~U[2,5], centres~U[0.1,0.9]^3, seed 2000"},
+                "items_plain_fp64": items_plain, "pairs": st64["n_pairs"], "ghosts": st64["n_ghosts"],
+                "output_coeffs_per_s": coeffs, "fp64_value": value64, "speedup_vs_fp64_gpu": value / value64,
+                "ms_apply_kernel": ms_apply, "roofline": roof,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clocks}
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

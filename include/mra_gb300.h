@@ -1,0 +1,273 @@
+/*
+ * mra_gb300.h -- C ABI of the GB300 (sm_103a) adaptive non-standard-form apply.
+ *
+ * The library applies a radial-kernel operator T with kernel
+ * K_{mu,alpha}(r) (the kernel of (-Laplacian + mu^2)^{-alpha}) to a function f
+ * on B = [0,1]^3 stored as an adaptive tree of Legendre-multiwavelet scaling
+ * blocks, following Beylkin, Cheruvu and Perez, "Fast Adaptive Algorithms in the
+ * Non-Standard Form for Multidimensional Problems":
+ *   - the kernel is a weighted sum of Gaussians (Sec. 3, eqs. IntegralRepr and
+ *     KernelApproxByGaussians);
+ *   - the operator is applied in the modified non-standard form scale by scale
+ *     (Sec. 2.3, eq. apply_algo; Algorithm 3), with the separated 1-D blocks
+ *     F^{j;m,l} (eq. KernelFactor) and norm-based screening (Sec. 4);
+ *   - the per-scale outputs are assembled by eq. g_assemble and truncated.
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an int status: MRA_OK (0) or one of the codes below.
+ *     mra_last_error() returns a static, NUL-terminated message for the last
+ *     failure on the calling thread.
+ *   - Pointers named *_host point to host memory; all other array pointers are
+ *     device memory.  `stream` is a cudaStream_t passed as void* (NULL = the
+ *     legacy default stream).  Work is queued on that stream; calls return when
+ *     queued unless stated otherwise ("synchronous").
+ *   - Handles (mra_tree*, mra_op*) are owned by the library, opaque, and freed
+ *     exactly once with mra_free().  Output handles are set to NULL on failure.
+ *   - Device memory comes from the optional allocator hook (mra_alloc); when the
+ *     hook is NULL the library uses cudaMallocAsync / cudaFreeAsync on `stream`.
+ *   - There is no CPU fallback: every arithmetic step runs in the library's
+ *     CUDA kernels on the current device.
+ *
+ * Blocks are k x k x k arrays s[i1][i2][i3] (i3 fastest) of coefficients in the
+ * tensor basis phi^j_{i1,a1}(x1) phi^j_{i2,a2}(x2) phi^j_{i3,a3}(x3), where
+ * phi^j_{i,a}(x) = 2^{j/2} sqrt(2i+1) P_i(2^{j+1} x - 2a - 1) on box a of level j
+ * (Appendix, eq. scalingFNC).  Trees are complete 2^3-trees: every internal node
+ * has its 8 children (Algorithm 1 refines the 8 children together).
+ */
+#ifndef MRA_GB300_H
+#define MRA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MRA_OK        0
+#define MRA_EINVAL    1   /* invalid argument (k, eps, alpha, sizes, NULL, ...) */
+#define MRA_ENOMEM    2   /* the allocator returned NULL                        */
+#define MRA_ECUDA     3   /* a CUDA runtime call or kernel launch failed        */
+#define MRA_ETIMEOUT  4   /* a bounded device-side wait gave up                 */
+#define MRA_EDEPTH    5   /* warning: max_level reached with the l-inf test     */
+                          /* still failing; the tree is valid (Algorithm 1)     */
+#define MRA_ESTATE    6   /* the handle is not in the state the call needs      */
+
+#define MRA_MAX_K      12  /* largest basis order k (polynomials per direction) */
+#define MRA_MAX_LEVEL  12  /* deepest level j of a tree / operator table        */
+#define MRA_MAX_TERMS 512  /* largest number M of Gaussian terms                */
+
+typedef struct mra_tree mra_tree;
+typedef struct mra_op mra_op;
+
+/* Device allocator hook: alloc returns device memory of `bytes` usable on
+ * `stream` (NULL on failure); free releases it.  ctx is passed through. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void  (*free)(void* ptr, void* stream, void* ctx);
+    void* ctx;
+} mra_alloc;
+
+/* A density f(x) = sum_g (coef_g + r2coef_g |x - c_g|^2) exp(-expo_g |x - c_g|^2)
+ * (host arrays, copied by the call).  r2coef may be NULL (all zero).  This
+ * covers unit-mass Gaussians and the paper's Poisson test density
+ * rho = -Laplacian sum exp(-a r^2) (Sec. 6.1). */
+typedef struct {
+    int n;
+    const double* coef_host;     /* n      */
+    const double* r2coef_host;   /* n or NULL */
+    const double* expo_host;     /* n, > 0 */
+    const double* center_host;   /* 3n, (x, y, z) per term */
+} mra_density;
+
+/* Tree states */
+#define MRA_TREE_LEAVES     0  /* data on leaves only (adaptive tree, Sec. 2.2.1)  */
+#define MRA_TREE_REDUNDANT  1  /* s on all nodes, d norms on internal nodes        */
+#define MRA_TREE_NSFORM     2  /* per-scale outputs ghat^j on all nodes            */
+
+typedef struct {
+    int k;                     /* basis order                                     */
+    int n_nodes;               /* nodes, sorted by level then Morton key          */
+    int n_levels;              /* deepest level + 1                               */
+    int state;                 /* MRA_TREE_*                                      */
+    int depth_hit;             /* 1 when Algorithm 1 stopped at max_level         */
+    int level_offset[MRA_MAX_LEVEL + 2];  /* nodes of level j: [off[j], off[j+1]) */
+} mra_tree_info;
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 (Sec. 2.2): adaptive function decomposition in d = 3.
+ * Level by level, each box's k^3 Gauss-Legendre values are projected
+ * (eq. fvals2coefs, tensor form), interpolated to the GL nodes of its 8
+ * children and compared with direct evaluation; if any child differs by more
+ * than eps * max_g |f(c_g)| (l-infinity) the 8 children are processed, else the
+ * box is a leaf holding its own coefficients.  init_level: refine uniformly up
+ * to this level before testing.  uniform_level >= 0: build the uniform tree of
+ * that depth instead (no test).  Leaves deeper than max_level are never made;
+ * a failing test there returns MRA_EDEPTH with a valid tree.
+ * Output: *out in state MRA_TREE_LEAVES.  Synchronous (level sizes are read
+ * back to size the next level).
+ * Errors: MRA_EINVAL for k outside [1, MRA_MAX_K], eps <= 0, max_level outside
+ * [0, MRA_MAX_LEVEL], an empty density or non-positive exponents. */
+int mra_build_tree(const mra_density* f, int k, double eps, int max_level,
+                   int uniform_level, int init_level,
+                   const mra_alloc* alloc, void* stream, mra_tree** out);
+
+/* Create a tree from host arrays (e.g. an externally built tree).
+ * n nodes; coords_host: 4n int32 rows (j, a1, a2, a3) sorted by level then by
+ * box; leaf_host: n int32 flags; blocks_host: n * k^3 doubles (values of
+ * internal nodes are ignored).  The node set must be a complete 2^3-tree
+ * rooted at (0,0,0,0).  Output state MRA_TREE_LEAVES.  Synchronous.
+ * Errors: MRA_EINVAL for an unsorted, incomplete or out-of-range node set. */
+int mra_tree_import(int k, int n, const int32_t* coords_host, const int32_t* leaf_host,
+                    const double* blocks_host, const mra_alloc* alloc, void* stream,
+                    mra_tree** out);
+
+/* Copy a tree to host arrays (sizes from mra_tree_info).  Any pointer may be
+ * NULL to skip it.  coords_host: 4n int32; leaf_host: n int32; blocks_host:
+ * n k^3 doubles; dnorm_host: n doubles (wavelet norms, 0 on leaves).
+ * Synchronous on `stream`. */
+int mra_tree_export(const mra_tree* t, int32_t* coords_host, int32_t* leaf_host,
+                    double* blocks_host, double* dnorm_host, void* stream);
+
+int mra_tree_get_info(const mra_tree* t, mra_tree_info* info);
+
+/* Device views of a tree's arrays (valid until the tree is freed or changed
+ * by reconstruct/truncate): blocks (n k^3 doubles) and leaf flags (n int32). */
+int mra_tree_device_arrays(const mra_tree* t, double** blocks, int32_t** leaf);
+
+/* Overwrite the blocks of a tree from device memory on `stream` (n k^3 doubles,
+ * same node order).  The state is unchanged: the caller keeps the blocks
+ * consistent with it. */
+int mra_tree_set_blocks(mra_tree* t, const double* blocks, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Redundant tree (Sec. 2.2.1): bottom-up, each internal node receives
+ * s^j = sum_p (H^(p1) x H^(p2) x H^(p3)) s^{j+1}_{child p} (eq. decomp_scaling)
+ * and its seven wavelet blocks (eq. decomp_wavelet), i.e. the orthogonal
+ * 2k x 2k filter [[H0 H1],[G0 G1]] applied in each direction to the (2k)^3
+ * cube of its children.  G is the orthonormal completion of [H0 H1] by
+ * Gram-Schmidt of (e_i, -e_i)/sqrt(2) (the paper defers G to Alpert et al.;
+ * wavelet norms do not depend on the completion).  In place; state becomes
+ * MRA_TREE_REDUNDANT.  store_d != 0 also keeps the wavelet cubes so that
+ * mra_reconstruct(MRA_RECON_INVERSE) can undo the transform. */
+int mra_compress(mra_tree* t, int store_d, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* make_operator: the Gaussian sum of K_{mu,alpha} (Sec. 3) and the operator
+ * tables on levels 0..max_level:
+ *   - tau_m = e^{2 s_m}, w_m = h C_alpha exp(-mu^2 e^{-2 s_m}/4 + (3-2alpha)s_m),
+ *     s_m = A + m h (m = 1..M), C_alpha = 2 2^{-2alpha} pi^{-3/2} / Gamma(alpha);
+ *     A, B, h by the rule: h0 = pi^2/(2 ln(1/eps)); lower tail below
+ *     0.1 eps K_{0,alpha}(R); B = ln((ln(1/eps)+5)/delta^2)/2; h shrunk by 3 %
+ *     until the sup of |K - sum| / K_{0,alpha} on 4000 log-spaced r in
+ *     [delta, R] is <= eps (eq. KernelApproxByGaussians), delta = eps/10,
+ *     R = sqrt(3);
+ *   - F^{j;m,l}, l = -3..3 (eq. KernelFactor), from the cross-correlations
+ *     Phi_ii' (eq. CrossCor) by quadrature;
+ *   - block norms N_F, N_upF, N_dif (eq. BlockNorms, Frobenius) and the maximum
+ *     over the coarse core of the 18-term estimate (eq. NormEstimateUsing1DBlocks).
+ * FP64 throughout.  Synchronous (M is read back).
+ * Errors: MRA_EINVAL for mu < 0, alpha outside (0, 3/2), eps outside (0, 0.5],
+ * k outside [1, MRA_MAX_K], max_level outside [0, MRA_MAX_LEVEL]; MRA_ECUDA if
+ * more than MRA_MAX_TERMS terms would be needed. */
+int mra_make_operator(double mu, double alpha, double eps, int k, int max_level,
+                      const mra_alloc* alloc, void* stream, mra_op** out);
+
+typedef struct {
+    int M;                 /* number of Gaussian terms             */
+    int k, max_level;
+    double mu, alpha, eps;
+} mra_op_info;
+int mra_op_get_info(const mra_op* op, mra_op_info* info);
+
+/* Copy operator tables to host (any pointer may be NULL):
+ * w_host, tau_host: M doubles; F_host: (max_level+1) * M * 7 * k * k doubles,
+ * index [j][m][l+3][i][i']; nF_host: (max_level+1) * M * 7; est_host:
+ * (max_level+1) * M (max over the coarse core of the 18-term estimate, without
+ * w_m; 0 at j = 0).  Synchronous. */
+int mra_op_export(const mra_op* op, double* w_host, double* tau_host, double* F_host,
+                  double* nF_host, double* est_host, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 3 (Sec. 5): the modified ns-form apply in d = 3.
+ * For every node a of the input's redundant tree (the output skeleton) at
+ * level j, every translation t in the parity band (t_d in [-3,2] for even a_d,
+ * [-2,3] for odd a_d; eq. fine_scale_band with b_j = 3) whose input box
+ * b = a - t lies in [0, 2^j)^3, and every kept term m:
+ *     ghat^j_a += w_m (F^{j;m,t1} x F^{j;m,t2} x F^{j;m,t3}) f^j_b.
+ * Kept terms: eta = eps ||T_0 f_0|| / ||f||; J_m = finest j >= 1 with
+ * w_m Est(j,m) > eta/M (else 0); terms with j <= J_m; at internal nodes with
+ * j < J_m the core |t|_inf <= 1 is left to the finer scale (outer band,
+ * eq. apply_algo); per scale and Core/Boundary-1/2/3 subset, a term range
+ * [m1, m2] trimmed at both ends while the cumulative w_m prod max N_F stays
+ * below eta/432 (Sec. 4).  Missing input boxes are refined from their
+ * ancestor leaf (Step 2).
+ * The input tree must be MRA_TREE_REDUNDANT (mra_compress) and no deeper than
+ * the operator's max_level.  Output: a new tree in state MRA_TREE_NSFORM.
+ * Returns after the work is queued; stats (optional, host) are filled when the
+ * call returns (the call synchronises once to size the worklist). */
+
+#define MRA_PREC_FP64     0   /* FP64 SIMT contractions                        */
+#define MRA_PREC_FP32     1   /* FP32 SIMT contractions, FP64 accumulation     */
+#define MRA_PREC_TC_SPLIT 2   /* FP16 hi+lo split products on tcgen05 tensor   */
+                              /* cores, FP32 accumulation, FP64 accumulation   */
+                              /* into the output blocks                        */
+
+typedef struct {
+    int precision;          /* MRA_PREC_*                                     */
+    int block_screen;       /* 1: also drop items whose w prod N_F ||f_b|| is  */
+                            /* below eps ||T_0 f_0|| / sqrt(N 216 M)           */
+    int unscreened;         /* 1: every term at every scale (band only; tests) */
+    int reserved[5];
+} mra_apply_opts;
+
+typedef struct {
+    int64_t n_pairs;        /* (output node, translation) pairs                */
+    int64_t n_items;        /* (output node, translation, term) items          */
+    int64_t n_ghosts;       /* input blocks refined by Step 2                  */
+    int64_t n_out_nodes;
+    double eta;             /* operator-block threshold used                   */
+    double sigma;           /* ||T_0 f_0||                                     */
+    double fnorm;           /* ||f||_2                                         */
+    float ms_screen, ms_ghost, ms_apply; /* device times (CUDA events)         */
+} mra_apply_stats;
+
+int mra_apply_ns(const mra_op* op, const mra_tree* f, const mra_apply_opts* opts,
+                 void* stream, mra_tree** g_ns, mra_apply_stats* stats);
+
+/* ------------------------------------------------------------------------ */
+/* Reconstruct.
+ * MRA_RECON_ASSEMBLE: for an MRA_TREE_NSFORM tree, eq. g_assemble top-down
+ * (each child adds the d = 0 upsampling of its parent, eqs. recon_even /
+ * recon_odd), then mra_compress; if truncate != 0, leaf siblings whose
+ * parent has ||d|| < eps ||g|| / sqrt(N) are merged bottom-up (Algorithm 3,
+ * Step 4, "discard unnecessary blocks").  State becomes MRA_TREE_REDUNDANT
+ * (the tree may shrink).
+ * MRA_RECON_INVERSE: for an MRA_TREE_REDUNDANT tree compressed with
+ * store_d != 0, the inverse two-scale transform from the root down (the
+ * filter matrix is orthogonal; its transpose inverts it); state becomes
+ * MRA_TREE_LEAVES with the leaves rebuilt. */
+#define MRA_RECON_ASSEMBLE 0
+#define MRA_RECON_INVERSE  1
+int mra_reconstruct(mra_tree* t, int mode, int truncate, double eps, void* stream,
+                    double* truncation_l2_host);
+
+/* Free a tree or operator handle (exactly once; NULL is ignored). */
+int mra_free_tree(mra_tree* t);
+int mra_free_op(mra_op* op);
+
+/* Static message for the last error on this thread. */
+const char* mra_last_error(void);
+
+/* Library version string. */
+const char* mra_version(void);
+
+/* Number of kernels this library has launched in this process (all
+ * devices, all threads); differences bracket a region of interest. */
+unsigned long long mra_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRA_GB300_H */

@@ -61,6 +61,24 @@ class Density:
     def scale(self):
         return float(np.abs(self(self.centers)).max())
 
+    def on_grids(self, X):
+        """Values on tensor grids: X is a list of three (n, q) arrays of
+        per-direction coordinates; returns (n, q, q, q).  Each term factors as
+        exp(-a|x-c|^2) = prod_d exp(-a (x_d - c_d)^2), and the r^2 factor as a
+        sum over directions."""
+        n, q = X[0].shape
+        out = np.zeros((n, q, q, q))
+        for c, b, a, x0 in zip(self.coef, self.r2coef, self.expo, self.centers):
+            R = [(X[d] - x0[d]) ** 2 for d in range(3)]
+            E = [np.exp(-a * R[d]) for d in range(3)]
+            prod = E[0][:, :, None, None] * E[1][:, None, :, None] * E[2][:, None, None, :]
+            out += c * prod
+            if b != 0.0:
+                out += b * ((R[0] * E[0])[:, :, None, None] * E[1][:, None, :, None] * E[2][:, None, None, :]
+                            + E[0][:, :, None, None] * (R[1] * E[1])[:, None, :, None] * E[2][:, None, None, :]
+                            + E[0][:, :, None, None] * E[1][:, None, :, None] * (R[2] * E[2])[:, None, None, :])
+        return out
+
 
 def box_nodes(k, j, a):
     """GL nodes of box (j, a) per direction: array (3, k)."""
@@ -80,7 +98,7 @@ def project_values(k, j, vals):
     g, w = basis.gl01(k)
     P = basis.phi(k, g) * w                      # (i, q)
     v = vals.reshape(k, k, k)
-    s = np.einsum("ia,jb,kc,abc->ijk", P, P, P, v)
+    s = np.einsum("ia,jb,kc,abc->ijk", P, P, P, v, optimize=True)
     return s / 2.0 ** (1.5 * j)
 
 
@@ -89,44 +107,75 @@ def eval_block(k, j, a, s, pts):
     pts = np.asarray(pts, dtype=np.float64).reshape(-1, 3)
     u = pts * 2.0 ** j - np.asarray(a, dtype=np.float64)
     P = [basis.phi(k, u[:, d]) for d in range(3)]  # (i, n)
-    return np.einsum("ijk,in,jn,kn->n", s, P[0], P[1], P[2]) * 2.0 ** (1.5 * j)
+    return np.einsum("ijk,in,jn,kn->n", s, P[0], P[1], P[2], optimize=True) * 2.0 ** (1.5 * j)
 
 
-def build_tree(dens, k, eps, max_level, uniform_level=-1, init_level=0):
-    """Algorithm 1 (adaptive function decomposition) in d = 3.
+def _level_projection(dens, k, j, boxes, P, g):
+    """Values at each box's k^3 GL nodes and their projections, for a batch
+    of boxes (n, 3) at level j: eq. fvals2coefs in tensor form."""
+    h = 2.0 ** -j
+    X = [(g[None, :] + boxes[:, d:d + 1]) * h for d in range(3)]          # (n, k) per direction
+    vals = dens.on_grids(X)
+    return np.einsum("ia,jb,kc,nabc->nijk", P, P, P, vals, optimize=True) * 2.0 ** (-1.5 * j)
+
+
+def _children_error(dens, k, j, boxes, s, g, Q):
+    """max over the 8 children of |f - f~| at the children's GL nodes, where
+    f~ interpolates the parent's coefficients (Algorithm 1's test)."""
+    hc = 2.0 ** -(j + 1)
+    n = len(boxes)
+    err = np.zeros(n)
+    for p in OCTS:
+        X = [(g[None, :] + 2 * boxes[:, d:d + 1] + p[d]) * hc for d in range(3)]
+        direct = dens.on_grids(X)
+        interp = np.einsum("nijk,ai,bj,ck->nabc", s, Q[p[0]], Q[p[1]], Q[p[2]], optimize=True) * 2.0 ** (1.5 * j)
+        err = np.maximum(err, np.abs(direct - interp).reshape(n, -1).max(axis=1))
+    return err
+
+
+def build_tree(dens, k, eps, max_level, uniform_level=-1, init_level=0, chunk=64):
+    """Algorithm 1 (adaptive function decomposition) in d = 3, processed one
+    level at a time (the boxes of a level are independent).
 
     Returns (tree, depth_hit)."""
     tol = eps * dens.scale()
+    g, w = basis.gl01(k)
+    P = basis.phi(k, g) * w                                   # (i, q): projection
+    Q = [basis.phi(k, 0.5 * (g + p)).T for p in (0, 1)]       # (q, i): child-node values
     tree = {}
     depth_hit = False
-    todo = [(0, 0, 0, 0)]
-    while todo:
-        nxt = []
-        for key in todo:
-            j, a = key[0], key[1:]
-            vals = dens(grid(box_nodes(k, j, a)))
-            s = project_values(k, j, vals)
+    boxes = np.zeros((1, 3), dtype=np.int64)
+    j = 0
+    while len(boxes):
+        refine = np.zeros(len(boxes), dtype=bool)
+        S = np.zeros((len(boxes), k, k, k))
+        for c0 in range(0, len(boxes), chunk):
+            bx = boxes[c0:c0 + chunk]
+            s = _level_projection(dens, k, j, bx, P, g)
+            S[c0:c0 + chunk] = s
             if uniform_level >= 0:
-                refine = j < uniform_level
+                refine[c0:c0 + chunk] = j < uniform_level
             elif j < init_level:
-                refine = True
+                refine[c0:c0 + chunk] = True
             else:
-                err = 0.0
-                for p in OCTS:
-                    c = tuple(2 * a[d] + p[d] for d in range(3))
-                    pts = grid(box_nodes(k, j + 1, c))
-                    err = max(err, float(np.abs(dens(pts) - eval_block(k, j, a, s, pts)).max()))
-                refine = err > tol
-                if refine and j >= max_level:
-                    depth_hit = True
-                    refine = False
-            if refine:
+                fail = _children_error(dens, k, j, bx, s, g, Q) > tol
+                if j >= max_level:
+                    depth_hit = depth_hit or bool(fail.any())
+                    fail[:] = False
+                refine[c0:c0 + chunk] = fail
+        if j >= max_level:
+            refine[:] = False
+        nxt = []
+        for b, r, s in zip(boxes, refine, S):
+            key = (j,) + tuple(int(v) for v in b)
+            if r:
                 tree[key] = Node(False)
                 for p in OCTS:
-                    nxt.append((j + 1,) + tuple(2 * a[d] + p[d] for d in range(3)))
+                    nxt.append([2 * b[0] + p[0], 2 * b[1] + p[1], 2 * b[2] + p[2]])
             else:
                 tree[key] = Node(True, s)
-        todo = nxt
+        boxes = np.array(nxt, dtype=np.int64).reshape(-1, 3)
+        j += 1
     return tree, depth_hit
 
 
@@ -147,7 +196,7 @@ def _cube_of_children(tree, key, k):
 
 
 def _apply3(Wm, cube):
-    return np.einsum("ai,bj,ck,ijk->abc", Wm, Wm, Wm, cube)
+    return np.einsum("ai,bj,ck,ijk->abc", Wm, Wm, Wm, cube, optimize=True)
 
 
 def compress(tree, k):
@@ -155,17 +204,21 @@ def compress(tree, k):
     s^j = sum_p (H^(p1) x H^(p2) x H^(p3)) s^{j+1}_{child p} (eq. decomp_scaling)
     and the seven wavelet blocks (eq. decomp_wavelet), i.e. the 2k x 2k
     filter matrix W applied in each direction to the (2k)^3 cube of the
-    children.  d holds that cube with its scaling corner zeroed."""
+    children.  d holds that cube with its scaling corner zeroed.  The
+    internal nodes of one level are transformed together."""
     Wm = basis.filter_matrix(k)
     for j in range(levels(tree) - 2, -1, -1):
-        for key, node in tree.items():
-            if key[0] != j or node.leaf:
-                continue
-            out = _apply3(Wm, _cube_of_children(tree, key, k))
-            node.s = out[:k, :k, :k].copy()
-            out[:k, :k, :k] = 0.0
-            node.d = out
-            node.dnorm = float(np.linalg.norm(out))
+        keys = [key for key, node in tree.items() if key[0] == j and not node.leaf]
+        if not keys:
+            continue
+        cubes = np.stack([_cube_of_children(tree, key, k) for key in keys])
+        out = np.einsum("ai,bj,ck,nijk->nabc", Wm, Wm, Wm, cubes, optimize=True)
+        for key, o in zip(keys, out):
+            node = tree[key]
+            node.s = o[:k, :k, :k].copy()
+            o[:k, :k, :k] = 0.0
+            node.d = o
+            node.dnorm = float(np.linalg.norm(o))
     return tree
 
 
@@ -191,7 +244,7 @@ def upsample(k, s, p):
     """s^{j+1}_{2a+p} = (H^(p1)T x H^(p2)T x H^(p3)T) s^j_a (the d = 0 half of
     eqs. recon_even / recon_odd)."""
     H = basis.two_scale_H(k)
-    return np.einsum("ia,jb,kc,ijk->abc", H[p[0]], H[p[1]], H[p[2]], s)
+    return np.einsum("ia,jb,kc,ijk->abc", H[p[0]], H[p[1]], H[p[2]], s, optimize=True)
 
 
 def norm2(tree):

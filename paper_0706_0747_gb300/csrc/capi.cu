@@ -1,0 +1,266 @@
+// C ABI entry points (declared in include/mra_gb300.h): argument checks,
+// handle ownership, allocator hook and per-thread error messages.  All
+// arithmetic is done by the kernels in operator.cu, tree.cu and apply.cu.
+#include <stdarg.h>
+
+#include <atomic>
+
+#include "mra_internal.cuh"
+
+namespace mra {
+
+static thread_local char g_err[512] = "";
+static std::atomic<unsigned long long> g_launches(0);
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void* Alloc::get(size_t bytes) const {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (has) {
+        p = hook.alloc(bytes, (void*)stream, hook.ctx);
+    } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void Alloc::put(void* p) const {
+    if (!p) return;
+    if (has) hook.free(p, (void*)stream, hook.ctx);
+    else cudaFreeAsync(p, stream);
+}
+
+Alloc make_alloc(const mra_alloc* a, void* stream) {
+    Alloc A;
+    A.stream = (cudaStream_t)stream;
+    if (a && a->alloc && a->free) {
+        A.hook = *a;
+        A.has = true;
+    }
+    return A;
+}
+
+static bool tree_ok(const mra_tree* t) { return t && t->magic == MRA_TREE_MAGIC; }
+static bool op_ok(const mra_op* o) { return o && o->magic == MRA_OP_MAGIC; }
+
+}  // namespace mra
+
+using namespace mra;
+
+extern "C" {
+
+const char* mra_last_error(void) { return g_err; }
+const char* mra_version(void) { return "mra_gb300 0.1 (sm_103a)"; }
+unsigned long long mra_kernel_launches(void) { return g_launches.load(); }
+
+int mra_build_tree(const mra_density* f, int k, double eps, int max_level, int uniform_level, int init_level,
+                   const mra_alloc* alloc, void* stream, mra_tree** out) {
+    if (!out) { set_error("out is NULL"); return MRA_EINVAL; }
+    *out = nullptr;
+    if (!f || f->n <= 0 || !f->coef_host || !f->expo_host || !f->center_host) {
+        set_error("empty or NULL density");
+        return MRA_EINVAL;
+    }
+    if (k < 1 || k > MRA_MAX_K) { set_error("k=%d outside [1, %d]", k, MRA_MAX_K); return MRA_EINVAL; }
+    if (!(eps > 0.0)) { set_error("eps must be > 0"); return MRA_EINVAL; }
+    if (max_level < 0 || max_level > MRA_MAX_LEVEL) { set_error("max_level outside [0, %d]", MRA_MAX_LEVEL); return MRA_EINVAL; }
+    for (int g = 0; g < f->n; ++g)
+        if (!(f->expo_host[g] > 0.0)) { set_error("density exponent %d is not positive", g); return MRA_EINVAL; }
+    Alloc A = make_alloc(alloc, stream);
+    return build_tree_impl(f, k, eps, max_level, uniform_level, init_level, A, out);
+}
+
+int mra_tree_import(int k, int n, const int32_t* coords_host, const int32_t* leaf_host, const double* blocks_host,
+                    const mra_alloc* alloc, void* stream, mra_tree** out) {
+    if (!out) { set_error("out is NULL"); return MRA_EINVAL; }
+    *out = nullptr;
+    if (k < 1 || k > MRA_MAX_K || n < 1 || !coords_host || !leaf_host || !blocks_host) {
+        set_error("invalid import arguments");
+        return MRA_EINVAL;
+    }
+    mra_tree* t = new mra_tree();
+    t->magic = MRA_TREE_MAGIC;
+    t->k = k;
+    t->A = make_alloc(alloc, stream);
+    t->state = MRA_TREE_LEAVES;
+    t->depth_hit = 0;
+    int rc = tree_alloc_arrays(t, n, true);
+    if (rc == MRA_OK) rc = tree_link_and_upload(t, coords_host, leaf_host);
+    if (rc == MRA_OK) {
+        const size_t bytes = (size_t)n * k * k * k * sizeof(double);
+        cudaError_t e = cudaMemcpyAsync(t->s, blocks_host, bytes, cudaMemcpyHostToDevice, t->A.stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(t->dnorm, 0, n * sizeof(double), t->A.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(t->A.stream);
+        if (e != cudaSuccess) { set_error("import copy: %s", cudaGetErrorString(e)); rc = MRA_ECUDA; }
+    }
+    if (rc != MRA_OK) {
+        tree_free_arrays(t);
+        t->A.put(t->filt);
+        t->magic = 0;
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return MRA_OK;
+}
+
+int mra_tree_export(const mra_tree* t, int32_t* coords_host, int32_t* leaf_host, double* blocks_host,
+                    double* dnorm_host, void* stream) {
+    if (!tree_ok(t)) { set_error("invalid tree handle"); return MRA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = t->n;
+    if (coords_host) MRA_CK(cudaMemcpyAsync(coords_host, t->a.coord, 4 * (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (leaf_host) MRA_CK(cudaMemcpyAsync(leaf_host, t->a.leaf, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (blocks_host) MRA_CK(cudaMemcpyAsync(blocks_host, t->s, (size_t)n * t->k * t->k * t->k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (dnorm_host) MRA_CK(cudaMemcpyAsync(dnorm_host, t->dnorm, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaStreamSynchronize(st));
+    return MRA_OK;
+}
+
+int mra_tree_get_info(const mra_tree* t, mra_tree_info* info) {
+    if (!tree_ok(t) || !info) { set_error("invalid tree handle"); return MRA_EINVAL; }
+    info->k = t->k;
+    info->n_nodes = t->n;
+    info->n_levels = t->nlev;
+    info->state = t->state;
+    info->depth_hit = t->depth_hit;
+    memcpy(info->level_offset, t->off, sizeof(t->off));
+    return MRA_OK;
+}
+
+int mra_tree_device_arrays(const mra_tree* t, double** blocks, int32_t** leaf) {
+    if (!tree_ok(t)) { set_error("invalid tree handle"); return MRA_EINVAL; }
+    if (blocks) *blocks = t->s;
+    if (leaf) *leaf = t->a.leaf;
+    return MRA_OK;
+}
+
+int mra_tree_set_blocks(mra_tree* t, const double* blocks, void* stream) {
+    if (!tree_ok(t) || !blocks) { set_error("invalid tree handle or blocks"); return MRA_EINVAL; }
+    MRA_CK(cudaMemcpyAsync(t->s, blocks, (size_t)t->n * t->k * t->k * t->k * sizeof(double),
+                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return MRA_OK;
+}
+
+int mra_compress(mra_tree* t, int store_d, void* stream) {
+    if (!tree_ok(t)) { set_error("invalid tree handle"); return MRA_EINVAL; }
+    if (t->state == MRA_TREE_NSFORM) { set_error("compress needs leaf data; assemble an ns-form tree first"); return MRA_ESTATE; }
+    return compress_impl(t, store_d, (cudaStream_t)stream);
+}
+
+int mra_make_operator(double mu, double alpha, double eps, int k, int max_level, const mra_alloc* alloc, void* stream,
+                      mra_op** out) {
+    if (!out) { set_error("out is NULL"); return MRA_EINVAL; }
+    *out = nullptr;
+    if (!(mu >= 0.0)) { set_error("mu must be >= 0"); return MRA_EINVAL; }
+    if (!(alpha > 0.0 && alpha < 1.5)) { set_error("alpha must lie in (0, 3/2)"); return MRA_EINVAL; }
+    if (!(eps > 0.0 && eps <= 0.5)) { set_error("eps must lie in (0, 0.5]"); return MRA_EINVAL; }
+    if (k < 1 || k > MRA_MAX_K) { set_error("k=%d outside [1, %d]", k, MRA_MAX_K); return MRA_EINVAL; }
+    if (max_level < 0 || max_level > MRA_MAX_LEVEL) { set_error("max_level outside [0, %d]", MRA_MAX_LEVEL); return MRA_EINVAL; }
+    mra_op* op = new mra_op();
+    op->magic = MRA_OP_MAGIC;
+    op->k = k;
+    op->J = max_level;
+    op->mu = mu;
+    op->alpha = alpha;
+    op->eps = eps;
+    op->A = make_alloc(alloc, stream);
+    int rc = build_operator(op, (cudaStream_t)stream);
+    if (rc == MRA_OK) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) { set_error("make_operator: %s", cudaGetErrorString(e)); rc = MRA_ECUDA; }
+    }
+    if (rc != MRA_OK) {
+        mra_free_op(op);
+        return rc;
+    }
+    *out = op;
+    return MRA_OK;
+}
+
+int mra_op_get_info(const mra_op* op, mra_op_info* info) {
+    if (!op_ok(op) || !info) { set_error("invalid operator handle"); return MRA_EINVAL; }
+    info->M = op->M;
+    info->k = op->k;
+    info->max_level = op->J;
+    info->mu = op->mu;
+    info->alpha = op->alpha;
+    info->eps = op->eps;
+    return MRA_OK;
+}
+
+int mra_op_export(const mra_op* op, double* w_host, double* tau_host, double* F_host, double* nF_host,
+                  double* est_host, void* stream) {
+    if (!op_ok(op)) { set_error("invalid operator handle"); return MRA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t JM = (size_t)(op->J + 1) * op->M;
+    if (w_host) MRA_CK(cudaMemcpyAsync(w_host, op->w, op->M * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (tau_host) MRA_CK(cudaMemcpyAsync(tau_host, op->tau, op->M * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (F_host) MRA_CK(cudaMemcpyAsync(F_host, op->F, JM * 7 * op->k * op->k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (nF_host) MRA_CK(cudaMemcpyAsync(nF_host, op->nF, JM * 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (est_host) MRA_CK(cudaMemcpyAsync(est_host, op->est, JM * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaStreamSynchronize(st));
+    return MRA_OK;
+}
+
+int mra_apply_ns(const mra_op* op, const mra_tree* f, const mra_apply_opts* opts, void* stream, mra_tree** g_ns,
+                 mra_apply_stats* stats) {
+    if (!g_ns) { set_error("g_ns is NULL"); return MRA_EINVAL; }
+    *g_ns = nullptr;
+    if (!op_ok(op) || !tree_ok(f)) { set_error("invalid operator or tree handle"); return MRA_EINVAL; }
+    return apply_impl(op, f, opts, (cudaStream_t)stream, g_ns, stats);
+}
+
+int mra_reconstruct(mra_tree* t, int mode, int truncate, double eps, void* stream, double* truncation_l2_host) {
+    if (!tree_ok(t)) { set_error("invalid tree handle"); return MRA_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (truncation_l2_host) *truncation_l2_host = 0.0;
+    if (mode == MRA_RECON_ASSEMBLE) {
+        if (t->state != MRA_TREE_NSFORM) { set_error("assemble needs an ns-form tree"); return MRA_ESTATE; }
+        MRA_TRY(assemble_impl(t, st));
+        MRA_TRY(compress_impl(t, 0, st));
+        if (truncate) {
+            if (!(eps > 0.0)) { set_error("truncation eps must be > 0"); return MRA_EINVAL; }
+            MRA_TRY(truncate_impl(t, eps, st, truncation_l2_host));
+        }
+        return MRA_OK;
+    }
+    if (mode == MRA_RECON_INVERSE) {
+        if (t->state != MRA_TREE_REDUNDANT) { set_error("inverse needs a compressed tree"); return MRA_ESTATE; }
+        return inverse_impl(t, st);
+    }
+    set_error("unknown reconstruct mode %d", mode);
+    return MRA_EINVAL;
+}
+
+int mra_free_tree(mra_tree* t) {
+    if (!t) return MRA_OK;
+    if (!tree_ok(t)) { set_error("invalid tree handle"); return MRA_EINVAL; }
+    tree_free_arrays(t);
+    t->A.put(t->filt);
+    t->magic = 0;
+    delete t;
+    return MRA_OK;
+}
+
+int mra_free_op(mra_op* op) {
+    if (!op) return MRA_OK;
+    if (op->magic != MRA_OP_MAGIC) { set_error("invalid operator handle"); return MRA_EINVAL; }
+    const Alloc& A = op->A;
+    A.put(op->w); A.put(op->tau); A.put(op->F); A.put(op->F32); A.put(op->nF); A.put(op->est);
+    A.put(op->filt); A.put(op->scratch_i);
+    op->magic = 0;
+    delete op;
+    return MRA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,695 @@
+// Trees on the device: Algorithm 1 (adaptive decomposition), the redundant
+// tree (two-scale decomposition, eqs. decomp_scaling / decomp_wavelet), its
+// inverse (eqs. recon_even / recon_odd), the adaptive projection of
+// eq. g_assemble, and the final truncation (Algorithm 3, Step 4).
+//
+// Layout in HBM: nodes sorted by level, then by Morton key within a level, so
+// the 8 children of a node are contiguous in octant order (p1 p2 p3) and each
+// level is a sorted key range for binary search.  Blocks are k^3 FP64 arrays
+// s[i1][i2][i3] (i3 fastest), one per node, contiguous in node order.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "mra_internal.cuh"
+
+namespace mra {
+
+// ------------------------------------------------------------ small utilities
+// Single-block exclusive scan of n int32 values (n up to a few million); the
+// total is written to *total.
+__global__ void k_scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* total) {
+    __shared__ int32_t part[1024];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int per = (n + nt - 1) / nt;
+    const int lo = min(n, tid * per), hi = min(n, lo + per);
+    int32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += in[i];
+    part[tid] = s;
+    __syncthreads();
+    for (int d = 1; d < nt; d <<= 1) {
+        int32_t v = (tid >= d) ? part[tid - d] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    int32_t run = part[tid] - s;
+    for (int i = lo; i < hi; ++i) {
+        int32_t v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    if (tid == nt - 1 && total) *total = part[nt - 1];
+}
+
+int scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* total, cudaStream_t st) {
+    if (n <= 0) {
+        MRA_CK(cudaMemsetAsync(total, 0, sizeof(int32_t), st));
+        return MRA_OK;
+    }
+    k_scan_exclusive<<<1, 1024, 0, st>>>(in, out, n, total);
+    MRA_CK_LAUNCH();
+    return MRA_OK;
+}
+
+// out[along dim] = Mat * in[along dim] for a k^3 array in shared memory;
+// Mat is k x k row-major (out index, in index).  All threads of the block.
+__device__ void mode_product(const double* in, double* out, const double* Mat, int dim, int k) {
+    const int n = k * k * k;
+    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+        int i3 = idx % k, i2 = (idx / k) % k, i1 = idx / (k * k);
+        int r = dim == 0 ? i1 : (dim == 1 ? i2 : i3);
+        int stride = dim == 0 ? k * k : (dim == 1 ? k : 1);
+        const double* src = in + idx - r * stride;
+        double acc = 0.0;
+        for (int c = 0; c < k; ++c) acc += Mat[r * k + c] * src[c * stride];
+        out[idx] = acc;
+    }
+    __syncthreads();
+}
+
+// In-place 2k-point transform along one direction of a (2k)^3 cube:
+// line <- M line (transpose = 0) or M^T line (transpose = 1), M = 2k x 2k.
+__device__ void cube_transform(double* cube, int n2, const double* Mt, int transpose, int dim) {
+    const int lines = n2 * n2;
+    const int stride = dim == 0 ? n2 * n2 : (dim == 1 ? n2 : 1);
+    for (int ln = threadIdx.x; ln < lines; ln += blockDim.x) {
+        int u = ln / n2, v = ln % n2;
+        int base = dim == 0 ? (u * n2 + v) : (dim == 1 ? (u * n2 * n2 + v) : (u * n2 * n2 + v * n2));
+        double x[2 * MRA_MAX_K];
+        for (int c = 0; c < n2; ++c) x[c] = cube[base + c * stride];
+        for (int r = 0; r < n2; ++r) {
+            double acc = 0.0;
+            for (int c = 0; c < n2; ++c) acc += (transpose ? Mt[c * n2 + r] : Mt[r * n2 + c]) * x[c];
+            cube[base + r * stride] = acc;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += red[i];
+    __syncthreads();
+    return s;
+}
+
+__device__ double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s = fmax(s, red[i]);
+    __syncthreads();
+    return s;
+}
+
+// ------------------------------------------------------------ arrays
+int tree_alloc_arrays(mra_tree* t, int n, bool with_s) {
+    const Alloc& A = t->A;
+    const int k3 = t->k * t->k * t->k;
+    MRA_TRY(dalloc(A, &t->a.key, n));
+    MRA_TRY(dalloc(A, &t->a.coord, 4 * (size_t)n));
+    MRA_TRY(dalloc(A, &t->a.leaf, n));
+    MRA_TRY(dalloc(A, &t->a.child, n));
+    MRA_TRY(dalloc(A, &t->a.parent, n));
+    MRA_TRY(dalloc(A, &t->a.off, MRA_MAX_LEVEL + 2));
+    MRA_TRY(dalloc(A, &t->dnorm, n));
+    if (with_s) MRA_TRY(dalloc(A, &t->s, (size_t)n * k3));
+    if (!t->filt) {
+        MRA_TRY(dalloc(A, &t->filt, 6 * t->k * t->k));
+        MRA_TRY(launch_filters(t->k, t->filt, A.stream));
+    }
+    t->n = n;
+    return MRA_OK;
+}
+
+void tree_free_arrays(mra_tree* t) {
+    const Alloc& A = t->A;
+    A.put(t->a.key); A.put(t->a.coord); A.put(t->a.leaf); A.put(t->a.child); A.put(t->a.parent);
+    A.put(t->a.off); A.put(t->dnorm); A.put(t->s); A.put(t->dcube);
+    t->a = TreeArrays();
+    t->dnorm = nullptr; t->s = nullptr; t->dcube = nullptr;
+}
+
+// Host-side validation and linking of an imported node list; uploads key,
+// coord, leaf, child, parent and offsets.
+int tree_link_and_upload(mra_tree* t, const int32_t* coords, const int32_t* leaf) {
+    const int n = t->n;
+    std::vector<uint64_t> key(n);
+    std::vector<int32_t> child(n, -1), parent(n, -1), lf(n);
+    int off[MRA_MAX_LEVEL + 2];
+    for (int j = 0; j < MRA_MAX_LEVEL + 2; ++j) off[j] = n;
+    int nlev = 0;
+    for (int i = 0; i < n; ++i) {
+        int j = coords[4 * i];
+        if (j < 0 || j > MRA_MAX_LEVEL) { set_error("node %d: level %d out of range", i, j); return MRA_EINVAL; }
+        for (int d = 1; d < 4; ++d)
+            if (coords[4 * i + d] < 0 || coords[4 * i + d] >= (1 << j)) {
+                set_error("node %d: box index out of range", i);
+                return MRA_EINVAL;
+            }
+        key[i] = morton3(coords[4 * i + 1], coords[4 * i + 2], coords[4 * i + 3]);
+        if (i > 0) {
+            int jp = coords[4 * (i - 1)];
+            if (jp > j || (jp == j && key[i - 1] >= key[i])) { set_error("nodes not sorted by (level, Morton key) at %d", i); return MRA_EINVAL; }
+        }
+        if (off[j] == n) off[j] = i;
+        nlev = std::max(nlev, j + 1);
+        lf[i] = leaf[i] ? 1 : 0;
+    }
+    if (n == 0 || coords[0] != 0) { set_error("tree must start with the root (0,0,0,0)"); return MRA_EINVAL; }
+    for (int j = nlev; j >= 0; --j) if (off[j] == n && j < nlev) off[j] = off[j + 1];
+    for (int j = nlev; j < MRA_MAX_LEVEL + 2; ++j) off[j] = n;
+    // link children: every internal node must have its 8 children at level j+1
+    for (int i = 0; i < n; ++i) {
+        int j = coords[4 * i];
+        if (lf[i]) continue;
+        uint64_t ck = key[i] << 3;
+        int lo = off[j + 1], hi = off[j + 2];
+        int pos = (int)(std::lower_bound(key.begin() + lo, key.begin() + hi, ck) - key.begin());
+        if (pos + 8 > hi) { set_error("internal node %d lacks children", i); return MRA_EINVAL; }
+        for (int o = 0; o < 8; ++o)
+            if (key[pos + o] != ck + o) { set_error("internal node %d lacks child %d", i, o); return MRA_EINVAL; }
+        child[i] = pos;
+        for (int o = 0; o < 8; ++o) parent[pos + o] = i;
+    }
+    for (int i = 1; i < n; ++i)
+        if (parent[i] < 0) { set_error("node %d has no parent", i); return MRA_EINVAL; }
+    t->nlev = nlev;
+    memcpy(t->off, off, sizeof(off));
+    cudaStream_t st = t->A.stream;
+    MRA_CK(cudaMemcpyAsync(t->a.key, key.data(), n * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    MRA_CK(cudaMemcpyAsync(t->a.coord, coords, 4 * (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    MRA_CK(cudaMemcpyAsync(t->a.leaf, lf.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    MRA_CK(cudaMemcpyAsync(t->a.child, child.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    MRA_CK(cudaMemcpyAsync(t->a.parent, parent.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    MRA_CK(cudaMemcpyAsync(t->a.off, off, sizeof(off), cudaMemcpyHostToDevice, st));
+    MRA_CK(cudaStreamSynchronize(st));  // host vectors go out of scope
+    return MRA_OK;
+}
+
+int tree_clone_skeleton(const mra_tree* src, mra_tree** out) {
+    mra_tree* t = new mra_tree();
+    t->magic = MRA_TREE_MAGIC;
+    t->k = src->k;
+    t->A = src->A;
+    t->nlev = src->nlev;
+    t->state = src->state;
+    t->depth_hit = src->depth_hit;
+    memcpy(t->off, src->off, sizeof(t->off));
+    int rc = tree_alloc_arrays(t, src->n, true);
+    if (rc != MRA_OK) { tree_free_arrays(t); t->A.put(t->filt); delete t; return rc; }
+    cudaStream_t st = t->A.stream;
+    const int n = src->n;
+#define CPY(dst, s_, cnt) MRA_CK(cudaMemcpyAsync(dst, s_, (cnt) * sizeof(*(dst)), cudaMemcpyDeviceToDevice, st))
+    CPY(t->a.key, src->a.key, n);
+    CPY(t->a.coord, src->a.coord, 4 * (size_t)n);
+    CPY(t->a.leaf, src->a.leaf, n);
+    CPY(t->a.child, src->a.child, n);
+    CPY(t->a.parent, src->a.parent, n);
+    CPY(t->a.off, src->a.off, MRA_MAX_LEVEL + 2);
+#undef CPY
+    *out = t;
+    return MRA_OK;
+}
+
+// ------------------------------------------------------------ Algorithm 1
+struct DensDev {
+    int n;
+    const double *coef, *r2, *expo, *cen;
+};
+
+__device__ double dens_eval(const DensDev& D, double x, double y, double z) {
+    double f = 0.0;
+    for (int g = 0; g < D.n; ++g) {
+        double dx = x - D.cen[3 * g], dy = y - D.cen[3 * g + 1], dz = z - D.cen[3 * g + 2];
+        double r2 = dx * dx + dy * dy + dz * dz;
+        f += (D.coef[g] + D.r2[g] * r2) * exp(-D.expo[g] * r2);
+    }
+    return f;
+}
+
+__global__ void k_dens_scale(DensDev D, double eps, double* tol) {
+    __shared__ double red[32];
+    double m = 0.0;
+    for (int g = threadIdx.x; g < D.n; g += blockDim.x)
+        m = fmax(m, fabs(dens_eval(D, D.cen[3 * g], D.cen[3 * g + 1], D.cen[3 * g + 2])));
+    m = block_max(m, red);
+    if (threadIdx.x == 0) *tol = eps * m;
+}
+
+// One block per box of level j.  mode: 0 adaptive test, 1 refine, 2 leaf.
+__global__ void k_build_level(int k, int j, DensDev D, const int32_t* boxes, const double* tolp, int mode,
+                              int at_max, double* s_out, int32_t* refine, int32_t* depth_hit) {
+    extern __shared__ double sm[];
+    const int k3 = k * k * k, kk = k * k;
+    double* g = sm;             // k nodes
+    double* gw = g + k;         // k weights
+    double* P = gw + k;         // [i][q] phi_i(g_q) w_q
+    double* Q = P + kk;         // [p][q][i] phi_i((g_q + p)/2): (q, i) as a k x k matrix per p
+    double* v = Q + 2 * kk;     // k^3 values
+    double* t1 = v + k3;
+    double* t2 = t1 + k3;
+    double* s = t2 + k3;
+    __shared__ double red[32];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int a1 = boxes[3 * b], a2 = boxes[3 * b + 1], a3 = boxes[3 * b + 2];
+    if (tid == 0) gauss_legendre01(k, g, gw);
+    __syncthreads();
+    if (tid < k) {
+        double tmp[MRA_MAX_K];
+        phi_all(k, g[tid], tmp);
+        for (int i = 0; i < k; ++i) P[i * k + tid] = tmp[i] * gw[tid];
+        for (int p = 0; p < 2; ++p) {
+            phi_all(k, 0.5 * (g[tid] + p), tmp);
+            for (int i = 0; i < k; ++i) Q[p * kk + tid * k + i] = tmp[i];
+        }
+    }
+    const double h = exp2(-(double)j);
+    for (int idx = tid; idx < k3; idx += blockDim.x) {
+        int q3 = idx % k, q2 = (idx / k) % k, q1 = idx / kk;
+        v[idx] = dens_eval(D, (g[q1] + a1) * h, (g[q2] + a2) * h, (g[q3] + a3) * h);
+    }
+    __syncthreads();
+    // s = 2^{-3j/2} (P x P x P) v  (eq. fvals2coefs in tensor form)
+    mode_product(v, t1, P, 2, k);
+    mode_product(t1, t2, P, 1, k);
+    mode_product(t2, s, P, 0, k);
+    const double sc = exp2(-1.5 * j);
+    for (int idx = tid; idx < k3; idx += blockDim.x) s[idx] *= sc;
+    __syncthreads();
+    int ref = (mode == 1);
+    if (mode == 0) {
+        double err = 0.0;
+        const double hc = 0.5 * h, up = exp2(1.5 * j);
+        for (int o = 0; o < 8; ++o) {
+            int p1 = (o >> 2) & 1, p2 = (o >> 1) & 1, p3 = o & 1;
+            // interpolate: f~ = 2^{3j/2} sum_i s_i prod_d phi_{i_d}((g_q + p_d)/2)
+            mode_product(s, t1, Q + p3 * kk, 2, k);
+            mode_product(t1, t2, Q + p2 * kk, 1, k);
+            mode_product(t2, t1, Q + p1 * kk, 0, k);
+            for (int idx = tid; idx < k3; idx += blockDim.x) {
+                int q3 = idx % k, q2 = (idx / k) % k, q1 = idx / kk;
+                double f = dens_eval(D, (g[q1] + 2 * a1 + p1) * hc, (g[q2] + 2 * a2 + p2) * hc,
+                                     (g[q3] + 2 * a3 + p3) * hc);
+                err = fmax(err, fabs(f - up * t1[idx]));
+            }
+            __syncthreads();
+        }
+        err = block_max(err, red);
+        ref = err > *tolp;
+        if (ref && at_max) {
+            ref = 0;
+            if (tid == 0) atomicExch(depth_hit, 1);
+        }
+    }
+    for (int idx = tid; idx < k3; idx += blockDim.x) s_out[(size_t)b * k3 + idx] = s[idx];
+    if (tid == 0) refine[b] = ref;
+}
+
+// children of refined boxes (octant order) and the refined-parent list
+__global__ void k_make_children(int nb, const int32_t* boxes, const int32_t* refine, const int32_t* pos,
+                                int32_t* next, int32_t* parent_local) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb || !refine[b]) return;
+    int p = pos[b];
+    parent_local[p] = b;
+    for (int o = 0; o < 8; ++o) {
+        int c = 8 * p + o;
+        next[3 * c] = 2 * boxes[3 * b] + ((o >> 2) & 1);
+        next[3 * c + 1] = 2 * boxes[3 * b + 1] + ((o >> 1) & 1);
+        next[3 * c + 2] = 2 * boxes[3 * b + 2] + (o & 1);
+    }
+}
+
+// scatter one level into the final node arrays
+__global__ void k_place_level(int nb, int j, int base, int next_base, const int32_t* boxes, const int32_t* refine,
+                              const int32_t* pos, const int32_t* parent_local, int prev_base, int k3,
+                              const double* s_lvl, mra::TreeArrays a, double* s) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int i = base + b;
+    a.key[i] = morton3(boxes[3 * b], boxes[3 * b + 1], boxes[3 * b + 2]);
+    a.coord[4 * i] = j;
+    a.coord[4 * i + 1] = boxes[3 * b];
+    a.coord[4 * i + 2] = boxes[3 * b + 1];
+    a.coord[4 * i + 3] = boxes[3 * b + 2];
+    a.leaf[i] = refine[b] ? 0 : 1;
+    a.child[i] = refine[b] ? next_base + 8 * pos[b] : -1;
+    a.parent[i] = (j == 0) ? -1 : prev_base + parent_local[b / 8];
+    for (int e = 0; e < k3; ++e) s[(size_t)i * k3 + e] = s_lvl[(size_t)b * k3 + e];
+}
+
+int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int uniform_level, int init_level,
+                    const Alloc& A, mra_tree** out) {
+    cudaStream_t st = A.stream;
+    const int k3 = k * k * k;
+    const int ng = f->n;
+    double* dd;
+    MRA_TRY(dalloc(A, &dd, 6 * (size_t)ng + 1));
+    {
+        std::vector<double> h(6 * (size_t)ng + 1, 0.0);
+        for (int g = 0; g < ng; ++g) {
+            h[g] = f->coef_host[g];
+            h[ng + g] = f->r2coef_host ? f->r2coef_host[g] : 0.0;
+            h[2 * ng + g] = f->expo_host[g];
+            for (int d = 0; d < 3; ++d) h[3 * ng + 3 * g + d] = f->center_host[3 * g + d];
+        }
+        MRA_CK(cudaMemcpyAsync(dd, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        MRA_CK(cudaStreamSynchronize(st));
+    }
+    DensDev D{ng, dd, dd + ng, dd + 2 * ng, dd + 3 * ng};
+    double* tol;
+    int32_t *flags;  // [0] depth_hit, [1] total
+    MRA_TRY(dalloc(A, &tol, 1));
+    MRA_TRY(dalloc(A, &flags, 4));
+    MRA_CK(cudaMemsetAsync(flags, 0, 4 * sizeof(int32_t), st));
+    k_dens_scale<<<1, 256, 0, st>>>(D, eps, tol);
+    MRA_CK_LAUNCH();
+
+    struct Level {
+        int n;
+        int32_t *boxes, *refine, *pos, *parent_local;
+        double* s;
+    };
+    std::vector<Level> L;
+    int32_t* boxes0;
+    MRA_TRY(dalloc(A, &boxes0, 3));
+    MRA_CK(cudaMemsetAsync(boxes0, 0, 3 * sizeof(int32_t), st));
+    int nb = 1;
+    int32_t* cur = boxes0;
+    int32_t* plocal_prev = nullptr;
+    const size_t smem = (2 * k + 3 * k * k + 4 * (size_t)k3) * sizeof(double);
+    MRA_CK(cudaFuncSetAttribute(k_build_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int j = 0; j <= max_level; ++j) {
+        Level lv{nb, cur, nullptr, nullptr, plocal_prev, nullptr};
+        MRA_TRY(dalloc(A, &lv.refine, nb));
+        MRA_TRY(dalloc(A, &lv.pos, nb));
+        MRA_TRY(dalloc(A, &lv.s, (size_t)nb * k3));
+        int mode;
+        if (uniform_level >= 0) mode = (j < uniform_level) ? 1 : 2;
+        else mode = (j < init_level) ? 1 : 0;
+        if (j == max_level && mode == 1) mode = 2;
+        k_build_level<<<nb, 128, smem, st>>>(k, j, D, cur, tol, mode, j >= max_level, lv.s, lv.refine, flags);
+        MRA_CK_LAUNCH();
+        MRA_TRY(scan_exclusive(lv.refine, lv.pos, nb, flags + 1, st));
+        int32_t nref = 0;
+        MRA_CK(cudaMemcpyAsync(&nref, flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        MRA_CK(cudaStreamSynchronize(st));
+        L.push_back(lv);
+        if (nref == 0) break;
+        int32_t *next, *plocal;
+        MRA_TRY(dalloc(A, &next, 3 * 8 * (size_t)nref));
+        MRA_TRY(dalloc(A, &plocal, nref));
+        k_make_children<<<(nb + 255) / 256, 256, 0, st>>>(nb, cur, lv.refine, lv.pos, next, plocal);
+        MRA_CK_LAUNCH();
+        cur = next;
+        nb = 8 * nref;
+        plocal_prev = plocal;
+    }
+    mra_tree* t = new mra_tree();
+    t->magic = MRA_TREE_MAGIC;
+    t->k = k;
+    t->A = A;
+    t->state = MRA_TREE_LEAVES;
+    int n = 0;
+    for (auto& lv : L) n += lv.n;
+    int rc = tree_alloc_arrays(t, n, true);
+    if (rc != MRA_OK) return rc;
+    t->nlev = (int)L.size();
+    int base = 0;
+    for (int j = 0; j < MRA_MAX_LEVEL + 2; ++j) t->off[j] = n;
+    for (int j = 0; j < t->nlev; ++j) {
+        t->off[j] = base;
+        base += L[j].n;
+    }
+    base = 0;
+    for (int j = 0; j < t->nlev; ++j) {
+        int nbj = L[j].n;
+        int next_base = base + nbj;
+        int prev_base = j ? t->off[j - 1] : 0;
+        k_place_level<<<(nbj + 127) / 128, 128, 0, st>>>(nbj, j, base, next_base, L[j].boxes, L[j].refine, L[j].pos,
+                                                          L[j].parent_local, prev_base, k3, L[j].s, t->a, t->s);
+        MRA_CK_LAUNCH();
+        base = next_base;
+    }
+    MRA_CK(cudaMemcpyAsync(t->a.off, t->off, sizeof(t->off), cudaMemcpyHostToDevice, st));
+    MRA_CK(cudaMemsetAsync(t->dnorm, 0, n * sizeof(double), st));
+    int32_t hit = 0;
+    MRA_CK(cudaMemcpyAsync(&hit, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaStreamSynchronize(st));
+    t->depth_hit = hit;
+    for (auto& lv : L) {
+        A.put(lv.boxes); A.put(lv.refine); A.put(lv.pos); A.put(lv.s); A.put(lv.parent_local);
+    }
+    if (cur != L.back().boxes) A.put(cur);
+    A.put(dd); A.put(tol); A.put(flags);
+    *out = t;
+    return hit ? MRA_EDEPTH : MRA_OK;
+}
+
+// ------------------------------------------------------------ two-scale transforms
+// Block per node of level j (internal nodes only do work).
+// compress: the 8 children's blocks form a (2k)^3 cube, W is applied along each
+// direction, the k^3 corner is the parent's s and the rest its wavelet cube.
+__global__ void k_compress_level(int k, int lo, int hi, const int32_t* child, double* s, double* dnorm,
+                                 double* dcube, const double* filt) {
+    extern __shared__ double cube[];
+    __shared__ double red[32];
+    const int i = lo + blockIdx.x;
+    if (i >= hi || child[i] < 0) return;
+    const int n2 = 2 * k, k3 = k * k * k, c0 = child[i];
+    const double* W = filt + 2 * k * k;
+    for (int e = threadIdx.x; e < 8 * k3; e += blockDim.x) {
+        int o = e / k3, r = e % k3;
+        int i3 = r % k, i2 = (r / k) % k, i1 = r / (k * k);
+        int x1 = ((o >> 2) & 1) * k + i1, x2 = ((o >> 1) & 1) * k + i2, x3 = (o & 1) * k + i3;
+        cube[(x1 * n2 + x2) * n2 + x3] = s[(size_t)(c0 + o) * k3 + r];
+    }
+    __syncthreads();
+    for (int d = 0; d < 3; ++d) cube_transform(cube, n2, W, 0, d);
+    double acc = 0.0;
+    const int n3 = n2 * n2 * n2;
+    for (int e = threadIdx.x; e < n3; e += blockDim.x) {
+        int x3 = e % n2, x2 = (e / n2) % n2, x1 = e / (n2 * n2);
+        bool corner = x1 < k && x2 < k && x3 < k;
+        double v = cube[e];
+        if (corner) s[(size_t)i * k3 + (x1 * k + x2) * k + x3] = v;
+        else acc += v * v;
+        if (dcube) dcube[(size_t)i * n3 + e] = corner ? 0.0 : v;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) dnorm[i] = sqrt(acc);
+}
+
+// inverse (dcube != NULL: full s+d) or assemble (dcube == NULL: d = 0, the
+// children accumulate the upsampled parent block, eq. g_assemble).
+__global__ void k_expand_level(int k, int lo, int hi, const int32_t* child, double* s, const double* dcube,
+                               const double* filt) {
+    extern __shared__ double cube[];
+    const int i = lo + blockIdx.x;
+    if (i >= hi || child[i] < 0) return;
+    const int n2 = 2 * k, k3 = k * k * k, c0 = child[i], n3 = n2 * n2 * n2;
+    const double* W = filt + 2 * k * k;
+    for (int e = threadIdx.x; e < n3; e += blockDim.x) {
+        int x3 = e % n2, x2 = (e / n2) % n2, x1 = e / (n2 * n2);
+        bool corner = x1 < k && x2 < k && x3 < k;
+        double v = corner ? s[(size_t)i * k3 + (x1 * k + x2) * k + x3] : 0.0;
+        if (dcube && !corner) v = dcube[(size_t)i * n3 + e];
+        cube[e] = v;
+    }
+    __syncthreads();
+    for (int d = 0; d < 3; ++d) cube_transform(cube, n2, W, 1, d);
+    for (int e = threadIdx.x; e < 8 * k3; e += blockDim.x) {
+        int o = e / k3, r = e % k3;
+        int i3 = r % k, i2 = (r / k) % k, i1 = r / (k * k);
+        int x1 = ((o >> 2) & 1) * k + i1, x2 = ((o >> 1) & 1) * k + i2, x3 = (o & 1) * k + i3;
+        double v = cube[(x1 * n2 + x2) * n2 + x3];
+        size_t dst = (size_t)(c0 + o) * k3 + r;
+        if (dcube) s[dst] = v;
+        else s[dst] += v;
+    }
+}
+
+static int cube_smem(int k, size_t* bytes, const void* fn) {
+    *bytes = (size_t)8 * k * k * k * sizeof(double);
+    MRA_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes));
+    return MRA_OK;
+}
+
+int compress_impl(mra_tree* t, int store_d, cudaStream_t st) {
+    size_t smem;
+    MRA_TRY(cube_smem(t->k, &smem, (const void*)k_compress_level));
+    if (store_d && !t->dcube) MRA_TRY(dalloc(t->A, &t->dcube, (size_t)t->n * 8 * t->k * t->k * t->k));
+    MRA_CK(cudaMemsetAsync(t->dnorm, 0, t->n * sizeof(double), st));
+    for (int j = t->nlev - 2; j >= 0; --j) {
+        int lo = t->off[j], hi = t->off[j + 1];
+        if (hi <= lo) continue;
+        k_compress_level<<<hi - lo, 256, smem, st>>>(t->k, lo, hi, t->a.child, t->s, t->dnorm,
+                                                     store_d ? t->dcube : nullptr, t->filt);
+        MRA_CK_LAUNCH();
+    }
+    t->state = MRA_TREE_REDUNDANT;
+    return MRA_OK;
+}
+
+int inverse_impl(mra_tree* t, cudaStream_t st) {
+    if (!t->dcube) {
+        set_error("inverse transform needs a tree compressed with store_d");
+        return MRA_ESTATE;
+    }
+    size_t smem;
+    MRA_TRY(cube_smem(t->k, &smem, (const void*)k_expand_level));
+    for (int j = 0; j + 1 < t->nlev; ++j) {
+        int lo = t->off[j], hi = t->off[j + 1];
+        k_expand_level<<<hi - lo, 256, smem, st>>>(t->k, lo, hi, t->a.child, t->s, t->dcube, t->filt);
+        MRA_CK_LAUNCH();
+    }
+    t->state = MRA_TREE_LEAVES;
+    return MRA_OK;
+}
+
+int assemble_impl(mra_tree* t, cudaStream_t st) {
+    size_t smem;
+    MRA_TRY(cube_smem(t->k, &smem, (const void*)k_expand_level));
+    for (int j = 0; j + 1 < t->nlev; ++j) {
+        int lo = t->off[j], hi = t->off[j + 1];
+        k_expand_level<<<hi - lo, 256, smem, st>>>(t->k, lo, hi, t->a.child, t->s, nullptr, t->filt);
+        MRA_CK_LAUNCH();
+    }
+    t->state = MRA_TREE_LEAVES;
+    return MRA_OK;
+}
+
+// ------------------------------------------------------------ truncation
+__global__ void k_leaf_norm2(int n, int k3, const int32_t* leaf, const double* s, double* out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * k3;
+         e += (size_t)gridDim.x * blockDim.x) {
+        size_t i = e / k3;
+        if (leaf[i]) acc += s[e] * s[e];
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
+int leaf_norm2(const mra_tree* t, double* out, cudaStream_t st) {
+    k_leaf_norm2<<<256, 256, 0, st>>>(t->n, t->k * t->k * t->k, t->a.leaf, t->s, out);
+    MRA_CK_LAUNCH();
+    return MRA_OK;
+}
+
+// merge node i when its 8 children are leaves and ||d_i||^2 < thr2
+__global__ void k_merge_level(int lo, int hi, int n, const double* thr2, int32_t* leaf, const int32_t* child,
+                              const double* dnorm, int32_t* alive, double* removed2) {
+    int i = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= hi || leaf[i]) return;
+    double t = *thr2;
+    int c0 = child[i];
+    for (int o = 0; o < 8; ++o)
+        if (!leaf[c0 + o]) return;
+    if (dnorm[i] * dnorm[i] < t) {
+        leaf[i] = 1;
+        for (int o = 0; o < 8; ++o) alive[c0 + o] = 0;
+        atomicAdd(removed2, dnorm[i] * dnorm[i]);
+    }
+}
+
+__global__ void k_thr2(const double* norm2, int n, double eps, double* thr2) {
+    // (eps ||g|| / sqrt(N))^2
+    *thr2 = eps * eps * (*norm2) / (double)n;
+}
+
+__global__ void k_fill_i32(int32_t* p, int n, int32_t v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+__global__ void k_compact(int n, int k3, const int32_t* alive, const int32_t* newidx, mra::TreeArrays a,
+                          const double* s, const double* dnorm, mra::TreeArrays b, double* s2, double* dn2) {
+    int i = blockIdx.x;
+    if (i >= n || !alive[i]) return;
+    int d = newidx[i];
+    if (threadIdx.x == 0) {
+        b.key[d] = a.key[i];
+        for (int q = 0; q < 4; ++q) b.coord[4 * d + q] = a.coord[4 * i + q];
+        b.leaf[d] = a.leaf[i];
+        b.child[d] = a.leaf[i] ? -1 : newidx[a.child[i]];
+        b.parent[d] = a.parent[i] < 0 ? -1 : newidx[a.parent[i]];
+        dn2[d] = a.leaf[i] ? 0.0 : dnorm[i];
+    }
+    for (int e = threadIdx.x; e < k3; e += blockDim.x) s2[(size_t)d * k3 + e] = s[(size_t)i * k3 + e];
+}
+
+int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host) {
+    const int n = t->n, k3 = t->k * t->k * t->k;
+    double* dv;  // [0] ||g||^2, [1] thr^2, [2] removed^2
+    int32_t *alive, *newidx, *total;
+    MRA_TRY(dalloc(t->A, &dv, 4));
+    MRA_TRY(dalloc(t->A, &alive, n));
+    MRA_TRY(dalloc(t->A, &newidx, n));
+    MRA_TRY(dalloc(t->A, &total, 1));
+    MRA_CK(cudaMemsetAsync(dv, 0, 4 * sizeof(double), st));
+    k_leaf_norm2<<<256, 256, 0, st>>>(n, k3, t->a.leaf, t->s, dv);
+    MRA_CK_LAUNCH();
+    k_thr2<<<1, 1, 0, st>>>(dv, n, eps, dv + 1);
+    MRA_CK_LAUNCH();
+    k_fill_i32<<<(n + 255) / 256, 256, 0, st>>>(alive, n, 1);
+    MRA_CK_LAUNCH();
+    for (int j = t->nlev - 2; j >= 0; --j) {
+        int lo = t->off[j], hi = t->off[j + 1];
+        if (hi <= lo) continue;
+        k_merge_level<<<(hi - lo + 127) / 128, 128, 0, st>>>(lo, hi, n, dv + 1, t->a.leaf, t->a.child, t->dnorm, alive,
+                                                             dv + 2);
+        MRA_CK_LAUNCH();
+    }
+    MRA_TRY(scan_exclusive(alive, newidx, n, total, st));
+    std::vector<int32_t> hidx(n);
+    int32_t n2 = 0;
+    double rem2 = 0.0;
+    MRA_CK(cudaMemcpyAsync(hidx.data(), newidx, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaMemcpyAsync(&n2, total, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaMemcpyAsync(&rem2, dv + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaStreamSynchronize(st));
+    if (removed_host) *removed_host = sqrt(rem2);
+    if (n2 != n) {
+        mra_tree tmp;
+        tmp.k = t->k;
+        tmp.A = t->A;
+        tmp.filt = t->filt;
+        MRA_TRY(tree_alloc_arrays(&tmp, n2, true));
+        k_compact<<<n, 128, 0, st>>>(n, k3, alive, newidx, t->a, t->s, t->dnorm, tmp.a, tmp.s, tmp.dnorm);
+        MRA_CK_LAUNCH();
+        int off2[MRA_MAX_LEVEL + 2];
+        int nlev2 = 0;
+        // exclusive scan at a level's old first index = its new first index
+        for (int j = 0; j < MRA_MAX_LEVEL + 2; ++j) off2[j] = (t->off[j] < n) ? hidx[t->off[j]] : n2;
+        for (int j = 0; j < t->nlev; ++j)
+            if (off2[j] < n2) nlev2 = j + 1;
+        for (int j = nlev2; j < MRA_MAX_LEVEL + 2; ++j) off2[j] = n2;
+        tree_free_arrays(t);
+        t->a = tmp.a;
+        t->s = tmp.s;
+        t->dnorm = tmp.dnorm;
+        t->n = n2;
+        t->nlev = nlev2;
+        memcpy(t->off, off2, sizeof(off2));
+        MRA_CK(cudaMemcpyAsync(t->a.off, t->off, sizeof(t->off), cudaMemcpyHostToDevice, st));
+        tmp.filt = nullptr;
+    }
+    MRA_CK(cudaStreamSynchronize(st));
+    t->A.put(dv); t->A.put(alive); t->A.put(newidx); t->A.put(total);
+    return MRA_OK;
+}
+
+}  // namespace mra

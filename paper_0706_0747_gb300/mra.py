@@ -1,0 +1,338 @@
+"""Thin Python binding of the C ABI in include/mra_gb300.h (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library ``libmra_gb300.so`` (built in-tree by ``build.py``).  Importing this
+module fails loudly when the library is missing; there is no CPU fallback.
+PyTorch, when present, supplies the CUDA stream and (through the allocator
+hook) the caching allocator's device memory.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmra_gb300.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEPTH, ESTATE = 0, 1, 2, 3, 4, 5, 6
+PREC = {"fp64": 0, "fp32": 1, "tc": 2}
+TREE_LEAVES, TREE_REDUNDANT, TREE_NSFORM = 0, 1, 2
+MAX_LEVEL = 12
+
+
+class MraError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mra error {code}: {msg}")
+        self.code = code
+
+
+class Density(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("coef_host", ctypes.POINTER(ctypes.c_double)),
+                ("r2coef_host", ctypes.POINTER(ctypes.c_double)),
+                ("expo_host", ctypes.POINTER(ctypes.c_double)),
+                ("center_host", ctypes.POINTER(ctypes.c_double))]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Alloc(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class TreeInfo(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("n_nodes", ctypes.c_int), ("n_levels", ctypes.c_int),
+                ("state", ctypes.c_int), ("depth_hit", ctypes.c_int),
+                ("level_offset", ctypes.c_int * (MAX_LEVEL + 2))]
+
+
+class OpInfo(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("k", ctypes.c_int), ("max_level", ctypes.c_int),
+                ("mu", ctypes.c_double), ("alpha", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class ApplyOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("block_screen", ctypes.c_int),
+                ("unscreened", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+class ApplyStats(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int64), ("n_items", ctypes.c_int64), ("n_ghosts", ctypes.c_int64),
+                ("n_out_nodes", ctypes.c_int64), ("eta", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("fnorm", ctypes.c_double), ("ms_screen", ctypes.c_float), ("ms_ghost", ctypes.c_float),
+                ("ms_apply", ctypes.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_DP = ctypes.POINTER(ctypes.c_double)
+
+SIGNATURES = {
+    "mra_build_tree": [ctypes.POINTER(Density), ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                       ctypes.c_int, ctypes.POINTER(Alloc), _P, ctypes.POINTER(_P)],
+    "mra_tree_import": [ctypes.c_int, ctypes.c_int, _I32P, _I32P, _DP, ctypes.POINTER(Alloc), _P,
+                        ctypes.POINTER(_P)],
+    "mra_tree_export": [_P, _I32P, _I32P, _DP, _DP, _P],
+    "mra_tree_get_info": [_P, ctypes.POINTER(TreeInfo)],
+    "mra_tree_device_arrays": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)],
+    "mra_tree_set_blocks": [_P, _P, _P],
+    "mra_compress": [_P, ctypes.c_int, _P],
+    "mra_make_operator": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                          ctypes.POINTER(Alloc), _P, ctypes.POINTER(_P)],
+    "mra_op_get_info": [_P, ctypes.POINTER(OpInfo)],
+    "mra_op_export": [_P, _DP, _DP, _DP, _DP, _DP, _P],
+    "mra_apply_ns": [_P, _P, ctypes.POINTER(ApplyOpts), _P, ctypes.POINTER(_P), ctypes.POINTER(ApplyStats)],
+    "mra_reconstruct": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _DP],
+    "mra_free_tree": [_P],
+    "mra_free_op": [_P],
+    "mra_last_error": [],
+    "mra_version": [],
+    "mra_kernel_launches": [],
+}
+
+
+def lib():
+    """Load libmra_gb300.so (raises ImportError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_0706_0747_gb300/build.py "
+                              "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            if name in ("mra_last_error", "mra_version"):
+                fn.restype = ctypes.c_char_p
+            elif name == "mra_kernel_launches":
+                fn.restype = ctypes.c_ulonglong
+            else:
+                fn.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def symbols_declared():
+    return sorted(SIGNATURES)
+
+
+def _check(rc, allow=()):
+    if rc != OK and rc not in allow:
+        raise MraError(rc, lib().mra_last_error().decode())
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ----------------------------------------------------------- allocator hook
+_torch_hook = None
+
+
+def torch_allocator():
+    """An mra_alloc hook backed by torch's CUDA caching allocator (or None)."""
+    global _torch_hook
+    if _torch_hook is not None:
+        return _torch_hook
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+    except ImportError:
+        return None
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:
+            pass
+
+    hook = Alloc(ALLOC_FN(_alloc), FREE_FN(_free), None)
+    _torch_hook = hook
+    return hook
+
+
+def _alloc_ptr(allocator):
+    if allocator == "torch":
+        h = torch_allocator()
+        return ctypes.byref(h) if h is not None else None
+    if allocator is None:
+        return None
+    return ctypes.byref(allocator)
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_I32P)
+
+
+# ----------------------------------------------------------- handles
+class Tree:
+    def __init__(self, handle, keepalive=None):
+        self.h = handle
+        self._keep = keepalive
+
+    def info(self):
+        inf = TreeInfo()
+        _check(lib().mra_tree_get_info(self.h, ctypes.byref(inf)))
+        return inf
+
+    @property
+    def n(self):
+        return self.info().n_nodes
+
+    def export(self, stream=None):
+        inf = self.info()
+        n, k = inf.n_nodes, inf.k
+        coords = np.zeros((n, 4), dtype=np.int32)
+        leaf = np.zeros(n, dtype=np.int32)
+        blocks = np.zeros((n, k, k, k))
+        dnorm = np.zeros(n)
+        _check(lib().mra_tree_export(self.h, _ip(coords), _ip(leaf), _dp(blocks), _dp(dnorm), _stream(stream)))
+        return coords, leaf, blocks, dnorm
+
+    def device_arrays(self):
+        b, l = _P(), _P()
+        _check(lib().mra_tree_device_arrays(self.h, ctypes.byref(b), ctypes.byref(l)))
+        return b.value, l.value
+
+    def free(self):
+        if self.h:
+            lib().mra_free_tree(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Operator:
+    def __init__(self, handle):
+        self.h = handle
+
+    def info(self):
+        inf = OpInfo()
+        _check(lib().mra_op_get_info(self.h, ctypes.byref(inf)))
+        return inf
+
+    def export(self, stream=None):
+        inf = self.info()
+        M, k, J = inf.M, inf.k, inf.max_level
+        w, tau = np.zeros(M), np.zeros(M)
+        F = np.zeros((J + 1, M, 7, k, k))
+        nF = np.zeros((J + 1, M, 7))
+        est = np.zeros((J + 1, M))
+        _check(lib().mra_op_export(self.h, _dp(w), _dp(tau), _dp(F), _dp(nF), _dp(est), _stream(stream)))
+        return dict(w=w, tau=tau, F=F, nF=nF, est=est)
+
+    def free(self):
+        if self.h:
+            lib().mra_free_op(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------- entry points
+def build_tree(density, k, eps, max_level, uniform_level=-1, init_level=0, stream=None, allocator="torch"):
+    """mra_build_tree; density has coef, expo, centers (n,3), r2coef.  Returns
+    (Tree, depth_hit)."""
+    coef = np.ascontiguousarray(density.coef, dtype=np.float64)
+    expo = np.ascontiguousarray(density.expo, dtype=np.float64)
+    cen = np.ascontiguousarray(np.asarray(density.centers, dtype=np.float64).reshape(-1))
+    r2 = np.ascontiguousarray(getattr(density, "r2coef", np.zeros_like(coef)), dtype=np.float64)
+    d = Density(len(coef), _dp(coef), _dp(r2), _dp(expo), _dp(cen))
+    h = _P()
+    rc = lib().mra_build_tree(ctypes.byref(d), k, eps, max_level, uniform_level, init_level,
+                              _alloc_ptr(allocator), _stream(stream), ctypes.byref(h))
+    _check(rc, allow=(EDEPTH,))
+    return Tree(h.value), rc == EDEPTH
+
+
+def tree_import(k, coords, leaf, blocks, stream=None, allocator="torch"):
+    coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 4)
+    leaf = np.ascontiguousarray(leaf, dtype=np.int32)
+    blocks = np.ascontiguousarray(blocks, dtype=np.float64)
+    h = _P()
+    _check(lib().mra_tree_import(k, len(coords), _ip(coords), _ip(leaf), _dp(blocks), _alloc_ptr(allocator),
+                                 _stream(stream), ctypes.byref(h)))
+    return Tree(h.value)
+
+
+def tree_set_blocks(tree, device_ptr, stream=None):
+    """Overwrite the tree's blocks from device memory (n k^3 doubles)."""
+    _check(lib().mra_tree_set_blocks(tree.h, device_ptr, _stream(stream)))
+
+
+def compress(tree, store_d=False, stream=None):
+    _check(lib().mra_compress(tree.h, int(store_d), _stream(stream)))
+
+
+def make_operator(mu, alpha, eps, k, max_level, stream=None, allocator="torch"):
+    h = _P()
+    _check(lib().mra_make_operator(mu, alpha, eps, k, max_level, _alloc_ptr(allocator), _stream(stream),
+                                   ctypes.byref(h)))
+    return Operator(h.value)
+
+
+def apply_ns(op, tree, precision="fp64", block_screen=False, unscreened=False, stream=None, stats=True):
+    o = ApplyOpts(PREC[precision], int(block_screen), int(unscreened))
+    st = ApplyStats()
+    h = _P()
+    _check(lib().mra_apply_ns(op.h, tree.h, ctypes.byref(o), _stream(stream), ctypes.byref(h),
+                              ctypes.byref(st) if stats else None))
+    return Tree(h.value), (st.as_dict() if stats else None)
+
+
+def reconstruct(tree, mode="assemble", truncate=False, eps=0.0, stream=None):
+    rem = ctypes.c_double(0.0)
+    m = {"assemble": 0, "inverse": 1}[mode]
+    _check(lib().mra_reconstruct(tree.h, m, int(truncate), eps, _stream(stream), ctypes.byref(rem)))
+    return rem.value
+
+
+def free(handle):
+    handle.free()
+
+
+def kernel_launches():
+    return int(lib().mra_kernel_launches())
+
+
+def version():
+    return lib().mra_version().decode()
+
+
+def last_error():
+    return lib().mra_last_error().decode()

@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on
+the same seeded inputs.  Trees given to both sides are built by the oracle
+and imported, so apply parity does not depend on Algorithm 1's decisions;
+Algorithm 1 itself is compared separately.
+
+Tolerances: FP64 paths agree with the oracle to rounding (relative L2
+<= 1e-12; term/translation decisions are FP64 on both sides, so item counts
+match exactly); the FP32 path is gated at 10 eps (the per-config bound)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import apply as OA, operator as OO, tree as OT
+from paper_0706_0747_gb300 import workloads as W
+from tests.helpers import arrays_to_dict, oracle_density, oracle_to_arrays, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_0706_0747_gb300 import mra  # noqa: E402
+
+DENS2 = OT.Density([30.0, 12.0], [70.0, 150.0], [[0.45, 0.52, 0.5], [0.62, 0.41, 0.47]])
+
+
+def gpu_tree_from_oracle(tree, k):
+    c, l, b = oracle_to_arrays(tree, k)
+    return mra.tree_import(k, c, l, b)
+
+
+def export_dict(t):
+    c, l, b, dn = t.export()
+    return arrays_to_dict(c, b), {tuple(int(v) for v in cc): bool(x) for cc, x in zip(c, l)}, \
+        {tuple(int(v) for v in cc): d for cc, d in zip(c, dn)}
+
+
+@pytest.mark.parametrize("mu,alpha,eps,k,J", [(0.0, 1.0, 1e-4, 4, 3), (1.5, 1.0, 1e-6, 6, 4),
+                                              (0.0, 0.5, 1e-5, 5, 3)])
+def test_operator_tables(mu, alpha, eps, k, J):
+    op = mra.make_operator(mu, alpha, eps, k, J)
+    g = op.export()
+    o = OO.Operator(mu, alpha, eps, k, J)
+    assert len(g["w"]) == o.M
+    assert np.allclose(g["w"], o.w, rtol=1e-13, atol=0)
+    assert np.allclose(g["tau"], o.tau, rtol=1e-13, atol=0)
+    # F entries are O(1) at most; both quadratures are accurate to ~1e-15
+    assert np.abs(g["F"] - o.F).max() <= 2e-14
+    # norms inherit the entries' absolute rounding (k entries per row)
+    assert np.allclose(g["nF"], o.nF, rtol=1e-12, atol=k * 2e-14)
+    # the estimate contains N_dif = ||FF - U F U^T||, a difference of nearly
+    # equal blocks: its rounding is relative to the blocks' own scale (nF^3)
+    scale = o.nF.max(axis=2) ** 3
+    assert np.all(np.abs(g["est"] - o.est_core) <= 1e-7 * np.abs(o.est_core) + 1e-12 * scale)
+    op.free()
+
+
+def test_build_tree_matches_algorithm1():
+    k, eps = 4, 1e-4
+    tg, hit = mra.build_tree(DENS2, k, eps, 4, init_level=1)
+    to, hito = OT.build_tree(DENS2, k, eps, 4, init_level=1)
+    assert hit == hito
+    blocks, leaf, _ = export_dict(tg)
+    assert set(blocks) == set(to)
+    for key, n in to.items():
+        assert leaf[key] == n.leaf
+        if n.leaf:
+            assert np.abs(blocks[key] - n.s).max() <= 1e-12 * max(1.0, np.abs(n.s).max())
+
+
+def test_build_uniform_and_depth_cap():
+    tg, _ = mra.build_tree(DENS2, 3, 1e-3, 5, uniform_level=2)
+    assert tg.n == 1 + 8 + 64
+    # a Gaussian that level-2 boxes cannot resolve reports the cap
+    narrow = OT.Density([1.0], [2e3], [[0.52, 0.47, 0.5]])
+    tg2, hit = mra.build_tree(narrow, 4, 1e-6, 2, init_level=1)
+    to2, hito = OT.build_tree(narrow, 4, 1e-6, 2, init_level=1)
+    assert hit and hito and tg2.n == len(to2)
+
+
+def test_compress_and_inverse_round_trip():
+    k = 5
+    to, _ = OT.build_tree(DENS2, k, 1e-5, 4, init_level=1)
+    tg = gpu_tree_from_oracle(to, k)
+    mra.compress(tg, store_d=True)
+    OT.compress(to, k)
+    blocks, leaf, dn = export_dict(tg)
+    for key, n in to.items():
+        assert np.abs(blocks[key] - n.s).max() <= 1e-13 * max(1.0, np.abs(n.s).max())
+        if not n.leaf:
+            assert abs(dn[key] - n.dnorm) <= 1e-12 * max(n.dnorm, 1e-300) + 1e-14
+    ref = {key: b.copy() for key, b in blocks.items() if leaf[key]}
+    # zero the leaves on the device, then rebuild them from s^0 and d
+    c, l, b, _ = tg.export()
+    b[l.astype(bool)] = 0.0
+    dev = torch.from_numpy(b).cuda()
+    mra.tree_set_blocks(tg, dev.data_ptr())
+    mra.reconstruct(tg, mode="inverse")
+    blocks2, leaf2, _ = export_dict(tg)
+    err = math.sqrt(sum(((blocks2[key] - ref[key]) ** 2).sum() for key in ref))
+    nrm = math.sqrt(sum((b ** 2).sum() for b in ref.values()))
+    assert err <= 1e-13 * nrm * OT.levels(to)
+
+
+def run_both(tree_o, op_o, op_g, k, precision="fp64", **kw):
+    tg = gpu_tree_from_oracle(tree_o, k)
+    mra.compress(tg)
+    tc = OT.copy_tree(tree_o)
+    OT.compress(tc, k)
+    st_o = {}
+    kw_o = dict(kw)
+    if kw_o.pop("unscreened", False):
+        kw_o["screen"] = False
+    ghat_o = OA.apply_ns(op_o, tc, stats=st_o, **kw_o)
+    g, st_g = mra.apply_ns(op_g, tg, precision=precision, **kw)
+    ghat_g, _, _ = export_dict(g)
+    return tc, tg, g, ghat_o, ghat_g, st_o, st_g
+
+
+@pytest.fixture(scope="module")
+def small_cfg():
+    cfg, d = W.poisson_small()
+    dens = oracle_density(d)
+    tree, _ = OT.build_tree(dens, cfg.k, cfg.eps, cfg.max_level, uniform_level=cfg.uniform_level)
+    op_o = OO.Operator(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
+    op_g = mra.make_operator(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
+    return cfg, tree, op_o, op_g
+
+
+def test_apply_parity_poisson_k4_uniform3(small_cfg):
+    cfg, tree, op_o, op_g = small_cfg
+    tc, tg, g, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, cfg.k)
+    assert st_g["n_items"] == st_o["n_items"]
+    assert st_g["n_pairs"] == st_o["n_pairs"]
+    assert abs(st_g["eta"] - st_o["eta"]) <= 1e-13 * st_o["eta"]
+    assert rel_l2(ghat_g, ghat_o) <= 1e-12
+    # eq. g_assemble and the redundant output tree
+    gg = OA.assemble(op_o, tc, ghat_o)
+    OT.compress(gg, cfg.k)
+    mra.reconstruct(g, mode="assemble")
+    out_g, leaf_g, _ = export_dict(g)
+    assert rel_l2(out_g, {key: n.s for key, n in gg.items()}) <= 1e-12
+
+
+def test_apply_fp32_within_gate(small_cfg):
+    cfg, tree, op_o, op_g = small_cfg
+    _, _, _, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, cfg.k, precision="fp32")
+    assert st_g["n_items"] == st_o["n_items"]
+    assert rel_l2(ghat_g, ghat_o) <= 10 * cfg.eps
+
+
+@pytest.fixture(scope="module")
+def adaptive_cfg():
+    k, eps = 5, 1e-4
+    tree, _ = OT.build_tree(DENS2, k, eps, 4, init_level=1)
+    op_o = OO.Operator(0.0, 1.0, eps, k, 4)
+    op_g = mra.make_operator(0.0, 1.0, eps, k, 4)
+    return k, eps, tree, op_o, op_g
+
+
+def test_apply_parity_adaptive_with_ghosts(adaptive_cfg):
+    k, eps, tree, op_o, op_g = adaptive_cfg
+    _, _, _, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, k)
+    assert st_g["n_ghosts"] == st_o["n_refined"] > 0
+    assert st_g["n_items"] == st_o["n_items"]
+    assert rel_l2(ghat_g, ghat_o) <= 1e-12
+
+
+def test_apply_parity_unscreened(adaptive_cfg):
+    k, eps, tree, op_o, op_g = adaptive_cfg
+    _, _, _, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, k, unscreened=True)
+    assert st_g["n_items"] == st_o["n_items"]
+    assert rel_l2(ghat_g, ghat_o) <= 1e-12
+
+
+def test_apply_parity_block_screen(adaptive_cfg):
+    k, eps, tree, op_o, op_g = adaptive_cfg
+    _, _, _, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, k, block_screen=True)
+    # per-block decisions compare FP64 norms computed in different orders:
+    # allow a handful of items within rounding of the threshold
+    assert abs(st_g["n_items"] - st_o["n_items"]) <= max(2, st_o["n_items"] // 100000)
+    assert rel_l2(ghat_g, ghat_o) <= 1e-10
+
+
+@pytest.mark.parametrize("mu,alpha", [(1.5, 1.0), (0.0, 0.5)])
+def test_apply_parity_other_kernels(mu, alpha):
+    k, eps = 4, 1e-4
+    tree, _ = OT.build_tree(DENS2, k, eps, 3, init_level=1)
+    op_o = OO.Operator(mu, alpha, eps, k, 3)
+    op_g = mra.make_operator(mu, alpha, eps, k, 3)
+    _, _, _, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, k)
+    assert st_g["n_items"] == st_o["n_items"]
+    assert rel_l2(ghat_g, ghat_o) <= 1e-12
+
+
+def test_truncation_parity(adaptive_cfg):
+    k, eps, tree, op_o, op_g = adaptive_cfg
+    tc, tg, g, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, k)
+    gg = OA.assemble(op_o, tc, ghat_o)
+    gg, rem_o = OA.truncate(gg, k, 10 * eps)
+    rem_g = mra.reconstruct(g, mode="assemble", truncate=True, eps=10 * eps)
+    out_g, leaf_g, _ = export_dict(g)
+    assert set(out_g) == set(gg)
+    assert abs(rem_g - rem_o) <= 1e-9 * max(rem_o, 1e-300) + 1e-15
+    assert rel_l2(out_g, {key: n.s for key, n in gg.items()}) <= 1e-12
+
+
+def test_root_only_tree():
+    k = 4
+    tree, _ = OT.build_tree(DENS2, k, 1e-4, 0, uniform_level=0)
+    op_o = OO.Operator(0.0, 1.0, 1e-4, k, 0)
+    op_g = mra.make_operator(0.0, 1.0, 1e-4, k, 0)
+    _, _, _, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, k)
+    assert st_g["n_pairs"] == st_o["n_pairs"] == 1
+    assert rel_l2(ghat_g, ghat_o) <= 1e-13
+
+
+def test_rejects_deeper_tree_than_operator():
+    tree, _ = OT.build_tree(DENS2, 3, 1e-3, 3, uniform_level=3)
+    op_g = mra.make_operator(0.0, 1.0, 1e-3, 3, 2)
+    tg = gpu_tree_from_oracle(tree, 3)
+    mra.compress(tg)
+    with pytest.raises(mra.MraError) as e:
+        mra.apply_ns(op_g, tg)
+    assert e.value.code == mra.EINVAL
