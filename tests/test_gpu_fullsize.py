@@ -1,0 +1,146 @@
+"""GPU parity at the full workload sizes the benchmark runs.
+
+* 3-D Poisson, k = 8, eps = 1e-6, 64 Gaussians, adaptive to depth 7 (7,737
+  nodes): Algorithm 1 on the GPU against the oracle's tree, node by node; the
+  apply (launch configuration of bench.py) against the oracle on a seeded
+  sample of output nodes across all levels; the assembled output against
+  Parseval (a property at any size).
+* Bound-state Helmholtz (mu = 1.5), k = 8, eps = 1e-6, a 5-Gaussian fit of
+  exp(-2r), adaptive to depth 8: the whole apply against the oracle, and the
+  assembled output against the Gaussian-sum kernel applied exactly to the
+  box-truncated density.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import apply as OA, operator as OO, tree as OT
+from paper_0706_0747_gb300 import workloads as W
+from tests import closed_forms as CF
+from tests.helpers import arrays_to_dict, oracle_density, oracle_to_arrays, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_0706_0747_gb300 import mra  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def poisson_k8():
+    cfg, d = W.poisson_k8()
+    dens = oracle_density(d)
+    tree, hit = OT.build_tree(dens, cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
+    op_o = OO.Operator(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
+    op_g = mra.make_operator(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
+    return cfg, d, tree, hit, op_o, op_g
+
+
+def test_poisson_k8_tree_matches_algorithm1(poisson_k8):
+    cfg, d, tree, hit, _, _ = poisson_k8
+    tg, hit_g = mra.build_tree(d, cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
+    c, l, b, _ = tg.export()
+    assert hit_g == hit
+    got = arrays_to_dict(c, b)
+    assert set(got) == set(tree)
+    for cc, lf in zip(c, l):
+        key = tuple(int(v) for v in cc)
+        assert bool(lf) == tree[key].leaf
+    leaves = [key for key, n in tree.items() if n.leaf]
+    err = rel_l2({key: got[key] for key in leaves}, {key: tree[key].s for key in leaves})
+    assert err <= 1e-13
+
+
+def sample_nodes(tree, per_level=6, seed=11):
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(OT.levels(tree)):
+        keys = sorted(key for key in tree if key[0] == j)
+        pick = rng.choice(len(keys), size=min(per_level, len(keys)), replace=False)
+        out += [keys[i] for i in sorted(pick)]
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_poisson_k8_apply_sampled(poisson_k8, precision):
+    cfg, d, tree, hit, op_o, op_g = poisson_k8
+    c, l, b = oracle_to_arrays(tree, cfg.k)
+    tg = mra.tree_import(cfg.k, c, l, b)
+    mra.compress(tg)
+    g, st = mra.apply_ns(op_g, tg, precision=precision)
+    cg, _, bg, _ = g.export()
+    got = arrays_to_dict(cg, bg)
+    tc = OT.copy_tree(tree)
+    OT.compress(tc, cfg.k)
+    nodes = sample_nodes(tc)
+    st_o = {}
+    ref = OA.apply_ns(op_o, tc, stats=st_o, nodes=nodes)
+    assert abs(st["eta"] - st_o["eta"]) <= 1e-13 * st_o["eta"]
+    err = rel_l2({key: got[key] for key in nodes}, ref)
+    assert err <= (1e-12 if precision == "fp64" else 10 * cfg.eps), err
+
+
+def test_poisson_k8_assembled_parseval(poisson_k8):
+    cfg, d, tree, hit, op_o, op_g = poisson_k8
+    tg, _ = mra.build_tree(d, cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
+    mra.compress(tg)
+    g, st = mra.apply_ns(op_g, tg, precision="fp64")
+    mra.reconstruct(g, mode="assemble")
+    c, l, b, dn = g.export()
+    leaf2 = float((b[l.astype(bool)] ** 2).sum())
+    root = int(np.where((c == 0).all(axis=1))[0][0])
+    parseval = float((b[root] ** 2).sum() + (dn[~l.astype(bool)] ** 2).sum())
+    assert abs(parseval - leaf2) <= 1e-12 * leaf2
+
+
+@pytest.fixture(scope="module")
+def helmholtz():
+    cfg, d = W.helmholtz_slater()
+    dens = oracle_density(d)
+    tree, _ = OT.build_tree(dens, cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
+    op_o = OO.Operator(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
+    op_g = mra.make_operator(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
+    return cfg, d, tree, op_o, op_g
+
+
+def test_helmholtz_slater_full_parity(helmholtz):
+    cfg, d, tree, op_o, op_g = helmholtz
+    c, l, b = oracle_to_arrays(tree, cfg.k)
+    tg = mra.tree_import(cfg.k, c, l, b)
+    mra.compress(tg)
+    g, st = mra.apply_ns(op_g, tg, precision="fp64")
+    cg, _, bg, _ = g.export()
+    tc = OT.copy_tree(tree)
+    OT.compress(tc, cfg.k)
+    st_o = {}
+    ref = OA.apply_ns(op_o, tc, stats=st_o)
+    assert st["n_items"] == st_o["n_items"]
+    assert rel_l2(arrays_to_dict(cg, bg), ref) <= 1e-12
+
+
+def test_helmholtz_slater_against_truncated_closed_form(helmholtz):
+    """T applied to f 1_B on B (Sec. 2.2: f : B -> B) with the Gaussian-sum
+    kernel done exactly: sum over the fit's terms of coef * sum_m w_m prod_d
+    int_0^1 exp(-tau_m (x_d - y)^2) exp(-a (y - 1/2)^2) dy, projected on the
+    output leaves.  The input tree carries the eps-level representation error."""
+    cfg, d, tree, op_o, op_g = helmholtz
+    tg, _ = mra.build_tree(d, cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
+    mra.compress(tg)
+    g, st = mra.apply_ns(op_g, tg, precision="fp64")
+    mra.reconstruct(g, mode="assemble")
+    c, l, b, _ = g.export()
+    w, tau = op_o.w, op_o.tau          # the expected value uses the oracle's Gaussian sum
+    parts = [CF.truncated_gauss_sum_potential(w, tau, a, [0.5, 0.5, 0.5], coef=cc) for cc, a in zip(d.coef, d.expo)]
+
+    def exact(p):
+        return sum(f(p) for f in parts)
+    num = den = 0.0
+    for cc, lf, bb in zip(c, l, b):
+        if lf:
+            e = CF.project_leaf(exact, cfg.k, int(cc[0]), cc[1:], sub=1, q=cfg.k + 4)
+            num += ((bb - e) ** 2).sum()
+            den += (e ** 2).sum()
+    assert math.sqrt(num / den) <= 10 * cfg.eps
