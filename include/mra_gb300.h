@@ -236,6 +236,34 @@ typedef struct {
 int mra_apply_ns(const mra_op* op, const mra_tree* f, const mra_apply_opts* opts,
                  void* stream, mra_tree** g_ns, mra_apply_stats* stats);
 
+/* The same apply for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is a deployment variant of mra_apply_ns.
+ *
+ * Some callers cannot call cudaMalloc or cudaFree during the apply: code that
+ * runs where another component owns the device allocator, or work that must
+ * not change the device's memory map while it runs.  This entry point
+ * allocates nothing: its scratch (worklist, Step-2 hash set and refined input
+ * blocks) is one fixed 21 MiB array in device memory that every GPU loading the
+ * library holds until the process exits.
+ *   - f: an MRA_TREE_REDUNDANT tree with at most 1024 nodes and k <= 8, whose
+ *     Step-2 refinement needs at most 4096 input blocks; op as for
+ *     mra_apply_ns (static screening only, no per-block screen).
+ *   - precision: MRA_PREC_FP64 or MRA_PREC_FP32.
+ *   - ghat_out: caller-owned device memory of f's n_nodes * k^3 doubles; on
+ *     return it holds ghat^j for every node in f's node order (the data of the
+ *     MRA_TREE_NSFORM tree mra_apply_ns would return).
+ *   - n_items_host (optional): the number of (node, translation, term) items.
+ * Sizes beyond these limits return MRA_EINVAL with a message, before any work
+ * is queued (nodes, k) or right after the screen (refined blocks).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind; the call
+ * clears what must start at zero.  Calls that overlap on the GPU (other
+ * streams or threads) race on the array: serialise them.  The call
+ * synchronises `stream` once to read the worklist sizes. */
+int mra_apply_ns_noalloc(const mra_op* op, const mra_tree* f, int precision, double* ghat_out,
+                         void* stream, int64_t* n_items_host);
+
 /* ------------------------------------------------------------------------ */
 /* Reconstruct.
  * MRA_RECON_ASSEMBLE: for an MRA_TREE_NSFORM tree, eq. g_assemble top-down

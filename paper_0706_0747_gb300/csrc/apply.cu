@@ -632,3 +632,171 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
 }
 
 }  // namespace mra
+
+// ------------------------------------------------------------------ no-alloc apply
+// mra_apply_ns_noalloc: the same screen, Step-2 refinement and SIMT apply as
+// apply_impl, for callers that cannot allocate device memory (code running
+// where another component owns the allocator, or inside work that must not
+// call cudaMalloc/cudaFree).  Its scratch lives in one file-scope device array
+// of fixed size that every GPU loading the library keeps until exit.
+#include <atomic>
+#include <mutex>
+
+namespace mra {
+
+#define NA_MAX_NODES 1024
+#define NA_MAX_K 8
+#define NA_MAX_GHOSTS 4096
+#define NA_HASH_CAP 16384u
+
+struct NaLayout {
+    size_t dv, sched, count, pair_off, total, err, gtab, gid, gkeys, pairs, gblk, nitems, bytes;
+};
+
+static constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static NaLayout na_layout() {
+    NaLayout L;
+    size_t o = 0;
+    L.dv = o;       o = na_align(o + 4 * sizeof(double));
+    L.sched = o;    o = na_align(o + (MRA_MAX_TERMS + 16 * (MRA_MAX_LEVEL + 1)) * sizeof(int32_t));
+    L.count = o;    o = na_align(o + (NA_MAX_NODES + 1) * sizeof(int32_t));
+    L.pair_off = o; o = na_align(o + (NA_MAX_NODES + 1) * sizeof(int32_t));
+    L.total = o;    o = na_align(o + 2 * sizeof(int32_t));
+    L.err = o;      o = na_align(o + 2 * sizeof(int32_t));
+    L.gtab = o;     o = na_align(o + NA_HASH_CAP * sizeof(uint64_t));
+    L.gid = o;      o = na_align(o + NA_HASH_CAP * sizeof(int32_t));
+    L.gkeys = o;    o = na_align(o + NA_HASH_CAP * sizeof(uint64_t));
+    L.pairs = o;    o = na_align(o + (size_t)NA_MAX_NODES * 216 * sizeof(Pair));
+    L.gblk = o;     o = na_align(o + (size_t)NA_MAX_GHOSTS * NA_MAX_K * NA_MAX_K * NA_MAX_K * sizeof(double));
+    L.nitems = o;   o = na_align(o + sizeof(unsigned long long));
+    L.bytes = o;
+    return L;
+}
+
+// 21 MiB: enough for na_layout() (about 20.8 MiB); fixed at compile time.
+#define NA_SCRATCH_BYTES (21u * 1024u * 1024u)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_SCRATCH_BYTES];
+
+// Host-side device addresses of g_noalloc_scratch, one per device, obtained
+// once with cudaGetSymbolAddress while that device is current.  In host code
+// the symbol itself is only a host stand-in, never a device address.
+static unsigned char* g_na_ptr[256];
+static std::mutex g_na_mu;
+
+static int na_scratch(unsigned char** out) {
+    int dev = 0;
+    MRA_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) { set_error("device index %d out of range", dev); return MRA_EINVAL; }
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+            return MRA_ECUDA;
+        }
+        g_na_ptr[dev] = (unsigned char*)p;
+    }
+    *out = g_na_ptr[dev];
+    return MRA_OK;
+}
+
+int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, double* ghat, cudaStream_t st,
+                       int64_t* n_items_host) {
+    const int k = op->k, k3 = k * k * k, M = op->M, n = f->n, nlev = f->nlev;
+    static_assert(sizeof(Pair) == 16, "pair size");
+    const NaLayout L = na_layout();
+    static_assert(NA_SCRATCH_BYTES >= 20u * 1024u * 1024u, "scratch size");
+    if (L.bytes > NA_SCRATCH_BYTES) { set_error("internal: no-alloc scratch layout too large"); return MRA_ECUDA; }
+    if (f->k != k) { set_error("tree order k=%d differs from operator k=%d", f->k, k); return MRA_EINVAL; }
+    if (k > NA_MAX_K) { set_error("no-alloc apply supports k <= %d (got %d)", NA_MAX_K, k); return MRA_EINVAL; }
+    if (n > NA_MAX_NODES) { set_error("no-alloc apply supports at most %d nodes (got %d)", NA_MAX_NODES, n); return MRA_EINVAL; }
+    if (nlev - 1 > op->J) { set_error("tree depth %d exceeds operator max_level %d", nlev - 1, op->J); return MRA_EINVAL; }
+    if (f->state != MRA_TREE_REDUNDANT) { set_error("apply needs a compressed (redundant) tree"); return MRA_ESTATE; }
+    if (precision != MRA_PREC_FP64 && precision != MRA_PREC_FP32) { set_error("precision %d is not available", precision); return MRA_EINVAL; }
+    if (!ghat) { set_error("output buffer is NULL"); return MRA_EINVAL; }
+    unsigned char* base = nullptr;
+    MRA_TRY(na_scratch(&base));
+    double* dv = (double*)(base + L.dv);
+    int32_t* sched = (int32_t*)(base + L.sched);
+    int32_t* count = (int32_t*)(base + L.count);
+    int32_t* pair_off = (int32_t*)(base + L.pair_off);
+    int32_t* total = (int32_t*)(base + L.total);
+    int32_t* err = (int32_t*)(base + L.err);
+    uint64_t* gtab = (uint64_t*)(base + L.gtab);
+    int32_t* gid = (int32_t*)(base + L.gid);
+    uint64_t* gkeys = (uint64_t*)(base + L.gkeys);
+    Pair* pairs = (Pair*)(base + L.pairs);
+    double* gblk = (double*)(base + L.gblk);
+    unsigned long long* nitems = (unsigned long long*)(base + L.nitems);
+
+    // the array keeps the previous call's contents: clear what must start at zero
+    MRA_CK(cudaMemsetAsync(dv, 0, 4 * sizeof(double), st));
+    MRA_CK(cudaMemsetAsync(total, 0, 2 * sizeof(int32_t), st));
+    MRA_CK(cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), st));
+    MRA_CK(cudaMemsetAsync(nitems, 0, sizeof(unsigned long long), st));
+    k_fill_u64<<<64, 256, 0, st>>>(gtab, NA_HASH_CAP, GH_EMPTY);
+    MRA_CK_LAUNCH();
+    MRA_TRY(leaf_norm2(f, dv, st));
+    const size_t pilot_smem = (4 * (size_t)k3 + k * k) * sizeof(double);
+    k_pilot<<<1, 128, pilot_smem, st>>>(k, M, op->w, op->F, f->s, dv + 1);
+    MRA_CK_LAUNCH();
+    k_schedule<<<1, 256, 0, st>>>(M, nlev, 0, op->eps, op->w, op->nF, op->est, dv, dv + 1, sched, dv + 2);
+    MRA_CK_LAUNCH();
+    ScreenArgs sa;
+    sa.n = n; sa.M = M; sa.nlev = nlev;
+    sa.coord = f->a.coord; sa.leaf = f->a.leaf; sa.key = f->a.key; sa.off = f->a.off;
+    sa.sched = sched; sa.gtab = gtab; sa.gcap = NA_HASH_CAP; sa.gid = gid;
+    sa.count = count; sa.pair_off = pair_off; sa.pairs = nullptr; sa.err = err;
+    const int sblocks = (int)std::min<long>(4096, ((long)n * 32 + 255) / 256);
+    k_screen<false><<<sblocks, 256, 0, st>>>(sa);
+    MRA_CK_LAUNCH();
+    MRA_TRY(scan_exclusive(count, pair_off, n, total, st));
+    MRA_CK(cudaMemcpyAsync(pair_off + n, total, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    k_ghost_ids<<<64, 256, 0, st>>>(gtab, NA_HASH_CAP, gid, gkeys, total + 1);
+    MRA_CK_LAUNCH();
+    int32_t h[2] = {0, 0}, herr[2] = {0, 0};
+    MRA_CK(cudaMemcpyAsync(h, total, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaMemcpyAsync(herr, err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaStreamSynchronize(st));
+    if (herr[0] || h[1] > NA_MAX_GHOSTS) {
+        set_error("no-alloc apply supports at most %d refined input blocks (Step 2)", NA_MAX_GHOSTS);
+        return MRA_EINVAL;
+    }
+    const int nghost = h[1];
+    if (nghost > 0) {
+        const size_t gsm = (2 * (size_t)k * k + 3 * (size_t)k3) * sizeof(double);
+        k_ghost_refine<<<nghost, 128, gsm, st>>>(k, gkeys, f->a.key, f->a.off, f->a.leaf, f->s, f->filt, gblk, err);
+        MRA_CK_LAUNCH();
+    }
+    sa.pairs = pairs;
+    k_screen<true><<<sblocks, 256, 0, st>>>(sa);
+    MRA_CK_LAUNCH();
+    ApplyArgs aa;
+    aa.k = k; aa.M = M; aa.n = n; aa.pairs = pairs; aa.pair_off = pair_off; aa.coord = f->a.coord;
+    aa.s = f->s; aa.gblk = gblk; aa.w = op->w; aa.nF = op->nF; aa.Jm = sched; aa.out = ghat; aa.n_items = nitems;
+    aa.eta_blk = -1.0;
+    if (precision == MRA_PREC_FP64) {
+        aa.F = op->F;
+        size_t smem = (size_t)k3 * sizeof(double) + (4 * (size_t)k3 + 3 * k * k) * sizeof(double);
+        k_apply_simt<double><<<std::min(n, 152 * 16), 128, smem, st>>>(aa);
+        MRA_CK_LAUNCH();
+    } else {
+        aa.F = op->F32;
+        size_t smem = (size_t)k3 * sizeof(double) + (4 * (size_t)k3 + 3 * k * k) * sizeof(float);
+        k_apply_simt<float><<<std::min(n, 152 * 16), 128, smem, st>>>(aa);
+        MRA_CK_LAUNCH();
+    }
+    if (n_items_host) {
+        unsigned long long ni = 0;
+        MRA_CK(cudaMemcpyAsync(&ni, nitems, sizeof(ni), cudaMemcpyDeviceToHost, st));
+        MRA_CK(cudaMemcpyAsync(herr, err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        MRA_CK(cudaStreamSynchronize(st));
+        *n_items_host = (int64_t)ni;
+        if (herr[0] || herr[1]) { set_error("screen/ghost error code %d/%d", herr[0], herr[1]); return MRA_ECUDA; }
+    }
+    return MRA_OK;
+}
+
+}  // namespace mra

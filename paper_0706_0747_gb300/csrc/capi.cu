@@ -220,6 +220,12 @@ int mra_apply_ns(const mra_op* op, const mra_tree* f, const mra_apply_opts* opts
     return apply_impl(op, f, opts, (cudaStream_t)stream, g_ns, stats);
 }
 
+int mra_apply_ns_noalloc(const mra_op* op, const mra_tree* f, int precision, double* ghat_out, void* stream,
+                         int64_t* n_items_host) {
+    if (!op_ok(op) || !tree_ok(f)) { set_error("invalid operator or tree handle"); return MRA_EINVAL; }
+    return apply_noalloc_impl(op, f, precision, ghat_out, (cudaStream_t)stream, n_items_host);
+}
+
 int mra_reconstruct(mra_tree* t, int mode, int truncate, double eps, void* stream, double* truncation_l2_host) {
     if (!tree_ok(t)) { set_error("invalid tree handle"); return MRA_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;

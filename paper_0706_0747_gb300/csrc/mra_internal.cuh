@@ -120,6 +120,8 @@ int tree_clone_skeleton(const mra_tree* src, mra_tree** out);
 // apply.cu
 int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cudaStream_t st,
                mra_tree** g, mra_apply_stats* stats);
+int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, double* ghat, cudaStream_t st,
+                       int64_t* n_items_host);
 
 // ---------------------------------------------------------------- device helpers
 __host__ __device__ inline uint64_t spread3(uint32_t v) {

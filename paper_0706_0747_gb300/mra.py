@@ -87,6 +87,7 @@ SIGNATURES = {
     "mra_op_get_info": [_P, ctypes.POINTER(OpInfo)],
     "mra_op_export": [_P, _DP, _DP, _DP, _DP, _DP, _P],
     "mra_apply_ns": [_P, _P, ctypes.POINTER(ApplyOpts), _P, ctypes.POINTER(_P), ctypes.POINTER(ApplyStats)],
+    "mra_apply_ns_noalloc": [_P, _P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_int64)],
     "mra_reconstruct": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _DP],
     "mra_free_tree": [_P],
     "mra_free_op": [_P],
@@ -313,6 +314,14 @@ def apply_ns(op, tree, precision="fp64", block_screen=False, unscreened=False, s
     _check(lib().mra_apply_ns(op.h, tree.h, ctypes.byref(o), _stream(stream), ctypes.byref(h),
                               ctypes.byref(st) if stats else None))
     return Tree(h.value), (st.as_dict() if stats else None)
+
+
+def apply_ns_noalloc(op, tree, out_ptr, precision="fp64", stream=None):
+    """mra_apply_ns_noalloc: writes ghat into caller-owned device memory at
+    out_ptr (n_nodes * k^3 doubles); returns the item count."""
+    n = ctypes.c_int64(0)
+    _check(lib().mra_apply_ns_noalloc(op.h, tree.h, PREC[precision], out_ptr, _stream(stream), ctypes.byref(n)))
+    return n.value
 
 
 def reconstruct(tree, mode="assemble", truncate=False, eps=0.0, stream=None):
