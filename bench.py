@@ -193,7 +193,7 @@ def main():
     op = mra.make_operator(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
     tree, hit = mra.build_tree(dens, cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
     k, n = cfg.k, tree.n
-    avail = ["fp64", "fp32"]
+    avail = ["fp64", "fp32", "tc"]
     prec = args.precision if args.precision != "auto" else avail[-1]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 

@@ -219,7 +219,10 @@ typedef struct {
     int block_screen;       /* 1: also drop items whose w prod N_F ||f_b|| is  */
                             /* below eps ||T_0 f_0|| / sqrt(N 216 M)           */
     int unscreened;         /* 1: every term at every scale (band only; tests) */
-    int reserved[5];
+    int itemwise;           /* 1: SIMT paths apply each item's three mode     */
+                            /* products separately instead of the nested sums */
+                            /* of Algorithm 3 (same items; for comparison)    */
+    int reserved[4];
 } mra_apply_opts;
 
 typedef struct {

@@ -17,21 +17,12 @@
 #include <algorithm>
 #include <vector>
 
-#include "mra_internal.cuh"
+#include "apply_common.cuh"
 
 namespace mra {
 
 int scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* total, cudaStream_t st);
 int leaf_norm2(const mra_tree* t, double* out, cudaStream_t st);
-
-struct Pair {
-    int32_t out;    // output node
-    int32_t in;     // input node (>= 0) or -1 - ghost id
-    int16_t m_lo, m_hi;
-    int8_t t1, t2, t3;
-    uint8_t flags;  // bit 0: core translation at an internal node
-};
-static_assert(sizeof(Pair) == 16, "Pair is 16 bytes");
 
 // ------------------------------------------------------------------ pilot
 __global__ void k_pilot(int k, int M, const double* w, const double* F, const double* s0, double* sigma) {
@@ -380,22 +371,6 @@ __global__ void k_ghost_refine(int k, const uint64_t* gkeys, const uint64_t* key
 }
 
 // ------------------------------------------------------------------ apply
-struct ApplyArgs {
-    int k, M, n;
-    const Pair* pairs;
-    const int32_t* pair_off;
-    const int32_t* coord;
-    const double* s;
-    const double* gblk;
-    const double* w;
-    const void* F;         // double or float table [j][m][l+3][k][k]
-    const double* nF;
-    const int32_t* Jm;
-    double eta_blk;        // < 0: no per-block screen
-    double* out;
-    unsigned long long* n_items;
-};
-
 // Block per output node.  T is the contraction type (double or float); the
 // per-pair sum over terms is accumulated in T and added to the FP64 output.
 template <class T>
@@ -496,8 +471,12 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     if (nlev - 1 > op->J) { set_error("tree depth %d exceeds operator max_level %d", nlev - 1, op->J); return MRA_EINVAL; }
     if (f->state != MRA_TREE_REDUNDANT) { set_error("apply_ns needs a compressed (redundant) tree"); return MRA_ESTATE; }
     const int prec = o ? o->precision : MRA_PREC_FP64;
-    if (prec != MRA_PREC_FP64 && prec != MRA_PREC_FP32) {
+    if (prec != MRA_PREC_FP64 && prec != MRA_PREC_FP32 && prec != MRA_PREC_TC_SPLIT) {
         set_error("precision %d is not available", prec);
+        return MRA_EINVAL;
+    }
+    if (prec == MRA_PREC_TC_SPLIT && ((o && (o->block_screen || o->itemwise)) || k != 8)) {
+        set_error("the tensor-core apply needs k = 8 and the static screen");
         return MRA_EINVAL;
     }
     const Alloc& A = f->A;
@@ -590,7 +569,16 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         aa.eta_blk = op->eps * sig / sqrt((double)n * 216.0 * M);
     }
     int rc = MRA_OK;
-    if (prec == MRA_PREC_FP64) {
+    const bool itemwise = (o && o->itemwise) || aa.eta_blk >= 0.0;
+    if (prec == MRA_PREC_TC_SPLIT) {
+        // tcgen05 FP16 hi/lo split products (apply_tc.cu)
+        rc = launch_apply_tc(aa, nghost, nlev, op, st);
+        if (rc != MRA_OK) return rc;
+    } else if (!itemwise) {
+        // Algorithm 3's nested sums, factorised (apply_fact.cu)
+        aa.F = prec == MRA_PREC_FP64 ? (const void*)op->F : (const void*)op->F32;
+        MRA_TRY(launch_apply_fact(aa, prec, nlev, st));
+    } else if (prec == MRA_PREC_FP64) {
         aa.F = op->F;
         size_t smem = (size_t)k3 * sizeof(double) + (4 * (size_t)k3 + 3 * k * k) * sizeof(double);
         MRA_CK(cudaFuncSetAttribute(k_apply_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -1,0 +1,528 @@
+// Step 3 of Algorithm 3 on the 5th-generation tensor cores (tcgen05), k = 8.
+//
+// Same nested sums as apply_fact.cu, per output node a and chunk of TC_MC
+// terms m (w_m, F = F^{j;m,.}):
+//   stage I   per (t2,t3) line:  W_m[c1][(i2,i3)] = sum_{t1 kept} sum_i1 F^{t1}[c1][i1] x_t[i1][i2][i3]
+//             MMA M=64 rows (i2,i3), N=32 (m,c1), K=48 (t1,i1); the kept-item
+//             mask zeroes whole F^{t1} blocks of the B operand
+//   stage II  per plane t3 and term: V_m[(c1,i3)][c2] = sum_{t2,i2} W_m[c1][i2][i3] F^{t2}[c2][i2]
+//             MMA M=64, N=8, K=48 (t2,i2)
+//   stage III per plane and term: Y_m[(c1,c2)][c3] += sum_i3 V_m F^{t3}[c3][i3]
+//             MMA M=64, N=8, K=16 (i3, zero padded), accumulated over planes in TMEM
+//   ghat_a += w_m Y_m in FP64.
+// Every operand is FP16 split into hi + lo (v ~= hi + lo to 2^-22), and each
+// product is the three MMAs hi*hi + hi*lo + lo*hi into an FP32 accumulator.
+// Power-of-two scales keep every operand in FP16's normal range: per input
+// block (x * sx in (2^12, 2^13]), per (j, m) operator block (F * sF), per node
+// (sx_node = the smallest block scale of the neighbourhood), and per term for
+// W and V from bounds (|W| <= 48 max|F| max|x|, |V| <= 48 max|F| max|W|).
+//
+// One elected thread issues the MMAs and commits them to an mbarrier; the
+// 128 threads wait on it (bounded), read TMEM with tcgen05.ld and write the
+// next stage's operand into shared memory in the canonical no-swizzle
+// K-major layout (8-row x 16-byte core matrices).
+#include <climits>
+
+#include "apply_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace mra {
+
+#define TC_MC 4
+#define TC_THREADS 128
+#define TC_WAIT_LIMIT (1u << 26)
+
+// ---------------------------------------------------------------- prep
+// Input blocks (tree nodes then Step-2 blocks) -> FP16 hi/lo in the stage-I
+// A layout: element x[i1][i2][i3] at half index i2*64 + i3*8 + i1 (core
+// matrix i2, row i3, column i1), with a power-of-two scale per block.
+__global__ void k_tc_prep_blocks(int n, int ng, const double* s, const double* gblk, __half* xh, __half* xl,
+                                 float* sx, float* xmax) {
+    __shared__ float red[4];
+    const int b = blockIdx.x;
+    if (b >= n + ng) return;
+    const double* src = b < n ? s + (size_t)b * 512 : gblk + (size_t)(b - n) * 512;
+    double v[4];
+    float m = 0.0f;
+    for (int q = 0; q < 4; ++q) {
+        v[q] = src[threadIdx.x + 128 * q];
+        m = fmaxf(m, (float)fabs(v[q]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+    int e = 0;
+    if (m > 0.0f) frexpf(m, &e);
+    const double scale = ldexp(1.0, 13 - e);  // m * scale in [2^12, 2^13)
+    for (int q = 0; q < 4; ++q) {
+        const int idx = threadIdx.x + 128 * q;  // x[i1][i2][i3]
+        const int i1 = idx >> 6, i2 = (idx >> 3) & 7, i3 = idx & 7;
+        __half hi, lo;
+        tc::split_h((float)(v[q] * scale), hi, lo);
+        xh[(size_t)b * 512 + i2 * 64 + i3 * 8 + i1] = hi;
+        xl[(size_t)b * 512 + i2 * 64 + i3 * 8 + i1] = lo;
+    }
+    if (threadIdx.x == 0) {
+        sx[b] = (float)scale;
+        xmax[b] = m;
+    }
+}
+
+// Operator blocks F^{j;m,t}[c][i] -> FP16 hi/lo (natural row-major layout,
+// which is already the core-matrix layout of the B operands) with a
+// power-of-two scale per (j, m).
+__global__ void k_tc_prep_F(int M, const double* F, __half* Fh, __half* Fl, float* sF, float* maxF) {
+    __shared__ float red[4];
+    const int m = blockIdx.x, j = blockIdx.y;
+    const double* src = F + ((size_t)j * M + m) * 7 * 64;
+    float mx = 0.0f;
+    for (int e = threadIdx.x; e < 7 * 64; e += blockDim.x) mx = fmaxf(mx, (float)fabs(src[e]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+    int ex = 0;
+    if (mx > 0.0f) frexpf(mx, &ex);
+    const double scale = ldexp(1.0, 13 - ex);
+    for (int e = threadIdx.x; e < 7 * 64; e += blockDim.x) {
+        __half hi, lo;
+        tc::split_h((float)(src[e] * scale), hi, lo);
+        Fh[((size_t)j * M + m) * 7 * 64 + e] = hi;
+        Fl[((size_t)j * M + m) * 7 * 64 + e] = lo;
+    }
+    if (threadIdx.x == 0) {
+        sF[(size_t)j * M + m] = (float)scale;
+        maxF[(size_t)j * M + m] = mx;
+    }
+}
+
+struct TcArgs {
+    ApplyArgs A;
+    const __half* xh;
+    const __half* xl;
+    const float* sx;
+    const float* xmax;
+    const __half* Fh;
+    const __half* Fl;
+    const float* sF;
+    const float* maxF;
+    int* err;
+};
+
+// shared-memory map (bytes)
+#define SM_XH 0          // 6 blocks x 1 KB (stage I A, hi)
+#define SM_XL 6144
+#define SM_B1H 12288     // 4 terms x 6 cores x 128 B (stage I B)
+#define SM_B1L 15360
+#define SM_A2H 18432     // 4 terms x 6144 B (stage II A: 8 row groups x 6 K groups)
+#define SM_A2L 43008
+#define SM_B2H 67584     // 4 terms x 768 B (stage II B)
+#define SM_B2L 70656
+#define SM_A3H 73728     // 4 terms x 2048 B (stage III A: 8 row groups x 2 K groups)
+#define SM_A3L 81920
+#define SM_B3H 90112     // 4 terms x 256 B (stage III B)
+#define SM_B3L 91136
+#define SM_TAB 92160     // 4 x 216 int
+#define SM_MSK 95616     // 36 x TC_MC bytes
+#define SM_TOTAL 95872
+
+__device__ __forceinline__ float pow2floor(double x) {
+    if (!(x > 0.0)) return 0.0f;
+    int e;
+    frexp(x, &e);
+    e -= 1;
+    if (e > 126) e = 126;
+    if (e < -126) return 0.0f;
+    return ldexpf(1.0f, e);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_apply_tc(TcArgs T) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ int s_mlo, s_mhi, s_exp_min, s_abort;
+    __shared__ unsigned int s_xmax_bits;
+    __shared__ unsigned long long s_items;
+    __shared__ float s_c2[TC_MC], s_c3[TC_MC], s_g[6];
+    __shared__ double s_fin[TC_MC];
+
+    const ApplyArgs& A = T.A;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __half* B1H = (__half*)(sm + SM_B1H);
+    __half* B1L = (__half*)(sm + SM_B1L);
+    __half* A2H = (__half*)(sm + SM_A2H);
+    __half* A2L = (__half*)(sm + SM_A2L);
+    __half* B2H = (__half*)(sm + SM_B2H);
+    __half* B2L = (__half*)(sm + SM_B2L);
+    __half* A3H = (__half*)(sm + SM_A3H);
+    __half* A3L = (__half*)(sm + SM_A3L);
+    __half* B3H = (__half*)(sm + SM_B3H);
+    __half* B3L = (__half*)(sm + SM_B3L);
+    int* tin = (int*)(sm + SM_TAB);
+    int* tlo = tin + 216;
+    int* thi = tlo + 216;
+    int* tfl = thi + 216;
+    unsigned char* msk = sm + SM_MSK;
+
+    // zero everything once: the K padding of stage III stays zero
+    for (int e = tid; e < SM_TOTAL / 16; e += TC_THREADS) ((uint4*)sm)[e] = make_uint4(0, 0, 0, 0);
+    if (warp == 0) tc::tmem_alloc(&s_tmem, 128);
+    if (tid == 0) {
+        tc::mbar_init(&s_mbar, 1);
+        s_abort = 0;
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = s_tmem;
+    const uint32_t tD1 = tbase, tD2 = tbase + 32, tD3 = tbase + 64;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t idI = tc::idesc_f16(64, 32), idII = tc::idesc_f16(64, 8), idIII = tc::idesc_f16(64, 8);
+    uint32_t phase = 0;
+    const int row = warp * 16 + lane;  // accumulator row of this thread (M=64 layout), valid for lane < 16
+    const bool has_row = lane < 16;
+    const uint32_t sbase = tc::smem_u32(sm);
+
+    for (int node = blockIdx.x; node < A.n && !s_abort; node += gridDim.x) {
+        const int j = A.coord[4 * node];
+        const int a1 = A.coord[4 * node + 1], a2 = A.coord[4 * node + 2], a3 = A.coord[4 * node + 3];
+        const int p0 = A.pair_off[node], p1 = A.pair_off[node + 1];
+        for (int q = tid; q < 216; q += TC_THREADS) tin[q] = INT_MIN;
+        if (tid == 0) {
+            s_mlo = INT_MAX;
+            s_mhi = -1;
+            s_exp_min = INT_MAX;
+            s_xmax_bits = 0u;
+            s_items = 0;
+        }
+        __syncthreads();
+        for (int p = p0 + tid; p < p1; p += TC_THREADS) {
+            const Pair pr = A.pairs[p];
+            const int q1 = pr.t1 + ((a1 & 1) ? 2 : 3), q2 = pr.t2 + ((a2 & 1) ? 2 : 3),
+                      q3 = pr.t3 + ((a3 & 1) ? 2 : 3);
+            const int q = q1 * 36 + q2 * 6 + q3;
+            tin[q] = pr.in;
+            tlo[q] = pr.m_lo;
+            thi[q] = pr.m_hi;
+            tfl[q] = pr.flags;
+            atomicMin(&s_mlo, (int)pr.m_lo);
+            atomicMax(&s_mhi, (int)pr.m_hi);
+            const int b = pr.in >= 0 ? pr.in : A.n + (-1 - pr.in);
+            int e;
+            frexpf(T.sx[b], &e);
+            atomicMin(&s_exp_min, e);
+            atomicMax(&s_xmax_bits, __float_as_uint(T.xmax[b]));  // non-negative floats order as ints
+        }
+        __syncthreads();
+        const int mlo = s_mlo, mhi = s_mhi;
+        const float xmax_node = __uint_as_float(s_xmax_bits);
+        const float sx_node = ldexpf(1.0f, s_exp_min - 1);
+        double y[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) y[c] = 0.0;
+        if (mhi >= mlo && xmax_node > 0.0f) {
+            for (int m0 = mlo; m0 <= mhi && !s_abort; m0 += TC_MC) {
+                // masks of kept t1 per line and term; per-term scale factors
+                for (int e = tid; e < 36 * TC_MC; e += TC_THREADS) {
+                    const int line = e / TC_MC, mc = e % TC_MC, m = m0 + mc;
+                    unsigned char mk = 0;
+                    if (m <= mhi) {
+                        const int jm = A.Jm[m];
+                        if (jm >= j)
+                            for (int q1 = 0; q1 < 6; ++q1) {
+                                const int q = q1 * 36 + line;
+                                if (tin[q] == INT_MIN || m < tlo[q] || m > thi[q]) continue;
+                                if ((tfl[q] & 1) && jm > j) continue;
+                                mk |= (unsigned char)(1u << q1);
+                            }
+                    }
+                    msk[e] = mk;
+                }
+                if (tid < TC_MC) {
+                    const int m = m0 + tid;
+                    float c2 = 0.0f, c3 = 0.0f;
+                    double fin = 0.0;
+                    if (m <= mhi) {
+                        const double mf = T.maxF[(size_t)j * A.M + m], sf = T.sF[(size_t)j * A.M + m];
+                        if (mf > 0.0) {
+                            const double sW = pow2floor(8192.0 / (48.0 * mf * (double)xmax_node));
+                            const double sV = pow2floor(8192.0 / (48.0 * 48.0 * mf * mf * (double)xmax_node));
+                            if (sW > 0.0 && sV > 0.0) {
+                                c2 = (float)(sW / (sf * (double)sx_node));
+                                c3 = (float)(sV / (sW * sf));
+                                fin = A.w[m] / (sV * sf);
+                            }
+                        }
+                    }
+                    s_c2[tid] = c2;
+                    s_c3[tid] = c3;
+                    s_fin[tid] = fin;
+                }
+                // stage II B operand: core (K group q2) = F^{j;m,t2(q2)}[c2][i2]
+                for (int e = tid; e < TC_MC * 6 * 64; e += TC_THREADS) {
+                    const int mc = e / 384, q2 = (e / 64) % 6, r = e % 64;
+                    const int m = m0 + mc;
+                    __half h = __float2half(0.0f), l = h;
+                    if (m <= mhi) {
+                        const size_t src = (((size_t)j * A.M + m) * 7 + band_t(a2, q2) + 3) * 64 + r;
+                        h = T.Fh[src];
+                        l = T.Fl[src];
+                    }
+                    B2H[mc * 384 + q2 * 64 + r] = h;
+                    B2L[mc * 384 + q2 * 64 + r] = l;
+                }
+                __syncthreads();
+                int plane_started = 0;
+                for (int q3 = 0; q3 < 6 && !s_abort; ++q3) {
+                    unsigned plane_mask = 0;
+                    for (int e = q3 * TC_MC; e < 36 * TC_MC; e += 6 * TC_MC)
+                        for (int mc = 0; mc < TC_MC; ++mc) plane_mask |= msk[e + mc];
+                    if (!plane_mask) continue;  // uniform
+                    const int t3 = band_t(a3, q3);
+                    // stage III B operand (K group 0) and a zeroed stage II A
+                    for (int e = tid; e < TC_MC * 64; e += TC_THREADS) {
+                        const int mc = e / 64, r = e % 64, m = m0 + mc;
+                        __half h = __float2half(0.0f), l = h;
+                        if (m <= mhi) {
+                            const size_t src = (((size_t)j * A.M + m) * 7 + t3 + 3) * 64 + r;
+                            h = T.Fh[src];
+                            l = T.Fl[src];
+                        }
+                        B3H[mc * 128 + r] = h;
+                        B3L[mc * 128 + r] = l;
+                    }
+                    for (int e = tid; e < (2 * 24576) / 16; e += TC_THREADS)
+                        ((uint4*)(sm + SM_A2H))[e] = make_uint4(0, 0, 0, 0);
+                    __syncthreads();
+                    for (int q2 = 0; q2 < 6; ++q2) {
+                        const int line = q2 * 6 + q3;
+                        unsigned lm = 0;
+                        for (int mc = 0; mc < TC_MC; ++mc) lm |= msk[line * TC_MC + mc];
+                        if (!lm) continue;  // uniform
+                        // stage I A: the line's input blocks; per-slot scale ratio g
+                        if (tid < 6) {
+                            float g = 0.0f;
+                            if (lm & (1u << tid)) {
+                                const int in = tin[tid * 36 + line];
+                                const int b = in >= 0 ? in : A.n + (-1 - in);
+                                g = sx_node / T.sx[b];
+                            }
+                            s_g[tid] = g;
+                        }
+                        for (int e = tid; e < 6 * 64 * 2; e += TC_THREADS) {
+                            const int half = e / 384, q1 = (e / 64) % 6, v = e % 64;  // 64 uint4 per 1 KB
+                            uint4 val = make_uint4(0, 0, 0, 0);
+                            if (lm & (1u << q1)) {
+                                const int in = tin[q1 * 36 + line];
+                                const int b = in >= 0 ? in : A.n + (-1 - in);
+                                const uint4* src = (const uint4*)((half ? T.xl : T.xh) + (size_t)b * 512);
+                                val = src[v];
+                            }
+                            ((uint4*)(sm + (half ? SM_XL : SM_XH)))[q1 * 64 + v] = val;
+                        }
+                        __syncthreads();
+                        // stage I B: core (N group mc, K group q1) = mask ? g * F^{j;m,t1(q1)} : 0
+                        for (int e = tid; e < TC_MC * 6 * 64; e += TC_THREADS) {
+                            const int mc = e / 384, q1 = (e / 64) % 6, r = e % 64;
+                            const int m = m0 + mc;
+                            __half h = __float2half(0.0f), l = h;
+                            if ((msk[line * TC_MC + mc] >> q1) & 1u) {
+                                const size_t src = (((size_t)j * A.M + m) * 7 + band_t(a1, q1) + 3) * 64 + r;
+                                const float g = s_g[q1];
+                                h = __float2half_rn(__half2float(T.Fh[src]) * g);
+                                l = __float2half_rn(__half2float(T.Fl[src]) * g);
+                            }
+                            B1H[mc * 384 + q1 * 64 + r] = h;
+                            B1L[mc * 384 + q1 * 64 + r] = l;
+                        }
+                        tc::fence_async_smem();
+                        __syncthreads();
+                        if (tid == 0) {
+                            tc::fence_after();
+#pragma unroll
+                            for (int ks = 0; ks < 3; ++ks) {
+                                const uint64_t ah = tc::sdesc(sbase + SM_XH + ks * 2048, 1024, 128);
+                                const uint64_t al = tc::sdesc(sbase + SM_XL + ks * 2048, 1024, 128);
+                                const uint64_t bh = tc::sdesc(sbase + SM_B1H + ks * 256, 128, 768);
+                                const uint64_t bl = tc::sdesc(sbase + SM_B1L + ks * 256, 128, 768);
+                                tc::mma_f16(tD1, ah, bh, idI, ks > 0);
+                                tc::mma_f16(tD1, ah, bl, idI, 1);
+                                tc::mma_f16(tD1, al, bh, idI, 1);
+                            }
+                            tc::commit(&s_mbar);
+                            for (int mc = 0; mc < TC_MC; ++mc) s_items += __popc(msk[line * TC_MC + mc]);
+                        }
+                        const bool ok = tc::mbar_wait(&s_mbar, phase, TC_WAIT_LIMIT);
+                        phase ^= 1u;
+                        if (__syncthreads_or(!ok)) {
+                            if (tid == 0) { s_abort = 1; atomicExch(T.err, 4); }
+                            break;
+                        }
+                        tc::fence_after();
+                        // D_I -> stage II A, K group q2: row (c1, i3), column i2
+#pragma unroll
+                        for (int mc = 0; mc < TC_MC; ++mc) {
+                            float v[8];
+                            tc::tmem_ld8(tD1 + lane_off + mc * 8, v);
+                            if (has_row) {
+                                const int i2 = row >> 3, i3 = row & 7;
+                                const float c2 = s_c2[mc];
+#pragma unroll
+                                for (int c1 = 0; c1 < 8; ++c1) {
+                                    __half h, l;
+                                    tc::split_h(v[c1] * c2, h, l);
+                                    const int o = mc * 3072 + c1 * 384 + q2 * 64 + i3 * 8 + i2;
+                                    A2H[o] = h;
+                                    A2L[o] = l;
+                                }
+                            }
+                        }
+                        tc::fence_before();
+                        __syncthreads();
+                    }
+                    if (s_abort) break;
+                    // stage II: per term, M=64 (c1,i3) x N=8 (c2) x K=48 (t2,i2)
+                    tc::fence_async_smem();
+                    __syncthreads();
+                    if (tid == 0) {
+                        tc::fence_after();
+                        for (int mc = 0; mc < TC_MC; ++mc) {
+#pragma unroll
+                            for (int ks = 0; ks < 3; ++ks) {
+                                const uint64_t ah = tc::sdesc(sbase + SM_A2H + mc * 6144 + ks * 256, 128, 768);
+                                const uint64_t al = tc::sdesc(sbase + SM_A2L + mc * 6144 + ks * 256, 128, 768);
+                                const uint64_t bh = tc::sdesc(sbase + SM_B2H + mc * 768 + ks * 256, 128, 768);
+                                const uint64_t bl = tc::sdesc(sbase + SM_B2L + mc * 768 + ks * 256, 128, 768);
+                                tc::mma_f16(tD2 + mc * 8, ah, bh, idII, ks > 0);
+                                tc::mma_f16(tD2 + mc * 8, ah, bl, idII, 1);
+                                tc::mma_f16(tD2 + mc * 8, al, bh, idII, 1);
+                            }
+                        }
+                        tc::commit(&s_mbar);
+                    }
+                    {
+                        const bool ok = tc::mbar_wait(&s_mbar, phase, TC_WAIT_LIMIT);
+                        phase ^= 1u;
+                        if (__syncthreads_or(!ok)) {
+                            if (tid == 0) { s_abort = 1; atomicExch(T.err, 4); }
+                            break;
+                        }
+                    }
+                    tc::fence_after();
+                    // D_II -> stage III A: row (c1, c2), column i3 (K group 0)
+#pragma unroll
+                    for (int mc = 0; mc < TC_MC; ++mc) {
+                        float v[8];
+                        tc::tmem_ld8(tD2 + lane_off + mc * 8, v);
+                        if (has_row) {
+                            const int c1 = row >> 3, i3 = row & 7;
+                            const float c3 = s_c3[mc];
+#pragma unroll
+                            for (int c2 = 0; c2 < 8; ++c2) {
+                                __half h, l;
+                                tc::split_h(v[c2] * c3, h, l);
+                                const int o = mc * 1024 + c1 * 128 + c2 * 8 + i3;
+                                A3H[o] = h;
+                                A3L[o] = l;
+                            }
+                        }
+                    }
+                    tc::fence_before();
+                    tc::fence_async_smem();
+                    __syncthreads();
+                    // stage III: per term, M=64 (c1,c2) x N=8 (c3) x K=16 (i3 + zero padding)
+                    if (tid == 0) {
+                        tc::fence_after();
+                        for (int mc = 0; mc < TC_MC; ++mc) {
+                            const uint64_t ah = tc::sdesc(sbase + SM_A3H + mc * 2048, 128, 256);
+                            const uint64_t al = tc::sdesc(sbase + SM_A3L + mc * 2048, 128, 256);
+                            const uint64_t bh = tc::sdesc(sbase + SM_B3H + mc * 256, 128, 256);
+                            const uint64_t bl = tc::sdesc(sbase + SM_B3L + mc * 256, 128, 256);
+                            tc::mma_f16(tD3 + mc * 8, ah, bh, idIII, plane_started);
+                            tc::mma_f16(tD3 + mc * 8, ah, bl, idIII, 1);
+                            tc::mma_f16(tD3 + mc * 8, al, bh, idIII, 1);
+                        }
+                        tc::commit(&s_mbar);
+                    }
+                    {
+                        const bool ok = tc::mbar_wait(&s_mbar, phase, TC_WAIT_LIMIT);
+                        phase ^= 1u;
+                        if (__syncthreads_or(!ok)) {
+                            if (tid == 0) { s_abort = 1; atomicExch(T.err, 4); }
+                            break;
+                        }
+                    }
+                    tc::fence_after();
+                    plane_started = 1;
+                }
+                if (s_abort) break;
+                if (plane_started) {
+                    // ghat += w_m Y_m (FP64): row (c1, c2), column c3
+#pragma unroll
+                    for (int mc = 0; mc < TC_MC; ++mc) {
+                        float v[8];
+                        tc::tmem_ld8(tD3 + lane_off + mc * 8, v);
+                        const double fin = s_fin[mc];
+#pragma unroll
+                        for (int c3 = 0; c3 < 8; ++c3) y[c3] += fin * (double)v[c3];
+                    }
+                }
+                tc::fence_before();
+                __syncthreads();
+            }
+        }
+        if (has_row)
+#pragma unroll
+            for (int c3 = 0; c3 < 8; ++c3) A.out[(size_t)node * 512 + row * 8 + c3] = y[c3];
+        if (tid == 0 && A.n_items) atomicAdd(A.n_items, s_items);
+        __syncthreads();
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 128);
+}
+
+int launch_apply_tc(const ApplyArgs& A, int nghost, int nlev, const mra_op* op, cudaStream_t st) {
+    (void)nlev;
+    if (A.k != 8) {
+        set_error("the tensor-core apply supports k = 8 (got k = %d)", A.k);
+        return MRA_EINVAL;
+    }
+    const Alloc& Al = op->A;
+    const int nb = A.n + nghost;
+    const size_t JM = (size_t)(op->J + 1) * op->M;
+    __half *xh, *xl, *Fh, *Fl;
+    float *sx, *xmax, *sF, *maxF;
+    int* err;
+    MRA_TRY(dalloc(Al, &xh, (size_t)nb * 512));
+    MRA_TRY(dalloc(Al, &xl, (size_t)nb * 512));
+    MRA_TRY(dalloc(Al, &sx, nb));
+    MRA_TRY(dalloc(Al, &xmax, nb));
+    MRA_TRY(dalloc(Al, &Fh, JM * 7 * 64));
+    MRA_TRY(dalloc(Al, &Fl, JM * 7 * 64));
+    MRA_TRY(dalloc(Al, &sF, JM));
+    MRA_TRY(dalloc(Al, &maxF, JM));
+    MRA_TRY(dalloc(Al, &err, 1));
+    MRA_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    k_tc_prep_blocks<<<nb, 128, 0, st>>>(A.n, nghost, A.s, A.gblk, xh, xl, sx, xmax);
+    MRA_CK_LAUNCH();
+    k_tc_prep_F<<<dim3(op->M, op->J + 1), 128, 0, st>>>(op->M, op->F, Fh, Fl, sF, maxF);
+    MRA_CK_LAUNCH();
+    TcArgs T{A, xh, xl, sx, xmax, Fh, Fl, sF, maxF, err};
+    MRA_CK(cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL));
+    const int grid = std::min(A.n, 152 * 2);
+    k_apply_tc<<<grid, TC_THREADS, SM_TOTAL, st>>>(T);
+    MRA_CK_LAUNCH();
+    int herr = 0;
+    MRA_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaStreamSynchronize(st));
+    Al.put(xh); Al.put(xl); Al.put(sx); Al.put(xmax); Al.put(Fh); Al.put(Fl); Al.put(sF); Al.put(maxF); Al.put(err);
+    if (herr) {
+        set_error("tensor-core apply: an MMA completion wait reached its limit");
+        return MRA_ETIMEOUT;
+    }
+    return MRA_OK;
+}
+
+}  // namespace mra

@@ -54,7 +54,7 @@ class OpInfo(ctypes.Structure):
 
 class ApplyOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("block_screen", ctypes.c_int),
-                ("unscreened", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("unscreened", ctypes.c_int), ("itemwise", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class ApplyStats(ctypes.Structure):
@@ -307,8 +307,9 @@ def make_operator(mu, alpha, eps, k, max_level, stream=None, allocator="torch"):
     return Operator(h.value)
 
 
-def apply_ns(op, tree, precision="fp64", block_screen=False, unscreened=False, stream=None, stats=True):
-    o = ApplyOpts(PREC[precision], int(block_screen), int(unscreened))
+def apply_ns(op, tree, precision="fp64", block_screen=False, unscreened=False, itemwise=False, stream=None,
+             stats=True):
+    o = ApplyOpts(PREC[precision], int(block_screen), int(unscreened), int(itemwise))
     st = ApplyStats()
     h = _P()
     _check(lib().mra_apply_ns(op.h, tree.h, ctypes.byref(o), _stream(stream), ctypes.byref(h),

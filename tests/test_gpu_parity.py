@@ -111,6 +111,7 @@ def run_both(tree_o, op_o, op_g, k, precision="fp64", **kw):
     OT.compress(tc, k)
     st_o = {}
     kw_o = dict(kw)
+    kw_o.pop("itemwise", None)
     if kw_o.pop("unscreened", False):
         kw_o["screen"] = False
     ghat_o = OA.apply_ns(op_o, tc, stats=st_o, **kw_o)
@@ -166,6 +167,39 @@ def test_apply_parity_adaptive_with_ghosts(adaptive_cfg):
     assert st_g["n_ghosts"] == st_o["n_refined"] > 0
     assert st_g["n_items"] == st_o["n_items"]
     assert rel_l2(ghat_g, ghat_o) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_apply_parity_itemwise_kernel(adaptive_cfg, precision):
+    """The per-item formulation (three mode products per item) and the default
+    nested-sum formulation apply the same items."""
+    k, eps, tree, op_o, op_g = adaptive_cfg
+    _, _, _, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, k, precision=precision, itemwise=True)
+    assert st_g["n_items"] == st_o["n_items"]
+    assert rel_l2(ghat_g, ghat_o) <= (1e-12 if precision == "fp64" else 10 * eps)
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+def test_apply_tensor_core_split_k8(eps):
+    """tcgen05 FP16 hi/lo split products with FP32 accumulation: same items as
+    the oracle, every output block within the 10 eps gate."""
+    k = 8
+    tree, _ = OT.build_tree(DENS2, k, eps, 3, init_level=1)
+    op_o = OO.Operator(0.0, 1.0, eps, k, 3)
+    op_g = mra.make_operator(0.0, 1.0, eps, k, 3)
+    _, _, _, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, k, precision="tc")
+    assert st_g["n_items"] == st_o["n_items"]
+    assert rel_l2(ghat_g, ghat_o) <= 10 * eps
+
+
+def test_tensor_core_rejects_other_orders():
+    tree, _ = OT.build_tree(DENS2, 4, 1e-4, 2, uniform_level=2)
+    op_g = mra.make_operator(0.0, 1.0, 1e-4, 4, 2)
+    tg = gpu_tree_from_oracle(tree, 4)
+    mra.compress(tg)
+    with pytest.raises(mra.MraError) as e:
+        mra.apply_ns(op_g, tg, precision="tc")
+    assert e.value.code == mra.EINVAL
 
 
 def test_apply_parity_unscreened(adaptive_cfg):
