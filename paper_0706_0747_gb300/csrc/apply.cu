@@ -572,7 +572,7 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     const bool itemwise = (o && o->itemwise) || aa.eta_blk >= 0.0;
     if (prec == MRA_PREC_TC_SPLIT) {
         // tcgen05 FP16 hi/lo split products (apply_tc.cu)
-        rc = launch_apply_tc(aa, nghost, nlev, op, st);
+        rc = launch_apply_tc(aa, nghost, nlev, op, err + 1, st);
         if (rc != MRA_OK) return rc;
     } else if (!itemwise) {
         // Algorithm 3's nested sums, factorised (apply_fact.cu)
@@ -610,7 +610,8 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         cudaEventElapsedTime(&stats->ms_screen, ev[0], ev[1]);
         cudaEventElapsedTime(&stats->ms_ghost, ev[1], ev[2]);
         cudaEventElapsedTime(&stats->ms_apply, ev[2], ev[3]);
-        if (herr[0] || herr[1]) { set_error("screen/ghost error code %d/%d", herr[0], herr[1]); rc = MRA_ECUDA; }
+        if (herr[1] == 4) { set_error("tensor-core apply: an MMA completion wait reached its limit"); rc = MRA_ETIMEOUT; }
+        else if (herr[0] || herr[1]) { set_error("screen/ghost error code %d/%d", herr[0], herr[1]); rc = MRA_ECUDA; }
     }
     A.put(dv); A.put(sched); A.put(count); A.put(pair_off); A.put(total); A.put(err);
     A.put(gtab); A.put(gid); A.put(gkeys); A.put(pairs); A.put(gblk); A.put(nitems);

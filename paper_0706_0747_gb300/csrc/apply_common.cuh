@@ -30,6 +30,6 @@ struct ApplyArgs {
 };
 
 int launch_apply_fact(const ApplyArgs& A, int precision, int nlev, cudaStream_t st);
-int launch_apply_tc(const ApplyArgs& A, int nghost, int nlev, const mra_op* op, cudaStream_t st);
+int launch_apply_tc(const ApplyArgs& A, int nghost, int nlev, const mra_op* op, int* err, cudaStream_t st);
 
 }  // namespace mra

@@ -2,25 +2,26 @@
 //
 // Same nested sums as apply_fact.cu, per output node a and chunk of TC_MC
 // terms m (w_m, F = F^{j;m,.}):
-//   stage I   per (t2,t3) line:  W_m[c1][(i2,i3)] = sum_{t1 kept} sum_i1 F^{t1}[c1][i1] x_t[i1][i2][i3]
-//             MMA M=64 rows (i2,i3), N=32 (m,c1), K=48 (t1,i1); the kept-item
+//   stage I   per (t2,t3) line: W_m[c1][(i2,i3)] = sum_{t1 kept} sum_i1 F^{t1}[c1][i1] x_t[i1][i2][i3]
+//             MMA M=64 rows (i2,i3), N=8*TC_MC (m,c1), K=48 (t1,i1); the kept-item
 //             mask zeroes whole F^{t1} blocks of the B operand
-//   stage II  per plane t3 and term: V_m[(c1,i3)][c2] = sum_{t2,i2} W_m[c1][i2][i3] F^{t2}[c2][i2]
-//             MMA M=64, N=8, K=48 (t2,i2)
+//   stage II  per line and term: V_m[(c1,i3)][c2] += sum_i2 W_m[c1][i2][i3] F^{t2}[c2][i2]
+//             MMA M=64, N=8, K=16 (i2, zero padded), accumulated over the plane's lines in TMEM
 //   stage III per plane and term: Y_m[(c1,c2)][c3] += sum_i3 V_m F^{t3}[c3][i3]
 //             MMA M=64, N=8, K=16 (i3, zero padded), accumulated over planes in TMEM
 //   ghat_a += w_m Y_m in FP64.
 // Every operand is FP16 split into hi + lo (v ~= hi + lo to 2^-22), and each
 // product is the three MMAs hi*hi + hi*lo + lo*hi into an FP32 accumulator.
 // Power-of-two scales keep every operand in FP16's normal range: per input
-// block (x * sx in (2^12, 2^13]), per (j, m) operator block (F * sF), per node
+// block (x * sx in [2^12, 2^13)), per (j, m) operator block (F * sF), per node
 // (sx_node = the smallest block scale of the neighbourhood), and per term for
 // W and V from bounds (|W| <= 48 max|F| max|x|, |V| <= 48 max|F| max|W|).
 //
 // One elected thread issues the MMAs and commits them to an mbarrier; the
 // 128 threads wait on it (bounded), read TMEM with tcgen05.ld and write the
 // next stage's operand into shared memory in the canonical no-swizzle
-// K-major layout (8-row x 16-byte core matrices).
+// K-major layout (8-row x 16-byte core matrices).  Per line there is one
+// wait: stage II of a line runs while the next line's operands are staged.
 #include <climits>
 
 #include "apply_common.cuh"
@@ -28,9 +29,10 @@
 
 namespace mra {
 
-#define TC_MC 4
-#define TC_THREADS 128
+#define TC_MC 8
+#define TC_THREADS 256
 #define TC_WAIT_LIMIT (1u << 26)
+#define TC_TMEM_COLS 256
 
 // ---------------------------------------------------------------- prep
 // Input blocks (tree nodes then Step-2 blocks) -> FP16 hi/lo in the stage-I
@@ -110,22 +112,22 @@ struct TcArgs {
     int* err;
 };
 
-// shared-memory map (bytes)
-#define SM_XH 0          // 6 blocks x 1 KB (stage I A, hi)
+// shared-memory map (bytes); every operand region starts on a 128-byte boundary
+#define SM_XH 0          // 6 blocks x 1 KB: stage I A (hi)
 #define SM_XL 6144
-#define SM_B1H 12288     // 4 terms x 6 cores x 128 B (stage I B)
-#define SM_B1L 15360
-#define SM_A2H 18432     // 4 terms x 6144 B (stage II A: 8 row groups x 6 K groups)
-#define SM_A2L 43008
-#define SM_B2H 67584     // 4 terms x 768 B (stage II B)
-#define SM_B2L 70656
-#define SM_A3H 73728     // 4 terms x 2048 B (stage III A: 8 row groups x 2 K groups)
-#define SM_A3L 81920
-#define SM_B3H 90112     // 4 terms x 256 B (stage III B)
-#define SM_B3L 91136
-#define SM_TAB 92160     // 4 x 216 int
-#define SM_MSK 95616     // 36 x TC_MC bytes
-#define SM_TOTAL 95872
+#define SM_B1H 12288     // TC_MC terms x 6 K groups x 128 B: stage I B (hi)
+#define SM_B1L 18432
+#define SM_A2H 24576     // TC_MC terms x 2048 B: stage II A (8 row groups x 2 K groups); stage III A aliases it
+#define SM_A2L 40960
+#define SM_B2 57344      // 2 buffers x {hi, lo} x TC_MC terms x 256 B: stage II B (K group 1 zero)
+#define SM_B3H 65536     // TC_MC terms x 256 B: stage III B (K group 1 zero)
+#define SM_B3L 67584
+#define SM_FSH 69632     // TC_MC terms x 7 shifts x 64 halves: the chunk's F^{j;m,t} (hi)
+#define SM_FSL 76800
+#define SM_TAB 83968     // 4 x 216 int
+#define SM_MSK 87424     // 36 x TC_MC bytes
+#define SM_Y 87808       // 64 x 8 doubles: the second warp half's partial ghat
+#define SM_TOTAL 91904
 
 __device__ __forceinline__ float pow2floor(double x) {
     if (!(x > 0.0)) return 0.0f;
@@ -137,11 +139,11 @@ __device__ __forceinline__ float pow2floor(double x) {
     return ldexpf(1.0f, e);
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_apply_tc(TcArgs T) {
+__global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ int s_mlo, s_mhi, s_exp_min, s_abort;
+    __shared__ int s_mlo, s_mhi, s_exp_min;
     __shared__ unsigned int s_xmax_bits;
     __shared__ unsigned long long s_items;
     __shared__ float s_c2[TC_MC], s_c3[TC_MC], s_g[6];
@@ -153,38 +155,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_apply_tc(TcArgs T) {
     __half* B1L = (__half*)(sm + SM_B1L);
     __half* A2H = (__half*)(sm + SM_A2H);
     __half* A2L = (__half*)(sm + SM_A2L);
-    __half* B2H = (__half*)(sm + SM_B2H);
-    __half* B2L = (__half*)(sm + SM_B2L);
-    __half* A3H = (__half*)(sm + SM_A3H);
-    __half* A3L = (__half*)(sm + SM_A3L);
     __half* B3H = (__half*)(sm + SM_B3H);
     __half* B3L = (__half*)(sm + SM_B3L);
+    __half* FSH = (__half*)(sm + SM_FSH);
+    __half* FSL = (__half*)(sm + SM_FSL);
     int* tin = (int*)(sm + SM_TAB);
     int* tlo = tin + 216;
     int* thi = tlo + 216;
     int* tfl = thi + 216;
     unsigned char* msk = sm + SM_MSK;
 
-    // zero everything once: the K padding of stage III stays zero
+    // zero everything once: the K padding of stages II and III stays zero
     for (int e = tid; e < SM_TOTAL / 16; e += TC_THREADS) ((uint4*)sm)[e] = make_uint4(0, 0, 0, 0);
-    if (warp == 0) tc::tmem_alloc(&s_tmem, 128);
+    if (warp == 0) tc::tmem_alloc(&s_tmem, TC_TMEM_COLS);
     if (tid == 0) {
         tc::mbar_init(&s_mbar, 1);
-        s_abort = 0;
     }
     tc::fence_async_smem();
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = s_tmem;
-    const uint32_t tD1 = tbase, tD2 = tbase + 32, tD3 = tbase + 64;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-    const uint32_t idI = tc::idesc_f16(64, 32), idII = tc::idesc_f16(64, 8), idIII = tc::idesc_f16(64, 8);
+    const uint32_t tD1 = tbase, tD2 = tbase + 8 * TC_MC, tD3 = tbase + 16 * TC_MC;
+    // warps w and w+4 share TMEM lane quarter w and split the terms of a chunk
+    const int quarter = warp & 3, whalf = warp >> 2;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const int mc_lo = whalf * (TC_MC / 2), mc_hi = mc_lo + TC_MC / 2;
+    const uint32_t idI = tc::idesc_f16(64, 8 * TC_MC), idS = tc::idesc_f16(64, 8);
     uint32_t phase = 0;
-    const int row = warp * 16 + lane;  // accumulator row of this thread (M=64 layout), valid for lane < 16
+    const int row = quarter * 16 + lane;  // accumulator row of this thread (M=64 layout), valid for lane < 16
     const bool has_row = lane < 16;
     const uint32_t sbase = tc::smem_u32(sm);
 
-    for (int node = blockIdx.x; node < A.n && !s_abort; node += gridDim.x) {
+    // the abort decision comes from __syncthreads_or, so it is uniform
+    bool aborted = false;
+#define TC_WAIT_OR_ABORT()                                              \
+    {                                                                   \
+        const bool ok_ = tc::mbar_wait(&s_mbar, phase, TC_WAIT_LIMIT);  \
+        phase ^= 1u;                                                    \
+        if (__syncthreads_or(!ok_)) {                                   \
+            aborted = true;                                             \
+            if (tid == 0) atomicExch(T.err, 4);                         \
+        }                                                               \
+    }
+
+    for (int node = blockIdx.x; node < A.n && !aborted; node += gridDim.x) {
         const int j = A.coord[4 * node];
         const int a1 = A.coord[4 * node + 1], a2 = A.coord[4 * node + 2], a3 = A.coord[4 * node + 3];
         const int p0 = A.pair_off[node], p1 = A.pair_off[node + 1];
@@ -222,8 +236,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_apply_tc(TcArgs T) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) y[c] = 0.0;
         if (mhi >= mlo && xmax_node > 0.0f) {
-            for (int m0 = mlo; m0 <= mhi && !s_abort; m0 += TC_MC) {
-                // masks of kept t1 per line and term; per-term scale factors
+            for (int m0 = mlo; m0 <= mhi && !aborted; m0 += TC_MC) {
+                // the chunk's operator blocks, the kept-t1 masks per line, per-term scales
+                for (int e = tid; e < TC_MC * 7 * 64 / 8; e += TC_THREADS) {  // uint4 = 8 halves
+                    const int mc = e / 56, r = e % 56, m = m0 + mc;
+                    uint4 h = make_uint4(0, 0, 0, 0), l = h;
+                    if (m <= mhi) {
+                        const size_t src = ((size_t)j * A.M + m) * 56 + r;
+                        h = ((const uint4*)T.Fh)[src];
+                        l = ((const uint4*)T.Fl)[src];
+                    }
+                    ((uint4*)FSH)[e] = h;
+                    ((uint4*)FSL)[e] = l;
+                }
                 for (int e = tid; e < 36 * TC_MC; e += TC_THREADS) {
                     const int line = e / TC_MC, mc = e % TC_MC, m = m0 + mc;
                     unsigned char mk = 0;
@@ -259,48 +284,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_apply_tc(TcArgs T) {
                     s_c3[tid] = c3;
                     s_fin[tid] = fin;
                 }
-                // stage II B operand: core (K group q2) = F^{j;m,t2(q2)}[c2][i2]
-                for (int e = tid; e < TC_MC * 6 * 64; e += TC_THREADS) {
-                    const int mc = e / 384, q2 = (e / 64) % 6, r = e % 64;
-                    const int m = m0 + mc;
-                    __half h = __float2half(0.0f), l = h;
-                    if (m <= mhi) {
-                        const size_t src = (((size_t)j * A.M + m) * 7 + band_t(a2, q2) + 3) * 64 + r;
-                        h = T.Fh[src];
-                        l = T.Fl[src];
-                    }
-                    B2H[mc * 384 + q2 * 64 + r] = h;
-                    B2L[mc * 384 + q2 * 64 + r] = l;
-                }
                 __syncthreads();
                 int plane_started = 0;
-                for (int q3 = 0; q3 < 6 && !s_abort; ++q3) {
+                for (int q3 = 0; q3 < 6 && !aborted; ++q3) {
                     unsigned plane_mask = 0;
                     for (int e = q3 * TC_MC; e < 36 * TC_MC; e += 6 * TC_MC)
                         for (int mc = 0; mc < TC_MC; ++mc) plane_mask |= msk[e + mc];
                     if (!plane_mask) continue;  // uniform
                     const int t3 = band_t(a3, q3);
-                    // stage III B operand (K group 0) and a zeroed stage II A
-                    for (int e = tid; e < TC_MC * 64; e += TC_THREADS) {
-                        const int mc = e / 64, r = e % 64, m = m0 + mc;
-                        __half h = __float2half(0.0f), l = h;
-                        if (m <= mhi) {
-                            const size_t src = (((size_t)j * A.M + m) * 7 + t3 + 3) * 64 + r;
-                            h = T.Fh[src];
-                            l = T.Fl[src];
-                        }
-                        B3H[mc * 128 + r] = h;
-                        B3L[mc * 128 + r] = l;
+                    // stage III B: K group 0 = F^{t3}[c3][i3] (8 uint4 per term)
+                    for (int e = tid; e < 2 * TC_MC * 8; e += TC_THREADS) {
+                        const int hl = e / (TC_MC * 8), mc = (e / 8) % TC_MC, v = e % 8;
+                        const uint4* src = (const uint4*)(hl ? FSL : FSH) + (mc * 7 + t3 + 3) * 8 + v;
+                        ((uint4*)(hl ? B3L : B3H))[mc * 16 + v] = *src;
                     }
-                    for (int e = tid; e < (2 * 24576) / 16; e += TC_THREADS)
-                        ((uint4*)(sm + SM_A2H))[e] = make_uint4(0, 0, 0, 0);
-                    __syncthreads();
-                    for (int q2 = 0; q2 < 6; ++q2) {
+                    int line_no = 0;
+                    for (int q2 = 0; q2 < 6 && !aborted; ++q2) {
                         const int line = q2 * 6 + q3;
                         unsigned lm = 0;
                         for (int mc = 0; mc < TC_MC; ++mc) lm |= msk[line * TC_MC + mc];
                         if (!lm) continue;  // uniform
-                        // stage I A: the line's input blocks; per-slot scale ratio g
+                        const int t2 = band_t(a2, q2);
+                        const int par = line_no & 1;
+                        __half* B2H = (__half*)(sm + SM_B2 + par * (2 * TC_MC * 256));
+                        __half* B2L = B2H + TC_MC * 128;
+                        // stage I A (the line's input blocks) and the per-slot scale ratios
                         if (tid < 6) {
                             float g = 0.0f;
                             if (lm & (1u << tid)) {
@@ -311,30 +319,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_apply_tc(TcArgs T) {
                             s_g[tid] = g;
                         }
                         for (int e = tid; e < 6 * 64 * 2; e += TC_THREADS) {
-                            const int half = e / 384, q1 = (e / 64) % 6, v = e % 64;  // 64 uint4 per 1 KB
+                            const int hl = e / 384, q1 = (e / 64) % 6, v = e % 64;  // 64 uint4 per 1 KB
                             uint4 val = make_uint4(0, 0, 0, 0);
                             if (lm & (1u << q1)) {
                                 const int in = tin[q1 * 36 + line];
                                 const int b = in >= 0 ? in : A.n + (-1 - in);
-                                const uint4* src = (const uint4*)((half ? T.xl : T.xh) + (size_t)b * 512);
-                                val = src[v];
+                                val = ((const uint4*)((hl ? T.xl : T.xh) + (size_t)b * 512))[v];
                             }
-                            ((uint4*)(sm + (half ? SM_XL : SM_XH)))[q1 * 64 + v] = val;
+                            ((uint4*)(sm + (hl ? SM_XL : SM_XH)))[q1 * 64 + v] = val;
+                        }
+                        // stage II B for this line: K group 0 = F^{t2}[c2][i2]
+                        for (int e = tid; e < 2 * TC_MC * 8; e += TC_THREADS) {
+                            const int hl = e / (TC_MC * 8), mc = (e / 8) % TC_MC, v = e % 8;
+                            const uint4* src = (const uint4*)(hl ? FSL : FSH) + (mc * 7 + t2 + 3) * 8 + v;
+                            ((uint4*)(hl ? B2L : B2H))[mc * 16 + v] = *src;
                         }
                         __syncthreads();
-                        // stage I B: core (N group mc, K group q1) = mask ? g * F^{j;m,t1(q1)} : 0
-                        for (int e = tid; e < TC_MC * 6 * 64; e += TC_THREADS) {
-                            const int mc = e / 384, q1 = (e / 64) % 6, r = e % 64;
-                            const int m = m0 + mc;
-                            __half h = __float2half(0.0f), l = h;
+                        // stage I B: core (N group mc, K group q1) = mask ? g * F^{t1(q1)} : 0,
+                        // one 16-byte core row per step (power-of-two g: exact in FP16)
+                        for (int e = tid; e < 2 * TC_MC * 6 * 8; e += TC_THREADS) {
+                            const int hl = e / (TC_MC * 48), mc = (e / 48) % TC_MC, q1 = (e / 8) % 6, v = e % 8;
+                            uint4 out = make_uint4(0, 0, 0, 0);
                             if ((msk[line * TC_MC + mc] >> q1) & 1u) {
-                                const size_t src = (((size_t)j * A.M + m) * 7 + band_t(a1, q1) + 3) * 64 + r;
-                                const float g = s_g[q1];
-                                h = __float2half_rn(__half2float(T.Fh[src]) * g);
-                                l = __float2half_rn(__half2float(T.Fl[src]) * g);
+                                const uint4 in = ((const uint4*)(hl ? FSL : FSH))[(mc * 7 + band_t(a1, q1) + 3) * 8 + v];
+                                const __half2 g2 = __float2half2_rn(s_g[q1]);
+                                const __half2* pi = (const __half2*)&in;
+                                __half2* po = (__half2*)&out;
+#pragma unroll
+                                for (int h = 0; h < 4; ++h) po[h] = __hmul2(pi[h], g2);
                             }
-                            B1H[mc * 384 + q1 * 64 + r] = h;
-                            B1L[mc * 384 + q1 * 64 + r] = l;
+                            ((uint4*)(hl ? B1L : B1H))[mc * 48 + q1 * 8 + v] = out;
                         }
                         tc::fence_async_smem();
                         __syncthreads();
@@ -353,16 +367,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_apply_tc(TcArgs T) {
                             tc::commit(&s_mbar);
                             for (int mc = 0; mc < TC_MC; ++mc) s_items += __popc(msk[line * TC_MC + mc]);
                         }
-                        const bool ok = tc::mbar_wait(&s_mbar, phase, TC_WAIT_LIMIT);
-                        phase ^= 1u;
-                        if (__syncthreads_or(!ok)) {
-                            if (tid == 0) { s_abort = 1; atomicExch(T.err, 4); }
-                            break;
-                        }
+                        // also covers the previous line's stage II: A2 is free afterwards
+                        TC_WAIT_OR_ABORT();
+                        if (aborted) break;
                         tc::fence_after();
-                        // D_I -> stage II A, K group q2: row (c1, i3), column i2
+                        // D_I -> stage II A: row (c1, i3), K column i2
 #pragma unroll
-                        for (int mc = 0; mc < TC_MC; ++mc) {
+                        for (int mc = mc_lo; mc < mc_hi; ++mc) {
                             float v[8];
                             tc::tmem_ld8(tD1 + lane_off + mc * 8, v);
                             if (has_row) {
@@ -372,47 +383,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_apply_tc(TcArgs T) {
                                 for (int c1 = 0; c1 < 8; ++c1) {
                                     __half h, l;
                                     tc::split_h(v[c1] * c2, h, l);
-                                    const int o = mc * 3072 + c1 * 384 + q2 * 64 + i3 * 8 + i2;
+                                    const int o = mc * 1024 + c1 * 128 + i3 * 8 + i2;
                                     A2H[o] = h;
                                     A2L[o] = l;
                                 }
                             }
                         }
                         tc::fence_before();
+                        tc::fence_async_smem();
                         __syncthreads();
-                    }
-                    if (s_abort) break;
-                    // stage II: per term, M=64 (c1,i3) x N=8 (c2) x K=48 (t2,i2)
-                    tc::fence_async_smem();
-                    __syncthreads();
-                    if (tid == 0) {
-                        tc::fence_after();
-                        for (int mc = 0; mc < TC_MC; ++mc) {
-#pragma unroll
-                            for (int ks = 0; ks < 3; ++ks) {
-                                const uint64_t ah = tc::sdesc(sbase + SM_A2H + mc * 6144 + ks * 256, 128, 768);
-                                const uint64_t al = tc::sdesc(sbase + SM_A2L + mc * 6144 + ks * 256, 128, 768);
-                                const uint64_t bh = tc::sdesc(sbase + SM_B2H + mc * 768 + ks * 256, 128, 768);
-                                const uint64_t bl = tc::sdesc(sbase + SM_B2L + mc * 768 + ks * 256, 128, 768);
-                                tc::mma_f16(tD2 + mc * 8, ah, bh, idII, ks > 0);
-                                tc::mma_f16(tD2 + mc * 8, ah, bl, idII, 1);
-                                tc::mma_f16(tD2 + mc * 8, al, bh, idII, 1);
+                        // stage II: per term, V += A2 (M=64 (c1,i3) x K=16) x B2 (N=8 c2)
+                        if (tid == 0) {
+                            tc::fence_after();
+                            const uint32_t b2 = sbase + SM_B2 + par * (2 * TC_MC * 256);
+                            for (int mc = 0; mc < TC_MC; ++mc) {
+                                const uint64_t ah = tc::sdesc(sbase + SM_A2H + mc * 2048, 128, 256);
+                                const uint64_t al = tc::sdesc(sbase + SM_A2L + mc * 2048, 128, 256);
+                                const uint64_t bh = tc::sdesc(b2 + mc * 256, 128, 256);
+                                const uint64_t bl = tc::sdesc(b2 + TC_MC * 256 + mc * 256, 128, 256);
+                                tc::mma_f16(tD2 + mc * 8, ah, bh, idS, line_no > 0);
+                                tc::mma_f16(tD2 + mc * 8, ah, bl, idS, 1);
+                                tc::mma_f16(tD2 + mc * 8, al, bh, idS, 1);
                             }
                         }
-                        tc::commit(&s_mbar);
+                        ++line_no;
                     }
-                    {
-                        const bool ok = tc::mbar_wait(&s_mbar, phase, TC_WAIT_LIMIT);
-                        phase ^= 1u;
-                        if (__syncthreads_or(!ok)) {
-                            if (tid == 0) { s_abort = 1; atomicExch(T.err, 4); }
-                            break;
-                        }
-                    }
+                    if (aborted) break;
+                    // wait for the plane's last stage II, then D_II -> stage III A (aliases stage II A)
+                    if (tid == 0) tc::commit(&s_mbar);
+                    TC_WAIT_OR_ABORT();
+                    if (aborted) break;
                     tc::fence_after();
-                    // D_II -> stage III A: row (c1, c2), column i3 (K group 0)
 #pragma unroll
-                    for (int mc = 0; mc < TC_MC; ++mc) {
+                    for (int mc = mc_lo; mc < mc_hi; ++mc) {
                         float v[8];
                         tc::tmem_ld8(tD2 + lane_off + mc * 8, v);
                         if (has_row) {
@@ -423,44 +426,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_apply_tc(TcArgs T) {
                                 __half h, l;
                                 tc::split_h(v[c2] * c3, h, l);
                                 const int o = mc * 1024 + c1 * 128 + c2 * 8 + i3;
-                                A3H[o] = h;
-                                A3L[o] = l;
+                                A2H[o] = h;
+                                A2L[o] = l;
                             }
                         }
                     }
                     tc::fence_before();
                     tc::fence_async_smem();
                     __syncthreads();
-                    // stage III: per term, M=64 (c1,c2) x N=8 (c3) x K=16 (i3 + zero padding)
+                    // stage III: per term, Y += A3 (M=64 (c1,c2) x K=16) x B3 (N=8 c3)
                     if (tid == 0) {
                         tc::fence_after();
                         for (int mc = 0; mc < TC_MC; ++mc) {
-                            const uint64_t ah = tc::sdesc(sbase + SM_A3H + mc * 2048, 128, 256);
-                            const uint64_t al = tc::sdesc(sbase + SM_A3L + mc * 2048, 128, 256);
+                            const uint64_t ah = tc::sdesc(sbase + SM_A2H + mc * 2048, 128, 256);
+                            const uint64_t al = tc::sdesc(sbase + SM_A2L + mc * 2048, 128, 256);
                             const uint64_t bh = tc::sdesc(sbase + SM_B3H + mc * 256, 128, 256);
                             const uint64_t bl = tc::sdesc(sbase + SM_B3L + mc * 256, 128, 256);
-                            tc::mma_f16(tD3 + mc * 8, ah, bh, idIII, plane_started);
-                            tc::mma_f16(tD3 + mc * 8, ah, bl, idIII, 1);
-                            tc::mma_f16(tD3 + mc * 8, al, bh, idIII, 1);
+                            tc::mma_f16(tD3 + mc * 8, ah, bh, idS, plane_started);
+                            tc::mma_f16(tD3 + mc * 8, ah, bl, idS, 1);
+                            tc::mma_f16(tD3 + mc * 8, al, bh, idS, 1);
                         }
                         tc::commit(&s_mbar);
                     }
-                    {
-                        const bool ok = tc::mbar_wait(&s_mbar, phase, TC_WAIT_LIMIT);
-                        phase ^= 1u;
-                        if (__syncthreads_or(!ok)) {
-                            if (tid == 0) { s_abort = 1; atomicExch(T.err, 4); }
-                            break;
-                        }
-                    }
+                    // B3 and the aliased A2/A3 are rewritten by the next plane
+                    TC_WAIT_OR_ABORT();
+                    if (aborted) break;
                     tc::fence_after();
                     plane_started = 1;
                 }
-                if (s_abort) break;
+                if (aborted) break;
                 if (plane_started) {
                     // ghat += w_m Y_m (FP64): row (c1, c2), column c3
 #pragma unroll
-                    for (int mc = 0; mc < TC_MC; ++mc) {
+                    for (int mc = mc_lo; mc < mc_hi; ++mc) {
                         float v[8];
                         tc::tmem_ld8(tD3 + lane_off + mc * 8, v);
                         const double fin = s_fin[mc];
@@ -472,18 +470,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_apply_tc(TcArgs T) {
                 __syncthreads();
             }
         }
-        if (has_row)
+        double* ysm = (double*)(sm + SM_Y);
+        if (has_row && whalf == 1)
 #pragma unroll
-            for (int c3 = 0; c3 < 8; ++c3) A.out[(size_t)node * 512 + row * 8 + c3] = y[c3];
+            for (int c3 = 0; c3 < 8; ++c3) ysm[row * 8 + c3] = y[c3];
+        __syncthreads();
+        if (has_row && whalf == 0)
+#pragma unroll
+            for (int c3 = 0; c3 < 8; ++c3) A.out[(size_t)node * 512 + row * 8 + c3] = y[c3] + ysm[row * 8 + c3];
         if (tid == 0 && A.n_items) atomicAdd(A.n_items, s_items);
         __syncthreads();
     }
+#undef TC_WAIT_OR_ABORT
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tbase, 128);
+    if (warp == 0) tc::tmem_dealloc(tbase, TC_TMEM_COLS);
 }
 
-int launch_apply_tc(const ApplyArgs& A, int nghost, int nlev, const mra_op* op, cudaStream_t st) {
+int launch_apply_tc(const ApplyArgs& A, int nghost, int nlev, const mra_op* op, int* err, cudaStream_t st) {
     (void)nlev;
     if (A.k != 8) {
         set_error("the tensor-core apply supports k = 8 (got k = %d)", A.k);
@@ -494,7 +498,6 @@ int launch_apply_tc(const ApplyArgs& A, int nghost, int nlev, const mra_op* op, 
     const size_t JM = (size_t)(op->J + 1) * op->M;
     __half *xh, *xl, *Fh, *Fl;
     float *sx, *xmax, *sF, *maxF;
-    int* err;
     MRA_TRY(dalloc(Al, &xh, (size_t)nb * 512));
     MRA_TRY(dalloc(Al, &xl, (size_t)nb * 512));
     MRA_TRY(dalloc(Al, &sx, nb));
@@ -503,25 +506,18 @@ int launch_apply_tc(const ApplyArgs& A, int nghost, int nlev, const mra_op* op, 
     MRA_TRY(dalloc(Al, &Fl, JM * 7 * 64));
     MRA_TRY(dalloc(Al, &sF, JM));
     MRA_TRY(dalloc(Al, &maxF, JM));
-    MRA_TRY(dalloc(Al, &err, 1));
-    MRA_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
     k_tc_prep_blocks<<<nb, 128, 0, st>>>(A.n, nghost, A.s, A.gblk, xh, xl, sx, xmax);
     MRA_CK_LAUNCH();
     k_tc_prep_F<<<dim3(op->M, op->J + 1), 128, 0, st>>>(op->M, op->F, Fh, Fl, sF, maxF);
     MRA_CK_LAUNCH();
+    // err: the apply's error word; a wait that reaches its limit writes 4 there
     TcArgs T{A, xh, xl, sx, xmax, Fh, Fl, sF, maxF, err};
     MRA_CK(cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL));
-    const int grid = std::min(A.n, 152 * 2);
+    const int grid = std::min(A.n, 152 * 2);  // 2 CTAs per SM: 2 x 91 KB shared, 2 x 256 TMEM columns
     k_apply_tc<<<grid, TC_THREADS, SM_TOTAL, st>>>(T);
     MRA_CK_LAUNCH();
-    int herr = 0;
-    MRA_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    MRA_CK(cudaStreamSynchronize(st));
-    Al.put(xh); Al.put(xl); Al.put(sx); Al.put(xmax); Al.put(Fh); Al.put(Fl); Al.put(sF); Al.put(maxF); Al.put(err);
-    if (herr) {
-        set_error("tensor-core apply: an MMA completion wait reached its limit");
-        return MRA_ETIMEOUT;
-    }
+    // stream-ordered frees: released after the kernel completes
+    Al.put(xh); Al.put(xl); Al.put(sx); Al.put(xmax); Al.put(Fh); Al.put(Fl); Al.put(sF); Al.put(maxF);
     return MRA_OK;
 }
 
