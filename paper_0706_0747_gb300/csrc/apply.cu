@@ -77,6 +77,60 @@ __global__ void k_pilot(int k, int M, const double* w, const double* F, const do
     }
 }
 
+// The same pilot in two steps: block m writes w_m (F x F x F) s0 (F = F^{0;m,0})
+// to ym[m], then one block sums the terms in a fixed order (deterministic) and
+// takes the norm.
+__global__ void k_pilot_terms(int k, int M, const double* w, const double* F, const double* s0, double* ym) {
+    extern __shared__ double sm[];
+    const int k3 = k * k * k, kk = k * k, m = blockIdx.x;
+    double* x = sm;
+    double* z1 = x + k3;
+    double* z2 = z1 + k3;
+    double* Fm = z2 + k3;
+    const double* Fs = F + ((size_t)m * 7 + 3) * kk;  // j = 0, l = 0
+    for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = s0[e];
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) Fm[e] = Fs[e];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < k3; idx += blockDim.x) {  // dir 3
+        int c = idx % k, base = idx - c;
+        double a = 0.0;
+        for (int i = 0; i < k; ++i) a += Fm[c * k + i] * x[base + i];
+        z1[idx] = a;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < k3; idx += blockDim.x) {  // dir 2
+        int c3 = idx % k, c2 = (idx / k) % k, i1 = idx / kk;
+        double a = 0.0;
+        for (int i = 0; i < k; ++i) a += Fm[c2 * k + i] * z1[(i1 * k + i) * k + c3];
+        z2[idx] = a;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < k3; idx += blockDim.x) {  // dir 1
+        int r = idx % kk, c1 = idx / kk;
+        double a = 0.0;
+        for (int i = 0; i < k; ++i) a += Fm[c1 * k + i] * z2[i * kk + r];
+        ym[(size_t)m * k3 + idx] = w[m] * a;
+    }
+}
+
+__global__ void k_pilot_reduce(int k3, int M, const double* ym, double* sigma) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < k3; e += blockDim.x) {
+        double y = 0.0;
+        for (int m = 0; m < M; ++m) y += ym[(size_t)m * k3 + e];
+        acc += y * y;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+        *sigma = sqrt(s);
+    }
+}
+
 // ------------------------------------------------------------------ schedule
 // sched layout (int32): Jm[M] | m1[nlev*4] | m2[nlev*4] | cnt[nlev*4*2]
 __global__ void k_schedule(int M, int nlev, int unscreened, double eps, const double* w, const double* nF,
@@ -496,9 +550,13 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     MRA_CK(cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), st));
     MRA_CK(cudaMemsetAsync(total, 0, 2 * sizeof(int32_t), st));
     MRA_TRY(leaf_norm2(f, dv, st));
-    const size_t pilot_smem = (4 * (size_t)k3 + k * k) * sizeof(double);
-    k_pilot<<<1, 128, pilot_smem, st>>>(k, M, op->w, op->F, f->s, dv + 1);
+    double* ym;
+    MRA_TRY(dalloc(A, &ym, (size_t)M * k3));
+    k_pilot_terms<<<M, 128, (3 * (size_t)k3 + k * k) * sizeof(double), st>>>(k, M, op->w, op->F, f->s, ym);
     MRA_CK_LAUNCH();
+    k_pilot_reduce<<<1, 256, 0, st>>>(k3, M, ym, dv + 1);
+    MRA_CK_LAUNCH();
+    A.put(ym);
     const int unscreened = o ? o->unscreened : 0;
     k_schedule<<<1, 256, 0, st>>>(M, nlev, unscreened, op->eps, op->w, op->nF, op->est, dv, dv + 1, sched, dv + 2);
     MRA_CK_LAUNCH();

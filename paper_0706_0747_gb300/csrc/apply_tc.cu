@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
     __shared__ unsigned int s_xmax_bits;
     __shared__ unsigned long long s_items;
     __shared__ float s_c2[TC_MC], s_c3[TC_MC], s_g[6];
+    __shared__ unsigned char s_lm[36], s_pm[6];
     __shared__ double s_fin[TC_MC];
 
     const ApplyArgs& A = T.A;
@@ -188,14 +189,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
 
     // the abort decision comes from __syncthreads_or, so it is uniform
     bool aborted = false;
-#define TC_WAIT_OR_ABORT()                                              \
-    {                                                                   \
-        const bool ok_ = tc::mbar_wait(&s_mbar, phase, TC_WAIT_LIMIT);  \
-        phase ^= 1u;                                                    \
-        if (__syncthreads_or(!ok_)) {                                   \
-            aborted = true;                                             \
-            if (tid == 0) atomicExch(T.err, 4);                         \
-        }                                                               \
+    // warp 0 polls the mbarrier; the block barrier then releases the others
+#define TC_WAIT_OR_ABORT()                                                          \
+    {                                                                               \
+        bool ok_ = true;                                                            \
+        if (warp == 0) ok_ = tc::mbar_wait(&s_mbar, phase, TC_WAIT_LIMIT);          \
+        phase ^= 1u;                                                                \
+        if (__syncthreads_or(!ok_)) {                                               \
+            aborted = true;                                                         \
+            if (tid == 0) atomicExch(T.err, 4);                                     \
+        }                                                                           \
     }
 
     for (int node = blockIdx.x; node < A.n && !aborted; node += gridDim.x) {
@@ -285,12 +288,22 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     s_fin[tid] = fin;
                 }
                 __syncthreads();
+                // per line: the union of its terms' kept-t1 masks; per plane: any line
+                if (tid < 36) {
+                    unsigned v = 0;
+                    for (int mc = 0; mc < TC_MC; ++mc) v |= msk[tid * TC_MC + mc];
+                    s_lm[tid] = (unsigned char)v;
+                }
+                __syncthreads();
+                if (tid < 6) {
+                    unsigned v = 0;
+                    for (int q2 = 0; q2 < 6; ++q2) v |= s_lm[q2 * 6 + tid];
+                    s_pm[tid] = (unsigned char)v;
+                }
+                __syncthreads();
                 int plane_started = 0;
                 for (int q3 = 0; q3 < 6 && !aborted; ++q3) {
-                    unsigned plane_mask = 0;
-                    for (int e = q3 * TC_MC; e < 36 * TC_MC; e += 6 * TC_MC)
-                        for (int mc = 0; mc < TC_MC; ++mc) plane_mask |= msk[e + mc];
-                    if (!plane_mask) continue;  // uniform
+                    if (!s_pm[q3]) continue;  // uniform
                     const int t3 = band_t(a3, q3);
                     // stage III B: K group 0 = F^{t3}[c3][i3] (8 uint4 per term)
                     for (int e = tid; e < 2 * TC_MC * 8; e += TC_THREADS) {
@@ -301,8 +314,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     int line_no = 0;
                     for (int q2 = 0; q2 < 6 && !aborted; ++q2) {
                         const int line = q2 * 6 + q3;
-                        unsigned lm = 0;
-                        for (int mc = 0; mc < TC_MC; ++mc) lm |= msk[line * TC_MC + mc];
+                        const unsigned lm = s_lm[line];
                         if (!lm) continue;  // uniform
                         const int t2 = band_t(a2, q2);
                         const int par = line_no & 1;

@@ -206,7 +206,15 @@ int tree_clone_skeleton(const mra_tree* src, mra_tree** out) {
     t->state = src->state;
     t->depth_hit = src->depth_hit;
     memcpy(t->off, src->off, sizeof(t->off));
-    int rc = tree_alloc_arrays(t, src->n, true);
+    // the filters depend on k only: copy them instead of recomputing
+    int rc = dalloc(t->A, &t->filt, 6 * t->k * t->k);
+    if (rc == MRA_OK &&
+        cudaMemcpyAsync(t->filt, src->filt, 6 * t->k * t->k * sizeof(double), cudaMemcpyDeviceToDevice,
+                        t->A.stream) != cudaSuccess) {
+        set_error("filter copy failed");
+        rc = MRA_ECUDA;
+    }
+    if (rc == MRA_OK) rc = tree_alloc_arrays(t, src->n, true);
     if (rc != MRA_OK) { tree_free_arrays(t); t->A.put(t->filt); delete t; return rc; }
     cudaStream_t st = t->A.stream;
     const int n = src->n;
@@ -520,6 +528,120 @@ __global__ void k_expand_level(int k, int lo, int hi, const int32_t* child, doub
     }
 }
 
+// One stage of a separable transform in shared memory: `in` has extents
+// (n[0], n[1], n[2]) with n[dim] = nin; `out` has the same extents except
+// nout along dim; out = Mat (nout x nin, row-major) applied along dim.
+__device__ void stage_mul(const double* in, double* out, const int* n, int dim, const double* Mat, int nout) {
+    const int nin = n[dim];
+    int e[3] = {n[0], n[1], n[2]};
+    e[dim] = nout;
+    const int total = e[0] * e[1] * e[2];
+    const int sin[3] = {n[1] * n[2], n[2], 1};
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int x[3] = {idx / (e[1] * e[2]), (idx / e[2]) % e[1], idx % e[2]};
+        const int r = x[dim];
+        x[dim] = 0;
+        const double* src = in + x[0] * sin[0] + x[1] * sin[1] + x[2] * sin[2];
+        const int st = sin[dim];
+        double acc = 0.0;
+        for (int c = 0; c < nin; ++c) acc += Mat[r * nin + c] * src[c * st];
+        out[idx] = acc;
+    }
+    __syncthreads();
+}
+
+// U = [H0^T; H1^T] (2k x k): child block p from its parent, U[(p k + a)][i] = H^(p)[i][a];
+// D = U^T (k x 2k): parent block from its two children (the top rows of W).
+__device__ void load_UD(int k, const double* filt, double* U, double* D) {
+    const int kk = k * k;
+    for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) {
+        const int p = e / kk, i = (e / k) % k, a = e % k;  // H^(p)[i][a]
+        const double h = filt[p * kk + i * k + a];
+        U[(p * k + a) * k + i] = h;
+        D[i * 2 * k + p * k + a] = h;
+    }
+    __syncthreads();
+}
+
+// Assembly (eq. g_assemble) with d = 0: children += (U x U x U) s_parent, in
+// three stages (2k^4 + 4k^4 + 8k^4 multiply-adds).  Block per node of level j.
+__global__ void k_up_level(int k, int lo, int hi, const int32_t* child, double* s, const double* filt) {
+    extern __shared__ double sm[];
+    const int i = lo + blockIdx.x;
+    if (i >= hi || child[i] < 0) return;
+    const int k2 = 2 * k, k3 = k * k * k, c0 = child[i];
+    double* U = sm;
+    double* D = U + 2 * k * k;
+    double* x = D + 2 * k * k;     // k^3
+    double* t1 = x + k3;           // 2k^3
+    double* t2 = t1 + 2 * k3;      // 4k^3
+    load_UD(k, filt, U, D);
+    for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = s[(size_t)i * k3 + e];
+    __syncthreads();
+    int n0[3] = {k, k, k};
+    stage_mul(x, t1, n0, 0, U, k2);
+    int n1[3] = {k2, k, k};
+    stage_mul(t1, t2, n1, 1, U, k2);
+    // last stage on the fly, added into the children (octant (p1 p2 p3))
+    for (int idx = threadIdx.x; idx < 8 * k3; idx += blockDim.x) {
+        const int x1 = idx / (k2 * k2), x2 = (idx / k2) % k2, x3 = idx % k2;
+        const double* src = t2 + (x1 * k2 + x2) * k;
+        double acc = 0.0;
+        for (int c = 0; c < k; ++c) acc += U[x3 * k + c] * src[c];
+        const int o = ((x1 / k) << 2) | ((x2 / k) << 1) | (x3 / k);
+        s[(size_t)(c0 + o) * k3 + ((x1 % k) * k + (x2 % k)) * k + (x3 % k)] += acc;
+    }
+}
+
+// Redundant tree without stored wavelet cubes: s_parent = (D x D x D) cube of
+// the children (eq. decomp_scaling, 8k^4 + 4k^4 + 2k^4), and the wavelet norm
+// as ||cube - (U x U x U) s_parent||, which equals ||d|| because the filter
+// matrix is orthogonal (cube = W^T [s; d]).  Block per node of level j.
+__global__ void k_compress_fast_level(int k, int lo, int hi, const int32_t* child, double* s, double* dnorm,
+                                      const double* filt) {
+    extern __shared__ double sm[];
+    __shared__ double red[32];
+    const int i = lo + blockIdx.x;
+    if (i >= hi || child[i] < 0) return;
+    const int k2 = 2 * k, k3 = k * k * k, c0 = child[i];
+    double* U = sm;
+    double* D = U + 2 * k * k;
+    double* cube = D + 2 * k * k;  // 8k^3
+    double* r1 = cube + 8 * k3;    // 4k^3  (k, 2k, 2k), later (2k, 2k, k)
+    double* r2 = r1 + 4 * k3;      // 2k^3  (k, k, 2k),  later (2k, k, k)
+    double* sp = r2 + 2 * k3;      // k^3
+    load_UD(k, filt, U, D);
+    for (int e = threadIdx.x; e < 8 * k3; e += blockDim.x) {
+        const int o = e / k3, r = e % k3;
+        const int i1 = r / (k * k), i2 = (r / k) % k, i3 = r % k;
+        const int x1 = ((o >> 2) & 1) * k + i1, x2 = ((o >> 1) & 1) * k + i2, x3 = (o & 1) * k + i3;
+        cube[(x1 * k2 + x2) * k2 + x3] = s[(size_t)(c0 + o) * k3 + r];
+    }
+    __syncthreads();
+    int n0[3] = {k2, k2, k2};
+    stage_mul(cube, r1, n0, 0, D, k);
+    int n1[3] = {k, k2, k2};
+    stage_mul(r1, r2, n1, 1, D, k);
+    int n2[3] = {k, k, k2};
+    stage_mul(r2, sp, n2, 2, D, k);
+    for (int e = threadIdx.x; e < k3; e += blockDim.x) s[(size_t)i * k3 + e] = sp[e];
+    int m0[3] = {k, k, k};
+    stage_mul(sp, r2, m0, 0, U, k2);
+    int m1[3] = {k2, k, k};
+    stage_mul(r2, r1, m1, 1, U, k2);
+    double acc = 0.0;
+    for (int idx = threadIdx.x; idx < 8 * k3; idx += blockDim.x) {
+        const int x1 = idx / (k2 * k2), x2 = (idx / k2) % k2, x3 = idx % k2;
+        const double* src = r1 + (x1 * k2 + x2) * k;
+        double up = 0.0;
+        for (int c = 0; c < k; ++c) up += U[x3 * k + c] * src[c];
+        const double dv = cube[idx] - up;
+        acc += dv * dv;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) dnorm[i] = sqrt(acc);
+}
+
 static int cube_smem(int k, size_t* bytes, const void* fn) {
     *bytes = (size_t)8 * k * k * k * sizeof(double);
     MRA_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes));
@@ -527,6 +649,20 @@ static int cube_smem(int k, size_t* bytes, const void* fn) {
 }
 
 int compress_impl(mra_tree* t, int store_d, cudaStream_t st) {
+    if (!store_d) {
+        const int k = t->k;
+        const size_t smem = (4 * (size_t)k * k + 15 * (size_t)k * k * k) * sizeof(double);
+        MRA_CK(cudaFuncSetAttribute(k_compress_fast_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MRA_CK(cudaMemsetAsync(t->dnorm, 0, t->n * sizeof(double), st));
+        for (int j = t->nlev - 2; j >= 0; --j) {
+            int lo = t->off[j], hi = t->off[j + 1];
+            if (hi <= lo) continue;
+            k_compress_fast_level<<<hi - lo, 256, smem, st>>>(k, lo, hi, t->a.child, t->s, t->dnorm, t->filt);
+            MRA_CK_LAUNCH();
+        }
+        t->state = MRA_TREE_REDUNDANT;
+        return MRA_OK;
+    }
     size_t smem;
     MRA_TRY(cube_smem(t->k, &smem, (const void*)k_compress_level));
     if (store_d && !t->dcube) MRA_TRY(dalloc(t->A, &t->dcube, (size_t)t->n * 8 * t->k * t->k * t->k));
@@ -559,11 +695,13 @@ int inverse_impl(mra_tree* t, cudaStream_t st) {
 }
 
 int assemble_impl(mra_tree* t, cudaStream_t st) {
-    size_t smem;
-    MRA_TRY(cube_smem(t->k, &smem, (const void*)k_expand_level));
+    const int k = t->k;
+    const size_t smem = (4 * (size_t)k * k + 7 * (size_t)k * k * k) * sizeof(double);
+    MRA_CK(cudaFuncSetAttribute(k_up_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int j = 0; j + 1 < t->nlev; ++j) {
         int lo = t->off[j], hi = t->off[j + 1];
-        k_expand_level<<<hi - lo, 256, smem, st>>>(t->k, lo, hi, t->a.child, t->s, nullptr, t->filt);
+        if (hi <= lo) continue;
+        k_up_level<<<hi - lo, 256, smem, st>>>(k, lo, hi, t->a.child, t->s, t->filt);
         MRA_CK_LAUNCH();
     }
     t->state = MRA_TREE_LEAVES;

@@ -104,6 +104,22 @@ def test_compress_and_inverse_round_trip():
     assert err <= 1e-13 * nrm * OT.levels(to)
 
 
+@pytest.mark.parametrize("k", [3, 8])
+def test_compress_without_stored_cubes(k):
+    """The default compress (scaling blocks by the H half of the filter, wavelet
+    norms as ||children - up(parent)||) against the oracle's full transform."""
+    to, _ = OT.build_tree(DENS2, k, 1e-5, 4, init_level=1)
+    tg = gpu_tree_from_oracle(to, k)
+    mra.compress(tg)
+    OT.compress(to, k)
+    blocks, leaf, dn = export_dict(tg)
+    scale = max(n.dnorm for n in to.values())
+    for key, n in to.items():
+        assert np.abs(blocks[key] - n.s).max() <= 1e-13 * max(1.0, np.abs(n.s).max())
+        if not n.leaf:
+            assert abs(dn[key] - n.dnorm) <= 1e-12 * n.dnorm + 1e-14 * scale
+
+
 def run_both(tree_o, op_o, op_g, k, precision="fp64", **kw):
     tg = gpu_tree_from_oracle(tree_o, k)
     mra.compress(tg)
