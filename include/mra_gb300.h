@@ -268,6 +268,77 @@ int mra_apply_ns_noalloc(const mra_op* op, const mra_tree* f, int precision, dou
                          void* stream, int64_t* n_items_host);
 
 /* ------------------------------------------------------------------------ */
+/* Batched apply: one operator, many independent inputs.  The paper applies
+ * the operator to one function at a time (Algorithm 3); this group is its
+ * deployment form for many right-hand sides at once, with the same items
+ * per input as mra_apply_ns.
+ *
+ * mra_plan_create screens all trees together (synchronous: one host
+ * synchronisation sizes the joint worklist).  Each tree keeps its own norms,
+ * eta, J_m and term ranges; Step-2 blocks are found per tree.  The trees are
+ * borrowed, not copied: they must stay alive, compressed and unchanged in
+ * structure while the plan exists (their blocks may be rewritten, e.g. with
+ * mra_tree_set_blocks + mra_compress; the plan keeps the screen it made at
+ * creation).  op must outlive the plan.
+ *   - trees: ntrees (>= 1) handles in MRA_TREE_REDUNDANT state, order k of op,
+ *     depth <= op's max_level.
+ *   - opts (may be NULL): precision (default MRA_PREC_TC_SPLIT for k <= 8,
+ *     else MRA_PREC_FP64; the tensor-core path needs k <= 8) and use_graph
+ *     (default 1 when opts is NULL).
+ * mra_plan_execute queues, on `stream`: the gather of every tree's current
+ * blocks, the Step-2 refinement and one Step-3 launch over the nodes of all
+ * trees (a persistent kernel taking nodes from an atomic counter).  With
+ * use_graph the first execute captures these launches into a CUDA graph (on
+ * a stream the plan owns) and every execute launches that graph; `stream`
+ * must not be capturing.  Executes on one plan must not overlap.
+ * mra_plan_autotune (synchronous) times the tensor-core kernel variants on
+ * the plan's worklist, reps launches each: terms per chunk 8 or 4, CTAs per
+ * SM 2 or 1, node order as screened or heaviest first (most pairs).  The
+ * fastest becomes the plan's variant (ms_variant[v], v = (mc==4) +
+ * 2 (ctas==1) + 4 heavy_first); other precisions have one variant.
+ * mra_plan_set_variant chooses one by hand.  Both drop a captured graph.
+ * mra_plan_output copies the output of tree b (as of the last execute
+ * queued before it on `stream`) into a new MRA_TREE_NSFORM tree.
+ * mra_plan_get_info and mra_plan_tree_stats are synchronous; get_info also
+ * reports a device error of past executes (MRA_ETIMEOUT, MRA_ECUDA). */
+typedef struct mra_plan mra_plan;
+
+typedef struct {
+    int precision;          /* MRA_PREC_*                                     */
+    int use_graph;          /* 1: executes replay one captured CUDA graph      */
+    int reserved[6];
+} mra_plan_opts;
+
+typedef struct {
+    int n_trees;
+    int64_t n_nodes;        /* output nodes of all trees                       */
+    int64_t n_pairs;
+    int64_t n_ghosts;       /* Step-2 blocks of all trees                      */
+    int64_t n_items;        /* items applied by the last execute               */
+    int precision;
+    int terms_per_chunk;    /* tensor-core variant in use                      */
+    int ctas_per_sm;
+    int heavy_first;
+    int tuned;              /* 1 after mra_plan_autotune                       */
+    float ms_variant[8];    /* autotune: mean apply-kernel time per variant    */
+    int graph;              /* 1 when a captured graph exists                  */
+    int graph_kernels;      /* kernels in one execute's graph                  */
+    float ms_screen;        /* device time of the screen at creation           */
+} mra_plan_info;
+
+int mra_plan_create(const mra_op* op, mra_tree* const* trees, int ntrees, const mra_plan_opts* opts,
+                    void* stream, mra_plan** out);
+int mra_plan_execute(mra_plan* p, void* stream);
+int mra_plan_autotune(mra_plan* p, int reps, void* stream);
+int mra_plan_set_variant(mra_plan* p, int terms_per_chunk, int ctas_per_sm, int heavy_first);
+int mra_plan_output(const mra_plan* p, int b, void* stream, mra_tree** g_ns);
+int mra_plan_get_info(const mra_plan* p, mra_plan_info* info, void* stream);
+/* Per-tree screen results: fnorm, sigma, eta, n_pairs, n_out_nodes, and the
+ * items of the last execute; n_ghosts is -1 (counted per batch). */
+int mra_plan_tree_stats(const mra_plan* p, int b, void* stream, mra_apply_stats* stats);
+int mra_free_plan(mra_plan* p);
+
+/* ------------------------------------------------------------------------ */
 /* Reconstruct.
  * MRA_RECON_ASSEMBLE: for an MRA_TREE_NSFORM tree, eq. g_assemble top-down
  * (each child adds the d = 0 upsampling of its parent, eqs. recon_even /

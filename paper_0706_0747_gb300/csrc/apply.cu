@@ -77,17 +77,35 @@ __global__ void k_pilot(int k, int M, const double* w, const double* F, const do
     }
 }
 
-// The same pilot in two steps: block m writes w_m (F x F x F) s0 (F = F^{0;m,0})
-// to ym[m], then one block sums the terms in a fixed order (deterministic) and
-// takes the norm.
-__global__ void k_pilot_terms(int k, int M, const double* w, const double* F, const double* s0, double* ym) {
+// ------------------------------------------------------------------ forest
+__device__ inline int forest_tree(const Forest& F, int i) { return F.node_tree ? F.node_tree[i] : 0; }
+
+// ||f_b||^2 = sum over the leaves of tree b of ||s||^2 (Parseval); warp per node
+__global__ void k_forest_norm2(Forest F, double* dv) {
+    const int k3 = F.k * F.k * F.k, lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < F.n; i += nwarps) {
+        if (!F.leaf[i]) continue;
+        const double* s = F.s + (size_t)i * k3;
+        double acc = 0.0;
+        for (int e = lane; e < k3; e += 32) acc += s[e] * s[e];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) atomicAdd(&dv[4 * forest_tree(F, i)], acc);
+    }
+}
+
+// Pilot ||T_0 f_0|| in two steps: block (m, b) writes w_m (F x F x F) s0_b
+// (F = F^{0;m,0}, s0_b the root block of tree b) to ym[b][m]; then one block
+// per tree sums the terms in a fixed order and takes the norm.
+__global__ void k_pilot_terms(Forest F, int M, const double* w, const double* Ftab, double* ym) {
     extern __shared__ double sm[];
-    const int k3 = k * k * k, kk = k * k, m = blockIdx.x;
+    const int k = F.k, k3 = k * k * k, kk = k * k, m = blockIdx.x, b = blockIdx.y;
     double* x = sm;
     double* z1 = x + k3;
     double* z2 = z1 + k3;
     double* Fm = z2 + k3;
-    const double* Fs = F + ((size_t)m * 7 + 3) * kk;  // j = 0, l = 0
+    const double* s0 = F.s + (size_t)F.off[b * (F.lm + 1)] * k3;
+    const double* Fs = Ftab + ((size_t)m * 7 + 3) * kk;  // j = 0, l = 0
     for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = s0[e];
     for (int e = threadIdx.x; e < kk; e += blockDim.x) Fm[e] = Fs[e];
     __syncthreads();
@@ -105,20 +123,23 @@ __global__ void k_pilot_terms(int k, int M, const double* w, const double* F, co
         z2[idx] = a;
     }
     __syncthreads();
+    double* yo = ym + ((size_t)b * M + m) * k3;
     for (int idx = threadIdx.x; idx < k3; idx += blockDim.x) {  // dir 1
         int r = idx % kk, c1 = idx / kk;
         double a = 0.0;
         for (int i = 0; i < k; ++i) a += Fm[c1 * k + i] * z2[i * kk + r];
-        ym[(size_t)m * k3 + idx] = w[m] * a;
+        yo[idx] = w[m] * a;
     }
 }
 
-__global__ void k_pilot_reduce(int k3, int M, const double* ym, double* sigma) {
+__global__ void k_pilot_reduce(int k3, int M, const double* ym, double* dv) {
     __shared__ double red[32];
+    const int b = blockIdx.x;
+    const double* yb = ym + (size_t)b * M * k3;
     double acc = 0.0;
     for (int e = threadIdx.x; e < k3; e += blockDim.x) {
         double y = 0.0;
-        for (int m = 0; m < M; ++m) y += ym[(size_t)m * k3 + e];
+        for (int m = 0; m < M; ++m) y += yb[(size_t)m * k3 + e];
         acc += y * y;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -127,22 +148,26 @@ __global__ void k_pilot_reduce(int k3, int M, const double* ym, double* sigma) {
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-        *sigma = sqrt(s);
+        dv[4 * b + 1] = sqrt(s);
     }
 }
 
 // ------------------------------------------------------------------ schedule
-// sched layout (int32): Jm[M] | m1[nlev*4] | m2[nlev*4] | cnt[nlev*4*2]
-__global__ void k_schedule(int M, int nlev, int unscreened, double eps, const double* w, const double* nF,
-                           const double* est, const double* fnorm2, const double* sigma, int32_t* sched,
-                           double* eta_out) {
-    int32_t* Jm = sched;
+// Block per tree.  dv[4b]: ||f_b||^2, dv[4b+1]: sigma_b; writes eta_b to
+// dv[4b+2] and the tree's schedule at sched + b * sl, laid out (int32)
+//   Jm[M] | m1[lm*4] | m2[lm*4] | cnt[lm*4*2]   (sl = M + 16 lm)
+// Levels at or beyond the tree's own depth get empty ranges.
+__global__ void k_schedule(int M, int lm, const int32_t* nlev_tab, int unscreened, double eps, const double* w,
+                           const double* nF, const double* est, double* dv, int32_t* sched_all, int sl) {
+    const int b = blockIdx.x;
+    const int nlev = nlev_tab ? nlev_tab[b] : lm;
+    int32_t* Jm = sched_all + (size_t)b * sl;
     int32_t* m1 = Jm + M;
-    int32_t* m2 = m1 + nlev * 4;
-    int32_t* cnt = m2 + nlev * 4;
-    const double fn = sqrt(*fnorm2);
-    const double eta = fn > 0.0 ? eps * (*sigma) / fn : 0.0;
-    if (threadIdx.x == 0) *eta_out = eta;
+    int32_t* m2 = m1 + lm * 4;
+    int32_t* cnt = m2 + lm * 4;
+    const double fn = sqrt(dv[4 * b]);
+    const double eta = fn > 0.0 ? eps * dv[4 * b + 1] / fn : 0.0;
+    if (threadIdx.x == 0) dv[4 * b + 2] = eta;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
         int jm = 0;
         if (unscreened) jm = nlev - 1;
@@ -153,7 +178,7 @@ __global__ void k_schedule(int M, int nlev, int unscreened, double eps, const do
     }
     __syncthreads();
     const double budget = eta / (2.0 * 216.0);
-    for (int js = threadIdx.x; js < nlev * 4; js += blockDim.x) {
+    for (int js = threadIdx.x; js < lm * 4; js += blockDim.x) {
         const int j = js / 4, S = js % 4;
         int lo_m = 0, hi_m = -1;
         if (unscreened) {
@@ -172,10 +197,10 @@ __global__ void k_schedule(int M, int nlev, int unscreened, double eps, const do
                 auto e_of = [&](int m) {
                     const double* r = nF + ((size_t)j * M + m) * 7;
                     double c = fmax(fmax(r[2], r[3]), r[4]);
-                    double b = fmax(fmax(r[0], r[1]), fmax(r[5], r[6]));
+                    double bb = fmax(fmax(r[0], r[1]), fmax(r[5], r[6]));
                     double v = w[m];
                     for (int q = 0; q < S; ++q) v *= c;
-                    for (int q = S; q < 3; ++q) v *= b;
+                    for (int q = S; q < 3; ++q) v *= bb;
                     return v;
                 };
                 double acc = 0.0;
@@ -217,9 +242,11 @@ __global__ void k_schedule(int M, int nlev, int unscreened, double eps, const do
 
 // ------------------------------------------------------------------ screen
 #define GH_EMPTY 0xffffffffffffffffull
+#define GH_TREE_BITS 22
 
-__device__ inline uint64_t ghost_key(int j, int b1, int b2, int b3) {
-    return ((uint64_t)j << 58) | morton3(b1, b2, b3);
+// level (6 bits) | tree (22 bits) | Morton key of the box (36 bits, level <= 12)
+__device__ inline uint64_t ghost_key(int j, int tree, int b1, int b2, int b3) {
+    return ((uint64_t)j << 58) | ((uint64_t)tree << 36) | morton3(b1, b2, b3);
 }
 
 __device__ inline uint32_t hash64(uint64_t k) {
@@ -255,12 +282,9 @@ __device__ int ghost_find(const uint64_t* tab, uint32_t cap, uint64_t key) {
 }
 
 struct ScreenArgs {
-    int n, M, nlev;
-    const int32_t* coord;
-    const int32_t* leaf;
-    const uint64_t* key;
-    const int32_t* off;
-    const int32_t* sched;  // Jm | m1 | m2 | cnt
+    Forest F;
+    int M, sl;
+    const int32_t* sched;  // per tree: Jm | m1 | m2 | cnt
     uint64_t* gtab;
     uint32_t gcap;
     const int32_t* gid;    // slot -> ghost id (fill pass)
@@ -276,12 +300,16 @@ __global__ void k_screen(ScreenArgs A) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int32_t* m1 = A.sched + A.M;
-    const int32_t* m2 = m1 + A.nlev * 4;
-    const int32_t* cnt = m2 + A.nlev * 4;
-    for (int i = warp; i < A.n; i += nwarps) {
-        const int j = A.coord[4 * i], a1 = A.coord[4 * i + 1], a2 = A.coord[4 * i + 2], a3 = A.coord[4 * i + 3];
-        const int leaf = A.leaf[i];
+    const int lm = A.F.lm;
+    for (int i = warp; i < A.F.n; i += nwarps) {
+        const int b = forest_tree(A.F, i);
+        const int32_t* m1 = A.sched + (size_t)b * A.sl + A.M;
+        const int32_t* m2 = m1 + lm * 4;
+        const int32_t* cnt = m2 + lm * 4;
+        const int32_t* off = A.F.off + b * (lm + 1);
+        const int j = A.F.coord[4 * i], a1 = A.F.coord[4 * i + 1], a2 = A.F.coord[4 * i + 2],
+                  a3 = A.F.coord[4 * i + 3];
+        const int leaf = A.F.leaf[i];
         const int N = 1 << j;
         int running = 0;
         const int base = FILL ? A.pair_off[i] : 0;
@@ -299,10 +327,10 @@ __global__ void k_screen(ScreenArgs A) {
                     ci = (S == 3 && !leaf) ? 1 : 0;
                     if (cnt[(j * 4 + S) * 2 + ci] > 0) {
                         valid = true;
-                        int idx = find_key_exact(A.key, A.off[j], A.off[j + 1], morton3(b1, b2, b3));
+                        int idx = find_key_exact(A.F.key, off[j], off[j + 1], morton3(b1, b2, b3));
                         if (idx >= 0) in = idx;
                         else {
-                            uint64_t gk = ghost_key(j, b1, b2, b3);
+                            uint64_t gk = ghost_key(j, b, b1, b2, b3);
                             if (!FILL) {
                                 if (ghost_insert(A.gtab, A.gcap, gk) < 0) atomicExch(A.err, 1);
                             } else {
@@ -361,39 +389,39 @@ __device__ inline uint32_t compact1by2(uint64_t x) {
 }
 
 // Step 2: block per ghost; refine the covering ancestor leaf down to level j.
-__global__ void k_ghost_refine(int k, const uint64_t* gkeys, const uint64_t* key, const int32_t* off,
-                               const int32_t* leaf, const double* s, const double* filt, double* gblk,
-                               int32_t* err) {
+__global__ void k_ghost_refine(Forest F, const uint64_t* gkeys, double* gblk, int32_t* err) {
     extern __shared__ double sm[];
-    const int k3 = k * k * k, kk = k * k;
+    const int k = F.k, k3 = k * k * k, kk = k * k;
     double* HT = sm;             // 2 k x k: HT[p][a][i] = H^(p)[i][a]
     double* x = HT + 2 * kk;
     double* y = x + k3;
     double* z = y + k3;
     const uint64_t gk = gkeys[blockIdx.x];
     const int j = (int)(gk >> 58);
-    const uint64_t mk = gk & ((1ull << 58) - 1);
+    const int tree = (int)((gk >> 36) & ((1ull << GH_TREE_BITS) - 1));
+    const uint64_t mk = gk & ((1ull << 36) - 1);
     const int b1 = compact1by2(mk >> 2), b2 = compact1by2(mk >> 1), b3 = compact1by2(mk);
+    const int32_t* off = F.off + tree * (F.lm + 1);
     for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) {
         int p = e / kk, r = e % kk, a = r / k, i = r % k;
-        HT[e] = filt[p * kk + i * k + a];
+        HT[e] = F.filt[p * kk + i * k + a];
     }
     __shared__ int anc, jj;
     if (threadIdx.x == 0) {
         anc = -1;
         for (int lv = j - 1; lv >= 0 && anc < 0; --lv) {
             int sh = j - lv;
-            int idx = find_key_exact(key, off[lv], off[lv + 1], morton3(b1 >> sh, b2 >> sh, b3 >> sh));
+            int idx = find_key_exact(F.key, off[lv], off[lv + 1], morton3(b1 >> sh, b2 >> sh, b3 >> sh));
             if (idx >= 0) {
                 anc = idx;
                 jj = lv;
             }
         }
-        if (anc < 0 || !leaf[anc]) atomicExch(err, 3);
+        if (anc < 0 || !F.leaf[anc]) atomicExch(err, 3);
     }
     __syncthreads();
     if (anc < 0) return;
-    for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = s[(size_t)anc * k3 + e];
+    for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = F.s[(size_t)anc * k3 + e];
     __syncthreads();
     for (int lv = jj; lv < j; ++lv) {
         const int sh = j - lv - 1;
@@ -443,6 +471,7 @@ __global__ void __launch_bounds__(128) k_apply_simt(ApplyArgs A) {
     const int M = A.M;
     for (int i = blockIdx.x; i < A.n; i += gridDim.x) {
         const int j = A.coord[4 * i];
+        const int32_t* Jm = A.Jm + (A.node_tree ? A.node_tree[i] * A.jm_stride : 0);
         for (int e = threadIdx.x; e < k3; e += blockDim.x) y[e] = 0.0;
         if (threadIdx.x == 0) items = 0;
         const int p0 = A.pair_off[i], p1 = A.pair_off[i + 1];
@@ -467,7 +496,7 @@ __global__ void __launch_bounds__(128) k_apply_simt(ApplyArgs A) {
             }
             __syncthreads();
             for (int m = pr.m_lo; m <= pr.m_hi; ++m) {
-                const int jm = A.Jm[m];
+                const int jm = Jm[m];
                 if (jm < j) continue;
                 if ((pr.flags & 1) && jm > j) continue;
                 const size_t fb = ((size_t)j * M + m) * 7;
@@ -512,12 +541,107 @@ __global__ void __launch_bounds__(128) k_apply_simt(ApplyArgs A) {
             __syncthreads();
         }
         for (int e = threadIdx.x; e < k3; e += blockDim.x) A.out[(size_t)i * k3 + e] = y[e];
-        if (threadIdx.x == 0 && A.n_items) atomicAdd(A.n_items, items);
+        if (threadIdx.x == 0 && A.n_items) atomicAdd(A.n_items + (A.node_tree ? A.node_tree[i] : 0), items);
         __syncthreads();
     }
 }
 
 // ------------------------------------------------------------------ driver
+void screen_release(const Alloc& A, ScreenOut* S) {
+    A.put(S->dv); A.put(S->sched); A.put(S->count); A.put(S->pair_off); A.put(S->total); A.put(S->err);
+    A.put(S->gtab); A.put(S->gid); A.put(S->gkeys); A.put(S->pairs);
+    *S = ScreenOut();
+}
+
+// Pilot, schedule and the two-pass warp screen over a forest, with the one
+// host synchronisation that sizes the worklist.  The ghost hash set starts at
+// 64 slots per node; when a probe sequence reaches its limit the count pass
+// is redone with a set four times larger.
+int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc& A, cudaStream_t st, ScreenOut* S) {
+    const int k3 = F.k * F.k * F.k, M = op->M, n = F.n;
+    *S = ScreenOut();
+    S->sl = M + 16 * F.lm;
+    MRA_TRY(dalloc(A, &S->dv, 4 * (size_t)F.ntrees));
+    MRA_TRY(dalloc(A, &S->sched, (size_t)F.ntrees * S->sl));
+    MRA_TRY(dalloc(A, &S->count, (size_t)n + 1));
+    MRA_TRY(dalloc(A, &S->pair_off, (size_t)n + 1));
+    MRA_TRY(dalloc(A, &S->total, 2));
+    MRA_TRY(dalloc(A, &S->err, 2));
+    MRA_CK(cudaMemsetAsync(S->dv, 0, 4 * (size_t)F.ntrees * sizeof(double), st));
+    MRA_CK(cudaMemsetAsync(S->err, 0, 2 * sizeof(int32_t), st));
+    const int nb_norm = (int)std::max<long>(1, std::min<long>(152 * 16, ((long)n * 32 + 255) / 256));
+    k_forest_norm2<<<nb_norm, 256, 0, st>>>(F, S->dv);
+    MRA_CK_LAUNCH();
+    double* ym;
+    MRA_TRY(dalloc(A, &ym, (size_t)F.ntrees * M * k3));
+    k_pilot_terms<<<dim3(M, F.ntrees), 128, (3 * (size_t)k3 + F.k * F.k) * sizeof(double), st>>>(F, M, op->w, op->F, ym);
+    MRA_CK_LAUNCH();
+    k_pilot_reduce<<<F.ntrees, 256, 0, st>>>(k3, M, ym, S->dv);
+    MRA_CK_LAUNCH();
+    A.put(ym);
+    k_schedule<<<F.ntrees, 256, 0, st>>>(M, F.lm, F.nlev, unscreened, op->eps, op->w, op->nF, op->est, S->dv,
+                                         S->sched, S->sl);
+    MRA_CK_LAUNCH();
+
+    ScreenArgs sa;
+    sa.F = F; sa.M = M; sa.sl = S->sl; sa.sched = S->sched;
+    sa.count = S->count; sa.pair_off = S->pair_off; sa.pairs = nullptr; sa.err = S->err;
+    const int sblocks = (int)std::max<long>(1, std::min<long>(152 * 32, ((long)n * 32 + 255) / 256));
+    uint64_t cap = 1024;
+    while (cap < (uint64_t)n * 64ull) cap <<= 1;
+    int32_t h[2] = {0, 0}, herr[2] = {0, 0};
+    for (;;) {
+        if (cap > (1ull << 30)) { set_error("ghost hash set overflow"); return MRA_ECUDA; }
+        S->gcap = (uint32_t)cap;
+        MRA_TRY(dalloc(A, &S->gtab, cap));
+        MRA_TRY(dalloc(A, &S->gid, cap));
+        MRA_TRY(dalloc(A, &S->gkeys, cap));
+        MRA_CK(cudaMemsetAsync(S->total, 0, 2 * sizeof(int32_t), st));
+        k_fill_u64<<<1024, 256, 0, st>>>(S->gtab, cap, GH_EMPTY);
+        MRA_CK_LAUNCH();
+        sa.gtab = S->gtab; sa.gcap = S->gcap; sa.gid = S->gid;
+        k_screen<false><<<sblocks, 256, 0, st>>>(sa);
+        MRA_CK_LAUNCH();
+        MRA_TRY(scan_exclusive(S->count, S->pair_off, n, S->total, st));
+        MRA_CK(cudaMemcpyAsync(S->pair_off + n, S->total, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        k_ghost_ids<<<1024, 256, 0, st>>>(S->gtab, S->gcap, S->gid, S->gkeys, S->total + 1);
+        MRA_CK_LAUNCH();
+        // the one host synchronisation: pair and ghost counts size the worklist
+        MRA_CK(cudaMemcpyAsync(h, S->total, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        MRA_CK(cudaMemcpyAsync(herr, S->err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        MRA_CK(cudaStreamSynchronize(st));
+        if (!herr[0]) break;
+        A.put(S->gtab); A.put(S->gid); A.put(S->gkeys);
+        S->gtab = nullptr; S->gid = nullptr; S->gkeys = nullptr;
+        MRA_CK(cudaMemsetAsync(S->err, 0, 2 * sizeof(int32_t), st));
+        cap <<= 2;
+    }
+    S->npairs = h[0];
+    S->nghost = h[1];
+    MRA_TRY(dalloc(A, &S->pairs, (size_t)S->npairs + 1));
+    sa.pairs = S->pairs;
+    k_screen<true><<<sblocks, 256, 0, st>>>(sa);
+    MRA_CK_LAUNCH();
+    return MRA_OK;
+}
+
+int ghost_refine_forest(const Forest& F, const ScreenOut& S, double* gblk, cudaStream_t st) {
+    if (S.nghost <= 0) return MRA_OK;
+    const int k = F.k, k3 = k * k * k;
+    const size_t gsm = (2 * (size_t)k * k + 3 * (size_t)k3) * sizeof(double);
+    k_ghost_refine<<<S.nghost, 128, gsm, st>>>(F, S.gkeys, gblk, S.err + 1);
+    MRA_CK_LAUNCH();
+    return MRA_OK;
+}
+
+Forest forest_of_tree(const mra_tree* f) {
+    Forest F;
+    F.k = f->k; F.ntrees = 1; F.n = f->n; F.lm = f->nlev;
+    F.coord = f->a.coord; F.leaf = f->a.leaf; F.key = f->a.key; F.off = f->a.off;
+    F.node_tree = nullptr; F.nlev = nullptr; F.s = f->s; F.filt = f->filt;
+    return F;
+}
+
 int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cudaStream_t st, mra_tree** gout,
                mra_apply_stats* stats) {
     const int k = op->k, k3 = k * k * k, M = op->M, n = f->n, nlev = f->nlev;
@@ -529,8 +653,8 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         set_error("precision %d is not available", prec);
         return MRA_EINVAL;
     }
-    if (prec == MRA_PREC_TC_SPLIT && ((o && (o->block_screen || o->itemwise)) || k != 8)) {
-        set_error("the tensor-core apply needs k = 8 and the static screen");
+    if (prec == MRA_PREC_TC_SPLIT && ((o && (o->block_screen || o->itemwise)) || k > 8)) {
+        set_error("the tensor-core apply needs k <= 8 and the static screen");
         return MRA_EINVAL;
     }
     const Alloc& A = f->A;
@@ -538,74 +662,15 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     for (int e = 0; e < 4; ++e) MRA_CK(cudaEventCreate(&ev[e]));
     MRA_CK(cudaEventRecord(ev[0], st));
 
-    double* dv;  // [0] ||f||^2 [1] sigma [2] eta
-    int32_t *sched, *count, *pair_off, *total, *err;
-    MRA_TRY(dalloc(A, &dv, 4));
-    MRA_TRY(dalloc(A, &sched, M + nlev * 16));
-    MRA_TRY(dalloc(A, &count, n + 1));
-    MRA_TRY(dalloc(A, &pair_off, n + 1));
-    MRA_TRY(dalloc(A, &total, 2));
-    MRA_TRY(dalloc(A, &err, 2));
-    MRA_CK(cudaMemsetAsync(dv, 0, 4 * sizeof(double), st));
-    MRA_CK(cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), st));
-    MRA_CK(cudaMemsetAsync(total, 0, 2 * sizeof(int32_t), st));
-    MRA_TRY(leaf_norm2(f, dv, st));
-    double* ym;
-    MRA_TRY(dalloc(A, &ym, (size_t)M * k3));
-    k_pilot_terms<<<M, 128, (3 * (size_t)k3 + k * k) * sizeof(double), st>>>(k, M, op->w, op->F, f->s, ym);
-    MRA_CK_LAUNCH();
-    k_pilot_reduce<<<1, 256, 0, st>>>(k3, M, ym, dv + 1);
-    MRA_CK_LAUNCH();
-    A.put(ym);
+    const Forest F = forest_of_tree(f);
+    ScreenOut S;
     const int unscreened = o ? o->unscreened : 0;
-    k_schedule<<<1, 256, 0, st>>>(M, nlev, unscreened, op->eps, op->w, op->nF, op->est, dv, dv + 1, sched, dv + 2);
-    MRA_CK_LAUNCH();
-
-    // ghost hash set sized for the worst case (every band position missing)
-    uint64_t gcap64 = 1024;
-    while (gcap64 < (uint64_t)n * 216ull * 2ull && gcap64 < (1ull << 28)) gcap64 <<= 1;
-    const uint32_t gcap = (uint32_t)gcap64;
-    uint64_t* gtab;
-    int32_t* gid;
-    MRA_TRY(dalloc(A, &gtab, gcap));
-    MRA_TRY(dalloc(A, &gid, gcap));
-    k_fill_u64<<<1024, 256, 0, st>>>(gtab, gcap, GH_EMPTY);
-    MRA_CK_LAUNCH();
-
-    ScreenArgs sa;
-    sa.n = n; sa.M = M; sa.nlev = nlev;
-    sa.coord = f->a.coord; sa.leaf = f->a.leaf; sa.key = f->a.key; sa.off = f->a.off;
-    sa.sched = sched; sa.gtab = gtab; sa.gcap = gcap; sa.gid = gid;
-    sa.count = count; sa.pair_off = pair_off; sa.pairs = nullptr; sa.err = err;
-    const int sblocks = (int)std::min<long>(4096, ((long)n * 32 + 255) / 256);
-    k_screen<false><<<sblocks, 256, 0, st>>>(sa);
-    MRA_CK_LAUNCH();
-    MRA_TRY(scan_exclusive(count, pair_off, n, total, st));
-    MRA_CK(cudaMemcpyAsync(pair_off + n, total, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-    uint64_t* gkeys;
-    MRA_TRY(dalloc(A, &gkeys, gcap));
-    k_ghost_ids<<<1024, 256, 0, st>>>(gtab, gcap, gid, gkeys, total + 1);
-    MRA_CK_LAUNCH();
-    // the one host synchronisation: pair and ghost counts size the worklist
-    int32_t h[2] = {0, 0}, herr[2] = {0, 0};
-    MRA_CK(cudaMemcpyAsync(h, total, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    MRA_CK(cudaMemcpyAsync(herr, err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    MRA_CK(cudaStreamSynchronize(st));
-    if (herr[0]) { set_error("ghost hash set overflow"); return MRA_ECUDA; }
-    const int npairs = h[0], nghost = h[1];
-    Pair* pairs;
-    double* gblk;
-    MRA_TRY(dalloc(A, &pairs, (size_t)npairs + 1));
-    MRA_TRY(dalloc(A, &gblk, (size_t)(nghost + 1) * k3));
+    int rc = screen_forest(op, F, unscreened, A, st, &S);
+    if (rc != MRA_OK) { screen_release(A, &S); return rc; }
     MRA_CK(cudaEventRecord(ev[1], st));
-    if (nghost > 0) {
-        const size_t gsm = (2 * (size_t)k * k + 3 * (size_t)k3) * sizeof(double);
-        k_ghost_refine<<<nghost, 128, gsm, st>>>(k, gkeys, f->a.key, f->a.off, f->a.leaf, f->s, f->filt, gblk, err);
-        MRA_CK_LAUNCH();
-    }
-    sa.pairs = pairs;
-    k_screen<true><<<sblocks, 256, 0, st>>>(sa);
-    MRA_CK_LAUNCH();
+    double* gblk;
+    MRA_TRY(dalloc(A, &gblk, (size_t)(S.nghost + 1) * k3));
+    MRA_TRY(ghost_refine_forest(F, S, gblk, st));
     MRA_CK(cudaEventRecord(ev[2], st));
 
     mra_tree* g = nullptr;
@@ -616,26 +681,24 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     MRA_CK(cudaMemsetAsync(nitems, 0, sizeof(unsigned long long), st));
 
     ApplyArgs aa;
-    aa.k = k; aa.M = M; aa.n = n; aa.pairs = pairs; aa.pair_off = pair_off; aa.coord = f->a.coord;
-    aa.s = f->s; aa.gblk = gblk; aa.w = op->w; aa.nF = op->nF; aa.Jm = sched; aa.out = g->s; aa.n_items = nitems;
+    aa.k = k; aa.M = M; aa.n = n; aa.pairs = S.pairs; aa.pair_off = S.pair_off; aa.coord = f->a.coord;
+    aa.s = f->s; aa.gblk = gblk; aa.w = op->w; aa.nF = op->nF; aa.Jm = S.sched; aa.out = g->s; aa.n_items = nitems;
     aa.eta_blk = -1.0;
     if (o && o->block_screen) {
         // eps ||T_0 f_0|| / sqrt(N 216 M), evaluated on the host from the device sigma
         double sig = 0.0;
-        MRA_CK(cudaMemcpyAsync(&sig, dv + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MRA_CK(cudaMemcpyAsync(&sig, S.dv + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
         MRA_CK(cudaStreamSynchronize(st));
         aa.eta_blk = op->eps * sig / sqrt((double)n * 216.0 * M);
     }
-    int rc = MRA_OK;
     const bool itemwise = (o && o->itemwise) || aa.eta_blk >= 0.0;
     if (prec == MRA_PREC_TC_SPLIT) {
         // tcgen05 FP16 hi/lo split products (apply_tc.cu)
-        rc = launch_apply_tc(aa, nghost, nlev, op, err + 1, st);
-        if (rc != MRA_OK) return rc;
+        MRA_TRY(launch_apply_tc(aa, S.nghost, op, S.err + 1, st));
     } else if (!itemwise) {
         // Algorithm 3's nested sums, factorised (apply_fact.cu)
         aa.F = prec == MRA_PREC_FP64 ? (const void*)op->F : (const void*)op->F32;
-        MRA_TRY(launch_apply_fact(aa, prec, nlev, st));
+        MRA_TRY(launch_apply_fact(aa, prec, st));
     } else if (prec == MRA_PREC_FP64) {
         aa.F = op->F;
         size_t smem = (size_t)k3 * sizeof(double) + (4 * (size_t)k3 + 3 * k * k) * sizeof(double);
@@ -654,13 +717,14 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     if (stats) {
         unsigned long long ni = 0;
         double hv[3];
+        int32_t herr[2] = {0, 0};
         MRA_CK(cudaMemcpyAsync(&ni, nitems, sizeof(ni), cudaMemcpyDeviceToHost, st));
-        MRA_CK(cudaMemcpyAsync(hv, dv, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        MRA_CK(cudaMemcpyAsync(herr, err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        MRA_CK(cudaMemcpyAsync(hv, S.dv, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MRA_CK(cudaMemcpyAsync(herr, S.err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         MRA_CK(cudaStreamSynchronize(st));
-        stats->n_pairs = npairs;
+        stats->n_pairs = S.npairs;
         stats->n_items = (int64_t)ni;
-        stats->n_ghosts = nghost;
+        stats->n_ghosts = S.nghost;
         stats->n_out_nodes = n;
         stats->fnorm = sqrt(hv[0]);
         stats->sigma = hv[1];
@@ -671,8 +735,8 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         if (herr[1] == 4) { set_error("tensor-core apply: an MMA completion wait reached its limit"); rc = MRA_ETIMEOUT; }
         else if (herr[0] || herr[1]) { set_error("screen/ghost error code %d/%d", herr[0], herr[1]); rc = MRA_ECUDA; }
     }
-    A.put(dv); A.put(sched); A.put(count); A.put(pair_off); A.put(total); A.put(err);
-    A.put(gtab); A.put(gid); A.put(gkeys); A.put(pairs); A.put(gblk); A.put(nitems);
+    screen_release(A, &S);
+    A.put(gblk); A.put(nitems);
     for (int e = 0; e < 4; ++e) cudaEventDestroy(ev[e]);
     *gout = g;
     return rc;
@@ -789,12 +853,13 @@ int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, doubl
     const size_t pilot_smem = (4 * (size_t)k3 + k * k) * sizeof(double);
     k_pilot<<<1, 128, pilot_smem, st>>>(k, M, op->w, op->F, f->s, dv + 1);
     MRA_CK_LAUNCH();
-    k_schedule<<<1, 256, 0, st>>>(M, nlev, 0, op->eps, op->w, op->nF, op->est, dv, dv + 1, sched, dv + 2);
+    const int sl = M + 16 * nlev;
+    k_schedule<<<1, 256, 0, st>>>(M, nlev, nullptr, 0, op->eps, op->w, op->nF, op->est, dv, sched, sl);
     MRA_CK_LAUNCH();
+    const Forest F = forest_of_tree(f);
     ScreenArgs sa;
-    sa.n = n; sa.M = M; sa.nlev = nlev;
-    sa.coord = f->a.coord; sa.leaf = f->a.leaf; sa.key = f->a.key; sa.off = f->a.off;
-    sa.sched = sched; sa.gtab = gtab; sa.gcap = NA_HASH_CAP; sa.gid = gid;
+    sa.F = F; sa.M = M; sa.sl = sl; sa.sched = sched;
+    sa.gtab = gtab; sa.gcap = NA_HASH_CAP; sa.gid = gid;
     sa.count = count; sa.pair_off = pair_off; sa.pairs = nullptr; sa.err = err;
     const int sblocks = (int)std::min<long>(4096, ((long)n * 32 + 255) / 256);
     k_screen<false><<<sblocks, 256, 0, st>>>(sa);
@@ -814,7 +879,7 @@ int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, doubl
     const int nghost = h[1];
     if (nghost > 0) {
         const size_t gsm = (2 * (size_t)k * k + 3 * (size_t)k3) * sizeof(double);
-        k_ghost_refine<<<nghost, 128, gsm, st>>>(k, gkeys, f->a.key, f->a.off, f->a.leaf, f->s, f->filt, gblk, err);
+        k_ghost_refine<<<nghost, 128, gsm, st>>>(F, gkeys, gblk, err + 1);
         MRA_CK_LAUNCH();
     }
     sa.pairs = pairs;

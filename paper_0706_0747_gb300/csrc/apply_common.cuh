@@ -1,5 +1,7 @@
 // Worklist records shared by the apply kernels (apply.cu, apply_fact.cu).
 #pragma once
+#include <cuda_fp16.h>
+
 #include "mra_internal.cuh"
 
 namespace mra {
@@ -23,13 +25,86 @@ struct ApplyArgs {
     const double* w;
     const void* F;         // double or float table [j][m][l+3][k][k]
     const double* nF;
-    const int32_t* Jm;
+    const int32_t* Jm;     // per-tree term schedules: J_m of tree b at Jm[b * jm_stride + m]
+    const int32_t* node_tree = nullptr;  // tree of each node (NULL: one tree)
+    int jm_stride = 0;
     double eta_blk;        // < 0: no per-block screen
     double* out;
-    unsigned long long* n_items;
+    unsigned long long* n_items;  // items applied, per tree
 };
 
-int launch_apply_fact(const ApplyArgs& A, int precision, int nlev, cudaStream_t st);
-int launch_apply_tc(const ApplyArgs& A, int nghost, int nlev, const mra_op* op, int* err, cudaStream_t st);
+// tensor-core apply (apply_tc.cu)
+struct TcArgs {
+    ApplyArgs A;           // A.n: number of node blocks (Step-2 blocks follow them)
+    const __half* xh;      // FP16 hi/lo input blocks in the stage-I layout
+    const __half* xl;
+    const float* sx;       // per-block power-of-two scale
+    const float* xmax;     // per-block max |x|
+    const __half* Fh;      // FP16 hi/lo operator blocks, 8 x 8, per (j, m, t)
+    const __half* Fl;
+    const float* sF;       // per-(j, m) scale
+    const float* maxF;
+    int* err;              // set to 4 when a completion wait reaches its limit
+    int* counter;          // work counter (zeroed by tc_launch)
+    const int* order;      // node order (NULL: 0..nwork-1)
+    int nwork;
+    int kr;                // basis order (<= 8; padded to 8 inside)
+};
+
+struct TcBuffers {
+    __half *xh = nullptr, *xl = nullptr, *Fh = nullptr, *Fl = nullptr;
+    float *sx = nullptr, *xmax = nullptr, *sF = nullptr, *maxF = nullptr;
+    int* counter = nullptr;
+};
+
+// The screen works on a forest: one tree, or many trees whose node arrays are
+// concatenated (tree b owns a contiguous node range, level-major and Morton
+// sorted within a level, its root first).  Per tree: level offsets as
+// absolute node indices (lm + 1 entries), its number of levels, and in the
+// outputs its norms and schedule.
+struct Forest {
+    int k, ntrees, n, lm;        // order; trees; nodes in all; levels of the per-tree layouts
+    const int32_t* coord;        // [n][4]: (j, a1, a2, a3)
+    const int32_t* leaf;         // [n]
+    const uint64_t* key;         // [n]
+    const int32_t* off;          // [ntrees][lm + 1]
+    const int32_t* node_tree;    // [n] (NULL: one tree)
+    const int32_t* nlev;         // [ntrees] (NULL: lm)
+    const double* s;             // [n][k^3]
+    const double* filt;          // H0, H1 (k x k each)
+};
+
+// device results of the screen over a forest (screen_forest in apply.cu)
+struct ScreenOut {
+    double* dv = nullptr;         // [ntrees][4]: ||f_b||^2, sigma_b, eta_b, unused
+    int32_t* sched = nullptr;     // [ntrees][sl]: Jm | m1 | m2 | cnt
+    int sl = 0;
+    int32_t* count = nullptr;     // [n + 1] pairs per output node
+    int32_t* pair_off = nullptr;  // [n + 1]
+    int32_t* total = nullptr;     // [2]: pairs, Step-2 blocks
+    int32_t* err = nullptr;       // [0] screen, [1] Step 2 / apply
+    uint64_t* gtab = nullptr;     // ghost hash set
+    int32_t* gid = nullptr;
+    uint64_t* gkeys = nullptr;    // [nghost] level | tree | Morton key
+    uint32_t gcap = 0;
+    Pair* pairs = nullptr;        // [npairs], out and in are forest node indices
+    int npairs = 0, nghost = 0;
+};
+
+int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc& A, cudaStream_t st, ScreenOut* S);
+void screen_release(const Alloc& A, ScreenOut* S);
+int ghost_refine_forest(const Forest& F, const ScreenOut& S, double* gblk, cudaStream_t st);
+Forest forest_of_tree(const mra_tree* f);
+
+int tc_alloc(const mra_op* op, int nb, TcBuffers* B);            // nb: node + Step-2 blocks
+int tc_prep_F(const mra_op* op, const TcBuffers& B, cudaStream_t st);
+int tc_prep_blocks(int nb, int kr, int n, const double* s, const double* gblk, const TcBuffers& B, cudaStream_t st);
+void tc_release(const mra_op* op, TcBuffers* B);
+int tc_configure();
+TcArgs tc_args(const ApplyArgs& A, const TcBuffers& B, int* err);
+int tc_launch(const TcArgs& T, int mc, int ctas_per_sm, cudaStream_t st);
+
+int launch_apply_fact(const ApplyArgs& A, int precision, cudaStream_t st);
+int launch_apply_tc(const ApplyArgs& A, int nghost, const mra_op* op, int* err, cudaStream_t st);
 
 }  // namespace mra

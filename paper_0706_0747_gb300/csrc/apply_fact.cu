@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(NT) k_apply_fact(ApplyArgs A) {
         const int j = A.coord[4 * node];
         const int a1 = A.coord[4 * node + 1], a2 = A.coord[4 * node + 2], a3 = A.coord[4 * node + 3];
         const int p0 = A.pair_off[node], p1 = A.pair_off[node + 1];
+        const int32_t* Jm = A.Jm + (A.node_tree ? A.node_tree[node] * A.jm_stride : 0);
         for (int e = tid; e < K3; e += NT) y[e] = 0.0;
         for (int q = tid; q < 216; q += NT) tin[q] = INT_MIN;
         if (tid == 0) {
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(NT) k_apply_fact(ApplyArgs A) {
                 const int line = e / MC, mc = e % MC, m = m0 + mc;
                 unsigned char mk = 0;
                 if (m <= mhi) {
-                    const int jm = A.Jm[m];
+                    const int jm = Jm[m];
                     if (jm >= j)
                         for (int q1 = 0; q1 < 6; ++q1) {
                             const int q = q1 * 36 + line;
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(NT) k_apply_fact(ApplyArgs A) {
             }
         }
         for (int e = tid; e < K3; e += NT) A.out[(size_t)node * K3 + e] = y[e];
-        if (tid == 0 && A.n_items) atomicAdd(A.n_items, s_items);
+        if (tid == 0 && A.n_items) atomicAdd(A.n_items + (A.node_tree ? A.node_tree[node] : 0), s_items);
         __syncthreads();
     }
 }
@@ -208,8 +209,7 @@ static int launch_t(const ApplyArgs& A, cudaStream_t st) {
     return MRA_EINVAL;
 }
 
-int launch_apply_fact(const ApplyArgs& A, int precision, int nlev, cudaStream_t st) {
-    (void)nlev;
+int launch_apply_fact(const ApplyArgs& A, int precision, cudaStream_t st) {
     if (precision == MRA_PREC_FP64) return launch_t<double>(A, st);
     return launch_t<float>(A, st);
 }

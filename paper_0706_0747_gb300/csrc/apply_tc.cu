@@ -1,9 +1,10 @@
-// Step 3 of Algorithm 3 on the 5th-generation tensor cores (tcgen05), k = 8.
+// Step 3 of Algorithm 3 on the 5th-generation tensor cores (tcgen05), k <= 8
+// (orders below 8 are zero-padded to 8).
 //
-// Same nested sums as apply_fact.cu, per output node a and chunk of TC_MC
-// terms m (w_m, F = F^{j;m,.}):
+// Same nested sums as apply_fact.cu, per output node a and chunk of MC terms
+// m (w_m, F = F^{j;m,.}):
 //   stage I   per (t2,t3) line: W_m[c1][(i2,i3)] = sum_{t1 kept} sum_i1 F^{t1}[c1][i1] x_t[i1][i2][i3]
-//             MMA M=64 rows (i2,i3), N=8*TC_MC (m,c1), K=48 (t1,i1); the kept-item
+//             MMA M=64 rows (i2,i3), N=8*MC (m,c1), K=48 (t1,i1); the kept-item
 //             mask zeroes whole F^{t1} blocks of the B operand
 //   stage II  per line and term: V_m[(c1,i3)][c2] += sum_i2 W_m[c1][i2][i3] F^{t2}[c2][i2]
 //             MMA M=64, N=8, K=16 (i2, zero padded), accumulated over the plane's lines in TMEM
@@ -17,11 +18,14 @@
 // (sx_node = the smallest block scale of the neighbourhood), and per term for
 // W and V from bounds (|W| <= 48 max|F| max|x|, |V| <= 48 max|F| max|W|).
 //
-// One elected thread issues the MMAs and commits them to an mbarrier; the
-// 128 threads wait on it (bounded), read TMEM with tcgen05.ld and write the
-// next stage's operand into shared memory in the canonical no-swizzle
-// K-major layout (8-row x 16-byte core matrices).  Per line there is one
-// wait: stage II of a line runs while the next line's operands are staged.
+// One elected thread issues the MMAs and commits them to an mbarrier; warp 0
+// polls it (bounded) and a block barrier releases the rest; the 256 threads
+// read TMEM with tcgen05.ld and write the next stage's operand into shared
+// memory in the canonical no-swizzle K-major layout (8-row x 16-byte core
+// matrices).  Per line there is one wait: stage II of a line runs while the
+// next line's operands are staged.  CTAs are persistent and take nodes from
+// an atomic counter (optionally in a given order), so one launch can cover the
+// nodes of many trees.
 #include <climits>
 
 #include "apply_common.cuh"
@@ -29,25 +33,27 @@
 
 namespace mra {
 
-#define TC_MC 8
 #define TC_THREADS 256
 #define TC_WAIT_LIMIT (1u << 26)
-#define TC_TMEM_COLS 256
 
 // ---------------------------------------------------------------- prep
-// Input blocks (tree nodes then Step-2 blocks) -> FP16 hi/lo in the stage-I
-// A layout: element x[i1][i2][i3] at half index i2*64 + i3*8 + i1 (core
-// matrix i2, row i3, column i1), with a power-of-two scale per block.
-__global__ void k_tc_prep_blocks(int n, int ng, const double* s, const double* gblk, __half* xh, __half* xl,
-                                 float* sx, float* xmax) {
+// Input blocks -> FP16 hi/lo in the stage-I A layout: element x[i1][i2][i3]
+// (zero for indices >= kr) at half index i2*64 + i3*8 + i1 (core matrix i2,
+// row i3, column i1), with a power-of-two scale per block.  Block b is node b
+// of s (b < n) or Step-2 block b - n.
+__global__ void k_tc_prep_blocks(int nb, int kr, int n, const double* s, const double* gblk, __half* xh,
+                                 __half* xl, float* sx, float* xmax) {
     __shared__ float red[4];
     const int b = blockIdx.x;
-    if (b >= n + ng) return;
-    const double* src = b < n ? s + (size_t)b * 512 : gblk + (size_t)(b - n) * 512;
+    if (b >= nb) return;
+    const int k3 = kr * kr * kr;
+    const double* src = b < n ? s + (size_t)b * k3 : gblk + (size_t)(b - n) * k3;
     double v[4];
     float m = 0.0f;
     for (int q = 0; q < 4; ++q) {
-        v[q] = src[threadIdx.x + 128 * q];
+        const int idx = threadIdx.x + 128 * q;  // (i1, i2, i3) of the padded 8^3 block
+        const int i1 = idx >> 6, i2 = (idx >> 3) & 7, i3 = idx & 7;
+        v[q] = (i1 < kr && i2 < kr && i3 < kr) ? src[(i1 * kr + i2) * kr + i3] : 0.0;
         m = fmaxf(m, (float)fabs(v[q]));
     }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -58,7 +64,7 @@ __global__ void k_tc_prep_blocks(int n, int ng, const double* s, const double* g
     if (m > 0.0f) frexpf(m, &e);
     const double scale = ldexp(1.0, 13 - e);  // m * scale in [2^12, 2^13)
     for (int q = 0; q < 4; ++q) {
-        const int idx = threadIdx.x + 128 * q;  // x[i1][i2][i3]
+        const int idx = threadIdx.x + 128 * q;
         const int i1 = idx >> 6, i2 = (idx >> 3) & 7, i3 = idx & 7;
         __half hi, lo;
         tc::split_h((float)(v[q] * scale), hi, lo);
@@ -71,15 +77,15 @@ __global__ void k_tc_prep_blocks(int n, int ng, const double* s, const double* g
     }
 }
 
-// Operator blocks F^{j;m,t}[c][i] -> FP16 hi/lo (natural row-major layout,
-// which is already the core-matrix layout of the B operands) with a
+// Operator blocks F^{j;m,t}[c][i] (kr x kr) -> FP16 hi/lo 8 x 8 row-major
+// (already the core-matrix layout of the B operands), zero-padded, with a
 // power-of-two scale per (j, m).
-__global__ void k_tc_prep_F(int M, const double* F, __half* Fh, __half* Fl, float* sF, float* maxF) {
+__global__ void k_tc_prep_F(int M, int kr, const double* F, __half* Fh, __half* Fl, float* sF, float* maxF) {
     __shared__ float red[4];
     const int m = blockIdx.x, j = blockIdx.y;
-    const double* src = F + ((size_t)j * M + m) * 7 * 64;
+    const double* src = F + ((size_t)j * M + m) * 7 * kr * kr;
     float mx = 0.0f;
-    for (int e = threadIdx.x; e < 7 * 64; e += blockDim.x) mx = fmaxf(mx, (float)fabs(src[e]));
+    for (int e = threadIdx.x; e < 7 * kr * kr; e += blockDim.x) mx = fmaxf(mx, (float)fabs(src[e]));
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
@@ -88,8 +94,10 @@ __global__ void k_tc_prep_F(int M, const double* F, __half* Fh, __half* Fl, floa
     if (mx > 0.0f) frexpf(mx, &ex);
     const double scale = ldexp(1.0, 13 - ex);
     for (int e = threadIdx.x; e < 7 * 64; e += blockDim.x) {
+        const int t = e / 64, c = (e / 8) % 8, i = e % 8;
+        const double v = (c < kr && i < kr) ? src[(t * kr + c) * kr + i] : 0.0;
         __half hi, lo;
-        tc::split_h((float)(src[e] * scale), hi, lo);
+        tc::split_h((float)(v * scale), hi, lo);
         Fh[((size_t)j * M + m) * 7 * 64 + e] = hi;
         Fl[((size_t)j * M + m) * 7 * 64 + e] = lo;
     }
@@ -99,35 +107,27 @@ __global__ void k_tc_prep_F(int M, const double* F, __half* Fh, __half* Fl, floa
     }
 }
 
-struct TcArgs {
-    ApplyArgs A;
-    const __half* xh;
-    const __half* xl;
-    const float* sx;
-    const float* xmax;
-    const __half* Fh;
-    const __half* Fl;
-    const float* sF;
-    const float* maxF;
-    int* err;
+// shared-memory map (bytes) for MC terms per chunk; every operand region
+// starts on a 128-byte boundary
+template <int MC>
+struct TcSmem {
+    static constexpr int XH = 0;                    // 6 blocks x 1 KB: stage I A (hi)
+    static constexpr int XL = 6144;
+    static constexpr int B1H = 12288;               // MC terms x 6 K groups x 128 B: stage I B
+    static constexpr int B1L = B1H + MC * 768;
+    static constexpr int A2H = B1L + MC * 768;      // MC x 2048 B: stage II A; stage III A aliases it
+    static constexpr int A2L = A2H + MC * 2048;
+    static constexpr int B2 = A2L + MC * 2048;      // 2 buffers x {hi, lo} x MC x 256 B (K group 1 zero)
+    static constexpr int B3H = B2 + MC * 1024;      // MC x 256 B: stage III B (K group 1 zero)
+    static constexpr int B3L = B3H + MC * 256;
+    static constexpr int FSH = B3L + MC * 256;      // MC x 7 shifts x 64 halves: the chunk's F (hi)
+    static constexpr int FSL = FSH + MC * 896;
+    static constexpr int TAB = FSL + MC * 896;      // 4 x 216 int
+    static constexpr int MSK = TAB + 3456;          // 36 x MC bytes
+    static constexpr int Y = (MSK + 36 * MC + 127) / 128 * 128;  // 64 x 8 doubles (second warp half)
+    static constexpr int TOTAL = Y + 4096;
+    static constexpr int TMEM_COLS = (24 * MC <= 128) ? 128 : 256;
 };
-
-// shared-memory map (bytes); every operand region starts on a 128-byte boundary
-#define SM_XH 0          // 6 blocks x 1 KB: stage I A (hi)
-#define SM_XL 6144
-#define SM_B1H 12288     // TC_MC terms x 6 K groups x 128 B: stage I B (hi)
-#define SM_B1L 18432
-#define SM_A2H 24576     // TC_MC terms x 2048 B: stage II A (8 row groups x 2 K groups); stage III A aliases it
-#define SM_A2L 40960
-#define SM_B2 57344      // 2 buffers x {hi, lo} x TC_MC terms x 256 B: stage II B (K group 1 zero)
-#define SM_B3H 65536     // TC_MC terms x 256 B: stage III B (K group 1 zero)
-#define SM_B3L 67584
-#define SM_FSH 69632     // TC_MC terms x 7 shifts x 64 halves: the chunk's F^{j;m,t} (hi)
-#define SM_FSL 76800
-#define SM_TAB 83968     // 4 x 216 int
-#define SM_MSK 87424     // 36 x TC_MC bytes
-#define SM_Y 87808       // 64 x 8 doubles: the second warp half's partial ghat
-#define SM_TOTAL 91904
 
 __device__ __forceinline__ float pow2floor(double x) {
     if (!(x > 0.0)) return 0.0f;
@@ -139,49 +139,50 @@ __device__ __forceinline__ float pow2floor(double x) {
     return ldexpf(1.0f, e);
 }
 
+template <int MC>
 __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
+    using L = TcSmem<MC>;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ int s_mlo, s_mhi, s_exp_min;
+    __shared__ int s_mlo, s_mhi, s_exp_min, s_node;
     __shared__ unsigned int s_xmax_bits;
     __shared__ unsigned long long s_items;
-    __shared__ float s_c2[TC_MC], s_c3[TC_MC], s_g[6];
+    __shared__ float s_c2[MC], s_c3[MC], s_g[6];
     __shared__ unsigned char s_lm[36], s_pm[6];
-    __shared__ double s_fin[TC_MC];
+    __shared__ double s_fin[MC];
 
     const ApplyArgs& A = T.A;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    __half* B1H = (__half*)(sm + SM_B1H);
-    __half* B1L = (__half*)(sm + SM_B1L);
-    __half* A2H = (__half*)(sm + SM_A2H);
-    __half* A2L = (__half*)(sm + SM_A2L);
-    __half* B3H = (__half*)(sm + SM_B3H);
-    __half* B3L = (__half*)(sm + SM_B3L);
-    __half* FSH = (__half*)(sm + SM_FSH);
-    __half* FSL = (__half*)(sm + SM_FSL);
-    int* tin = (int*)(sm + SM_TAB);
+    const int kr = T.kr;
+    __half* B1H = (__half*)(sm + L::B1H);
+    __half* B1L = (__half*)(sm + L::B1L);
+    __half* A2H = (__half*)(sm + L::A2H);
+    __half* A2L = (__half*)(sm + L::A2L);
+    __half* B3H = (__half*)(sm + L::B3H);
+    __half* B3L = (__half*)(sm + L::B3L);
+    __half* FSH = (__half*)(sm + L::FSH);
+    __half* FSL = (__half*)(sm + L::FSL);
+    int* tin = (int*)(sm + L::TAB);
     int* tlo = tin + 216;
     int* thi = tlo + 216;
     int* tfl = thi + 216;
-    unsigned char* msk = sm + SM_MSK;
+    unsigned char* msk = sm + L::MSK;
 
     // zero everything once: the K padding of stages II and III stays zero
-    for (int e = tid; e < SM_TOTAL / 16; e += TC_THREADS) ((uint4*)sm)[e] = make_uint4(0, 0, 0, 0);
-    if (warp == 0) tc::tmem_alloc(&s_tmem, TC_TMEM_COLS);
-    if (tid == 0) {
-        tc::mbar_init(&s_mbar, 1);
-    }
+    for (int e = tid; e < L::TOTAL / 16; e += TC_THREADS) ((uint4*)sm)[e] = make_uint4(0, 0, 0, 0);
+    if (warp == 0) tc::tmem_alloc(&s_tmem, L::TMEM_COLS);
+    if (tid == 0) tc::mbar_init(&s_mbar, 1);
     tc::fence_async_smem();
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = s_tmem;
-    const uint32_t tD1 = tbase, tD2 = tbase + 8 * TC_MC, tD3 = tbase + 16 * TC_MC;
+    const uint32_t tD1 = tbase, tD2 = tbase + 8 * MC, tD3 = tbase + 16 * MC;
     // warps w and w+4 share TMEM lane quarter w and split the terms of a chunk
     const int quarter = warp & 3, whalf = warp >> 2;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    const int mc_lo = whalf * (TC_MC / 2), mc_hi = mc_lo + TC_MC / 2;
-    const uint32_t idI = tc::idesc_f16(64, 8 * TC_MC), idS = tc::idesc_f16(64, 8);
+    const int mc_lo = whalf * (MC / 2), mc_hi = mc_lo + MC / 2;
+    const uint32_t idI = tc::idesc_f16(64, 8 * MC), idS = tc::idesc_f16(64, 8);
     uint32_t phase = 0;
     const int row = quarter * 16 + lane;  // accumulator row of this thread (M=64 layout), valid for lane < 16
     const bool has_row = lane < 16;
@@ -201,7 +202,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
         }                                                                           \
     }
 
-    for (int node = blockIdx.x; node < A.n && !aborted; node += gridDim.x) {
+    while (!aborted) {
+        if (tid == 0) s_node = atomicAdd(T.counter, 1);
+        __syncthreads();
+        const int widx = s_node;
+        if (widx >= T.nwork) break;
+        const int node = T.order ? T.order[widx] : widx;
+        const int jm_base = A.node_tree ? A.node_tree[node] * A.jm_stride : 0;
         const int j = A.coord[4 * node];
         const int a1 = A.coord[4 * node + 1], a2 = A.coord[4 * node + 2], a3 = A.coord[4 * node + 3];
         const int p0 = A.pair_off[node], p1 = A.pair_off[node + 1];
@@ -239,9 +246,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) y[c] = 0.0;
         if (mhi >= mlo && xmax_node > 0.0f) {
-            for (int m0 = mlo; m0 <= mhi && !aborted; m0 += TC_MC) {
+            for (int m0 = mlo; m0 <= mhi && !aborted; m0 += MC) {
                 // the chunk's operator blocks, the kept-t1 masks per line, per-term scales
-                for (int e = tid; e < TC_MC * 7 * 64 / 8; e += TC_THREADS) {  // uint4 = 8 halves
+                for (int e = tid; e < MC * 7 * 64 / 8; e += TC_THREADS) {  // uint4 = 8 halves
                     const int mc = e / 56, r = e % 56, m = m0 + mc;
                     uint4 h = make_uint4(0, 0, 0, 0), l = h;
                     if (m <= mhi) {
@@ -252,11 +259,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     ((uint4*)FSH)[e] = h;
                     ((uint4*)FSL)[e] = l;
                 }
-                for (int e = tid; e < 36 * TC_MC; e += TC_THREADS) {
-                    const int line = e / TC_MC, mc = e % TC_MC, m = m0 + mc;
+                for (int e = tid; e < 36 * MC; e += TC_THREADS) {
+                    const int line = e / MC, mc = e % MC, m = m0 + mc;
                     unsigned char mk = 0;
                     if (m <= mhi) {
-                        const int jm = A.Jm[m];
+                        const int jm = A.Jm[jm_base + m];
                         if (jm >= j)
                             for (int q1 = 0; q1 < 6; ++q1) {
                                 const int q = q1 * 36 + line;
@@ -267,7 +274,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     }
                     msk[e] = mk;
                 }
-                if (tid < TC_MC) {
+                if (tid < MC) {
                     const int m = m0 + tid;
                     float c2 = 0.0f, c3 = 0.0f;
                     double fin = 0.0;
@@ -291,7 +298,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                 // per line: the union of its terms' kept-t1 masks; per plane: any line
                 if (tid < 36) {
                     unsigned v = 0;
-                    for (int mc = 0; mc < TC_MC; ++mc) v |= msk[tid * TC_MC + mc];
+                    for (int mc = 0; mc < MC; ++mc) v |= msk[tid * MC + mc];
                     s_lm[tid] = (unsigned char)v;
                 }
                 __syncthreads();
@@ -306,8 +313,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     if (!s_pm[q3]) continue;  // uniform
                     const int t3 = band_t(a3, q3);
                     // stage III B: K group 0 = F^{t3}[c3][i3] (8 uint4 per term)
-                    for (int e = tid; e < 2 * TC_MC * 8; e += TC_THREADS) {
-                        const int hl = e / (TC_MC * 8), mc = (e / 8) % TC_MC, v = e % 8;
+                    for (int e = tid; e < 2 * MC * 8; e += TC_THREADS) {
+                        const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
                         const uint4* src = (const uint4*)(hl ? FSL : FSH) + (mc * 7 + t3 + 3) * 8 + v;
                         ((uint4*)(hl ? B3L : B3H))[mc * 16 + v] = *src;
                     }
@@ -318,8 +325,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                         if (!lm) continue;  // uniform
                         const int t2 = band_t(a2, q2);
                         const int par = line_no & 1;
-                        __half* B2H = (__half*)(sm + SM_B2 + par * (2 * TC_MC * 256));
-                        __half* B2L = B2H + TC_MC * 128;
+                        __half* B2H = (__half*)(sm + L::B2 + par * (2 * MC * 256));
+                        __half* B2L = B2H + MC * 128;
                         // stage I A (the line's input blocks) and the per-slot scale ratios
                         if (tid < 6) {
                             float g = 0.0f;
@@ -338,21 +345,21 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                                 const int b = in >= 0 ? in : A.n + (-1 - in);
                                 val = ((const uint4*)((hl ? T.xl : T.xh) + (size_t)b * 512))[v];
                             }
-                            ((uint4*)(sm + (hl ? SM_XL : SM_XH)))[q1 * 64 + v] = val;
+                            ((uint4*)(sm + (hl ? L::XL : L::XH)))[q1 * 64 + v] = val;
                         }
                         // stage II B for this line: K group 0 = F^{t2}[c2][i2]
-                        for (int e = tid; e < 2 * TC_MC * 8; e += TC_THREADS) {
-                            const int hl = e / (TC_MC * 8), mc = (e / 8) % TC_MC, v = e % 8;
+                        for (int e = tid; e < 2 * MC * 8; e += TC_THREADS) {
+                            const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
                             const uint4* src = (const uint4*)(hl ? FSL : FSH) + (mc * 7 + t2 + 3) * 8 + v;
                             ((uint4*)(hl ? B2L : B2H))[mc * 16 + v] = *src;
                         }
                         __syncthreads();
                         // stage I B: core (N group mc, K group q1) = mask ? g * F^{t1(q1)} : 0,
                         // one 16-byte core row per step (power-of-two g: exact in FP16)
-                        for (int e = tid; e < 2 * TC_MC * 6 * 8; e += TC_THREADS) {
-                            const int hl = e / (TC_MC * 48), mc = (e / 48) % TC_MC, q1 = (e / 8) % 6, v = e % 8;
+                        for (int e = tid; e < 2 * MC * 6 * 8; e += TC_THREADS) {
+                            const int hl = e / (MC * 48), mc = (e / 48) % MC, q1 = (e / 8) % 6, v = e % 8;
                             uint4 out = make_uint4(0, 0, 0, 0);
-                            if ((msk[line * TC_MC + mc] >> q1) & 1u) {
+                            if ((msk[line * MC + mc] >> q1) & 1u) {
                                 const uint4 in = ((const uint4*)(hl ? FSL : FSH))[(mc * 7 + band_t(a1, q1) + 3) * 8 + v];
                                 const __half2 g2 = __float2half2_rn(s_g[q1]);
                                 const __half2* pi = (const __half2*)&in;
@@ -368,16 +375,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                             tc::fence_after();
 #pragma unroll
                             for (int ks = 0; ks < 3; ++ks) {
-                                const uint64_t ah = tc::sdesc(sbase + SM_XH + ks * 2048, 1024, 128);
-                                const uint64_t al = tc::sdesc(sbase + SM_XL + ks * 2048, 1024, 128);
-                                const uint64_t bh = tc::sdesc(sbase + SM_B1H + ks * 256, 128, 768);
-                                const uint64_t bl = tc::sdesc(sbase + SM_B1L + ks * 256, 128, 768);
+                                const uint64_t ah = tc::sdesc(sbase + L::XH + ks * 2048, 1024, 128);
+                                const uint64_t al = tc::sdesc(sbase + L::XL + ks * 2048, 1024, 128);
+                                const uint64_t bh = tc::sdesc(sbase + L::B1H + ks * 256, 128, 768);
+                                const uint64_t bl = tc::sdesc(sbase + L::B1L + ks * 256, 128, 768);
                                 tc::mma_f16(tD1, ah, bh, idI, ks > 0);
                                 tc::mma_f16(tD1, ah, bl, idI, 1);
                                 tc::mma_f16(tD1, al, bh, idI, 1);
                             }
                             tc::commit(&s_mbar);
-                            for (int mc = 0; mc < TC_MC; ++mc) s_items += __popc(msk[line * TC_MC + mc]);
+                            for (int mc = 0; mc < MC; ++mc) s_items += __popc(msk[line * MC + mc]);
                         }
                         // also covers the previous line's stage II: A2 is free afterwards
                         TC_WAIT_OR_ABORT();
@@ -407,12 +414,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                         // stage II: per term, V += A2 (M=64 (c1,i3) x K=16) x B2 (N=8 c2)
                         if (tid == 0) {
                             tc::fence_after();
-                            const uint32_t b2 = sbase + SM_B2 + par * (2 * TC_MC * 256);
-                            for (int mc = 0; mc < TC_MC; ++mc) {
-                                const uint64_t ah = tc::sdesc(sbase + SM_A2H + mc * 2048, 128, 256);
-                                const uint64_t al = tc::sdesc(sbase + SM_A2L + mc * 2048, 128, 256);
+                            const uint32_t b2 = sbase + L::B2 + par * (2 * MC * 256);
+                            for (int mc = 0; mc < MC; ++mc) {
+                                const uint64_t ah = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
+                                const uint64_t al = tc::sdesc(sbase + L::A2L + mc * 2048, 128, 256);
                                 const uint64_t bh = tc::sdesc(b2 + mc * 256, 128, 256);
-                                const uint64_t bl = tc::sdesc(b2 + TC_MC * 256 + mc * 256, 128, 256);
+                                const uint64_t bl = tc::sdesc(b2 + MC * 256 + mc * 256, 128, 256);
                                 tc::mma_f16(tD2 + mc * 8, ah, bh, idS, line_no > 0);
                                 tc::mma_f16(tD2 + mc * 8, ah, bl, idS, 1);
                                 tc::mma_f16(tD2 + mc * 8, al, bh, idS, 1);
@@ -449,11 +456,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     // stage III: per term, Y += A3 (M=64 (c1,c2) x K=16) x B3 (N=8 c3)
                     if (tid == 0) {
                         tc::fence_after();
-                        for (int mc = 0; mc < TC_MC; ++mc) {
-                            const uint64_t ah = tc::sdesc(sbase + SM_A2H + mc * 2048, 128, 256);
-                            const uint64_t al = tc::sdesc(sbase + SM_A2L + mc * 2048, 128, 256);
-                            const uint64_t bh = tc::sdesc(sbase + SM_B3H + mc * 256, 128, 256);
-                            const uint64_t bl = tc::sdesc(sbase + SM_B3L + mc * 256, 128, 256);
+                        for (int mc = 0; mc < MC; ++mc) {
+                            const uint64_t ah = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
+                            const uint64_t al = tc::sdesc(sbase + L::A2L + mc * 2048, 128, 256);
+                            const uint64_t bh = tc::sdesc(sbase + L::B3H + mc * 256, 128, 256);
+                            const uint64_t bl = tc::sdesc(sbase + L::B3L + mc * 256, 128, 256);
                             tc::mma_f16(tD3 + mc * 8, ah, bh, idS, plane_started);
                             tc::mma_f16(tD3 + mc * 8, ah, bl, idS, 1);
                             tc::mma_f16(tD3 + mc * 8, al, bh, idS, 1);
@@ -482,54 +489,109 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                 __syncthreads();
             }
         }
-        double* ysm = (double*)(sm + SM_Y);
+        double* ysm = (double*)(sm + L::Y);
         if (has_row && whalf == 1)
 #pragma unroll
             for (int c3 = 0; c3 < 8; ++c3) ysm[row * 8 + c3] = y[c3];
         __syncthreads();
-        if (has_row && whalf == 0)
+        const int c1 = row >> 3, c2 = row & 7;
+        if (has_row && whalf == 0 && c1 < kr && c2 < kr)
 #pragma unroll
-            for (int c3 = 0; c3 < 8; ++c3) A.out[(size_t)node * 512 + row * 8 + c3] = y[c3] + ysm[row * 8 + c3];
-        if (tid == 0 && A.n_items) atomicAdd(A.n_items, s_items);
+            for (int c3 = 0; c3 < 8; ++c3)
+                if (c3 < kr) A.out[(size_t)node * kr * kr * kr + (c1 * kr + c2) * kr + c3] = y[c3] + ysm[row * 8 + c3];
+        if (tid == 0 && A.n_items) atomicAdd(A.n_items + (A.node_tree ? A.node_tree[node] : 0), s_items);
         __syncthreads();
     }
 #undef TC_WAIT_OR_ABORT
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tbase, TC_TMEM_COLS);
+    if (warp == 0) tc::tmem_dealloc(tbase, L::TMEM_COLS);
 }
 
-int launch_apply_tc(const ApplyArgs& A, int nghost, int nlev, const mra_op* op, int* err, cudaStream_t st) {
-    (void)nlev;
-    if (A.k != 8) {
-        set_error("the tensor-core apply supports k = 8 (got k = %d)", A.k);
+// ---------------------------------------------------------------- host side
+int tc_alloc(const mra_op* op, int nb, TcBuffers* B) {
+    const Alloc& Al = op->A;
+    const size_t JM = (size_t)(op->J + 1) * op->M;
+    MRA_TRY(dalloc(Al, &B->xh, (size_t)nb * 512));
+    MRA_TRY(dalloc(Al, &B->xl, (size_t)nb * 512));
+    MRA_TRY(dalloc(Al, &B->sx, nb));
+    MRA_TRY(dalloc(Al, &B->xmax, nb));
+    MRA_TRY(dalloc(Al, &B->Fh, JM * 7 * 64));
+    MRA_TRY(dalloc(Al, &B->Fl, JM * 7 * 64));
+    MRA_TRY(dalloc(Al, &B->sF, JM));
+    MRA_TRY(dalloc(Al, &B->maxF, JM));
+    MRA_TRY(dalloc(Al, &B->counter, 1));
+    return MRA_OK;
+}
+
+int tc_prep_F(const mra_op* op, const TcBuffers& B, cudaStream_t st) {
+    k_tc_prep_F<<<dim3(op->M, op->J + 1), 128, 0, st>>>(op->M, op->k, op->F, B.Fh, B.Fl, B.sF, B.maxF);
+    MRA_CK_LAUNCH();
+    return MRA_OK;
+}
+
+int tc_prep_blocks(int nb, int kr, int n, const double* s, const double* gblk, const TcBuffers& B, cudaStream_t st) {
+    if (nb <= 0) return MRA_OK;
+    k_tc_prep_blocks<<<nb, 128, 0, st>>>(nb, kr, n, s, gblk, B.xh, B.xl, B.sx, B.xmax);
+    MRA_CK_LAUNCH();
+    return MRA_OK;
+}
+
+void tc_release(const mra_op* op, TcBuffers* B) {
+    const Alloc& Al = op->A;
+    Al.put(B->xh); Al.put(B->xl); Al.put(B->sx); Al.put(B->xmax);
+    Al.put(B->Fh); Al.put(B->Fl); Al.put(B->sF); Al.put(B->maxF); Al.put(B->counter);
+    *B = TcBuffers();
+}
+
+// dynamic shared memory of both chunk sizes (outside any stream capture)
+int tc_configure() {
+    MRA_CK(cudaFuncSetAttribute(k_apply_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<4>::TOTAL));
+    MRA_CK(cudaFuncSetAttribute(k_apply_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<8>::TOTAL));
+    return MRA_OK;
+}
+
+template <int MC>
+static int launch_mc(const TcArgs& T, int ctas_per_sm, cudaStream_t st) {
+    const int grid = std::max(1, std::min(T.nwork, 152 * ctas_per_sm));
+    k_apply_tc<MC><<<grid, TC_THREADS, TcSmem<MC>::TOTAL, st>>>(T);
+    MRA_CK_LAUNCH();
+    return MRA_OK;
+}
+
+// variant: terms per chunk (4 or 8) and CTAs per SM (1 or 2); TMEM and shared
+// memory allow 2 CTAs per SM for both chunk sizes.  tc_configure() first.
+int tc_launch(const TcArgs& T, int mc, int ctas_per_sm, cudaStream_t st) {
+    MRA_CK(cudaMemsetAsync(T.counter, 0, sizeof(int), st));
+    if (mc == 4) return launch_mc<4>(T, ctas_per_sm, st);
+    return launch_mc<8>(T, ctas_per_sm, st);
+}
+
+TcArgs tc_args(const ApplyArgs& A, const TcBuffers& B, int* err) {
+    TcArgs T;
+    T.A = A;
+    T.xh = B.xh; T.xl = B.xl; T.sx = B.sx; T.xmax = B.xmax;
+    T.Fh = B.Fh; T.Fl = B.Fl; T.sF = B.sF; T.maxF = B.maxF;
+    T.err = err;  // the apply's error word: a wait that reaches its limit writes 4
+    T.counter = B.counter;
+    T.order = nullptr;
+    T.nwork = A.n;
+    T.kr = A.k;
+    return T;
+}
+
+int launch_apply_tc(const ApplyArgs& A, int nghost, const mra_op* op, int* err, cudaStream_t st) {
+    if (A.k > 8) {
+        set_error("the tensor-core apply supports k <= 8 (got k = %d)", A.k);
         return MRA_EINVAL;
     }
-    const Alloc& Al = op->A;
-    const int nb = A.n + nghost;
-    const size_t JM = (size_t)(op->J + 1) * op->M;
-    __half *xh, *xl, *Fh, *Fl;
-    float *sx, *xmax, *sF, *maxF;
-    MRA_TRY(dalloc(Al, &xh, (size_t)nb * 512));
-    MRA_TRY(dalloc(Al, &xl, (size_t)nb * 512));
-    MRA_TRY(dalloc(Al, &sx, nb));
-    MRA_TRY(dalloc(Al, &xmax, nb));
-    MRA_TRY(dalloc(Al, &Fh, JM * 7 * 64));
-    MRA_TRY(dalloc(Al, &Fl, JM * 7 * 64));
-    MRA_TRY(dalloc(Al, &sF, JM));
-    MRA_TRY(dalloc(Al, &maxF, JM));
-    k_tc_prep_blocks<<<nb, 128, 0, st>>>(A.n, nghost, A.s, A.gblk, xh, xl, sx, xmax);
-    MRA_CK_LAUNCH();
-    k_tc_prep_F<<<dim3(op->M, op->J + 1), 128, 0, st>>>(op->M, op->F, Fh, Fl, sF, maxF);
-    MRA_CK_LAUNCH();
-    // err: the apply's error word; a wait that reaches its limit writes 4 there
-    TcArgs T{A, xh, xl, sx, xmax, Fh, Fl, sF, maxF, err};
-    MRA_CK(cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL));
-    const int grid = std::min(A.n, 152 * 2);  // 2 CTAs per SM: 2 x 91 KB shared, 2 x 256 TMEM columns
-    k_apply_tc<<<grid, TC_THREADS, SM_TOTAL, st>>>(T);
-    MRA_CK_LAUNCH();
-    // stream-ordered frees: released after the kernel completes
-    Al.put(xh); Al.put(xl); Al.put(sx); Al.put(xmax); Al.put(Fh); Al.put(Fl); Al.put(sF); Al.put(maxF);
+    TcBuffers B;
+    MRA_TRY(tc_alloc(op, A.n + nghost, &B));
+    MRA_TRY(tc_prep_F(op, B, st));
+    MRA_TRY(tc_prep_blocks(A.n + nghost, A.k, A.n, A.s, A.gblk, B, st));
+    MRA_TRY(tc_configure());
+    MRA_TRY(tc_launch(tc_args(A, B, err), 8, 2, st));
+    tc_release(op, &B);  // stream-ordered frees: released after the kernel completes
     return MRA_OK;
 }
 

@@ -13,6 +13,7 @@ static thread_local char g_err[512] = "";
 static std::atomic<unsigned long long> g_launches(0);
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch_add(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     va_list ap;

@@ -67,6 +67,23 @@ class ApplyStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_trees", ctypes.c_int), ("n_nodes", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+                ("n_ghosts", ctypes.c_int64), ("n_items", ctypes.c_int64), ("precision", ctypes.c_int),
+                ("terms_per_chunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("heavy_first", ctypes.c_int),
+                ("tuned", ctypes.c_int), ("ms_variant", ctypes.c_float * 8), ("graph", ctypes.c_int),
+                ("graph_kernels", ctypes.c_int), ("ms_screen", ctypes.c_float)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["ms_variant"] = list(self.ms_variant)
+        return d
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I32P = ctypes.POINTER(ctypes.c_int32)
@@ -89,6 +106,14 @@ SIGNATURES = {
     "mra_apply_ns": [_P, _P, ctypes.POINTER(ApplyOpts), _P, ctypes.POINTER(_P), ctypes.POINTER(ApplyStats)],
     "mra_apply_ns_noalloc": [_P, _P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_int64)],
     "mra_reconstruct": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _DP],
+    "mra_plan_create": [_P, ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(PlanOpts), _P, ctypes.POINTER(_P)],
+    "mra_plan_execute": [_P, _P],
+    "mra_plan_autotune": [_P, ctypes.c_int, _P],
+    "mra_plan_set_variant": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "mra_plan_output": [_P, ctypes.c_int, _P, ctypes.POINTER(_P)],
+    "mra_plan_get_info": [_P, ctypes.POINTER(PlanInfo), _P],
+    "mra_plan_tree_stats": [_P, ctypes.c_int, _P, ctypes.POINTER(ApplyStats)],
+    "mra_free_plan": [_P],
     "mra_free_tree": [_P],
     "mra_free_op": [_P],
     "mra_last_error": [],
@@ -323,6 +348,65 @@ def apply_ns_noalloc(op, tree, out_ptr, precision="fp64", stream=None):
     n = ctypes.c_int64(0)
     _check(lib().mra_apply_ns_noalloc(op.h, tree.h, PREC[precision], out_ptr, _stream(stream), ctypes.byref(n)))
     return n.value
+
+
+class Plan:
+    """Batched apply of one operator to many trees (mra_plan_*).  Keeps the
+    operator and the trees alive for its own lifetime."""
+
+    def __init__(self, handle, op, trees):
+        self.h = handle
+        self._op = op
+        self._trees = list(trees)
+
+    def execute(self, stream=None):
+        _check(lib().mra_plan_execute(self.h, _stream(stream)))
+
+    def autotune(self, reps=3, stream=None):
+        _check(lib().mra_plan_autotune(self.h, int(reps), _stream(stream)))
+        return self.info(stream)
+
+    def set_variant(self, terms_per_chunk=8, ctas_per_sm=2, heavy_first=False):
+        _check(lib().mra_plan_set_variant(self.h, int(terms_per_chunk), int(ctas_per_sm), int(heavy_first)))
+
+    def output(self, b, stream=None):
+        h = _P()
+        _check(lib().mra_plan_output(self.h, int(b), _stream(stream), ctypes.byref(h)))
+        return Tree(h.value)
+
+    def info(self, stream=None):
+        inf = PlanInfo()
+        _check(lib().mra_plan_get_info(self.h, ctypes.byref(inf), _stream(stream)))
+        return inf.as_dict()
+
+    def tree_stats(self, b, stream=None):
+        st = ApplyStats()
+        _check(lib().mra_plan_tree_stats(self.h, int(b), _stream(stream), ctypes.byref(st)))
+        return st.as_dict()
+
+    def free(self):
+        if self.h:
+            lib().mra_free_plan(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def plan_create(op, trees, precision=None, use_graph=True, stream=None):
+    """mra_plan_create over compressed trees (all of op's order k)."""
+    arr = (_P * len(trees))(*[t.h for t in trees])
+    opts = None
+    if precision is not None or not use_graph:
+        k = op.info().k
+        prec = PREC[precision] if precision is not None else (PREC["tc"] if k <= 8 else PREC["fp64"])
+        opts = ctypes.byref(PlanOpts(prec, int(use_graph)))
+    h = _P()
+    _check(lib().mra_plan_create(op.h, arr, len(trees), opts, _stream(stream), ctypes.byref(h)))
+    return Plan(h.value, op, trees)
 
 
 def reconstruct(tree, mode="assemble", truncate=False, eps=0.0, stream=None):

@@ -208,10 +208,23 @@ def test_apply_tensor_core_split_k8(eps):
     assert rel_l2(ghat_g, ghat_o) <= 10 * eps
 
 
-def test_tensor_core_rejects_other_orders():
-    tree, _ = OT.build_tree(DENS2, 4, 1e-4, 2, uniform_level=2)
-    op_g = mra.make_operator(0.0, 1.0, 1e-4, 4, 2)
-    tg = gpu_tree_from_oracle(tree, 4)
+@pytest.mark.parametrize("k,eps", [(4, 1e-4), (6, 1e-5)])
+def test_apply_tensor_core_padded_orders(k, eps):
+    """Orders below 8 run on the same 8 x 8 MMA tiles with zero padding: the
+    padded rows and columns contribute nothing and the output keeps k^3."""
+    tree, _ = OT.build_tree(DENS2, k, eps, 3, init_level=1)
+    op_o = OO.Operator(0.0, 1.0, eps, k, 3)
+    op_g = mra.make_operator(0.0, 1.0, eps, k, 3)
+    _, _, _, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, k, precision="tc")
+    assert st_g["n_items"] == st_o["n_items"]
+    assert st_g["n_ghosts"] == st_o["n_refined"]
+    assert rel_l2(ghat_g, ghat_o) <= 10 * eps
+
+
+def test_tensor_core_rejects_orders_above_8():
+    tree, _ = OT.build_tree(DENS2, 10, 1e-4, 1, uniform_level=1)
+    op_g = mra.make_operator(0.0, 1.0, 1e-4, 10, 1)
+    tg = gpu_tree_from_oracle(tree, 10)
     mra.compress(tg)
     with pytest.raises(mra.MraError) as e:
         mra.apply_ns(op_g, tg, precision="tc")
