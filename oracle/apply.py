@@ -35,6 +35,12 @@ Readings of the passages the paper leaves open:
 * Optional per-block screen (``block_screen=True``, the per-block check the
   paper avoids): an item is also dropped when w_m prod_d nF(j,m,t_d)
   ||f_{a-t}|| <= eps ||T_0 f_0|| / sqrt(N_nodes * 216 * M).
+* Optional per-pair screen (``pair_screen=True``): the same per-item test
+  decides a term range per (output box, translation) pair -- from the first
+  to the last term that passes it -- and every term of the static schedule
+  inside that range is applied (a pair with no passing term is dropped).
+  This is the exact norm screen that judges the learned schedule's per-box
+  cut-offs, and ``screen_data`` returns its per-box targets.
 * Step 2: a missing input block is refined from its ancestor leaf with the
   d = 0 half of eqs. recon_even / recon_odd and cached.
 * Output skeleton: a copy of the input's redundant tree (Algorithm 2/3,
@@ -156,7 +162,13 @@ class _Inputs:
         return s
 
 
-def apply_ns(op, tree, block_screen=False, stats=None, nodes=None, screen=True):
+def _pair_terms(op, j, t, ms, xn, eta_blk):
+    # terms of ms whose bound w_m prod_d nF(j,m,t_d) ||x|| exceeds eta_blk
+    return [m for m in ms if op.w[m] * op.nF[j, m, t[0] + 3] * op.nF[j, m, t[1] + 3]
+            * op.nF[j, m, t[2] + 3] * xn > eta_blk]
+
+
+def apply_ns(op, tree, block_screen=False, stats=None, nodes=None, screen=True, pair_screen=False):
     """Algorithm 3, Steps 1-3: returns ghat (dict key -> (k,k,k)) on the
     skeleton of the compressed input tree.  ``nodes`` restricts the output
     boxes (for sampled checks); all nodes by default."""
@@ -167,7 +179,7 @@ def apply_ns(op, tree, block_screen=False, stats=None, nodes=None, screen=True):
     fnorm = T.norm2(tree)
     sigma = pilot_sigma(op, tree)
     sch = Schedule(op, sigma, fnorm, nlev, screen=screen)
-    eta_blk = op.eps * sigma / np.sqrt(len(tree) * 216.0 * op.M) if block_screen else -1.0
+    eta_blk = op.eps * sigma / np.sqrt(len(tree) * 216.0 * op.M) if (block_screen or pair_screen) else -1.0
     inp = _Inputs(tree, k)
     ghat = {}
     n_items = 0
@@ -185,12 +197,11 @@ def apply_ns(op, tree, block_screen=False, stats=None, nodes=None, screen=True):
             if not ms:
                 continue
             x = inp.get(j, b)
-            if block_screen:
-                xn = float(np.linalg.norm(x))
-                ms = [m for m in ms if op.w[m] * op.nF[j, m, t[0] + 3] * op.nF[j, m, t[1] + 3]
-                      * op.nF[j, m, t[2] + 3] * xn > eta_blk]
-                if not ms:
+            if block_screen or pair_screen:
+                keep = _pair_terms(op, j, t, ms, float(np.linalg.norm(x)), eta_blk)
+                if not keep:
                     continue
+                ms = keep if block_screen else [m for m in ms if keep[0] <= m <= keep[-1]]
             ms = np.array(ms)
             y += separated_apply(op.w[ms], op.F[j, ms, t[0] + 3], op.F[j, ms, t[1] + 3],
                                  op.F[j, ms, t[2] + 3], x)
@@ -202,6 +213,73 @@ def apply_ns(op, tree, block_screen=False, stats=None, nodes=None, screen=True):
                           eta=sch.eta, sigma=sigma, fnorm=fnorm, Jm=sch.Jm.copy(),
                           m1=sch.m1.copy(), m2=sch.m2.copy()))
     return ghat
+
+
+def screen_data(op, tree, J=None):
+    """Per-box inputs and targets of the learned schedule, from the static
+    screen and the exact per-pair screen on a compressed tree.
+
+    Features (16 per box, in this order): j / J; leaf flag;
+    log10(||s_a|| / eta_blk) / 10; for each class S = 0..3 the maximum and
+    the sum of ||x_b|| / eta_blk over the box's static pairs of that class,
+    each as log10(.) / 10 (0 when the class has no pair); the number of such
+    pairs / 64 per class; mu / 2.  eta_blk = eps ||T_0 f_0|| / sqrt(N 216 M).
+    Targets (12 per box): per class S, [E_S, LO_S, HI_S] with E_S = 1 when no
+    term of any pair of the class passes the exact test, else 0 and the first
+    / last passing term over the class's pairs divided by (M - 1) (0, 0 when
+    empty).  Returns (keys, X (n, 16), Y (n, 12)) in sorted key order."""
+    k, M = op.k, op.M
+    J = op.max_level if J is None else J
+    nlev = T.levels(tree)
+    fnorm = T.norm2(tree)
+    sigma = pilot_sigma(op, tree)
+    sch = Schedule(op, sigma, fnorm, nlev)
+    eta_blk = op.eps * sigma / np.sqrt(len(tree) * 216.0 * M)
+    inp = _Inputs(tree, k)
+    keys = sorted(tree.keys())
+    X = np.zeros((len(keys), 16))
+    Y = np.zeros((len(keys), 12))
+
+    def lg(v):
+        return np.log10(max(v, 1e-300)) / 10.0
+    for r, key in enumerate(keys):
+        j, a = key[0], key[1:]
+        leaf = tree[key].leaf
+        mx = np.zeros(4)
+        sm = np.zeros(4)
+        cnt = np.zeros(4)
+        lo = np.full(4, M)
+        hi = np.full(4, -1)
+        for t in band(a):
+            b = tuple(a[d] - t[d] for d in range(3))
+            if min(b) < 0 or max(b) >= 2 ** j:
+                continue
+            ms = sch.terms(j, t, leaf)
+            if not ms:
+                continue
+            S = sum(1 for v in t if abs(v) <= 1)
+            xn = float(np.linalg.norm(inp.get(j, b)))
+            mx[S] = max(mx[S], xn / eta_blk)
+            sm[S] += xn / eta_blk
+            cnt[S] += 1
+            keep = _pair_terms(op, j, t, ms, xn, eta_blk)
+            if keep:
+                lo[S] = min(lo[S], keep[0])
+                hi[S] = max(hi[S], keep[-1])
+        X[r, 0] = j / J
+        X[r, 1] = 1.0 if leaf else 0.0
+        X[r, 2] = lg(float(np.linalg.norm(tree[key].s)) / eta_blk)
+        for S in range(4):
+            X[r, 3 + S] = lg(mx[S]) if cnt[S] else 0.0
+            X[r, 7 + S] = lg(sm[S]) if cnt[S] else 0.0
+            X[r, 11 + S] = cnt[S] / 64.0
+            if hi[S] >= 0:
+                Y[r, 3 * S + 1] = lo[S] / (M - 1)
+                Y[r, 3 * S + 2] = hi[S] / (M - 1)
+            else:
+                Y[r, 3 * S] = 1.0
+        X[r, 15] = op.mu / 2.0
+    return keys, X, Y
 
 
 def assemble(op, tree, ghat):
