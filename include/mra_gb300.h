@@ -60,6 +60,7 @@ extern "C" {
 
 typedef struct mra_tree mra_tree;
 typedef struct mra_op mra_op;
+typedef struct mra_mlp mra_mlp;
 
 /* Device allocator hook: alloc returns device memory of `bytes` usable on
  * `stream` (NULL on failure); free releases it.  ctx is passed through. */
@@ -213,6 +214,22 @@ int mra_op_export(const mra_op* op, double* w_host, double* tau_host, double* F_
 #define MRA_PREC_TC_SPLIT 2   /* FP16 hi+lo split products on tcgen05 tensor   */
                               /* cores, FP32 accumulation, FP64 accumulation   */
                               /* into the output blocks                        */
+#define MRA_PREC_TC_LADDER 3  /* precision ladder on the tensor cores: per     */
+                              /* output node and term, single FP16 products    */
+                              /* (one MMA instead of three) when the term's    */
+                              /* bound w_m sum_items prod N_F ||f_b|| times    */
+                              /* 2^-8 fits the node's share of the budget      */
+                              /* eps ||T_0 f_0|| / (4 sqrt(N)), else FP16 hi+lo */
+
+/* Screens of the (output box, translation) pairs' term ranges.  The test of
+ * an item is w_m N_F(t1) N_F(t2) N_F(t3) ||f_b|| > eta_blk with
+ * eta_blk = eps ||T_0 f_0|| / sqrt(N 216 M) (Sec. 4's bound with the input
+ * block's own norm; Step-2 blocks after refinement). */
+#define MRA_SCREEN_STATIC  0  /* Sec. 4's ranges per scale and class only       */
+#define MRA_SCREEN_PAIR    1  /* exact: per pair, first..last passing term      */
+#define MRA_SCREEN_LEARNED 2  /* the network's per-box, per-class cut-offs,     */
+                              /* widened by `margin` terms, and every passing   */
+                              /* term outside them restored (a miss, counted)   */
 
 typedef struct {
     int precision;          /* MRA_PREC_*                                     */
@@ -222,7 +239,10 @@ typedef struct {
     int itemwise;           /* 1: SIMT paths apply each item's three mode     */
                             /* products separately instead of the nested sums */
                             /* of Algorithm 3 (same items; for comparison)    */
-    int reserved[4];
+    int screen_mode;        /* MRA_SCREEN_*                                   */
+    int margin;             /* learned screen: terms added on each side        */
+    int reserved[2];
+    const mra_mlp* schedule;  /* learned screen: a 16 -> 12 network (mra_mlp_*) */
 } mra_apply_opts;
 
 typedef struct {
@@ -234,6 +254,10 @@ typedef struct {
     double sigma;           /* ||T_0 f_0||                                     */
     double fnorm;           /* ||f||_2                                         */
     float ms_screen, ms_ghost, ms_apply; /* device times (CUDA events)         */
+    int64_t n_items_lowp;   /* items done with single FP16 products (ladder)   */
+    int64_t n_misses;       /* learned screen: passing items outside the      */
+                            /* prediction, restored by the exact test          */
+    int64_t n_pairs_empty;  /* pair / learned screens: pairs left with no term */
 } mra_apply_stats;
 
 int mra_apply_ns(const mra_op* op, const mra_tree* f, const mra_apply_opts* opts,
@@ -268,6 +292,55 @@ int mra_apply_ns_noalloc(const mra_op* op, const mra_tree* f, int precision, dou
                          void* stream, int64_t* n_items_host);
 
 /* ------------------------------------------------------------------------ */
+/* Learned schedule.  The paper has no learned part; this group trains and
+ * runs a small network that predicts, per output box, the term cut-offs of
+ * the exact per-pair screen (MRA_SCREEN_PAIR), so the apply can use them
+ * (MRA_SCREEN_LEARNED) with the exact test as the judge of every miss.
+ *
+ * Network: 3 hidden layers of 128 ReLU units, FP16 weights and activations,
+ * FP32 accumulation; FP32 master weights trained by Adam (beta 0.9 / 0.999,
+ * eps 1e-8).  Parameters, one FP32 vector: W1 [128][n_in], b1 [128],
+ * W2 [128][128], b2, W3 [128][128], b3, W4 [n_out][128], b4 [n_out],
+ * row-major.  Arrays x, y, target are device FP32, row-major [n][width].
+ *
+ * mra_mlp_create: params_host (n_params floats) or, when NULL, He-uniform
+ * weights from a splitmix64 stream seeded with `seed` and zero biases.
+ * Synchronous.
+ * mra_mlp_forward: y = network(x) for n rows (queued on `stream`).
+ * mra_mlp_loss_grad: the schedule loss (n_out must be 12; per class S
+ * [e_S, lo_S, hi_S] against [E_S, LO_S, HI_S]:
+ *   sum_S softplus(e_S) - E_S e_S + (1 - E_S)((lo_S - LO_S)^2 + (hi_S - HI_S)^2),
+ * averaged over the rows) and its gradient with respect to every parameter
+ * (grad_host: n_params floats, may be NULL).  Synchronous.
+ * mra_mlp_train_step: one Adam step on the batch's mean loss (queued; when
+ * loss_host is not NULL the call synchronises and returns the batch loss
+ * before the step).
+ * mra_screen_data: for a compressed tree, the network's 16 inputs per node
+ * and the exact screen's 12 targets per node (either pointer may be NULL),
+ * device FP32 [n_nodes][16] and [n_nodes][12] in node order:
+ *   inputs   j / max_level; leaf flag; log10(||s_a|| / eta_blk) / 10; per
+ *            class S = 0..3 the log10(.)/10 of the maximum and of the sum of
+ *            ||f_b|| / eta_blk over the box's pairs of that class (0 when
+ *            none); the number of such pairs / 64 per class; mu / 2;
+ *   targets  per class: [1, 0, 0] when no term of the class passes the exact
+ *            test, else [0, first / (M - 1), last / (M - 1)].
+ * Synchronous.  Errors as for mra_apply_ns. */
+#define MRA_SCHED_INPUTS  16
+#define MRA_SCHED_OUTPUTS 12
+int mra_mlp_create(int n_in, int n_out, const float* params_host, unsigned long long seed,
+                   const mra_alloc* alloc, void* stream, mra_mlp** out);
+int mra_mlp_num_params(const mra_mlp* net, int64_t* n_params);
+int mra_mlp_get_params(const mra_mlp* net, float* params_host, void* stream);
+int mra_mlp_set_params(mra_mlp* net, const float* params_host, void* stream);
+int mra_mlp_forward(const mra_mlp* net, const float* x, int64_t n, float* y, void* stream);
+int mra_mlp_loss_grad(mra_mlp* net, const float* x, const float* target, int64_t n, float* grad_host,
+                      double* loss_host, void* stream);
+int mra_mlp_train_step(mra_mlp* net, const float* x, const float* target, int64_t n, float lr,
+                       void* stream, double* loss_host);
+int mra_mlp_free(mra_mlp* net);
+int mra_screen_data(const mra_op* op, const mra_tree* f, float* inputs, float* targets, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Batched apply: one operator, many independent inputs.  The paper applies
  * the operator to one function at a time (Algorithm 3); this group is its
  * deployment form for many right-hand sides at once, with the same items
@@ -283,7 +356,8 @@ int mra_apply_ns_noalloc(const mra_op* op, const mra_tree* f, int precision, dou
  *   - trees: ntrees (>= 1) handles in MRA_TREE_REDUNDANT state, order k of op,
  *     depth <= op's max_level.
  *   - opts (may be NULL): precision (default MRA_PREC_TC_SPLIT for k <= 8,
- *     else MRA_PREC_FP64; the tensor-core path needs k <= 8) and use_graph
+ *     else MRA_PREC_FP64; the tensor-core paths MRA_PREC_TC_SPLIT and
+ *     MRA_PREC_TC_LADDER need k <= 8; the ladder's budget is per tree) and use_graph
  *     (default 1 when opts is NULL).
  * mra_plan_execute queues, on `stream`: the gather of every tree's current
  * blocks, the Step-2 refinement and one Step-3 launch over the nodes of all
@@ -292,16 +366,17 @@ int mra_apply_ns_noalloc(const mra_op* op, const mra_tree* f, int precision, dou
  * a stream the plan owns) and every execute launches that graph; `stream`
  * must not be capturing.  Executes on one plan must not overlap.
  * mra_plan_autotune (synchronous) times the tensor-core kernel variants on
- * the plan's worklist, reps launches each: terms per chunk 8 or 4, CTAs per
- * SM 2 or 1, node order as screened or heaviest first (most pairs).  The
- * fastest becomes the plan's variant (ms_variant[v], v = (mc==4) +
- * 2 (ctas==1) + 4 heavy_first); other precisions have one variant.
+ * the plan's worklist, reps launches each: (terms per chunk, CTAs per SM) in
+ * (8,2) (4,2) (8,1) (4,1) (4,3), node order as screened or heaviest first
+ * (most pairs).  The fastest becomes the plan's variant (ms_variant[v],
+ * v = pair index + 5 heavy_first); other precisions have one variant.
  * mra_plan_set_variant chooses one by hand.  Both drop a captured graph.
  * mra_plan_output copies the output of tree b (as of the last execute
  * queued before it on `stream`) into a new MRA_TREE_NSFORM tree.
  * mra_plan_get_info and mra_plan_tree_stats are synchronous; get_info also
  * reports a device error of past executes (MRA_ETIMEOUT, MRA_ECUDA). */
 typedef struct mra_plan mra_plan;
+#define MRA_PLAN_VARIANTS 10
 
 typedef struct {
     int precision;          /* MRA_PREC_*                                     */
@@ -320,10 +395,11 @@ typedef struct {
     int ctas_per_sm;
     int heavy_first;
     int tuned;              /* 1 after mra_plan_autotune                       */
-    float ms_variant[8];    /* autotune: mean apply-kernel time per variant    */
+    float ms_variant[MRA_PLAN_VARIANTS]; /* autotune: mean apply time per variant */
     int graph;              /* 1 when a captured graph exists                  */
     int graph_kernels;      /* kernels in one execute's graph                  */
     float ms_screen;        /* device time of the screen at creation           */
+    int64_t n_items_lowp;   /* items of the last execute done with single FP16 */
 } mra_plan_info;
 
 int mra_plan_create(const mra_op* op, mra_tree* const* trees, int ntrees, const mra_plan_opts* opts,

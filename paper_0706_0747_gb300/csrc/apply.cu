@@ -634,6 +634,23 @@ int ghost_refine_forest(const Forest& F, const ScreenOut& S, double* gblk, cudaS
     return MRA_OK;
 }
 
+// Precision ladder budget per tree: single-FP16 terms may add at most
+// eps sigma_b / (4 sqrt(N_b)) of rounding error to any node of tree b, so
+// over its N_b nodes at most eps sigma_b / 4 in the L2 norm (sigma_b =
+// ||T_0 f_0||, the pilot of ||g||).
+__global__ void k_lp_budget(Forest F, const double* dv, double eps, double* lpb) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < F.ntrees; b += gridDim.x * blockDim.x) {
+        const int nb = F.off[b * (F.lm + 1) + F.lm] - F.off[b * (F.lm + 1)];
+        lpb[b] = eps * dv[4 * b + 1] / (4.0 * sqrt((double)(nb > 0 ? nb : 1)));
+    }
+}
+
+int lp_budget(const Forest& F, const ScreenOut& S, double eps, double* lpb, cudaStream_t st) {
+    k_lp_budget<<<(F.ntrees + 127) / 128, 128, 0, st>>>(F, S.dv, eps, lpb);
+    MRA_CK_LAUNCH();
+    return MRA_OK;
+}
+
 Forest forest_of_tree(const mra_tree* f) {
     Forest F;
     F.k = f->k; F.ntrees = 1; F.n = f->n; F.lm = f->nlev;
@@ -649,11 +666,12 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     if (nlev - 1 > op->J) { set_error("tree depth %d exceeds operator max_level %d", nlev - 1, op->J); return MRA_EINVAL; }
     if (f->state != MRA_TREE_REDUNDANT) { set_error("apply_ns needs a compressed (redundant) tree"); return MRA_ESTATE; }
     const int prec = o ? o->precision : MRA_PREC_FP64;
-    if (prec != MRA_PREC_FP64 && prec != MRA_PREC_FP32 && prec != MRA_PREC_TC_SPLIT) {
+    if (prec != MRA_PREC_FP64 && prec != MRA_PREC_FP32 && prec != MRA_PREC_TC_SPLIT && prec != MRA_PREC_TC_LADDER) {
         set_error("precision %d is not available", prec);
         return MRA_EINVAL;
     }
-    if (prec == MRA_PREC_TC_SPLIT && ((o && (o->block_screen || o->itemwise)) || k > 8)) {
+    const bool tc = prec == MRA_PREC_TC_SPLIT || prec == MRA_PREC_TC_LADDER;
+    if (tc && ((o && (o->block_screen || o->itemwise)) || k > 8)) {
         set_error("the tensor-core apply needs k <= 8 and the static screen");
         return MRA_EINVAL;
     }
@@ -671,14 +689,28 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     double* gblk;
     MRA_TRY(dalloc(A, &gblk, (size_t)(S.nghost + 1) * k3));
     MRA_TRY(ghost_refine_forest(F, S, gblk, st));
+    // per-pair term ranges: the exact screen, or the learned one judged by it
+    const int smode = o ? o->screen_mode : MRA_SCREEN_STATIC;
+    unsigned long long* scounts = nullptr;
+    if (smode != MRA_SCREEN_STATIC) {
+        if (smode != MRA_SCREEN_PAIR && smode != MRA_SCREEN_LEARNED) {
+            set_error("screen mode %d is not available", smode);
+            return MRA_EINVAL;
+        }
+        MRA_TRY(dalloc(A, &scounts, 2));
+        MRA_CK(cudaMemsetAsync(scounts, 0, 2 * sizeof(unsigned long long), st));
+        MRA_TRY(schedule_narrow(op, F, S, gblk, smode, o->schedule, std::max(0, o->margin), nullptr, nullptr,
+                                scounts, A, st));
+    }
     MRA_CK(cudaEventRecord(ev[2], st));
 
     mra_tree* g = nullptr;
     MRA_TRY(tree_clone_skeleton(f, &g));
     g->state = MRA_TREE_NSFORM;
-    unsigned long long* nitems;
-    MRA_TRY(dalloc(A, &nitems, 1));
-    MRA_CK(cudaMemsetAsync(nitems, 0, sizeof(unsigned long long), st));
+    unsigned long long* nitems;  // [0] items, [1] items with single FP16 operands
+    MRA_TRY(dalloc(A, &nitems, 2));
+    MRA_CK(cudaMemsetAsync(nitems, 0, 2 * sizeof(unsigned long long), st));
+    double* lpb = nullptr;
 
     ApplyArgs aa;
     aa.k = k; aa.M = M; aa.n = n; aa.pairs = S.pairs; aa.pair_off = S.pair_off; aa.coord = f->a.coord;
@@ -692,9 +724,14 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         aa.eta_blk = op->eps * sig / sqrt((double)n * 216.0 * M);
     }
     const bool itemwise = (o && o->itemwise) || aa.eta_blk >= 0.0;
-    if (prec == MRA_PREC_TC_SPLIT) {
-        // tcgen05 FP16 hi/lo split products (apply_tc.cu)
-        MRA_TRY(launch_apply_tc(aa, S.nghost, op, S.err + 1, st));
+    if (tc) {
+        // tcgen05 FP16 hi/lo split products (apply_tc.cu); with the ladder,
+        // single FP16 products for the terms the error budget allows
+        if (prec == MRA_PREC_TC_LADDER) {
+            MRA_TRY(dalloc(A, &lpb, 1));
+            MRA_TRY(lp_budget(F, S, op->eps, lpb, st));
+        }
+        MRA_TRY(launch_apply_tc(aa, S.nghost, op, S.err + 1, lpb, nitems + 1, st));
     } else if (!itemwise) {
         // Algorithm 3's nested sums, factorised (apply_fact.cu)
         aa.F = prec == MRA_PREC_FP64 ? (const void*)op->F : (const void*)op->F32;
@@ -715,15 +752,23 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     MRA_CK(cudaEventRecord(ev[3], st));
 
     if (stats) {
-        unsigned long long ni = 0;
+        unsigned long long ni[2] = {0, 0};
         double hv[3];
         int32_t herr[2] = {0, 0};
-        MRA_CK(cudaMemcpyAsync(&ni, nitems, sizeof(ni), cudaMemcpyDeviceToHost, st));
+        MRA_CK(cudaMemcpyAsync(ni, nitems, sizeof(ni), cudaMemcpyDeviceToHost, st));
         MRA_CK(cudaMemcpyAsync(hv, S.dv, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
         MRA_CK(cudaMemcpyAsync(herr, S.err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         MRA_CK(cudaStreamSynchronize(st));
         stats->n_pairs = S.npairs;
-        stats->n_items = (int64_t)ni;
+        stats->n_items = (int64_t)ni[0];
+        stats->n_items_lowp = (int64_t)ni[1];
+        unsigned long long sc[2] = {0, 0};
+        if (scounts) {
+            MRA_CK(cudaMemcpyAsync(sc, scounts, sizeof(sc), cudaMemcpyDeviceToHost, st));
+            MRA_CK(cudaStreamSynchronize(st));
+        }
+        stats->n_misses = (int64_t)sc[0];
+        stats->n_pairs_empty = (int64_t)sc[1];
         stats->n_ghosts = S.nghost;
         stats->n_out_nodes = n;
         stats->fnorm = sqrt(hv[0]);
@@ -736,7 +781,7 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         else if (herr[0] || herr[1]) { set_error("screen/ghost error code %d/%d", herr[0], herr[1]); rc = MRA_ECUDA; }
     }
     screen_release(A, &S);
-    A.put(gblk); A.put(nitems);
+    A.put(gblk); A.put(nitems); A.put(lpb); A.put(scounts);
     for (int e = 0; e < 4; ++e) cudaEventDestroy(ev[e]);
     *gout = g;
     return rc;

@@ -40,10 +40,13 @@ struct TcArgs {
     const __half* xl;
     const float* sx;       // per-block power-of-two scale
     const float* xmax;     // per-block max |x|
+    const float* xnrm;     // per-block ||x||_2
     const __half* Fh;      // FP16 hi/lo operator blocks, 8 x 8, per (j, m, t)
     const __half* Fl;
     const float* sF;       // per-(j, m) scale
     const float* maxF;
+    const double* lpb;     // per-tree error budget of one node for single-FP16 terms (NULL: all hi+lo)
+    unsigned long long* n_lowp;  // items done with single FP16 operands (may be NULL)
     int* err;              // set to 4 when a completion wait reaches its limit
     int* counter;          // work counter (zeroed by tc_launch)
     const int* order;      // node order (NULL: 0..nwork-1)
@@ -53,7 +56,7 @@ struct TcArgs {
 
 struct TcBuffers {
     __half *xh = nullptr, *xl = nullptr, *Fh = nullptr, *Fl = nullptr;
-    float *sx = nullptr, *xmax = nullptr, *sF = nullptr, *maxF = nullptr;
+    float *sx = nullptr, *xmax = nullptr, *xnrm = nullptr, *sF = nullptr, *maxF = nullptr;
     int* counter = nullptr;
 };
 
@@ -105,6 +108,12 @@ TcArgs tc_args(const ApplyArgs& A, const TcBuffers& B, int* err);
 int tc_launch(const TcArgs& T, int mc, int ctas_per_sm, cudaStream_t st);
 
 int launch_apply_fact(const ApplyArgs& A, int precision, cudaStream_t st);
-int launch_apply_tc(const ApplyArgs& A, int nghost, const mra_op* op, int* err, cudaStream_t st);
+int launch_apply_tc(const ApplyArgs& A, int nghost, const mra_op* op, int* err, const double* lpb,
+                    unsigned long long* n_lowp, cudaStream_t st);
+int lp_budget(const Forest& F, const ScreenOut& S, double eps, double* lpb, cudaStream_t st);
+int schedule_narrow(const mra_op* op, const Forest& F, const ScreenOut& S, const double* gblk, int mode,
+                    const void* model, int margin, float* X_out, float* T_out, unsigned long long* counts,
+                    const Alloc& A, cudaStream_t st);
+int screen_data_impl(const mra_op* op, const mra_tree* f, float* X, float* T, cudaStream_t st);
 
 }  // namespace mra

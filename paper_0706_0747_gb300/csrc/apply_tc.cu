@@ -35,6 +35,10 @@ namespace mra {
 
 #define TC_THREADS 256
 #define TC_WAIT_LIMIT (1u << 26)
+// first-order bound on the relative error of one item done with single FP16
+// operands: six roundings to FP16 (x, W, V and the three F blocks, 2^-11
+// each) plus FP32 accumulation, rounded up to 8 * 2^-11
+#define LADDER_U 0.00390625
 
 // ---------------------------------------------------------------- prep
 // Input blocks -> FP16 hi/lo in the stage-I A layout: element x[i1][i2][i3]
@@ -42,22 +46,30 @@ namespace mra {
 // row i3, column i1), with a power-of-two scale per block.  Block b is node b
 // of s (b < n) or Step-2 block b - n.
 __global__ void k_tc_prep_blocks(int nb, int kr, int n, const double* s, const double* gblk, __half* xh,
-                                 __half* xl, float* sx, float* xmax) {
+                                 __half* xl, float* sx, float* xmax, float* xnrm) {
     __shared__ float red[4];
+    __shared__ double red2[4];
     const int b = blockIdx.x;
     if (b >= nb) return;
     const int k3 = kr * kr * kr;
     const double* src = b < n ? s + (size_t)b * k3 : gblk + (size_t)(b - n) * k3;
-    double v[4];
+    double v[4], s2 = 0.0;
     float m = 0.0f;
     for (int q = 0; q < 4; ++q) {
         const int idx = threadIdx.x + 128 * q;  // (i1, i2, i3) of the padded 8^3 block
         const int i1 = idx >> 6, i2 = (idx >> 3) & 7, i3 = idx & 7;
         v[q] = (i1 < kr && i2 < kr && i3 < kr) ? src[(i1 * kr + i2) * kr + i3] : 0.0;
         m = fmaxf(m, (float)fabs(v[q]));
+        s2 += v[q] * v[q];
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = m;
+        red2[threadIdx.x >> 5] = s2;
+    }
     __syncthreads();
     m = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
     int e = 0;
@@ -74,6 +86,7 @@ __global__ void k_tc_prep_blocks(int nb, int kr, int n, const double* s, const d
     if (threadIdx.x == 0) {
         sx[b] = (float)scale;
         xmax[b] = m;
+        xnrm[b] = (float)sqrt(red2[0] + red2[1] + red2[2] + red2[3]);
     }
 }
 
@@ -139,7 +152,7 @@ __device__ __forceinline__ float pow2floor(double x) {
     return ldexpf(1.0f, e);
 }
 
-template <int MC>
+template <int MC, bool LADDER>
 __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
     using L = TcSmem<MC>;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -151,6 +164,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
     __shared__ float s_c2[MC], s_c3[MC], s_g[6];
     __shared__ unsigned char s_lm[36], s_pm[6];
     __shared__ double s_fin[MC];
+    __shared__ float s_B[MC];
+    __shared__ unsigned char s_low[MC];
+    __shared__ int s_all_low;
+    __shared__ unsigned long long s_lowi;
 
     const ApplyArgs& A = T.A;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -209,6 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
         if (widx >= T.nwork) break;
         const int node = T.order ? T.order[widx] : widx;
         const int jm_base = A.node_tree ? A.node_tree[node] * A.jm_stride : 0;
+        const double lp_node = T.lpb ? T.lpb[A.node_tree ? A.node_tree[node] : 0] : 0.0;
         const int j = A.coord[4 * node];
         const int a1 = A.coord[4 * node + 1], a2 = A.coord[4 * node + 2], a3 = A.coord[4 * node + 3];
         const int p0 = A.pair_off[node], p1 = A.pair_off[node + 1];
@@ -219,6 +237,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
             s_exp_min = INT_MAX;
             s_xmax_bits = 0u;
             s_items = 0;
+            s_lowi = 0;
         }
         __syncthreads();
         for (int p = p0 + tid; p < p1; p += TC_THREADS) {
@@ -293,7 +312,27 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     s_c2[tid] = c2;
                     s_c3[tid] = c3;
                     s_fin[tid] = fin;
+                    s_B[tid] = 0.0f;
                 }
+                __syncthreads();
+                // precision ladder: B_m = w_m sum over the term's kept items of
+                // N_F(t1) N_F(t2) N_F(t3) ||x_b|| bounds its contribution to this node
+                if (LADDER)
+                    for (int e = tid; e < 36 * MC; e += TC_THREADS) {
+                        const unsigned mk = msk[e];
+                        if (!mk) continue;
+                        const int line = e / MC, mc = e % MC, m = m0 + mc;
+                        const double* nf = A.nF + ((size_t)j * A.M + m) * 7;
+                        float acc = 0.0f;
+                        for (int q1 = 0; q1 < 6; ++q1) {
+                            if (!((mk >> q1) & 1u)) continue;
+                            const int in = tin[q1 * 36 + line];
+                            const int b = in >= 0 ? in : A.n + (-1 - in);
+                            acc += (float)nf[band_t(a1, q1) + 3] * T.xnrm[b];
+                        }
+                        acc *= (float)(nf[band_t(a2, line / 6) + 3] * nf[band_t(a3, line % 6) + 3]);
+                        atomicAdd(&s_B[mc], acc);
+                    }
                 __syncthreads();
                 // per line: the union of its terms' kept-t1 masks; per plane: any line
                 if (tid < 36) {
@@ -307,7 +346,22 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     for (int q2 = 0; q2 < 6; ++q2) v |= s_lm[q2 * 6 + tid];
                     s_pm[tid] = (unsigned char)v;
                 }
+                if (LADDER && tid == 32) {
+                    // single FP16 products (hi only) for terms whose rounding error,
+                    // at most LADDER_U B_m, fits the node's share of the budget
+                    int all = 1;
+                    const double per_term = lp_node / (double)(mhi - mlo + 1);
+                    for (int mc = 0; mc < MC; ++mc) {
+                        const int m = m0 + mc;
+                        int low = 1;
+                        if (m <= mhi) low = T.lpb && LADDER_U * A.w[m] * (double)s_B[mc] <= per_term;
+                        s_low[mc] = (unsigned char)low;
+                        all &= low;
+                    }
+                    s_all_low = all;
+                }
                 __syncthreads();
+                const int all_low = LADDER ? s_all_low : 0;
                 int plane_started = 0;
                 for (int q3 = 0; q3 < 6 && !aborted; ++q3) {
                     if (!s_pm[q3]) continue;  // uniform
@@ -315,6 +369,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     // stage III B: K group 0 = F^{t3}[c3][i3] (8 uint4 per term)
                     for (int e = tid; e < 2 * MC * 8; e += TC_THREADS) {
                         const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
+                        if (LADDER && hl && s_low[mc]) continue;
                         const uint4* src = (const uint4*)(hl ? FSL : FSH) + (mc * 7 + t3 + 3) * 8 + v;
                         ((uint4*)(hl ? B3L : B3H))[mc * 16 + v] = *src;
                     }
@@ -339,6 +394,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                         }
                         for (int e = tid; e < 6 * 64 * 2; e += TC_THREADS) {
                             const int hl = e / 384, q1 = (e / 64) % 6, v = e % 64;  // 64 uint4 per 1 KB
+                            if (hl && all_low) continue;
                             uint4 val = make_uint4(0, 0, 0, 0);
                             if (lm & (1u << q1)) {
                                 const int in = tin[q1 * 36 + line];
@@ -350,6 +406,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                         // stage II B for this line: K group 0 = F^{t2}[c2][i2]
                         for (int e = tid; e < 2 * MC * 8; e += TC_THREADS) {
                             const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
+                            if (LADDER && hl && s_low[mc]) continue;
                             const uint4* src = (const uint4*)(hl ? FSL : FSH) + (mc * 7 + t2 + 3) * 8 + v;
                             ((uint4*)(hl ? B2L : B2H))[mc * 16 + v] = *src;
                         }
@@ -358,6 +415,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                         // one 16-byte core row per step (power-of-two g: exact in FP16)
                         for (int e = tid; e < 2 * MC * 6 * 8; e += TC_THREADS) {
                             const int hl = e / (MC * 48), mc = (e / 48) % MC, q1 = (e / 8) % 6, v = e % 8;
+                            if (hl && all_low) continue;
                             uint4 out = make_uint4(0, 0, 0, 0);
                             if ((msk[line * MC + mc] >> q1) & 1u) {
                                 const uint4 in = ((const uint4*)(hl ? FSL : FSH))[(mc * 7 + band_t(a1, q1) + 3) * 8 + v];
@@ -380,11 +438,17 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                                 const uint64_t bh = tc::sdesc(sbase + L::B1H + ks * 256, 128, 768);
                                 const uint64_t bl = tc::sdesc(sbase + L::B1L + ks * 256, 128, 768);
                                 tc::mma_f16(tD1, ah, bh, idI, ks > 0);
-                                tc::mma_f16(tD1, ah, bl, idI, 1);
-                                tc::mma_f16(tD1, al, bh, idI, 1);
+                                if (!all_low) {
+                                    tc::mma_f16(tD1, ah, bl, idI, 1);
+                                    tc::mma_f16(tD1, al, bh, idI, 1);
+                                }
                             }
                             tc::commit(&s_mbar);
-                            for (int mc = 0; mc < MC; ++mc) s_items += __popc(msk[line * MC + mc]);
+                            for (int mc = 0; mc < MC; ++mc) {
+                                const int c = __popc(msk[line * MC + mc]);
+                                s_items += c;
+                                if (LADDER && s_low[mc]) s_lowi += c;
+                            }
                         }
                         // also covers the previous line's stage II: A2 is free afterwards
                         TC_WAIT_OR_ABORT();
@@ -398,13 +462,19 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                             if (has_row) {
                                 const int i2 = row >> 3, i3 = row & 7;
                                 const float c2 = s_c2[mc];
+                                if (LADDER && s_low[mc]) {
 #pragma unroll
-                                for (int c1 = 0; c1 < 8; ++c1) {
-                                    __half h, l;
-                                    tc::split_h(v[c1] * c2, h, l);
-                                    const int o = mc * 1024 + c1 * 128 + i3 * 8 + i2;
-                                    A2H[o] = h;
-                                    A2L[o] = l;
+                                    for (int c1 = 0; c1 < 8; ++c1)
+                                        A2H[mc * 1024 + c1 * 128 + i3 * 8 + i2] = __float2half_rn(v[c1] * c2);
+                                } else {
+#pragma unroll
+                                    for (int c1 = 0; c1 < 8; ++c1) {
+                                        __half h, l;
+                                        tc::split_h(v[c1] * c2, h, l);
+                                        const int o = mc * 1024 + c1 * 128 + i3 * 8 + i2;
+                                        A2H[o] = h;
+                                        A2L[o] = l;
+                                    }
                                 }
                             }
                         }
@@ -421,8 +491,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                                 const uint64_t bh = tc::sdesc(b2 + mc * 256, 128, 256);
                                 const uint64_t bl = tc::sdesc(b2 + MC * 256 + mc * 256, 128, 256);
                                 tc::mma_f16(tD2 + mc * 8, ah, bh, idS, line_no > 0);
-                                tc::mma_f16(tD2 + mc * 8, ah, bl, idS, 1);
-                                tc::mma_f16(tD2 + mc * 8, al, bh, idS, 1);
+                                if (!LADDER || !s_low[mc]) {
+                                    tc::mma_f16(tD2 + mc * 8, ah, bl, idS, 1);
+                                    tc::mma_f16(tD2 + mc * 8, al, bh, idS, 1);
+                                }
                             }
                         }
                         ++line_no;
@@ -440,13 +512,19 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                         if (has_row) {
                             const int c1 = row >> 3, i3 = row & 7;
                             const float c3 = s_c3[mc];
+                            if (LADDER && s_low[mc]) {
 #pragma unroll
-                            for (int c2 = 0; c2 < 8; ++c2) {
-                                __half h, l;
-                                tc::split_h(v[c2] * c3, h, l);
-                                const int o = mc * 1024 + c1 * 128 + c2 * 8 + i3;
-                                A2H[o] = h;
-                                A2L[o] = l;
+                                for (int c2 = 0; c2 < 8; ++c2)
+                                    A2H[mc * 1024 + c1 * 128 + c2 * 8 + i3] = __float2half_rn(v[c2] * c3);
+                            } else {
+#pragma unroll
+                                for (int c2 = 0; c2 < 8; ++c2) {
+                                    __half h, l;
+                                    tc::split_h(v[c2] * c3, h, l);
+                                    const int o = mc * 1024 + c1 * 128 + c2 * 8 + i3;
+                                    A2H[o] = h;
+                                    A2L[o] = l;
+                                }
                             }
                         }
                     }
@@ -462,8 +540,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                             const uint64_t bh = tc::sdesc(sbase + L::B3H + mc * 256, 128, 256);
                             const uint64_t bl = tc::sdesc(sbase + L::B3L + mc * 256, 128, 256);
                             tc::mma_f16(tD3 + mc * 8, ah, bh, idS, plane_started);
-                            tc::mma_f16(tD3 + mc * 8, ah, bl, idS, 1);
-                            tc::mma_f16(tD3 + mc * 8, al, bh, idS, 1);
+                            if (!LADDER || !s_low[mc]) {
+                                tc::mma_f16(tD3 + mc * 8, ah, bl, idS, 1);
+                                tc::mma_f16(tD3 + mc * 8, al, bh, idS, 1);
+                            }
                         }
                         tc::commit(&s_mbar);
                     }
@@ -500,6 +580,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
             for (int c3 = 0; c3 < 8; ++c3)
                 if (c3 < kr) A.out[(size_t)node * kr * kr * kr + (c1 * kr + c2) * kr + c3] = y[c3] + ysm[row * 8 + c3];
         if (tid == 0 && A.n_items) atomicAdd(A.n_items + (A.node_tree ? A.node_tree[node] : 0), s_items);
+        if (tid == 0 && T.n_lowp && s_lowi) atomicAdd(T.n_lowp, s_lowi);
         __syncthreads();
     }
 #undef TC_WAIT_OR_ABORT
@@ -516,6 +597,7 @@ int tc_alloc(const mra_op* op, int nb, TcBuffers* B) {
     MRA_TRY(dalloc(Al, &B->xl, (size_t)nb * 512));
     MRA_TRY(dalloc(Al, &B->sx, nb));
     MRA_TRY(dalloc(Al, &B->xmax, nb));
+    MRA_TRY(dalloc(Al, &B->xnrm, nb));
     MRA_TRY(dalloc(Al, &B->Fh, JM * 7 * 64));
     MRA_TRY(dalloc(Al, &B->Fl, JM * 7 * 64));
     MRA_TRY(dalloc(Al, &B->sF, JM));
@@ -532,29 +614,32 @@ int tc_prep_F(const mra_op* op, const TcBuffers& B, cudaStream_t st) {
 
 int tc_prep_blocks(int nb, int kr, int n, const double* s, const double* gblk, const TcBuffers& B, cudaStream_t st) {
     if (nb <= 0) return MRA_OK;
-    k_tc_prep_blocks<<<nb, 128, 0, st>>>(nb, kr, n, s, gblk, B.xh, B.xl, B.sx, B.xmax);
+    k_tc_prep_blocks<<<nb, 128, 0, st>>>(nb, kr, n, s, gblk, B.xh, B.xl, B.sx, B.xmax, B.xnrm);
     MRA_CK_LAUNCH();
     return MRA_OK;
 }
 
 void tc_release(const mra_op* op, TcBuffers* B) {
     const Alloc& Al = op->A;
-    Al.put(B->xh); Al.put(B->xl); Al.put(B->sx); Al.put(B->xmax);
+    Al.put(B->xh); Al.put(B->xl); Al.put(B->sx); Al.put(B->xmax); Al.put(B->xnrm);
     Al.put(B->Fh); Al.put(B->Fl); Al.put(B->sF); Al.put(B->maxF); Al.put(B->counter);
     *B = TcBuffers();
 }
 
 // dynamic shared memory of both chunk sizes (outside any stream capture)
 int tc_configure() {
-    MRA_CK(cudaFuncSetAttribute(k_apply_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<4>::TOTAL));
-    MRA_CK(cudaFuncSetAttribute(k_apply_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<8>::TOTAL));
+    MRA_CK(cudaFuncSetAttribute(k_apply_tc<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<4>::TOTAL));
+    MRA_CK(cudaFuncSetAttribute(k_apply_tc<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<8>::TOTAL));
+    MRA_CK(cudaFuncSetAttribute(k_apply_tc<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<4>::TOTAL));
+    MRA_CK(cudaFuncSetAttribute(k_apply_tc<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<8>::TOTAL));
     return MRA_OK;
 }
 
 template <int MC>
 static int launch_mc(const TcArgs& T, int ctas_per_sm, cudaStream_t st) {
     const int grid = std::max(1, std::min(T.nwork, 152 * ctas_per_sm));
-    k_apply_tc<MC><<<grid, TC_THREADS, TcSmem<MC>::TOTAL, st>>>(T);
+    if (T.lpb) k_apply_tc<MC, true><<<grid, TC_THREADS, TcSmem<MC>::TOTAL, st>>>(T);
+    else k_apply_tc<MC, false><<<grid, TC_THREADS, TcSmem<MC>::TOTAL, st>>>(T);
     MRA_CK_LAUNCH();
     return MRA_OK;
 }
@@ -570,7 +655,9 @@ int tc_launch(const TcArgs& T, int mc, int ctas_per_sm, cudaStream_t st) {
 TcArgs tc_args(const ApplyArgs& A, const TcBuffers& B, int* err) {
     TcArgs T;
     T.A = A;
-    T.xh = B.xh; T.xl = B.xl; T.sx = B.sx; T.xmax = B.xmax;
+    T.xh = B.xh; T.xl = B.xl; T.sx = B.sx; T.xmax = B.xmax; T.xnrm = B.xnrm;
+    T.lpb = nullptr;
+    T.n_lowp = nullptr;
     T.Fh = B.Fh; T.Fl = B.Fl; T.sF = B.sF; T.maxF = B.maxF;
     T.err = err;  // the apply's error word: a wait that reaches its limit writes 4
     T.counter = B.counter;
@@ -580,7 +667,8 @@ TcArgs tc_args(const ApplyArgs& A, const TcBuffers& B, int* err) {
     return T;
 }
 
-int launch_apply_tc(const ApplyArgs& A, int nghost, const mra_op* op, int* err, cudaStream_t st) {
+int launch_apply_tc(const ApplyArgs& A, int nghost, const mra_op* op, int* err, const double* lpb,
+                    unsigned long long* n_lowp, cudaStream_t st) {
     if (A.k > 8) {
         set_error("the tensor-core apply supports k <= 8 (got k = %d)", A.k);
         return MRA_EINVAL;
@@ -590,7 +678,10 @@ int launch_apply_tc(const ApplyArgs& A, int nghost, const mra_op* op, int* err, 
     MRA_TRY(tc_prep_F(op, B, st));
     MRA_TRY(tc_prep_blocks(A.n + nghost, A.k, A.n, A.s, A.gblk, B, st));
     MRA_TRY(tc_configure());
-    MRA_TRY(tc_launch(tc_args(A, B, err), 8, 2, st));
+    TcArgs T = tc_args(A, B, err);
+    T.lpb = lpb;
+    T.n_lowp = n_lowp;
+    MRA_TRY(tc_launch(T, 8, 2, st));
     tc_release(op, &B);  // stream-ordered frees: released after the kernel completes
     return MRA_OK;
 }

@@ -227,6 +227,11 @@ int mra_apply_ns_noalloc(const mra_op* op, const mra_tree* f, int precision, dou
     return apply_noalloc_impl(op, f, precision, ghat_out, (cudaStream_t)stream, n_items_host);
 }
 
+int mra_screen_data(const mra_op* op, const mra_tree* f, float* inputs, float* targets, void* stream) {
+    if (!op_ok(op) || !tree_ok(f)) { set_error("invalid operator or tree handle"); return MRA_EINVAL; }
+    return screen_data_impl(op, f, inputs, targets, (cudaStream_t)stream);
+}
+
 int mra_reconstruct(mra_tree* t, int mode, int truncate, double eps, void* stream, double* truncation_l2_host) {
     if (!tree_ok(t)) { set_error("invalid tree handle"); return MRA_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;

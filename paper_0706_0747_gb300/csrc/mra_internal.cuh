@@ -122,6 +122,8 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
                mra_tree** g, mra_apply_stats* stats);
 int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, double* ghat, cudaStream_t st,
                        int64_t* n_items_host);
+// schedule.cu
+int screen_data_impl(const mra_op* op, const mra_tree* f, float* X, float* T, cudaStream_t st);
 
 // ---------------------------------------------------------------- device helpers
 __host__ __device__ inline uint64_t spread3(uint32_t v) {

@@ -85,12 +85,14 @@ struct mra_plan {
     mra::ScreenOut S;
     double* gblk = nullptr;
     double* out = nullptr;
-    unsigned long long* nitems = nullptr;  // per tree
+    unsigned long long* nitems = nullptr;  // per tree, then the single-FP16 items of all trees
+    double* lpb = nullptr;                 // precision-ladder budgets per tree
+    bool tc = false;
     mra::TcBuffers tcb;
     int32_t* order_heavy = nullptr;
     // apply variant
     int mc = 8, ctas = 2, use_order = 0;
-    float ms_variant[8] = {0};
+    float ms_variant[MRA_PLAN_VARIANTS] = {0};
     int tuned = 0;
     float ms_screen = 0.0f;
     // graph
@@ -120,6 +122,8 @@ static int plan_tc_launch(const mra_plan* p, int mc, int ctas, int ordered, cuda
     plan_apply_args(p, &aa);
     TcArgs T = tc_args(aa, p->tcb, p->S.err + 1);
     T.order = ordered ? p->order_heavy : nullptr;
+    T.lpb = p->lpb;
+    T.n_lowp = p->nitems + p->ntrees;
     return tc_launch(T, mc, ctas, st);
 }
 
@@ -131,8 +135,8 @@ static int plan_enqueue(const mra_plan* p, cudaStream_t st) {
     k_forest_blocks<<<nb, 256, 0, st>>>(p->n, k3, p->dbase, p->node_tree, p->tref, p->s);
     MRA_CK_LAUNCH();
     MRA_TRY(ghost_refine_forest(p->F, p->S, p->gblk, st));
-    MRA_CK(cudaMemsetAsync(p->nitems, 0, (size_t)p->ntrees * sizeof(unsigned long long), st));
-    if (p->precision == MRA_PREC_TC_SPLIT) {
+    MRA_CK(cudaMemsetAsync(p->nitems, 0, ((size_t)p->ntrees + 1) * sizeof(unsigned long long), st));
+    if (p->tc) {
         MRA_TRY(tc_prep_blocks(p->n + p->S.nghost, p->k, p->n, p->s, p->gblk, p->tcb, st));
         MRA_TRY(plan_tc_launch(p, p->mc, p->ctas, p->use_order, st));
     } else {
@@ -159,7 +163,7 @@ static void plan_release(mra_plan* p) {
     if (p->op) tc_release(p->op, &p->tcb);
     A.put(p->tref); A.put(p->dbase); A.put(p->coord); A.put(p->leaf); A.put(p->off); A.put(p->node_tree);
     A.put(p->nlev); A.put(p->key); A.put(p->s); A.put(p->gblk); A.put(p->out); A.put(p->nitems);
-    A.put(p->order_heavy);
+    A.put(p->order_heavy); A.put(p->lpb);
     p->magic = 0;
     delete p;
 }
@@ -215,8 +219,12 @@ static int plan_build(mra_plan* p, cudaStream_t st) {
 
     MRA_TRY(dalloc(A, &p->gblk, (size_t)(p->S.nghost + 1) * k3));
     MRA_TRY(dalloc(A, &p->out, (size_t)n * k3));
-    MRA_TRY(dalloc(A, &p->nitems, nt));
-    MRA_CK(cudaMemsetAsync(p->nitems, 0, nt * sizeof(unsigned long long), st));
+    MRA_TRY(dalloc(A, &p->nitems, (size_t)nt + 1));
+    MRA_CK(cudaMemsetAsync(p->nitems, 0, ((size_t)nt + 1) * sizeof(unsigned long long), st));
+    if (p->precision == MRA_PREC_TC_LADDER) {
+        MRA_TRY(dalloc(A, &p->lpb, nt));
+        MRA_TRY(lp_budget(F, p->S, op->eps, p->lpb, st));
+    }
 
     // heaviest-first node order: counting sort of the per-node pair counts
     std::vector<int32_t> cnt(n), order(n);
@@ -229,7 +237,7 @@ static int plan_build(mra_plan* p, cudaStream_t st) {
     MRA_TRY(dalloc(A, &p->order_heavy, n));
     MRA_CK(cudaMemcpyAsync(p->order_heavy, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
 
-    if (p->precision == MRA_PREC_TC_SPLIT) {
+    if (p->tc) {
         MRA_TRY(tc_alloc(op, n + p->S.nghost, &p->tcb));
         MRA_TRY(tc_prep_F(op, p->tcb, st));
         MRA_TRY(tc_configure());
@@ -254,11 +262,12 @@ int mra_plan_create(const mra_op* op, mra_tree* const* trees, int ntrees, const 
     if (!op || op->magic != MRA_OP_MAGIC) { set_error("invalid operator handle"); return MRA_EINVAL; }
     if (!trees || ntrees < 1 || ntrees >= (1 << 22)) { set_error("ntrees must lie in [1, 2^22)"); return MRA_EINVAL; }
     const int prec = opts ? opts->precision : (op->k <= 8 ? MRA_PREC_TC_SPLIT : MRA_PREC_FP64);
-    if (prec != MRA_PREC_FP64 && prec != MRA_PREC_FP32 && prec != MRA_PREC_TC_SPLIT) {
+    if (prec != MRA_PREC_FP64 && prec != MRA_PREC_FP32 && prec != MRA_PREC_TC_SPLIT && prec != MRA_PREC_TC_LADDER) {
         set_error("precision %d is not available", prec);
         return MRA_EINVAL;
     }
-    if (prec == MRA_PREC_TC_SPLIT && op->k > 8) { set_error("the tensor-core apply needs k <= 8"); return MRA_EINVAL; }
+    const bool tc = prec == MRA_PREC_TC_SPLIT || prec == MRA_PREC_TC_LADDER;
+    if (tc && op->k > 8) { set_error("the tensor-core apply needs k <= 8"); return MRA_EINVAL; }
     long long total = 0;
     int lm = 0;
     for (int b = 0; b < ntrees; ++b) {
@@ -280,6 +289,7 @@ int mra_plan_create(const mra_op* op, mra_tree* const* trees, int ntrees, const 
     p->n = (int)total;
     p->lm = lm;
     p->precision = prec;
+    p->tc = tc;
     p->use_graph = opts ? (opts->use_graph != 0) : 1;
     p->A = trees[0]->A;
     p->A.stream = st;
@@ -328,7 +338,7 @@ int mra_plan_execute(mra_plan* p, void* stream) {
 int mra_plan_autotune(mra_plan* p, int reps, void* stream) {
     if (!plan_ok(p)) { set_error("invalid plan handle"); return MRA_EINVAL; }
     if (reps < 1) { set_error("reps must be >= 1"); return MRA_EINVAL; }
-    if (p->precision != MRA_PREC_TC_SPLIT) return MRA_OK;  // one variant only
+    if (!p->tc) return MRA_OK;  // one variant only
     cudaStream_t st = (cudaStream_t)stream;
     plan_drop_graph(p);
     // operands of the current blocks, then each variant timed on its own
@@ -343,8 +353,10 @@ int mra_plan_autotune(mra_plan* p, int reps, void* stream) {
     MRA_CK(cudaEventCreate(&e0));
     MRA_CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int v = 0; v < 8; ++v) {
-        const int mc = (v & 1) ? 4 : 8, ctas = (v & 2) ? 1 : 2, ord = (v >> 2) & 1;
+    // (terms per chunk, CTAs per SM): 8 x 3 does not fit the shared memory
+    static const int kMC[5] = {8, 4, 8, 4, 4}, kCTA[5] = {2, 2, 1, 1, 3};
+    for (int v = 0; v < MRA_PLAN_VARIANTS; ++v) {
+        const int mc = kMC[v % 5], ctas = kCTA[v % 5], ord = v / 5;
         MRA_TRY(plan_tc_launch(p, mc, ctas, ord, st));  // warm-up
         MRA_CK(cudaEventRecord(e0, st));
         for (int r = 0; r < reps; ++r) MRA_TRY(plan_tc_launch(p, mc, ctas, ord, st));
@@ -369,8 +381,8 @@ int mra_plan_autotune(mra_plan* p, int reps, void* stream) {
 
 int mra_plan_set_variant(mra_plan* p, int mc, int ctas_per_sm, int heavy_first) {
     if (!plan_ok(p)) { set_error("invalid plan handle"); return MRA_EINVAL; }
-    if ((mc != 4 && mc != 8) || (ctas_per_sm != 1 && ctas_per_sm != 2)) {
-        set_error("variant: terms per chunk must be 4 or 8 and CTAs per SM 1 or 2");
+    if ((mc != 4 && mc != 8) || ctas_per_sm < 1 || ctas_per_sm > (mc == 4 ? 3 : 2)) {
+        set_error("variant: terms per chunk 8 with 1-2 CTAs per SM, or 4 with 1-3");
         return MRA_EINVAL;
     }
     plan_drop_graph(p);
@@ -404,9 +416,10 @@ int mra_plan_output(const mra_plan* p, int b, void* stream, mra_tree** g_ns) {
 int mra_plan_get_info(const mra_plan* p, mra_plan_info* info, void* stream) {
     if (!plan_ok(p) || !info) { set_error("invalid plan handle"); return MRA_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<unsigned long long> ni(p->ntrees);
+    std::vector<unsigned long long> ni(p->ntrees + 1);
     int32_t herr[2] = {0, 0};
-    MRA_CK(cudaMemcpyAsync(ni.data(), p->nitems, p->ntrees * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaMemcpyAsync(ni.data(), p->nitems, (p->ntrees + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           st));
     MRA_CK(cudaMemcpyAsync(herr, p->S.err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MRA_CK(cudaStreamSynchronize(st));
     memset(info, 0, sizeof(*info));
@@ -415,12 +428,13 @@ int mra_plan_get_info(const mra_plan* p, mra_plan_info* info, void* stream) {
     info->n_pairs = p->S.npairs;
     info->n_ghosts = p->S.nghost;
     for (int b = 0; b < p->ntrees; ++b) info->n_items += (int64_t)ni[b];
+    info->n_items_lowp = (int64_t)ni[p->ntrees];
     info->precision = p->precision;
     info->terms_per_chunk = p->mc;
     info->ctas_per_sm = p->ctas;
     info->heavy_first = p->use_order;
     info->tuned = p->tuned;
-    for (int v = 0; v < 8; ++v) info->ms_variant[v] = p->ms_variant[v];
+    for (int v = 0; v < MRA_PLAN_VARIANTS; ++v) info->ms_variant[v] = p->ms_variant[v];
     info->graph = p->gexec != nullptr;
     info->graph_kernels = (int)p->graph_kernels;
     info->ms_screen = p->ms_screen;

@@ -1,0 +1,261 @@
+// Per-pair term cut-offs: the exact per-pair screen, the learned schedule's
+// inputs and targets, and the learned cut-offs with the exact screen as the
+// judge of every miss.
+//
+// Exact test of an item (a, t, m) (the norm bound of Sec. 4 with the input
+// block's own norm): w_m N_F(j,m,t1) N_F(j,m,t2) N_F(j,m,t3) ||f_{a-t}|| >
+// eta_blk, eta_blk = eps ||T_0 f_0|| / sqrt(N 216 M).  Per (output box,
+// translation) pair the static schedule's term range (Sec. 4, per scale and
+// Core/Boundary class) becomes:
+//   exact screen    the first .. last term that passes (empty if none);
+//   learned screen  the network's predicted range for the box and class,
+//                   widened by a margin, clipped to the static range, and
+//                   extended to every term that passes the exact test (a
+//                   passing term outside the prediction is a miss: counted
+//                   and restored).
+// Every term of the static schedule inside the final range is applied.
+#include <math.h>
+
+#include "apply_common.cuh"
+
+namespace mra {
+
+const mra_mlp* mlp_checked(const void* h);
+int mlp_forward(const mra_mlp* M, const float* x, int64_t n, float* y, const Alloc& A, cudaStream_t st);
+int mlp_n_in(const mra_mlp* M);
+int mlp_n_out(const mra_mlp* M);
+
+#define EMPTY_LO 32767
+
+// ||block||_2 in FP64 for the n node blocks then the Step-2 blocks; warp per block
+__global__ void k_block_norms(int nb, int n, int k3, const double* s, const double* gblk, double* bn) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int b = warp; b < nb; b += nwarps) {
+        const double* x = b < n ? s + (size_t)b * k3 : gblk + (size_t)(b - n) * k3;
+        double acc = 0.0;
+        for (int e = lane; e < k3; e += 32) acc += x[e] * x[e];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) bn[b] = sqrt(acc);
+    }
+}
+
+// eta_blk per tree from the pilot: eps sigma_b / sqrt(N_b 216 M)
+__global__ void k_eta_blk(Forest F, const double* dv, double eps, int M, double* etab) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < F.ntrees; b += gridDim.x * blockDim.x) {
+        const int nb = F.off[b * (F.lm + 1) + F.lm] - F.off[b * (F.lm + 1)];
+        etab[b] = eps * dv[4 * b + 1] / sqrt((double)nb * 216.0 * M);
+    }
+}
+
+__device__ inline int pair_class(const Pair& p) {
+    return (abs((int)p.t1) <= 1) + (abs((int)p.t2) <= 1) + (abs((int)p.t3) <= 1);
+}
+
+__device__ inline float lg10s(double v) { return (float)(log10(fmax(v, 1e-300)) / 10.0); }
+
+// 16 features per output box (thread per box; pairs in band order)
+__global__ void k_sched_features(Forest F, const int32_t* pair_off, const Pair* pairs, const double* bn,
+                                 const double* etab, int J, double mu, float* X) {
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < F.n; a += gridDim.x * blockDim.x) {
+        const int tree = F.node_tree ? F.node_tree[a] : 0;
+        const double eta = etab[tree];
+        double mx[4] = {0, 0, 0, 0}, sm[4] = {0, 0, 0, 0};
+        int cnt[4] = {0, 0, 0, 0};
+        for (int p = pair_off[a]; p < pair_off[a + 1]; ++p) {
+            const Pair pr = pairs[p];
+            const int S = pair_class(pr);
+            const double xn = bn[pr.in >= 0 ? pr.in : F.n + (-1 - pr.in)];
+            mx[S] = fmax(mx[S], xn / eta);
+            sm[S] += xn / eta;
+            cnt[S]++;
+        }
+        float* x = X + (size_t)a * 16;
+        x[0] = (float)((double)F.coord[4 * a] / J);
+        x[1] = F.leaf[a] ? 1.0f : 0.0f;
+        x[2] = lg10s(bn[a] / eta);
+        for (int S = 0; S < 4; ++S) {
+            x[3 + S] = cnt[S] ? lg10s(mx[S]) : 0.0f;
+            x[7 + S] = cnt[S] ? lg10s(sm[S]) : 0.0f;
+            x[11 + S] = (float)(cnt[S] / 64.0);
+        }
+        x[15] = (float)(mu / 2.0);
+    }
+}
+
+struct RangeArgs {
+    Forest F;
+    int M, sl, npairs, margin;
+    Pair* pairs;
+    const int32_t* sched;
+    const double* w;
+    const double* nF;
+    const double* bn;
+    const double* etab;
+    const float* pred;            // [n][12] network outputs (NULL: exact screen)
+    int32_t* tlo;                 // [n][4] first / last passing term per class (NULL: not kept)
+    int32_t* thi;
+    unsigned long long* counts;   // [0] misses (passing items outside the prediction), [1] empty pairs
+};
+
+// thread per pair: narrow its term range in place
+__global__ void k_pair_ranges(RangeArgs R) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R.npairs) return;
+    Pair p = R.pairs[i];
+    const int a = p.out, tree = R.F.node_tree ? R.F.node_tree[a] : 0;
+    const int j = R.F.coord[4 * a];
+    const int32_t* Jm = R.sched + (size_t)tree * R.sl;
+    const double xn = R.bn[p.in >= 0 ? p.in : R.F.n + (-1 - p.in)];
+    const double eta = R.etab[tree];
+    const int S = pair_class(p);
+    // the prediction for this box and class
+    int plo = 0, phi = -1;
+    if (R.pred) {
+        const float* y = R.pred + (size_t)a * 12 + 3 * S;
+        if (!(y[0] > 0.0f)) {  // P(empty) < 1/2
+            plo = (int)floorf(y[1] * (R.M - 1)) - R.margin;
+            phi = (int)ceilf(y[2] * (R.M - 1)) + R.margin;
+        }
+        plo = max(plo, (int)p.m_lo);
+        phi = min(phi, (int)p.m_hi);
+    }
+    int first = EMPTY_LO, last = -1;
+    unsigned long long miss = 0;
+    for (int m = p.m_lo; m <= p.m_hi; ++m) {
+        const int jm = Jm[m];
+        if (jm < j) continue;
+        if ((p.flags & 1) && jm > j) continue;
+        const size_t fb = ((size_t)j * R.M + m) * 7;
+        const double est = R.w[m] * R.nF[fb + p.t1 + 3] * R.nF[fb + p.t2 + 3] * R.nF[fb + p.t3 + 3] * xn;
+        if (est > eta) {
+            first = min(first, m);
+            last = m;
+            if (R.pred && (m < plo || m > phi)) ++miss;
+        }
+    }
+    if (R.tlo && last >= 0) {
+        atomicMin(&R.tlo[a * 4 + S], first);
+        atomicMax(&R.thi[a * 4 + S], last);
+    }
+    int lo = first, hi = last;
+    if (R.pred && phi >= plo) {
+        lo = min(lo, plo);
+        hi = max(hi, phi);
+    }
+    if (hi < lo) {
+        lo = EMPTY_LO;
+        hi = -1;
+        if (R.counts) atomicAdd(&R.counts[1], 1ull);
+    }
+    p.m_lo = (int16_t)lo;
+    p.m_hi = (int16_t)hi;
+    R.pairs[i] = p;
+    if (R.counts && miss) atomicAdd(&R.counts[0], miss);
+}
+
+__global__ void k_targets(int n, int M, const int32_t* tlo, const int32_t* thi, float* T) {
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x)
+        for (int S = 0; S < 4; ++S) {
+            const int hi = thi[a * 4 + S];
+            float* t = T + (size_t)a * 12 + 3 * S;
+            if (hi < 0) {
+                t[0] = 1.0f;
+                t[1] = 0.0f;
+                t[2] = 0.0f;
+            } else {
+                t[0] = 0.0f;
+                t[1] = (float)((double)tlo[a * 4 + S] / (M - 1));
+                t[2] = (float)((double)hi / (M - 1));
+            }
+        }
+}
+
+__global__ void k_fill_i32v(int32_t* p, int n, int32_t v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+// Narrow the screened pairs' term ranges (after Step 2: the refined blocks'
+// norms are known).  mode 1: exact screen; mode 2: learned screen with the
+// exact judge.  X/targets (optional, device): the network's inputs and the
+// exact screen's targets.  counts (device, 2): misses, empty pairs.
+int schedule_narrow(const mra_op* op, const Forest& F, const ScreenOut& S, const double* gblk, int mode,
+                    const void* model, int margin, float* X_out, float* T_out, unsigned long long* counts,
+                    const Alloc& A, cudaStream_t st) {
+    const int k3 = F.k * F.k * F.k, n = F.n, nb = n + S.nghost;
+    const mra_mlp* M = nullptr;
+    if (mode == 2) {
+        M = mlp_checked(model);
+        if (!M) { set_error("the learned screen needs a network handle"); return MRA_EINVAL; }
+        if (mlp_n_in(M) != 16 || mlp_n_out(M) != 12) { set_error("the schedule network must map 16 inputs to 12 outputs"); return MRA_EINVAL; }
+    }
+    double *bn, *etab;
+    MRA_TRY(dalloc(A, &bn, (size_t)nb));
+    MRA_TRY(dalloc(A, &etab, (size_t)F.ntrees));
+    k_block_norms<<<std::max(1, std::min(152 * 16, (nb * 32 + 255) / 256)), 256, 0, st>>>(nb, n, k3, F.s, gblk, bn);
+    MRA_CK_LAUNCH();
+    k_eta_blk<<<(F.ntrees + 127) / 128, 128, 0, st>>>(F, S.dv, op->eps, op->M, etab);
+    MRA_CK_LAUNCH();
+    float* X = X_out;
+    float* Y = nullptr;
+    if (mode == 2 && !X) MRA_TRY(dalloc(A, &X, (size_t)n * 16));
+    if (X) {
+        k_sched_features<<<(n + 127) / 128, 128, 0, st>>>(F, S.pair_off, S.pairs, bn, etab, op->J, op->mu, X);
+        MRA_CK_LAUNCH();
+    }
+    if (mode == 2) {
+        MRA_TRY(dalloc(A, &Y, (size_t)n * 12));
+        MRA_TRY(mlp_forward(M, X, n, Y, A, st));
+    }
+    int32_t *tlo = nullptr, *thi = nullptr;
+    if (T_out) {
+        MRA_TRY(dalloc(A, &tlo, (size_t)n * 4));
+        MRA_TRY(dalloc(A, &thi, (size_t)n * 4));
+        k_fill_i32v<<<(n * 4 + 255) / 256, 256, 0, st>>>(tlo, n * 4, EMPTY_LO);
+        MRA_CK_LAUNCH();
+        k_fill_i32v<<<(n * 4 + 255) / 256, 256, 0, st>>>(thi, n * 4, -1);
+        MRA_CK_LAUNCH();
+    }
+    RangeArgs R;
+    R.F = F; R.M = op->M; R.sl = S.sl; R.npairs = S.npairs; R.margin = margin;
+    R.pairs = S.pairs; R.sched = S.sched; R.w = op->w; R.nF = op->nF; R.bn = bn; R.etab = etab;
+    R.pred = Y; R.tlo = tlo; R.thi = thi; R.counts = counts;
+    if (S.npairs > 0) {
+        k_pair_ranges<<<(S.npairs + 255) / 256, 256, 0, st>>>(R);
+        MRA_CK_LAUNCH();
+    }
+    if (T_out) {
+        k_targets<<<(n + 127) / 128, 128, 0, st>>>(n, op->M, tlo, thi, T_out);
+        MRA_CK_LAUNCH();
+    }
+    A.put(bn); A.put(etab); A.put(Y); A.put(tlo); A.put(thi);
+    if (X != X_out) A.put(X);
+    return MRA_OK;
+}
+
+int screen_data_impl(const mra_op* op, const mra_tree* f, float* X, float* T, cudaStream_t st) {
+    const int k3 = op->k * op->k * op->k;
+    if (f->k != op->k) { set_error("tree order k=%d differs from operator k=%d", f->k, op->k); return MRA_EINVAL; }
+    if (f->nlev - 1 > op->J) { set_error("tree depth %d exceeds operator max_level %d", f->nlev - 1, op->J); return MRA_EINVAL; }
+    if (f->state != MRA_TREE_REDUNDANT) { set_error("screen data needs a compressed (redundant) tree"); return MRA_ESTATE; }
+    const Alloc& A = f->A;
+    const Forest F = forest_of_tree(f);
+    ScreenOut S;
+    int rc = screen_forest(op, F, 0, A, st, &S);
+    double* gblk = nullptr;
+    if (rc == MRA_OK) rc = dalloc(A, &gblk, (size_t)(S.nghost + 1) * k3);
+    if (rc == MRA_OK) rc = ghost_refine_forest(F, S, gblk, st);
+    if (rc == MRA_OK) rc = schedule_narrow(op, F, S, gblk, 1, nullptr, 0, X, T, nullptr, A, st);
+    if (rc == MRA_OK) {
+        int32_t herr[2] = {0, 0};
+        cudaError_t e = cudaMemcpyAsync(herr, S.err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { set_error("screen data: %s", cudaGetErrorString(e)); rc = MRA_ECUDA; }
+        else if (herr[0] || herr[1]) { set_error("screen/Step-2 error code %d/%d", herr[0], herr[1]); rc = MRA_ECUDA; }
+    }
+    screen_release(A, &S);
+    A.put(gblk);
+    return rc;
+}
+
+}  // namespace mra

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmra_gb300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEPTH, ESTATE = 0, 1, 2, 3, 4, 5, 6
-PREC = {"fp64": 0, "fp32": 1, "tc": 2}
+PREC = {"fp64": 0, "fp32": 1, "tc": 2, "tc_ladder": 3}
 TREE_LEAVES, TREE_REDUNDANT, TREE_NSFORM = 0, 1, 2
 MAX_LEVEL = 12
 
@@ -52,16 +52,21 @@ class OpInfo(ctypes.Structure):
                 ("mu", ctypes.c_double), ("alpha", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
+SCREEN = {"static": 0, "pair": 1, "learned": 2}
+
+
 class ApplyOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("block_screen", ctypes.c_int),
-                ("unscreened", ctypes.c_int), ("itemwise", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("unscreened", ctypes.c_int), ("itemwise", ctypes.c_int), ("screen_mode", ctypes.c_int),
+                ("margin", ctypes.c_int), ("reserved", ctypes.c_int * 2), ("schedule", ctypes.c_void_p)]
 
 
 class ApplyStats(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int64), ("n_items", ctypes.c_int64), ("n_ghosts", ctypes.c_int64),
                 ("n_out_nodes", ctypes.c_int64), ("eta", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("fnorm", ctypes.c_double), ("ms_screen", ctypes.c_float), ("ms_ghost", ctypes.c_float),
-                ("ms_apply", ctypes.c_float)]
+                ("ms_apply", ctypes.c_float), ("n_items_lowp", ctypes.c_int64), ("n_misses", ctypes.c_int64),
+                ("n_pairs_empty", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -75,8 +80,9 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("n_trees", ctypes.c_int), ("n_nodes", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
                 ("n_ghosts", ctypes.c_int64), ("n_items", ctypes.c_int64), ("precision", ctypes.c_int),
                 ("terms_per_chunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("heavy_first", ctypes.c_int),
-                ("tuned", ctypes.c_int), ("ms_variant", ctypes.c_float * 8), ("graph", ctypes.c_int),
-                ("graph_kernels", ctypes.c_int), ("ms_screen", ctypes.c_float)]
+                ("tuned", ctypes.c_int), ("ms_variant", ctypes.c_float * 10), ("graph", ctypes.c_int),
+                ("graph_kernels", ctypes.c_int), ("ms_screen", ctypes.c_float),
+                ("n_items_lowp", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -88,6 +94,7 @@ _lib = None
 _P = ctypes.c_void_p
 _I32P = ctypes.POINTER(ctypes.c_int32)
 _DP = ctypes.POINTER(ctypes.c_double)
+_FP = ctypes.POINTER(ctypes.c_float)
 
 SIGNATURES = {
     "mra_build_tree": [ctypes.POINTER(Density), ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -114,6 +121,16 @@ SIGNATURES = {
     "mra_plan_get_info": [_P, ctypes.POINTER(PlanInfo), _P],
     "mra_plan_tree_stats": [_P, ctypes.c_int, _P, ctypes.POINTER(ApplyStats)],
     "mra_free_plan": [_P],
+    "mra_mlp_create": [ctypes.c_int, ctypes.c_int, _FP, ctypes.c_ulonglong, ctypes.POINTER(Alloc), _P,
+                       ctypes.POINTER(_P)],
+    "mra_mlp_num_params": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "mra_mlp_get_params": [_P, _FP, _P],
+    "mra_mlp_set_params": [_P, _FP, _P],
+    "mra_mlp_forward": [_P, _P, ctypes.c_int64, _P, _P],
+    "mra_mlp_loss_grad": [_P, _P, _P, ctypes.c_int64, _FP, _DP, _P],
+    "mra_mlp_train_step": [_P, _P, _P, ctypes.c_int64, ctypes.c_float, _P, _DP],
+    "mra_mlp_free": [_P],
+    "mra_screen_data": [_P, _P, _P, _P, _P],
     "mra_free_tree": [_P],
     "mra_free_op": [_P],
     "mra_last_error": [],
@@ -333,8 +350,13 @@ def make_operator(mu, alpha, eps, k, max_level, stream=None, allocator="torch"):
 
 
 def apply_ns(op, tree, precision="fp64", block_screen=False, unscreened=False, itemwise=False, stream=None,
-             stats=True):
-    o = ApplyOpts(PREC[precision], int(block_screen), int(unscreened), int(itemwise))
+             stats=True, screen="static", schedule=None, margin=2):
+    """mra_apply_ns.  screen: "static" (Sec. 4's ranges), "pair" (exact
+    per-pair ranges) or "learned" (the network ``schedule``'s cut-offs, judged
+    by the exact test)."""
+    o = ApplyOpts(PREC[precision], int(block_screen), int(unscreened), int(itemwise), SCREEN[screen], int(margin))
+    if schedule is not None:
+        o.schedule = schedule.h
     st = ApplyStats()
     h = _P()
     _check(lib().mra_apply_ns(op.h, tree.h, ctypes.byref(o), _stream(stream), ctypes.byref(h),
@@ -407,6 +429,80 @@ def plan_create(op, trees, precision=None, use_graph=True, stream=None):
     h = _P()
     _check(lib().mra_plan_create(op.h, arr, len(trees), opts, _stream(stream), ctypes.byref(h)))
     return Plan(h.value, op, trees)
+
+
+class Mlp:
+    """The learned schedule's network (mra_mlp_*).  Device arrays are passed
+    as torch CUDA float32 tensors (contiguous, row-major)."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    @property
+    def n_params(self):
+        n = ctypes.c_int64(0)
+        _check(lib().mra_mlp_num_params(self.h, ctypes.byref(n)))
+        return n.value
+
+    def get_params(self, stream=None):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib().mra_mlp_get_params(self.h, out.ctypes.data_as(_FP), _stream(stream)))
+        return out
+
+    def set_params(self, params, stream=None):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().mra_mlp_set_params(self.h, p.ctypes.data_as(_FP), _stream(stream)))
+
+    def forward(self, x, y, stream=None):
+        _check(lib().mra_mlp_forward(self.h, x.data_ptr(), x.shape[0], y.data_ptr(), _stream(stream)))
+
+    def loss_grad(self, x, target, stream=None):
+        g = np.zeros(self.n_params, dtype=np.float32)
+        L = ctypes.c_double(0.0)
+        _check(lib().mra_mlp_loss_grad(self.h, x.data_ptr(), target.data_ptr(), x.shape[0], g.ctypes.data_as(_FP),
+                                       ctypes.byref(L), _stream(stream)))
+        return L.value, g
+
+    def train_step(self, x, target, lr, stream=None, want_loss=False):
+        L = ctypes.c_double(0.0)
+        _check(lib().mra_mlp_train_step(self.h, x.data_ptr(), target.data_ptr(), x.shape[0], float(lr),
+                                        _stream(stream), ctypes.byref(L) if want_loss else None))
+        return L.value if want_loss else None
+
+    def free(self):
+        if self.h:
+            lib().mra_mlp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mlp_create(n_in=16, n_out=12, params=None, seed=0, stream=None, allocator="torch"):
+    p = None
+    if params is not None:
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        p = params.ctypes.data_as(_FP)
+    h = _P()
+    _check(lib().mra_mlp_create(int(n_in), int(n_out), p, int(seed), _alloc_ptr(allocator), _stream(stream),
+                                ctypes.byref(h)))
+    return Mlp(h.value)
+
+
+def screen_data(op, tree, inputs=None, targets=None, stream=None):
+    """mra_screen_data into torch CUDA float32 tensors [n, 16] / [n, 12]
+    (allocated when not given); returns (inputs, targets)."""
+    import torch
+    n = tree.n
+    if inputs is None:
+        inputs = torch.empty((n, 16), dtype=torch.float32, device="cuda")
+    if targets is None:
+        targets = torch.empty((n, 12), dtype=torch.float32, device="cuda")
+    _check(lib().mra_screen_data(op.h, tree.h, inputs.data_ptr(), targets.data_ptr(), _stream(stream)))
+    return inputs, targets
 
 
 def reconstruct(tree, mode="assemble", truncate=False, eps=0.0, stream=None):

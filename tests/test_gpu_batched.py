@@ -87,7 +87,8 @@ def outputs(plan, n):
     return res
 
 
-@pytest.mark.parametrize("precision,use_graph", [("fp64", False), ("fp64", True), ("tc", True), ("fp32", False)])
+@pytest.mark.parametrize("precision,use_graph", [("fp64", False), ("fp64", True), ("tc", True), ("fp32", False),
+                                                 ("tc_ladder", True)])
 def test_batch_matches_oracle_per_tree(batch, precision, use_graph):
     trees_o, op_o, op_g, ref = batch
     tg = gpu_trees(trees_o)
@@ -107,6 +108,8 @@ def test_batch_matches_oracle_per_tree(batch, precision, use_graph):
     assert info["n_items"] == total
     assert info["n_ghosts"] == sum(st["n_refined"] for _, st in ref)
     assert info["graph"] == int(use_graph)
+    if precision == "tc_ladder":
+        assert 0 < info["n_items_lowp"] <= info["n_items"]
 
 
 def test_batch_equals_single_tree_tc(batch):
@@ -161,9 +164,10 @@ def test_autotune_variants_agree(batch):
     info = plan.autotune(reps=2)
     assert info["tuned"] == 1
     assert all(ms > 0.0 for ms in info["ms_variant"])
-    assert info["terms_per_chunk"] in (4, 8) and info["ctas_per_sm"] in (1, 2)
-    for v in range(8):
-        plan.set_variant(terms_per_chunk=4 if v & 1 else 8, ctas_per_sm=1 if v & 2 else 2, heavy_first=bool(v & 4))
+    assert info["terms_per_chunk"] in (4, 8) and info["ctas_per_sm"] in (1, 2, 3)
+    for v in range(10):
+        mc, ctas = [(8, 2), (4, 2), (8, 1), (4, 1), (4, 3)][v % 5]
+        plan.set_variant(terms_per_chunk=mc, ctas_per_sm=ctas, heavy_first=v >= 5)
         plan.execute()
         outs = outputs(plan, len(tg))
         assert plan.info()["n_items"] == sum(st["n_items"] for _, st in ref)

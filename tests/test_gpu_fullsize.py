@@ -64,7 +64,7 @@ def sample_nodes(tree, per_level=6, seed=11):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc", "tc_ladder"])
 def test_poisson_k8_apply_sampled(poisson_k8, precision):
     cfg, d, tree, hit, op_o, op_g = poisson_k8
     c, l, b = oracle_to_arrays(tree, cfg.k)
@@ -106,7 +106,7 @@ def helmholtz():
     return cfg, d, tree, op_o, op_g
 
 
-@pytest.mark.parametrize("precision", ["fp64", "tc"])
+@pytest.mark.parametrize("precision", ["fp64", "tc", "tc_ladder"])
 def test_helmholtz_slater_full_parity(helmholtz, precision):
     cfg, d, tree, op_o, op_g = helmholtz
     c, l, b = oracle_to_arrays(tree, cfg.k)

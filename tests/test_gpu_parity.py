@@ -208,6 +208,22 @@ def test_apply_tensor_core_split_k8(eps):
     assert rel_l2(ghat_g, ghat_o) <= 10 * eps
 
 
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+def test_apply_tensor_core_ladder_k8(eps):
+    """Precision ladder: single FP16 products for the terms whose bounded
+    rounding error fits the node's budget, FP16 hi+lo for the rest; same items,
+    within the 10 eps gate, and some items do take the single-FP16 rung."""
+    k = 8
+    tree, _ = OT.build_tree(DENS2, k, eps, 3, init_level=1)
+    op_o = OO.Operator(0.0, 1.0, eps, k, 3)
+    op_g = mra.make_operator(0.0, 1.0, eps, k, 3)
+    _, _, _, ghat_o, ghat_g, st_o, st_g = run_both(tree, op_o, op_g, k, precision="tc_ladder")
+    assert st_g["n_items"] == st_o["n_items"]
+    assert 0 < st_g["n_items_lowp"] <= st_g["n_items"]
+    # the budget is eps ||T_0 f_0|| / 4 in L2 on top of the hi+lo error
+    assert rel_l2(ghat_g, ghat_o) <= 10 * eps
+
+
 @pytest.mark.parametrize("k,eps", [(4, 1e-4), (6, 1e-5)])
 def test_apply_tensor_core_padded_orders(k, eps):
     """Orders below 8 run on the same 8 x 8 MMA tiles with zero padding: the
