@@ -124,9 +124,9 @@ __global__ void k_tc_prep_F(int M, int kr, const double* F, __half* Fh, __half* 
 // starts on a 128-byte boundary
 template <int MC>
 struct TcSmem {
-    static constexpr int XH = 0;                    // 6 blocks x 1 KB: stage I A (hi)
-    static constexpr int XL = 6144;
-    static constexpr int B1H = 12288;               // MC terms x 6 K groups x 128 B: stage I B
+    static constexpr int XH = 0;                    // 2 buffers x 6 blocks x 1 KB: stage I A (hi)
+    static constexpr int XL = 12288;                // (lo); buffer p at + p * 6144
+    static constexpr int B1H = 24576;               // MC terms x 6 K groups x 128 B: stage I B
     static constexpr int B1L = B1H + MC * 768;
     static constexpr int A2H = B1L + MC * 768;      // MC x 2048 B: stage II A; stage III A aliases it
     static constexpr int A2L = A2H + MC * 2048;
@@ -373,16 +373,40 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                         const uint4* src = (const uint4*)(hl ? FSL : FSH) + (mc * 7 + t3 + 3) * 8 + v;
                         ((uint4*)(hl ? B3L : B3H))[mc * 16 + v] = *src;
                     }
+                    // stage I A (a line's six input blocks) is copied asynchronously into one
+                    // of two buffers while the previous line computes
+                    auto next_line = [&](int q2) {
+                        for (++q2; q2 < 6; ++q2)
+                            if (s_lm[q2 * 6 + q3]) break;
+                        return q2;
+                    };
+                    auto fetch_line = [&](int line, int buf) {
+                        const unsigned lmx = s_lm[line];
+                        for (int e = tid; e < 6 * 64 * 2; e += TC_THREADS) {
+                            const int hl = e / 384, q1 = (e / 64) % 6, v = e % 64;  // 64 uint4 per 1 KB
+                            if (hl && all_low) continue;
+                            uint4* dst = (uint4*)(sm + (hl ? L::XL : L::XH) + buf * 6144) + q1 * 64 + v;
+                            if (lmx & (1u << q1)) {
+                                const int in = tin[q1 * 36 + line];
+                                const int b = in >= 0 ? in : A.n + (-1 - in);
+                                tc::cp_async16(dst, (const uint4*)((hl ? T.xl : T.xh) + (size_t)b * 512) + v);
+                            } else {
+                                *dst = make_uint4(0, 0, 0, 0);
+                            }
+                        }
+                        tc::cp_async_commit();
+                    };
                     int line_no = 0;
-                    for (int q2 = 0; q2 < 6 && !aborted; ++q2) {
+                    int q2 = next_line(-1);
+                    if (q2 < 6) fetch_line(q2 * 6 + q3, 0);
+                    for (; q2 < 6 && !aborted;) {
                         const int line = q2 * 6 + q3;
                         const unsigned lm = s_lm[line];
-                        if (!lm) continue;  // uniform
                         const int t2 = band_t(a2, q2);
                         const int par = line_no & 1;
                         __half* B2H = (__half*)(sm + L::B2 + par * (2 * MC * 256));
                         __half* B2L = B2H + MC * 128;
-                        // stage I A (the line's input blocks) and the per-slot scale ratios
+                        // the per-slot scale ratios of this line
                         if (tid < 6) {
                             float g = 0.0f;
                             if (lm & (1u << tid)) {
@@ -392,17 +416,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                             }
                             s_g[tid] = g;
                         }
-                        for (int e = tid; e < 6 * 64 * 2; e += TC_THREADS) {
-                            const int hl = e / 384, q1 = (e / 64) % 6, v = e % 64;  // 64 uint4 per 1 KB
-                            if (hl && all_low) continue;
-                            uint4 val = make_uint4(0, 0, 0, 0);
-                            if (lm & (1u << q1)) {
-                                const int in = tin[q1 * 36 + line];
-                                const int b = in >= 0 ? in : A.n + (-1 - in);
-                                val = ((const uint4*)((hl ? T.xl : T.xh) + (size_t)b * 512))[v];
-                            }
-                            ((uint4*)(sm + (hl ? L::XL : L::XH)))[q1 * 64 + v] = val;
-                        }
+                        tc::cp_async_wait_all();
+                        __syncthreads();
+                        // the next line's blocks go to the other buffer (its stage I is done)
+                        const int q2n = next_line(q2);
+                        if (q2n < 6) fetch_line(q2n * 6 + q3, par ^ 1);
                         // stage II B for this line: K group 0 = F^{t2}[c2][i2]
                         for (int e = tid; e < 2 * MC * 8; e += TC_THREADS) {
                             const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
@@ -410,7 +428,6 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                             const uint4* src = (const uint4*)(hl ? FSL : FSH) + (mc * 7 + t2 + 3) * 8 + v;
                             ((uint4*)(hl ? B2L : B2H))[mc * 16 + v] = *src;
                         }
-                        __syncthreads();
                         // stage I B: core (N group mc, K group q1) = mask ? g * F^{t1(q1)} : 0,
                         // one 16-byte core row per step (power-of-two g: exact in FP16)
                         for (int e = tid; e < 2 * MC * 6 * 8; e += TC_THREADS) {
@@ -433,8 +450,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                             tc::fence_after();
 #pragma unroll
                             for (int ks = 0; ks < 3; ++ks) {
-                                const uint64_t ah = tc::sdesc(sbase + L::XH + ks * 2048, 1024, 128);
-                                const uint64_t al = tc::sdesc(sbase + L::XL + ks * 2048, 1024, 128);
+                                const uint64_t ah = tc::sdesc(sbase + L::XH + par * 6144 + ks * 2048, 1024, 128);
+                                const uint64_t al = tc::sdesc(sbase + L::XL + par * 6144 + ks * 2048, 1024, 128);
                                 const uint64_t bh = tc::sdesc(sbase + L::B1H + ks * 256, 128, 768);
                                 const uint64_t bl = tc::sdesc(sbase + L::B1L + ks * 256, 128, 768);
                                 tc::mma_f16(tD1, ah, bh, idI, ks > 0);
@@ -498,7 +515,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                             }
                         }
                         ++line_no;
+                        q2 = q2n;
                     }
+                    tc::cp_async_wait_all();
                     if (aborted) break;
                     // wait for the plane's last stage II, then D_II -> stage III A (aliases stage II A)
                     if (tid == 0) tc::commit(&s_mbar);
@@ -584,6 +603,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
         __syncthreads();
     }
 #undef TC_WAIT_OR_ABORT
+    tc::cp_async_wait_all();
     tc::fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, L::TMEM_COLS);

@@ -77,6 +77,13 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// 16-byte asynchronous global -> shared copies (completion by wait_all)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // FP32 -> FP16 hi + FP16 lo with v ~= hi + lo to about 2^-22 relative
 __device__ __forceinline__ void split_h(float v, __half& hi, __half& lo) {
     hi = __float2half_rn(v);
