@@ -12,7 +12,9 @@
 //             MMA M=64, N=8, K=16 (i3, zero padded), accumulated over planes in TMEM
 //   ghat_a += w_m Y_m in FP64.
 // Every operand is FP16 split into hi + lo (v ~= hi + lo to 2^-22), and each
-// product is the three MMAs hi*hi + hi*lo + lo*hi into an FP32 accumulator.
+// product is hi*hi + hi*lo + lo*hi into an FP32 accumulator: three MMAs in
+// stage I; in stages II and III, whose contraction (8) fills half of an
+// MMA's K = 16, two: A = [A_hi | A_lo] against [B_hi ; B_hi] and [B_lo ; 0].
 // Power-of-two scales keep every operand in FP16's normal range: per input
 // block (x * sx in [2^12, 2^13)), per (j, m) operator block (F * sF), per node
 // (sx_node = the smallest block scale of the neighbourhood), and per term for
@@ -128,9 +130,8 @@ struct TcSmem {
     static constexpr int XL = 12288;                // (lo); buffer p at + p * 6144
     static constexpr int B1H = 24576;               // MC terms x 6 K groups x 128 B: stage I B
     static constexpr int B1L = B1H + MC * 768;
-    static constexpr int A2H = B1L + MC * 768;      // MC x 2048 B: stage II A; stage III A aliases it
-    static constexpr int A2L = A2H + MC * 2048;
-    static constexpr int B2 = A2L + MC * 2048;      // 2 buffers x {hi, lo} x MC x 256 B (K group 1 zero)
+    static constexpr int A2H = B1L + MC * 768;      // MC x 2048 B: stage II A (K: hi | lo); stage III A aliases it
+    static constexpr int B2 = A2H + MC * 2048;      // 2 buffers x {hi, lo} x MC x 256 B
     static constexpr int B3H = B2 + MC * 1024;      // MC x 256 B: stage III B (K group 1 zero)
     static constexpr int B3L = B3H + MC * 256;
     static constexpr int FSH = B3L + MC * 256;      // MC x 7 shifts x 64 halves: the chunk's F (hi)
@@ -175,7 +176,6 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
     __half* B1H = (__half*)(sm + L::B1H);
     __half* B1L = (__half*)(sm + L::B1L);
     __half* A2H = (__half*)(sm + L::A2H);
-    __half* A2L = (__half*)(sm + L::A2L);
     __half* B3H = (__half*)(sm + L::B3H);
     __half* B3L = (__half*)(sm + L::B3L);
     __half* FSH = (__half*)(sm + L::FSH);
@@ -366,12 +366,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                 for (int q3 = 0; q3 < 6 && !aborted; ++q3) {
                     if (!s_pm[q3]) continue;  // uniform
                     const int t3 = band_t(a3, q3);
-                    // stage III B: K group 0 = F^{t3}[c3][i3] (8 uint4 per term)
+                    // stage III B: hi = [F^{t3}_hi ; F^{t3}_hi] and lo = [F^{t3}_lo ; 0] in K, so
+                    // that A3 = [A_hi | A_lo] gives A_hi F_hi + A_lo F_hi and A_hi F_lo in two
+                    // MMAs (a single-FP16 term has a zero second K group in hi)
                     for (int e = tid; e < 2 * MC * 8; e += TC_THREADS) {
                         const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
-                        if (LADDER && hl && s_low[mc]) continue;
-                        const uint4* src = (const uint4*)(hl ? FSL : FSH) + (mc * 7 + t3 + 3) * 8 + v;
-                        ((uint4*)(hl ? B3L : B3H))[mc * 16 + v] = *src;
+                        const bool low = LADDER && s_low[mc];
+                        if (hl && low) continue;
+                        const uint4 src = ((const uint4*)(hl ? FSL : FSH))[(mc * 7 + t3 + 3) * 8 + v];
+                        ((uint4*)(hl ? B3L : B3H))[mc * 16 + v] = src;
+                        if (!hl) ((uint4*)B3H)[mc * 16 + 8 + v] = low ? make_uint4(0, 0, 0, 0) : src;
                     }
                     // stage I A (a line's six input blocks) is copied asynchronously into one
                     // of two buffers while the previous line computes
@@ -421,12 +425,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                         // the next line's blocks go to the other buffer (its stage I is done)
                         const int q2n = next_line(q2);
                         if (q2n < 6) fetch_line(q2n * 6 + q3, par ^ 1);
-                        // stage II B for this line: K group 0 = F^{t2}[c2][i2]
+                        // stage II B for this line: hi = [F^{t2}_hi ; F^{t2}_hi], lo = [F^{t2}_lo ; 0]
                         for (int e = tid; e < 2 * MC * 8; e += TC_THREADS) {
                             const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
-                            if (LADDER && hl && s_low[mc]) continue;
-                            const uint4* src = (const uint4*)(hl ? FSL : FSH) + (mc * 7 + t2 + 3) * 8 + v;
-                            ((uint4*)(hl ? B2L : B2H))[mc * 16 + v] = *src;
+                            const bool low = LADDER && s_low[mc];
+                            if (hl && low) continue;
+                            const uint4 src = ((const uint4*)(hl ? FSL : FSH))[(mc * 7 + t2 + 3) * 8 + v];
+                            ((uint4*)(hl ? B2L : B2H))[mc * 16 + v] = src;
+                            if (!hl) ((uint4*)B2H)[mc * 16 + 8 + v] = low ? make_uint4(0, 0, 0, 0) : src;
                         }
                         // stage I B: core (N group mc, K group q1) = mask ? g * F^{t1(q1)} : 0,
                         // one 16-byte core row per step (power-of-two g: exact in FP16)
@@ -490,7 +496,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                                         tc::split_h(v[c1] * c2, h, l);
                                         const int o = mc * 1024 + c1 * 128 + i3 * 8 + i2;
                                         A2H[o] = h;
-                                        A2L[o] = l;
+                                        A2H[o + 64] = l;  // K group 1
                                     }
                                 }
                             }
@@ -503,15 +509,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                             tc::fence_after();
                             const uint32_t b2 = sbase + L::B2 + par * (2 * MC * 256);
                             for (int mc = 0; mc < MC; ++mc) {
-                                const uint64_t ah = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
-                                const uint64_t al = tc::sdesc(sbase + L::A2L + mc * 2048, 128, 256);
+                                const uint64_t a = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
                                 const uint64_t bh = tc::sdesc(b2 + mc * 256, 128, 256);
                                 const uint64_t bl = tc::sdesc(b2 + MC * 256 + mc * 256, 128, 256);
-                                tc::mma_f16(tD2 + mc * 8, ah, bh, idS, line_no > 0);
-                                if (!LADDER || !s_low[mc]) {
-                                    tc::mma_f16(tD2 + mc * 8, ah, bl, idS, 1);
-                                    tc::mma_f16(tD2 + mc * 8, al, bh, idS, 1);
-                                }
+                                tc::mma_f16(tD2 + mc * 8, a, bh, idS, line_no > 0);
+                                if (!LADDER || !s_low[mc]) tc::mma_f16(tD2 + mc * 8, a, bl, idS, 1);
                             }
                         }
                         ++line_no;
@@ -542,7 +544,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                                     tc::split_h(v[c2] * c3, h, l);
                                     const int o = mc * 1024 + c1 * 128 + c2 * 8 + i3;
                                     A2H[o] = h;
-                                    A2L[o] = l;
+                                    A2H[o + 64] = l;  // K group 1
                                 }
                             }
                         }
@@ -554,15 +556,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     if (tid == 0) {
                         tc::fence_after();
                         for (int mc = 0; mc < MC; ++mc) {
-                            const uint64_t ah = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
-                            const uint64_t al = tc::sdesc(sbase + L::A2L + mc * 2048, 128, 256);
+                            const uint64_t a = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
                             const uint64_t bh = tc::sdesc(sbase + L::B3H + mc * 256, 128, 256);
                             const uint64_t bl = tc::sdesc(sbase + L::B3L + mc * 256, 128, 256);
-                            tc::mma_f16(tD3 + mc * 8, ah, bh, idS, plane_started);
-                            if (!LADDER || !s_low[mc]) {
-                                tc::mma_f16(tD3 + mc * 8, ah, bl, idS, 1);
-                                tc::mma_f16(tD3 + mc * 8, al, bh, idS, 1);
-                            }
+                            tc::mma_f16(tD3 + mc * 8, a, bh, idS, plane_started);
+                            if (!LADDER || !s_low[mc]) tc::mma_f16(tD3 + mc * 8, a, bl, idS, 1);
                         }
                         tc::commit(&s_mbar);
                     }
@@ -649,6 +647,10 @@ void tc_release(const mra_op* op, TcBuffers* B) {
 // dynamic shared memory of both chunk sizes (outside any stream capture)
 int tc_configure() {
     MRA_CK(cudaFuncSetAttribute(k_apply_tc<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<4>::TOTAL));
+    MRA_CK(cudaFuncSetAttribute(k_apply_tc<4, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    MRA_CK(cudaFuncSetAttribute(k_apply_tc<8, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    MRA_CK(cudaFuncSetAttribute(k_apply_tc<4, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    MRA_CK(cudaFuncSetAttribute(k_apply_tc<8, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     MRA_CK(cudaFuncSetAttribute(k_apply_tc<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<8>::TOTAL));
     MRA_CK(cudaFuncSetAttribute(k_apply_tc<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<4>::TOTAL));
     MRA_CK(cudaFuncSetAttribute(k_apply_tc<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<8>::TOTAL));
