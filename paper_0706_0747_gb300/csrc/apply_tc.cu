@@ -201,8 +201,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
     const int mc_lo = whalf * (MC / 2), mc_hi = mc_lo + MC / 2;
     const uint32_t idI = tc::idesc_f16(64, 8 * MC), idS = tc::idesc_f16(64, 8);
     uint32_t phase = 0;
-    const int row = quarter * 16 + lane;  // accumulator row of this thread (M=64 layout), valid for lane < 16
-    const bool has_row = lane < 16;
+    // accumulator rows of this thread in the M=64 layout (16x256b read-outs):
+    // 16 quarter + lane/4 and that + 8, columns cA and cA + 1 of each term
+    const int rA = quarter * 16 + (lane >> 2), cA = 2 * (lane & 3);
     const uint32_t sbase = tc::smem_u32(sm);
 
     // the abort decision comes from __syncthreads_or, so it is uniform
@@ -261,9 +262,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
         const int mlo = s_mlo, mhi = s_mhi;
         const float xmax_node = __uint_as_float(s_xmax_bits);
         const float sx_node = ldexpf(1.0f, s_exp_min - 1);
-        double y[8];
+        double y[4];  // (row rA + 8 s, column cA + h) at y[2 s + h]
 #pragma unroll
-        for (int c = 0; c < 8; ++c) y[c] = 0.0;
+        for (int c = 0; c < 4; ++c) y[c] = 0.0;
         if (mhi >= mlo && xmax_node > 0.0f) {
             for (int m0 = mlo; m0 <= mhi && !aborted; m0 += MC) {
                 // the chunk's operator blocks, the kept-t1 masks per line, per-term scales
@@ -477,27 +478,24 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                         TC_WAIT_OR_ABORT();
                         if (aborted) break;
                         tc::fence_after();
-                        // D_I -> stage II A: row (c1, i3), K column i2
+                        // D_I -> stage II A: row (c1, i3), K column i2.  This thread holds
+                        // D_I rows (i2, i3) = (2 quarter, lane/4) and (2 quarter + 1, lane/4):
+                        // K neighbours, stored as one half2 per c1
 #pragma unroll
                         for (int mc = mc_lo; mc < mc_hi; ++mc) {
-                            float v[8];
-                            tc::tmem_ld8(tD1 + lane_off + mc * 8, v);
-                            if (has_row) {
-                                const int i2 = row >> 3, i3 = row & 7;
-                                const float c2 = s_c2[mc];
-                                if (LADDER && s_low[mc]) {
+                            float v[4];
+                            tc::tmem_ld16x256(tD1 + lane_off + mc * 8, v);
+                            const int i3 = lane >> 2;
+                            const float c2 = s_c2[mc];
 #pragma unroll
-                                    for (int c1 = 0; c1 < 8; ++c1)
-                                        A2H[mc * 1024 + c1 * 128 + i3 * 8 + i2] = __float2half_rn(v[c1] * c2);
-                                } else {
-#pragma unroll
-                                    for (int c1 = 0; c1 < 8; ++c1) {
-                                        __half h, l;
-                                        tc::split_h(v[c1] * c2, h, l);
-                                        const int o = mc * 1024 + c1 * 128 + i3 * 8 + i2;
-                                        A2H[o] = h;
-                                        A2H[o + 64] = l;  // K group 1
-                                    }
+                            for (int h = 0; h < 2; ++h) {
+                                const float x0 = v[h] * c2, x1 = v[2 + h] * c2;
+                                const int o = mc * 1024 + (cA + h) * 128 + i3 * 8 + 2 * quarter;
+                                const __half2 hi = __floats2half2_rn(x0, x1);
+                                *(__half2*)&A2H[o] = hi;
+                                if (!LADDER || !s_low[mc]) {
+                                    const float2 hf = __half22float2(hi);
+                                    *(__half2*)&A2H[o + 64] = __floats2half2_rn(x0 - hf.x, x1 - hf.y);  // K group 1
                                 }
                             }
                         }
@@ -526,26 +524,24 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     TC_WAIT_OR_ABORT();
                     if (aborted) break;
                     tc::fence_after();
+                    // D_II rows (c1, i3) = (2 quarter + s, lane/4), columns c2 = cA + h
 #pragma unroll
                     for (int mc = mc_lo; mc < mc_hi; ++mc) {
-                        float v[8];
-                        tc::tmem_ld8(tD2 + lane_off + mc * 8, v);
-                        if (has_row) {
-                            const int c1 = row >> 3, i3 = row & 7;
-                            const float c3 = s_c3[mc];
+                        float v[4];
+                        tc::tmem_ld16x256(tD2 + lane_off + mc * 8, v);
+                        const int i3 = lane >> 2;
+                        const float c3 = s_c3[mc];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int c1 = 2 * quarter + (q >> 1), c2 = cA + (q & 1);
+                            const int o = mc * 1024 + c1 * 128 + c2 * 8 + i3;
                             if (LADDER && s_low[mc]) {
-#pragma unroll
-                                for (int c2 = 0; c2 < 8; ++c2)
-                                    A2H[mc * 1024 + c1 * 128 + c2 * 8 + i3] = __float2half_rn(v[c2] * c3);
+                                A2H[o] = __float2half_rn(v[q] * c3);
                             } else {
-#pragma unroll
-                                for (int c2 = 0; c2 < 8; ++c2) {
-                                    __half h, l;
-                                    tc::split_h(v[c2] * c3, h, l);
-                                    const int o = mc * 1024 + c1 * 128 + c2 * 8 + i3;
-                                    A2H[o] = h;
-                                    A2H[o + 64] = l;  // K group 1
-                                }
+                                __half h, l;
+                                tc::split_h(v[q] * c3, h, l);
+                                A2H[o] = h;
+                                A2H[o + 64] = l;  // K group 1
                             }
                         }
                     }
@@ -575,27 +571,30 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     // ghat += w_m Y_m (FP64): row (c1, c2), column c3
 #pragma unroll
                     for (int mc = mc_lo; mc < mc_hi; ++mc) {
-                        float v[8];
-                        tc::tmem_ld8(tD3 + lane_off + mc * 8, v);
+                        float v[4];
+                        tc::tmem_ld16x256(tD3 + lane_off + mc * 8, v);
                         const double fin = s_fin[mc];
 #pragma unroll
-                        for (int c3 = 0; c3 < 8; ++c3) y[c3] += fin * (double)v[c3];
+                        for (int q = 0; q < 4; ++q) y[q] += fin * (double)v[q];
                     }
                 }
                 tc::fence_before();
                 __syncthreads();
             }
         }
+        // Y rows (c1, c2) = rA + 8 s, columns c3 = cA + h; the two warp halves add up
         double* ysm = (double*)(sm + L::Y);
-        if (has_row && whalf == 1)
+        if (whalf == 1)
 #pragma unroll
-            for (int c3 = 0; c3 < 8; ++c3) ysm[row * 8 + c3] = y[c3];
+            for (int q = 0; q < 4; ++q) ysm[(rA + 8 * (q >> 1)) * 8 + cA + (q & 1)] = y[q];
         __syncthreads();
-        const int c1 = row >> 3, c2 = row & 7;
-        if (has_row && whalf == 0 && c1 < kr && c2 < kr)
+        if (whalf == 0)
 #pragma unroll
-            for (int c3 = 0; c3 < 8; ++c3)
-                if (c3 < kr) A.out[(size_t)node * kr * kr * kr + (c1 * kr + c2) * kr + c3] = y[c3] + ysm[row * 8 + c3];
+            for (int q = 0; q < 4; ++q) {
+                const int r = rA + 8 * (q >> 1), c1 = r >> 3, c2 = r & 7, c3 = cA + (q & 1);
+                if (c1 < kr && c2 < kr && c3 < kr)
+                    A.out[(size_t)node * kr * kr * kr + (c1 * kr + c2) * kr + c3] = y[q] + ysm[r * 8 + c3];
+            }
         if (tid == 0 && A.n_items) atomicAdd(A.n_items + (A.node_tree ? A.node_tree[node] : 0), s_items);
         if (tid == 0 && T.n_lowp && s_lowi) atomicAdd(T.n_lowp, s_lowi);
         __syncthreads();

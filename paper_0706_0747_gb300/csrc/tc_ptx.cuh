@@ -77,6 +77,19 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// 16 lanes x 256 bits (8 consecutive 32-bit columns) from lane base `taddr`:
+// thread t of the warp gets v[0], v[1] = lane t/4, columns 2(t%4), 2(t%4)+1
+// and v[2], v[3] = lane t/4 + 8, the same columns
+__device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, float* v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = __uint_as_float(r[q]);
+}
+
 // 16-byte asynchronous global -> shared copies (completion by wait_all)
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
