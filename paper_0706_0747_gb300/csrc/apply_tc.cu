@@ -126,22 +126,26 @@ __global__ void k_tc_prep_F(int M, int kr, const double* F, __half* Fh, __half* 
 // starts on a 128-byte boundary
 template <int MC>
 struct TcSmem {
-    static constexpr int XH = 0;                    // 2 buffers x 6 blocks x 1 KB: stage I A (hi)
+    static constexpr int XH = 0;                    // 2 buffers x 6 blocks x 1 KB: stage I A (hi); the final y
     static constexpr int XL = 12288;                // (lo); buffer p at + p * 6144
     static constexpr int B1H = 24576;               // MC terms x 6 K groups x 128 B: stage I B
     static constexpr int B1L = B1H + MC * 768;
     static constexpr int A2H = B1L + MC * 768;      // MC x 2048 B: stage II A (K: hi | lo); stage III A aliases it
     static constexpr int B2 = A2H + MC * 2048;      // 2 buffers x {hi, lo} x MC x 256 B
-    static constexpr int B3H = B2 + MC * 1024;      // MC x 256 B: stage III B (K group 1 zero)
+    static constexpr int B3H = B2 + MC * 1024;      // MC x 256 B: stage III B
     static constexpr int B3L = B3H + MC * 256;
-    static constexpr int FSH = B3L + MC * 256;      // MC x 7 shifts x 64 halves: the chunk's F (hi)
-    static constexpr int FSL = FSH + MC * 896;
-    static constexpr int TAB = FSL + MC * 896;      // 4 x 216 int
-    static constexpr int MSK = TAB + 3456;          // 36 x MC bytes
-    static constexpr int Y = (MSK + 36 * MC + 127) / 128 * 128;  // 64 x 8 doubles (second warp half)
-    static constexpr int TOTAL = Y + 4096;
-    static constexpr int TMEM_COLS = (24 * MC <= 128) ? 128 : 256;
+    static constexpr int TIN = B3L + MC * 256;      // 216 int: input block per band position
+    static constexpr int TLO = TIN + 864;           // 216 int16: term range
+    static constexpr int THI = TLO + 432;
+    static constexpr int TFL = THI + 432;           // 216 bytes: flags
+    static constexpr int MSK = TFL + 216;           // 36 x MC bytes
+    static constexpr int TOTAL = (MSK + 36 * MC + 127) / 128 * 128;
+    // D_I and D_II (stage III's result reuses D_I's columns)
+    static constexpr int TMEM_COLS = (16 * MC <= 64) ? 64 : ((16 * MC <= 128) ? 128 : 256);
 };
+// three CTAs per SM (the register limit) for either chunk size
+static_assert(3 * (TcSmem<8>::TOTAL + 2048) <= 232448, "8 terms per chunk: three CTAs per SM");
+static_assert(3 * TcSmem<8>::TMEM_COLS <= 512, "three CTAs' tensor memory");
 
 __device__ __forceinline__ float pow2floor(double x) {
     if (!(x > 0.0)) return 0.0f;
@@ -154,7 +158,7 @@ __device__ __forceinline__ float pow2floor(double x) {
 }
 
 template <int MC, bool LADDER>
-__global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
+__global__ void __launch_bounds__(TC_THREADS, 3) k_apply_tc(TcArgs T) {
     using L = TcSmem<MC>;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint32_t s_tmem;
@@ -178,12 +182,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
     __half* A2H = (__half*)(sm + L::A2H);
     __half* B3H = (__half*)(sm + L::B3H);
     __half* B3L = (__half*)(sm + L::B3L);
-    __half* FSH = (__half*)(sm + L::FSH);
-    __half* FSL = (__half*)(sm + L::FSL);
-    int* tin = (int*)(sm + L::TAB);
-    int* tlo = tin + 216;
-    int* thi = tlo + 216;
-    int* tfl = thi + 216;
+    // the chunk's operator blocks are read from L1/L2: F (hi, lo) of term m0 + mc at shift t
+    const uint4* FH = (const uint4*)T.Fh;
+    const uint4* FL = (const uint4*)T.Fl;
+    int* tin = (int*)(sm + L::TIN);
+    int16_t* tlo = (int16_t*)(sm + L::TLO);
+    int16_t* thi = (int16_t*)(sm + L::THI);
+    unsigned char* tfl = sm + L::TFL;
     unsigned char* msk = sm + L::MSK;
 
     // zero everything once: the K padding of stages II and III stays zero
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = s_tmem;
-    const uint32_t tD1 = tbase, tD2 = tbase + 8 * MC, tD3 = tbase + 16 * MC;
+    const uint32_t tD1 = tbase, tD2 = tbase + 8 * MC, tD3 = tbase;  // stage III reuses D_I
     // warps w and w+4 share TMEM lane quarter w and split the terms of a chunk
     const int quarter = warp & 3, whalf = warp >> 2;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
@@ -267,18 +272,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
         for (int c = 0; c < 4; ++c) y[c] = 0.0;
         if (mhi >= mlo && xmax_node > 0.0f) {
             for (int m0 = mlo; m0 <= mhi && !aborted; m0 += MC) {
-                // the chunk's operator blocks, the kept-t1 masks per line, per-term scales
-                for (int e = tid; e < MC * 7 * 64 / 8; e += TC_THREADS) {  // uint4 = 8 halves
-                    const int mc = e / 56, r = e % 56, m = m0 + mc;
-                    uint4 h = make_uint4(0, 0, 0, 0), l = h;
-                    if (m <= mhi) {
-                        const size_t src = ((size_t)j * A.M + m) * 56 + r;
-                        h = ((const uint4*)T.Fh)[src];
-                        l = ((const uint4*)T.Fl)[src];
-                    }
-                    ((uint4*)FSH)[e] = h;
-                    ((uint4*)FSL)[e] = l;
-                }
+                // the kept-t1 masks per line and the per-term scales of the chunk
+                const size_t fbase = ((size_t)j * A.M + m0) * 56;  // uint4 index of F(m0, t = -3)
                 for (int e = tid; e < 36 * MC; e += TC_THREADS) {
                     const int line = e / MC, mc = e % MC, m = m0 + mc;
                     unsigned char mk = 0;
@@ -363,7 +358,6 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                 }
                 __syncthreads();
                 const int all_low = LADDER ? s_all_low : 0;
-                int plane_started = 0;
                 for (int q3 = 0; q3 < 6 && !aborted; ++q3) {
                     if (!s_pm[q3]) continue;  // uniform
                     const int t3 = band_t(a3, q3);
@@ -374,7 +368,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                         const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
                         const bool low = LADDER && s_low[mc];
                         if (hl && low) continue;
-                        const uint4 src = ((const uint4*)(hl ? FSL : FSH))[(mc * 7 + t3 + 3) * 8 + v];
+                        const uint4 src = m0 + mc <= mhi ? (hl ? FL : FH)[fbase + (mc * 7 + t3 + 3) * 8 + v]
+                                                         : make_uint4(0, 0, 0, 0);
                         ((uint4*)(hl ? B3L : B3H))[mc * 16 + v] = src;
                         if (!hl) ((uint4*)B3H)[mc * 16 + 8 + v] = low ? make_uint4(0, 0, 0, 0) : src;
                     }
@@ -431,7 +426,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                             const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
                             const bool low = LADDER && s_low[mc];
                             if (hl && low) continue;
-                            const uint4 src = ((const uint4*)(hl ? FSL : FSH))[(mc * 7 + t2 + 3) * 8 + v];
+                            const uint4 src = m0 + mc <= mhi ? (hl ? FL : FH)[fbase + (mc * 7 + t2 + 3) * 8 + v]
+                                                             : make_uint4(0, 0, 0, 0);
                             ((uint4*)(hl ? B2L : B2H))[mc * 16 + v] = src;
                             if (!hl) ((uint4*)B2H)[mc * 16 + 8 + v] = low ? make_uint4(0, 0, 0, 0) : src;
                         }
@@ -442,7 +438,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                             if (hl && all_low) continue;
                             uint4 out = make_uint4(0, 0, 0, 0);
                             if ((msk[line * MC + mc] >> q1) & 1u) {
-                                const uint4 in = ((const uint4*)(hl ? FSL : FSH))[(mc * 7 + band_t(a1, q1) + 3) * 8 + v];
+                                const uint4 in = (hl ? FL : FH)[fbase + (mc * 7 + band_t(a1, q1) + 3) * 8 + v];
                                 const __half2 g2 = __float2half2_rn(s_g[q1]);
                                 const __half2* pi = (const __half2*)&in;
                                 __half2* po = (__half2*)&out;
@@ -555,7 +551,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                             const uint64_t a = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
                             const uint64_t bh = tc::sdesc(sbase + L::B3H + mc * 256, 128, 256);
                             const uint64_t bl = tc::sdesc(sbase + L::B3L + mc * 256, 128, 256);
-                            tc::mma_f16(tD3 + mc * 8, a, bh, idS, plane_started);
+                            tc::mma_f16(tD3 + mc * 8, a, bh, idS, 0);
                             if (!LADDER || !s_low[mc]) tc::mma_f16(tD3 + mc * 8, a, bl, idS, 1);
                         }
                         tc::commit(&s_mbar);
@@ -564,11 +560,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
                     TC_WAIT_OR_ABORT();
                     if (aborted) break;
                     tc::fence_after();
-                    plane_started = 1;
-                }
-                if (aborted) break;
-                if (plane_started) {
-                    // ghat += w_m Y_m (FP64): row (c1, c2), column c3
+                    // ghat += w_m Y_m (FP64): row (c1, c2), column c3; D_I is free again after this
 #pragma unroll
                     for (int mc = mc_lo; mc < mc_hi; ++mc) {
                         float v[4];
@@ -577,13 +569,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_apply_tc(TcArgs T) {
 #pragma unroll
                         for (int q = 0; q < 4; ++q) y[q] += fin * (double)v[q];
                     }
+                    tc::fence_before();
                 }
+                if (aborted) break;
                 tc::fence_before();
                 __syncthreads();
             }
         }
         // Y rows (c1, c2) = rA + 8 s, columns c3 = cA + h; the two warp halves add up
-        double* ysm = (double*)(sm + L::Y);
+        double* ysm = (double*)(sm + L::XH);  // every copy into the X buffers is complete here
         if (whalf == 1)
 #pragma unroll
             for (int q = 0; q < 4; ++q) ysm[(rA + 8 * (q >> 1)) * 8 + cA + (q & 1)] = y[q];
@@ -665,8 +659,9 @@ static int launch_mc(const TcArgs& T, int ctas_per_sm, cudaStream_t st) {
     return MRA_OK;
 }
 
-// variant: terms per chunk (4 or 8) and CTAs per SM (1 or 2); TMEM and shared
-// memory allow 2 CTAs per SM for both chunk sizes.  tc_configure() first.
+// variant: terms per chunk (4 or 8) and CTAs per SM (1 to 3); registers,
+// TMEM and shared memory allow 3 CTAs per SM for both chunk sizes.
+// tc_configure() first.
 int tc_launch(const TcArgs& T, int mc, int ctas_per_sm, cudaStream_t st) {
     MRA_CK(cudaMemsetAsync(T.counter, 0, sizeof(int), st));
     if (mc == 4) return launch_mc<4>(T, ctas_per_sm, st);
@@ -702,7 +697,7 @@ int launch_apply_tc(const ApplyArgs& A, int nghost, const mra_op* op, int* err, 
     TcArgs T = tc_args(A, B, err);
     T.lpb = lpb;
     T.n_lowp = n_lowp;
-    MRA_TRY(tc_launch(T, 8, 2, st));
+    MRA_TRY(tc_launch(T, 8, 3, st));
     tc_release(op, &B);  // stream-ordered frees: released after the kernel completes
     return MRA_OK;
 }
