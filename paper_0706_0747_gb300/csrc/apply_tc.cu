@@ -76,7 +76,9 @@ __global__ void k_tc_prep_blocks(int nb, int kr, int n, const double* s, const d
     m = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
     int e = 0;
     if (m > 0.0f) frexpf(m, &e);
-    const double scale = ldexp(1.0, 13 - e);  // m * scale in [2^12, 2^13)
+    // m * scale in [2^12, 2^13); blocks below 2^-100 keep the scale 2^113 (a
+    // finite float) and round to zero in FP16
+    const double scale = ldexp(1.0, 13 - max(e, -100));
     for (int q = 0; q < 4; ++q) {
         const int idx = threadIdx.x + 128 * q;
         const int i1 = idx >> 6, i2 = (idx >> 3) & 7, i3 = idx & 7;
@@ -107,7 +109,7 @@ __global__ void k_tc_prep_F(int M, int kr, const double* F, __half* Fh, __half* 
     mx = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
     int ex = 0;
     if (mx > 0.0f) frexpf(mx, &ex);
-    const double scale = ldexp(1.0, 13 - ex);
+    const double scale = ldexp(1.0, 13 - max(ex, -100));  // a finite float scale, as for the blocks
     for (int e = threadIdx.x; e < 7 * 64; e += blockDim.x) {
         const int t = e / 64, c = (e / 8) % 8, i = e % 8;
         const double v = (c < kr && i < kr) ? src[(t * kr + c) * kr + i] : 0.0;
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_apply_tc(TcArgs T) {
     __shared__ int s_mlo, s_mhi, s_exp_min, s_node;
     __shared__ unsigned int s_xmax_bits;
     __shared__ unsigned long long s_items;
-    __shared__ float s_c2[MC], s_c3[MC], s_g[6];
+    __shared__ float s_c2[MC], s_c3[MC];
     __shared__ unsigned char s_lm[36], s_pm[6];
     __shared__ double s_fin[MC];
     __shared__ float s_B[MC];
@@ -396,32 +398,14 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_apply_tc(TcArgs T) {
                         }
                         tc::cp_async_commit();
                     };
-                    int line_no = 0;
-                    int q2 = next_line(-1);
-                    if (q2 < 6) fetch_line(q2 * 6 + q3, 0);
-                    for (; q2 < 6 && !aborted;) {
-                        const int line = q2 * 6 + q3;
-                        const unsigned lm = s_lm[line];
-                        const int t2 = band_t(a2, q2);
-                        const int par = line_no & 1;
-                        __half* B2H = (__half*)(sm + L::B2 + par * (2 * MC * 256));
+                    // stage II and I operands of line q2 into B2 buffer `par` and B1: stage II
+                    // B = [F^{t2}_hi ; F^{t2}_hi] (hi), [F^{t2}_lo ; 0] (lo); stage I B core
+                    // (N group mc, K group q1) = mask ? g * F^{t1(q1)} : 0 with the power-of-two
+                    // ratio g = sx_node / sx_b (exact in FP16)
+                    auto build_B = [&](int q2b, int parb) {
+                        const int lineb = q2b * 6 + q3, t2 = band_t(a2, q2b);
+                        __half* B2H = (__half*)(sm + L::B2 + parb * (2 * MC * 256));
                         __half* B2L = B2H + MC * 128;
-                        // the per-slot scale ratios of this line
-                        if (tid < 6) {
-                            float g = 0.0f;
-                            if (lm & (1u << tid)) {
-                                const int in = tin[tid * 36 + line];
-                                const int b = in >= 0 ? in : A.n + (-1 - in);
-                                g = sx_node / T.sx[b];
-                            }
-                            s_g[tid] = g;
-                        }
-                        tc::cp_async_wait_all();
-                        __syncthreads();
-                        // the next line's blocks go to the other buffer (its stage I is done)
-                        const int q2n = next_line(q2);
-                        if (q2n < 6) fetch_line(q2n * 6 + q3, par ^ 1);
-                        // stage II B for this line: hi = [F^{t2}_hi ; F^{t2}_hi], lo = [F^{t2}_lo ; 0]
                         for (int e = tid; e < 2 * MC * 8; e += TC_THREADS) {
                             const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
                             const bool low = LADDER && s_low[mc];
@@ -431,46 +415,67 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_apply_tc(TcArgs T) {
                             ((uint4*)(hl ? B2L : B2H))[mc * 16 + v] = src;
                             if (!hl) ((uint4*)B2H)[mc * 16 + 8 + v] = low ? make_uint4(0, 0, 0, 0) : src;
                         }
-                        // stage I B: core (N group mc, K group q1) = mask ? g * F^{t1(q1)} : 0,
-                        // one 16-byte core row per step (power-of-two g: exact in FP16)
                         for (int e = tid; e < 2 * MC * 6 * 8; e += TC_THREADS) {
                             const int hl = e / (MC * 48), mc = (e / 48) % MC, q1 = (e / 8) % 6, v = e % 8;
                             if (hl && all_low) continue;
                             uint4 out = make_uint4(0, 0, 0, 0);
-                            if ((msk[line * MC + mc] >> q1) & 1u) {
-                                const uint4 in = (hl ? FL : FH)[fbase + (mc * 7 + band_t(a1, q1) + 3) * 8 + v];
-                                const __half2 g2 = __float2half2_rn(s_g[q1]);
-                                const __half2* pi = (const __half2*)&in;
+                            if ((msk[lineb * MC + mc] >> q1) & 1u) {
+                                const int in = tin[q1 * 36 + lineb];
+                                const float sxb = T.sx[in >= 0 ? in : A.n + (-1 - in)];
+                                const float g = sx_node / sxb;
+                                const uint4 fin4 = (hl ? FL : FH)[fbase + (mc * 7 + band_t(a1, q1) + 3) * 8 + v];
+                                const __half2 g2 = __float2half2_rn(g);
+                                const __half2* pi = (const __half2*)&fin4;
                                 __half2* po = (__half2*)&out;
 #pragma unroll
                                 for (int h = 0; h < 4; ++h) po[h] = __hmul2(pi[h], g2);
                             }
                             ((uint4*)(hl ? B1L : B1H))[mc * 48 + q1 * 8 + v] = out;
                         }
-                        tc::fence_async_smem();
-                        __syncthreads();
-                        if (tid == 0) {
-                            tc::fence_after();
+                    };
+                    // stage I of line q2 from X buffer parx (thread 0)
+                    auto issue_stage1 = [&](int q2i, int parx) {
+                        const int linei = q2i * 6 + q3;
 #pragma unroll
-                            for (int ks = 0; ks < 3; ++ks) {
-                                const uint64_t ah = tc::sdesc(sbase + L::XH + par * 6144 + ks * 2048, 1024, 128);
-                                const uint64_t al = tc::sdesc(sbase + L::XL + par * 6144 + ks * 2048, 1024, 128);
-                                const uint64_t bh = tc::sdesc(sbase + L::B1H + ks * 256, 128, 768);
-                                const uint64_t bl = tc::sdesc(sbase + L::B1L + ks * 256, 128, 768);
-                                tc::mma_f16(tD1, ah, bh, idI, ks > 0);
-                                if (!all_low) {
-                                    tc::mma_f16(tD1, ah, bl, idI, 1);
-                                    tc::mma_f16(tD1, al, bh, idI, 1);
-                                }
-                            }
-                            tc::commit(&s_mbar);
-                            for (int mc = 0; mc < MC; ++mc) {
-                                const int c = __popc(msk[line * MC + mc]);
-                                s_items += c;
-                                if (LADDER && s_low[mc]) s_lowi += c;
+                        for (int ks = 0; ks < 3; ++ks) {
+                            const uint64_t ah = tc::sdesc(sbase + L::XH + parx * 6144 + ks * 2048, 1024, 128);
+                            const uint64_t al = tc::sdesc(sbase + L::XL + parx * 6144 + ks * 2048, 1024, 128);
+                            const uint64_t bh = tc::sdesc(sbase + L::B1H + ks * 256, 128, 768);
+                            const uint64_t bl = tc::sdesc(sbase + L::B1L + ks * 256, 128, 768);
+                            tc::mma_f16(tD1, ah, bh, idI, ks > 0);
+                            if (!all_low) {
+                                tc::mma_f16(tD1, ah, bl, idI, 1);
+                                tc::mma_f16(tD1, al, bh, idI, 1);
                             }
                         }
-                        // also covers the previous line's stage II: A2 is free afterwards
+                        for (int mc = 0; mc < MC; ++mc) {
+                            const int c = __popc(msk[linei * MC + mc]);
+                            s_items += c;
+                            if (LADDER && s_low[mc]) s_lowi += c;
+                        }
+                    };
+                    // Software pipeline over the plane's lines: one wait and two block
+                    // barriers per line.  While line L's stage I runs, the previous line's
+                    // stage II runs too; after the wait the threads convert D_I(L), build
+                    // line L+1's B operands, and copy line L+2's input blocks; then one
+                    // thread issues stage II(L) and stage I(L+1) under a single commit.
+                    int q2 = next_line(-1);
+                    int q2n = next_line(q2);
+                    fetch_line(q2 * 6 + q3, 0);
+                    build_B(q2, 0);
+                    tc::cp_async_wait_all();
+                    if (q2n < 6) fetch_line(q2n * 6 + q3, 1);
+                    tc::fence_async_smem();
+                    __syncthreads();
+                    if (tid == 0) {
+                        tc::fence_after();
+                        issue_stage1(q2, 0);
+                        tc::commit(&s_mbar);
+                    }
+                    for (int li = 0;; ++li) {
+                        const int par = li & 1;
+                        // stage I(L) and stage II(L-1) complete: D_I, B1, A2 and the buffers
+                        // of the other parity are free
                         TC_WAIT_OR_ABORT();
                         if (aborted) break;
                         tc::fence_after();
@@ -495,28 +500,37 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_apply_tc(TcArgs T) {
                                 }
                             }
                         }
+                        const int q2nn = q2n < 6 ? next_line(q2n) : 6;
+                        if (q2n < 6) {
+                            build_B(q2n, par ^ 1);
+                            tc::cp_async_wait_all();  // line L+1's input blocks
+                            if (q2nn < 6) fetch_line(q2nn * 6 + q3, par);
+                        }
                         tc::fence_before();
                         tc::fence_async_smem();
                         __syncthreads();
-                        // stage II: per term, V += A2 (M=64 (c1,i3) x K=16) x B2 (N=8 c2)
                         if (tid == 0) {
                             tc::fence_after();
+                            // stage II(L): per term, V += A2 (M=64 (c1,i3) x K=16) x B2 (N=8 c2)
                             const uint32_t b2 = sbase + L::B2 + par * (2 * MC * 256);
                             for (int mc = 0; mc < MC; ++mc) {
                                 const uint64_t a = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
                                 const uint64_t bh = tc::sdesc(b2 + mc * 256, 128, 256);
                                 const uint64_t bl = tc::sdesc(b2 + MC * 256 + mc * 256, 128, 256);
-                                tc::mma_f16(tD2 + mc * 8, a, bh, idS, line_no > 0);
+                                tc::mma_f16(tD2 + mc * 8, a, bh, idS, li > 0);
                                 if (!LADDER || !s_low[mc]) tc::mma_f16(tD2 + mc * 8, a, bl, idS, 1);
                             }
+                            if (q2n < 6) issue_stage1(q2n, par ^ 1);
+                            tc::commit(&s_mbar);
                         }
-                        ++line_no;
+                        if (q2n >= 6) break;
                         q2 = q2n;
+                        q2n = q2nn;
                     }
                     tc::cp_async_wait_all();
                     if (aborted) break;
-                    // wait for the plane's last stage II, then D_II -> stage III A (aliases stage II A)
-                    if (tid == 0) tc::commit(&s_mbar);
+                    // wait for the plane's last stage II (committed with it), then
+                    // D_II -> stage III A (aliases stage II A)
                     TC_WAIT_OR_ABORT();
                     if (aborted) break;
                     tc::fence_after();
