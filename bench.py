@@ -45,6 +45,11 @@ def peaks():
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_TFLOPS = 1.25
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# apply kernel on this workload, from one ncu capture of the current kernel
+# version; None where no capture of the current kernel exists.
+TRAFFIC_BYTES = {"tc": 140.5e6}
+
 
 class Clocks:
     """nvidia-smi sampling during the timed region."""
@@ -412,7 +417,7 @@ def main():
     else:
         peak, bound = FP64_TFLOPS, "alu"
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": f"apply ({prec})", "peak_source": pk_kind if bound == "tensor" else
+            "traffic": TRAFFIC_BYTES.get(prec), "traffic_unit": "bytes per launch (ncu)", "kernel": f"apply ({prec})", "peak_source": pk_kind if bound == "tensor" else
             "unit counts x 2070 MHz" if prec == "fp32" else "nominal FP64 rate of the part",
             "flops_per_item": flops_item}
 
