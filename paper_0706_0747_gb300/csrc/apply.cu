@@ -452,6 +452,118 @@ __global__ void k_ghost_refine(Forest F, const uint64_t* gkeys, double* gblk, in
     for (int e = threadIdx.x; e < k3; e += blockDim.x) gblk[(size_t)blockIdx.x * k3 + e] = x[e];
 }
 
+// Ghost ids in sorted key order: gid[slot of key i] = i.
+__global__ void k_ghost_reid(int ng, const uint64_t* gkeys, const uint64_t* tab, uint32_t cap, int32_t* gid,
+                             int32_t* err) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
+        const int slot = ghost_find(tab, cap, gkeys[i]);
+        if (slot >= 0) gid[slot] = i;
+        else atomicExch(err, 2);
+    }
+}
+
+// out = Mat along dimension `dim` of the k^3 array x (Mat k x k, out[c] = sum_i Mat[c][i] x[i]).
+__device__ void mode_mul(int k, const double* Mat, const double* x, double* out, int dim) {
+    const int k3 = k * k * k, kk = k * k;
+    for (int idx = threadIdx.x; idx < k3; idx += blockDim.x) {
+        const int i1 = idx / kk, i2 = (idx / k) % k, i3 = idx % k;
+        const int c = dim == 0 ? i1 : (dim == 1 ? i2 : i3);
+        const int st = dim == 0 ? kk : (dim == 1 ? k : 1);
+        const double* src = x + idx - c * st;
+        double a = 0.0;
+        for (int i = 0; i < k; ++i) a += Mat[c * k + i] * src[i * st];
+        out[idx] = a;
+    }
+    __syncthreads();
+}
+
+// Step 2 by sibling groups.  The ghost keys are sorted, so the children of one
+// parent box are consecutive; the block of a group's first ghost refines the
+// ancestor leaf to the parent (the path's per-direction two-scale matrices
+// multiplied first, then one three-mode product), then every child of the
+// group, sharing the direction-3 and direction-2 partial products among the
+// children (d = 0 half of eqs. recon_even / recon_odd).
+__global__ void k_ghost_refine_groups(Forest F, int ng, const uint64_t* gkeys, double* gblk, int32_t* err) {
+    extern __shared__ double sm[];
+    const int k = F.k, k3 = k * k * k, kk = k * k;
+    const int g0 = blockIdx.x;
+    const uint64_t key0 = gkeys[g0];
+    if (g0 > 0 && (gkeys[g0 - 1] >> 3) == (key0 >> 3)) return;  // not the first child of its group
+    double* HT = sm;           // 2 k x k: HT[p][a][i] = H^(p)[i][a]
+    double* P = HT + 2 * kk;   // 3 k x k: the path matrices per direction
+    double* Q = P + 3 * kk;    // 3 k x k: scratch
+    double* x = Q + 3 * kk;    // k^3: the parent
+    double* y = x + k3;        // 2 k^3: direction 3 by p3
+    double* z = y + 2 * k3;    // 4 k^3: direction 2 by (p2, p3)
+    double* w = z + 4 * k3;    // k^3
+    const int j = (int)(key0 >> 58);
+    const int tree = (int)((key0 >> 36) & ((1ull << GH_TREE_BITS) - 1));
+    const uint64_t mk = key0 & ((1ull << 36) - 1);
+    const int b1 = compact1by2(mk >> 2) >> 1, b2 = compact1by2(mk >> 1) >> 1, b3 = compact1by2(mk) >> 1;  // parent
+    const int jp = j - 1;
+    const int32_t* off = F.off + tree * (F.lm + 1);
+    for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) {
+        int p = e / kk, r = e % kk, a = r / k, i = r % k;
+        HT[e] = F.filt[p * kk + i * k + a];
+    }
+    __shared__ int anc, jj, gn;
+    if (threadIdx.x == 0) {
+        int n = 1;
+        while (g0 + n < ng && n < 8 && (gkeys[g0 + n] >> 3) == (key0 >> 3)) ++n;
+        gn = n;
+        anc = -1;
+        for (int lv = jp; lv >= 0 && anc < 0; --lv) {
+            const int sh = jp - lv;
+            const int idx = find_key_exact(F.key, off[lv], off[lv + 1], morton3(b1 >> sh, b2 >> sh, b3 >> sh));
+            if (idx >= 0) {
+                anc = idx;
+                jj = lv;
+            }
+        }
+        if (anc < 0 || !F.leaf[anc]) atomicExch(err, 3);
+    }
+    __syncthreads();
+    if (anc < 0) return;
+    for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = F.s[(size_t)anc * k3 + e];
+    if (jj < jp) {
+        // P_d = H^(p_last)T ... H^(p_first)T along the path ancestor -> parent
+        const int bd[3] = {b1, b2, b3};
+        for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+            const int d = e / kk, r = e % kk;
+            P[e] = HT[((bd[d] >> (jp - jj - 1)) & 1) * kk + r];
+        }
+        __syncthreads();
+        for (int lv = jj + 1; lv < jp; ++lv) {
+            for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+                const int d = e / kk, a = (e % kk) / k, i = e % k;
+                const double* H = HT + ((bd[d] >> (jp - lv - 1)) & 1) * kk;
+                double acc = 0.0;
+                for (int c = 0; c < k; ++c) acc += H[a * k + c] * P[d * kk + c * k + i];
+                Q[e] = acc;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) P[e] = Q[e];
+            __syncthreads();
+        }
+        mode_mul(k, P + 2 * kk, x, y, 2);
+        mode_mul(k, P + kk, y, z, 1);
+        mode_mul(k, P, z, x, 0);
+    } else {
+        __syncthreads();
+    }
+    // the children: direction 3 for p3 = 0, 1; direction 2 for (p2, p3); direction 1 per child
+    mode_mul(k, HT, x, y, 2);
+    mode_mul(k, HT + kk, x, y + k3, 2);
+    for (int q = 0; q < 4; ++q) mode_mul(k, HT + (q >> 1) * kk, y + (q & 1) * k3, z + q * k3, 1);
+    for (int g = 0; g < gn; ++g) {
+        const uint64_t cm = gkeys[g0 + g] & 7ull;  // octant (p1 p2 p3) of the child
+        const int p1 = (int)(cm >> 2) & 1, p23 = (int)(cm & 3);
+        mode_mul(k, HT + p1 * kk, z + p23 * k3, w, 0);
+        for (int e = threadIdx.x; e < k3; e += blockDim.x) gblk[(size_t)(g0 + g) * k3 + e] = w[e];
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ apply
 // Block per output node.  T is the contraction type (double or float); the
 // per-pair sum over terms is accumulated in T and added to the FP64 output.
@@ -618,6 +730,12 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
     }
     S->npairs = h[0];
     S->nghost = h[1];
+    // ghost ids in key order: siblings (children of one parent box) become consecutive
+    if (S->nghost > 1) {
+        MRA_TRY(sort_keys_u64(A, S->gkeys, S->nghost, st));
+        k_ghost_reid<<<(S->nghost + 255) / 256, 256, 0, st>>>(S->nghost, S->gkeys, S->gtab, S->gcap, S->gid, S->err);
+        MRA_CK_LAUNCH();
+    }
     MRA_TRY(dalloc(A, &S->pairs, (size_t)S->npairs + 1));
     sa.pairs = S->pairs;
     k_screen<true><<<sblocks, 256, 0, st>>>(sa);
@@ -628,8 +746,9 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
 int ghost_refine_forest(const Forest& F, const ScreenOut& S, double* gblk, cudaStream_t st) {
     if (S.nghost <= 0) return MRA_OK;
     const int k = F.k, k3 = k * k * k;
-    const size_t gsm = (2 * (size_t)k * k + 3 * (size_t)k3) * sizeof(double);
-    k_ghost_refine<<<S.nghost, 128, gsm, st>>>(F, S.gkeys, gblk, S.err + 1);
+    const size_t gsm = (8 * (size_t)k * k + 8 * (size_t)k3) * sizeof(double);
+    MRA_CK(cudaFuncSetAttribute(k_ghost_refine_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    k_ghost_refine_groups<<<S.nghost, 128, gsm, st>>>(F, S.nghost, S.gkeys, gblk, S.err + 1);
     MRA_CK_LAUNCH();
     return MRA_OK;
 }

@@ -47,50 +47,56 @@ namespace mra {
 // (zero for indices >= kr) at half index i2*64 + i3*8 + i1 (core matrix i2,
 // row i3, column i1), with a power-of-two scale per block.  Block b is node b
 // of s (b < n) or Step-2 block b - n.
-__global__ void k_tc_prep_blocks(int nb, int kr, int n, const double* s, const double* gblk, __half* xh,
-                                 __half* xl, float* sx, float* xmax, float* xnrm) {
-    __shared__ float red[4];
-    __shared__ double red2[4];
-    const int b = blockIdx.x;
-    if (b >= nb) return;
+#define PREP_WARPS 8
+__global__ void __launch_bounds__(32 * PREP_WARPS) k_tc_prep_blocks(int nb, int kr, int n, const double* s,
+                                                                  const double* gblk, __half* xh, __half* xl,
+                                                                  float* sx, float* xmax, float* xnrm) {
+    // warp per block: coalesced FP64 reads into shared memory, then each lane
+    // writes the 8 values (i1 = 0..7) of two (i2, i3) rows as one 16-byte hi
+    // and one 16-byte lo store
+    __shared__ double xs[PREP_WARPS][512];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int k3 = kr * kr * kr;
-    const double* src = b < n ? s + (size_t)b * k3 : gblk + (size_t)(b - n) * k3;
-    double v[4], s2 = 0.0;
-    float m = 0.0f;
-    for (int q = 0; q < 4; ++q) {
-        const int idx = threadIdx.x + 128 * q;  // (i1, i2, i3) of the padded 8^3 block
-        const int i1 = idx >> 6, i2 = (idx >> 3) & 7, i3 = idx & 7;
-        v[q] = (i1 < kr && i2 < kr && i3 < kr) ? src[(i1 * kr + i2) * kr + i3] : 0.0;
-        m = fmaxf(m, (float)fabs(v[q]));
-        s2 += v[q] * v[q];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[threadIdx.x >> 5] = m;
-        red2[threadIdx.x >> 5] = s2;
-    }
-    __syncthreads();
-    m = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
-    int e = 0;
-    if (m > 0.0f) frexpf(m, &e);
-    // m * scale in [2^12, 2^13); blocks below 2^-100 keep the scale 2^113 (a
-    // finite float) and round to zero in FP16
-    const double scale = ldexp(1.0, 13 - max(e, -100));
-    for (int q = 0; q < 4; ++q) {
-        const int idx = threadIdx.x + 128 * q;
-        const int i1 = idx >> 6, i2 = (idx >> 3) & 7, i3 = idx & 7;
-        __half hi, lo;
-        tc::split_h((float)(v[q] * scale), hi, lo);
-        xh[(size_t)b * 512 + i2 * 64 + i3 * 8 + i1] = hi;
-        xl[(size_t)b * 512 + i2 * 64 + i3 * 8 + i1] = lo;
-    }
-    if (threadIdx.x == 0) {
-        sx[b] = (float)scale;
-        xmax[b] = m;
-        xnrm[b] = (float)sqrt(red2[0] + red2[1] + red2[2] + red2[3]);
+    double* x = xs[wl];
+    for (int b = blockIdx.x * PREP_WARPS + wl; b < nb; b += gridDim.x * PREP_WARPS) {
+        const double* src = b < n ? s + (size_t)b * k3 : gblk + (size_t)(b - n) * k3;
+        double s2 = 0.0;
+        float m = 0.0f;
+        for (int e = lane; e < k3; e += 32) {
+            const double v = src[e];
+            x[e] = v;
+            m = fmaxf(m, (float)fabs(v));
+            s2 += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        __syncwarp();
+        int e = 0;
+        if (m > 0.0f) frexpf(m, &e);
+        // m * scale in [2^12, 2^13); blocks below 2^-100 keep the scale 2^113 (a
+        // finite float) and round to zero in FP16
+        const double scale = ldexp(1.0, 13 - max(e, -100));
+        for (int p = lane; p < 64; p += 32) {  // row (i2, i3) of the stage-I layout
+            const int i2 = p >> 3, i3 = p & 7;
+            uint4 h4, l4;
+            __half* hh = (__half*)&h4;
+            __half* ll = (__half*)&l4;
+#pragma unroll
+            for (int i1 = 0; i1 < 8; ++i1) {
+                const double v = (i1 < kr && i2 < kr && i3 < kr) ? x[(i1 * kr + i2) * kr + i3] : 0.0;
+                tc::split_h((float)(v * scale), hh[i1], ll[i1]);
+            }
+            ((uint4*)(xh + (size_t)b * 512))[p] = h4;
+            ((uint4*)(xl + (size_t)b * 512))[p] = l4;
+        }
+        if (lane == 0) {
+            sx[b] = (float)scale;
+            xmax[b] = m;
+            xnrm[b] = (float)sqrt(s2);
+        }
+        __syncwarp();
     }
 }
 
@@ -639,7 +645,8 @@ int tc_prep_F(const mra_op* op, const TcBuffers& B, cudaStream_t st) {
 
 int tc_prep_blocks(int nb, int kr, int n, const double* s, const double* gblk, const TcBuffers& B, cudaStream_t st) {
     if (nb <= 0) return MRA_OK;
-    k_tc_prep_blocks<<<nb, 128, 0, st>>>(nb, kr, n, s, gblk, B.xh, B.xl, B.sx, B.xmax, B.xnrm);
+    const int grid = std::max(1, std::min(152 * 8, (nb + PREP_WARPS - 1) / PREP_WARPS));
+    k_tc_prep_blocks<<<grid, 32 * PREP_WARPS, 0, st>>>(nb, kr, n, s, gblk, B.xh, B.xl, B.sx, B.xmax, B.xnrm);
     MRA_CK_LAUNCH();
     return MRA_OK;
 }
