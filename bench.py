@@ -228,6 +228,25 @@ def batched_section(K, Wu, flush, stream, peak_tensor, prec):
                          "note": "k = 6 runs on 8 x 8 tiles padded with zeros"}}
 
 
+# ---------------------------------------------------------------- replicas
+def slowest_ms(local_ms, ws, device):
+    """The slowest replica's time: the maximum over the ranks of the
+    process group (the local time when there is one rank)."""
+    if ws <= 1:
+        return local_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_step, steps, ws, slowest):
+    """Whole-job throughput of ws independent replicas: the units all ranks
+    processed over the slowest rank's time (ms)."""
+    return ws * units_per_step * steps / (slowest / 1e3)
+
+
 # ---------------------------------------------------------------- GPU arm
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -313,9 +332,7 @@ def main():
         launches = mra.kernel_launches() - l0
         torch.cuda.synchronize()
         if ws > 1:
-            t = torch.tensor([tot_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot_ms = float(t.item())
+            tot_ms = slowest_ms(tot_ms, ws, "cuda")
             dist.barrier()
         return tot_ms, ms_apply, stats, n_out, launches
 
@@ -381,9 +398,9 @@ def main():
                  "ms_apply_kernel": statistics.median(r[1]),
                  "rel_l2_vs_fp64": errs.get(p, 0.0), "items_single_fp16": lowp.get(p, 0)}
              for p, r in runs.items()}
-    value = ws * items_plain * K / (ms / 1e3)
-    value64 = ws * items_plain * K / (ms64 / 1e3)
-    coeffs = ws * nout * k ** 3 * K / (ms / 1e3)
+    value = replica_value(items_plain, K, ws, ms)
+    value64 = replica_value(items_plain, K, ws, ms64)
+    coeffs = replica_value(nout * k ** 3, K, ws, ms)
 
     # e2e through the C ABI with host buffers (import -> hot path -> export)
     coords, leaf, blocks, _ = tree.export()

@@ -462,9 +462,11 @@ __global__ void k_ghost_reid(int ng, const uint64_t* gkeys, const uint64_t* tab,
     }
 }
 
-// out = Mat along dimension `dim` of the k^3 array x (Mat k x k, out[c] = sum_i Mat[c][i] x[i]).
-__device__ void mode_mul(int k, const double* Mat, const double* x, double* out, int dim) {
-    const int k3 = k * k * k, kk = k * k;
+// out = Mat along dimension `dim` of the k^3 array x (Mat k x k, out[c] = sum_i Mat[c][i] x[i]);
+// KT > 0 fixes k at compile time.
+template <int KT>
+__device__ void mode_mul(int kdyn, const double* Mat, const double* x, double* out, int dim) {
+    const int k = KT ? KT : kdyn, k3 = k * k * k, kk = k * k;
     for (int idx = threadIdx.x; idx < k3; idx += blockDim.x) {
         const int i1 = idx / kk, i2 = (idx / k) % k, i3 = idx % k;
         const int c = dim == 0 ? i1 : (dim == 1 ? i2 : i3);
@@ -483,9 +485,10 @@ __device__ void mode_mul(int k, const double* Mat, const double* x, double* out,
 // multiplied first, then one three-mode product), then every child of the
 // group, sharing the direction-3 and direction-2 partial products among the
 // children (d = 0 half of eqs. recon_even / recon_odd).
+template <int KT>
 __global__ void k_ghost_refine_groups(Forest F, int ng, const uint64_t* gkeys, double* gblk, int32_t* err) {
     extern __shared__ double sm[];
-    const int k = F.k, k3 = k * k * k, kk = k * k;
+    const int k = KT ? KT : F.k, k3 = k * k * k, kk = k * k;
     const int g0 = blockIdx.x;
     const uint64_t key0 = gkeys[g0];
     if (g0 > 0 && (gkeys[g0 - 1] >> 3) == (key0 >> 3)) return;  // not the first child of its group
@@ -545,20 +548,20 @@ __global__ void k_ghost_refine_groups(Forest F, int ng, const uint64_t* gkeys, d
             for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) P[e] = Q[e];
             __syncthreads();
         }
-        mode_mul(k, P + 2 * kk, x, y, 2);
-        mode_mul(k, P + kk, y, z, 1);
-        mode_mul(k, P, z, x, 0);
+        mode_mul<KT>(k, P + 2 * kk, x, y, 2);
+        mode_mul<KT>(k, P + kk, y, z, 1);
+        mode_mul<KT>(k, P, z, x, 0);
     } else {
         __syncthreads();
     }
     // the children: direction 3 for p3 = 0, 1; direction 2 for (p2, p3); direction 1 per child
-    mode_mul(k, HT, x, y, 2);
-    mode_mul(k, HT + kk, x, y + k3, 2);
-    for (int q = 0; q < 4; ++q) mode_mul(k, HT + (q >> 1) * kk, y + (q & 1) * k3, z + q * k3, 1);
+    mode_mul<KT>(k, HT, x, y, 2);
+    mode_mul<KT>(k, HT + kk, x, y + k3, 2);
+    for (int q = 0; q < 4; ++q) mode_mul<KT>(k, HT + (q >> 1) * kk, y + (q & 1) * k3, z + q * k3, 1);
     for (int g = 0; g < gn; ++g) {
         const uint64_t cm = gkeys[g0 + g] & 7ull;  // octant (p1 p2 p3) of the child
         const int p1 = (int)(cm >> 2) & 1, p23 = (int)(cm & 3);
-        mode_mul(k, HT + p1 * kk, z + p23 * k3, w, 0);
+        mode_mul<KT>(k, HT + p1 * kk, z + p23 * k3, w, 0);
         for (int e = threadIdx.x; e < k3; e += blockDim.x) gblk[(size_t)(g0 + g) * k3 + e] = w[e];
         __syncthreads();
     }
@@ -747,8 +750,10 @@ int ghost_refine_forest(const Forest& F, const ScreenOut& S, double* gblk, cudaS
     if (S.nghost <= 0) return MRA_OK;
     const int k = F.k, k3 = k * k * k;
     const size_t gsm = (8 * (size_t)k * k + 8 * (size_t)k3) * sizeof(double);
-    MRA_CK(cudaFuncSetAttribute(k_ghost_refine_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
-    k_ghost_refine_groups<<<S.nghost, 128, gsm, st>>>(F, S.nghost, S.gkeys, gblk, S.err + 1);
+    auto fn = k == 8 ? k_ghost_refine_groups<8> : (k == 6 ? k_ghost_refine_groups<6> :
+                                                 (k == 4 ? k_ghost_refine_groups<4> : k_ghost_refine_groups<0>));
+    MRA_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    fn<<<S.nghost, 128, gsm, st>>>(F, S.nghost, S.gkeys, gblk, S.err + 1);
     MRA_CK_LAUNCH();
     return MRA_OK;
 }

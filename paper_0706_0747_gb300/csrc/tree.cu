@@ -642,6 +642,122 @@ __global__ void k_compress_fast_level(int k, int lo, int hi, const int32_t* chil
     if (threadIdx.x == 0) dnorm[i] = sqrt(acc);
 }
 
+// The same two kernels with the order k fixed at compile time (the shapes of
+// every stage known, so the index arithmetic is by constants).
+template <int N0, int N1, int N2, int DIM, int NOUT>
+__device__ __forceinline__ void stage_t(const double* in, double* out, const double* Mat) {
+    constexpr int E0 = DIM == 0 ? NOUT : N0, E1 = DIM == 1 ? NOUT : N1, E2 = DIM == 2 ? NOUT : N2;
+    constexpr int NIN = DIM == 0 ? N0 : (DIM == 1 ? N1 : N2);
+    constexpr int S0 = N1 * N2, S1 = N2, ST = DIM == 0 ? S0 : (DIM == 1 ? S1 : 1);
+    for (int idx = threadIdx.x; idx < E0 * E1 * E2; idx += blockDim.x) {
+        const int x0 = idx / (E1 * E2), x1 = (idx / E2) % E1, x2 = idx % E2;
+        const int r = DIM == 0 ? x0 : (DIM == 1 ? x1 : x2);
+        const double* src = in + (DIM == 0 ? 0 : x0 * S0) + (DIM == 1 ? 0 : x1 * S1) + (DIM == 2 ? 0 : x2);
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < NIN; ++c) acc += Mat[r * NIN + c] * src[c * ST];
+        out[idx] = acc;
+    }
+    __syncthreads();
+}
+
+template <int K>
+__global__ void k_up_level_t(int lo, int hi, const int32_t* child, double* s, const double* filt) {
+    constexpr int K2 = 2 * K, K3 = K * K * K;
+    extern __shared__ double sm[];
+    const int i = lo + blockIdx.x;
+    if (i >= hi || child[i] < 0) return;
+    const int c0 = child[i];
+    double* U = sm;
+    double* D = U + 2 * K * K;
+    double* x = D + 2 * K * K;  // K^3
+    double* t1 = x + K3;        // 2K^3
+    double* t2 = t1 + 2 * K3;   // 4K^3
+    load_UD(K, filt, U, D);
+    for (int e = threadIdx.x; e < K3; e += blockDim.x) x[e] = s[(size_t)i * K3 + e];
+    __syncthreads();
+    stage_t<K, K, K, 0, K2>(x, t1, U);
+    stage_t<K2, K, K, 1, K2>(t1, t2, U);
+    for (int idx = threadIdx.x; idx < 8 * K3; idx += blockDim.x) {
+        const int x1 = idx / (K2 * K2), x2 = (idx / K2) % K2, x3 = idx % K2;
+        const double* src = t2 + (x1 * K2 + x2) * K;
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc += U[x3 * K + c] * src[c];
+        const int o = ((x1 / K) << 2) | ((x2 / K) << 1) | (x3 / K);
+        s[(size_t)(c0 + o) * K3 + ((x1 % K) * K + (x2 % K)) * K + (x3 % K)] += acc;
+    }
+}
+
+template <int K>
+__global__ void k_compress_fast_level_t(int lo, int hi, const int32_t* child, double* s, double* dnorm,
+                                        const double* filt) {
+    constexpr int K2 = 2 * K, K3 = K * K * K;
+    extern __shared__ double sm[];
+    __shared__ double red[32];
+    const int i = lo + blockIdx.x;
+    if (i >= hi || child[i] < 0) return;
+    const int c0 = child[i];
+    double* U = sm;
+    double* D = U + 2 * K * K;
+    double* cube = D + 2 * K * K;  // 8K^3
+    double* r1 = cube + 8 * K3;    // 4K^3
+    double* r2 = r1 + 4 * K3;      // 2K^3
+    double* sp = r2 + 2 * K3;      // K^3
+    load_UD(K, filt, U, D);
+    for (int e = threadIdx.x; e < 8 * K3; e += blockDim.x) {
+        const int o = e / K3, r = e % K3;
+        const int i1 = r / (K * K), i2 = (r / K) % K, i3 = r % K;
+        const int x1 = ((o >> 2) & 1) * K + i1, x2 = ((o >> 1) & 1) * K + i2, x3 = (o & 1) * K + i3;
+        cube[(x1 * K2 + x2) * K2 + x3] = s[(size_t)(c0 + o) * K3 + r];
+    }
+    __syncthreads();
+    stage_t<K2, K2, K2, 0, K>(cube, r1, D);
+    stage_t<K, K2, K2, 1, K>(r1, r2, D);
+    stage_t<K, K, K2, 2, K>(r2, sp, D);
+    for (int e = threadIdx.x; e < K3; e += blockDim.x) s[(size_t)i * K3 + e] = sp[e];
+    stage_t<K, K, K, 0, K2>(sp, r2, U);
+    stage_t<K2, K, K, 1, K2>(r2, r1, U);
+    double acc = 0.0;
+    for (int idx = threadIdx.x; idx < 8 * K3; idx += blockDim.x) {
+        const int x1 = idx / (K2 * K2), x2 = (idx / K2) % K2, x3 = idx % K2;
+        const double* src = r1 + (x1 * K2 + x2) * K;
+        double up = 0.0;
+#pragma unroll
+        for (int c = 0; c < K; ++c) up += U[x3 * K + c] * src[c];
+        const double dv = cube[idx] - up;
+        acc += dv * dv;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) dnorm[i] = sqrt(acc);
+}
+
+template <int K>
+static int compress_fast_t(mra_tree* t, cudaStream_t st) {
+    const size_t smem = (4 * (size_t)K * K + 15 * (size_t)K * K * K) * sizeof(double);
+    MRA_CK(cudaFuncSetAttribute(k_compress_fast_level_t<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int j = t->nlev - 2; j >= 0; --j) {
+        int lo = t->off[j], hi = t->off[j + 1];
+        if (hi <= lo) continue;
+        k_compress_fast_level_t<K><<<hi - lo, 256, smem, st>>>(lo, hi, t->a.child, t->s, t->dnorm, t->filt);
+        MRA_CK_LAUNCH();
+    }
+    return MRA_OK;
+}
+
+template <int K>
+static int assemble_t(mra_tree* t, cudaStream_t st) {
+    const size_t smem = (4 * (size_t)K * K + 7 * (size_t)K * K * K) * sizeof(double);
+    MRA_CK(cudaFuncSetAttribute(k_up_level_t<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int j = 0; j + 1 < t->nlev; ++j) {
+        int lo = t->off[j], hi = t->off[j + 1];
+        if (hi <= lo) continue;
+        k_up_level_t<K><<<hi - lo, 256, smem, st>>>(lo, hi, t->a.child, t->s, t->filt);
+        MRA_CK_LAUNCH();
+    }
+    return MRA_OK;
+}
+
 static int cube_smem(int k, size_t* bytes, const void* fn) {
     *bytes = (size_t)8 * k * k * k * sizeof(double);
     MRA_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes));
@@ -651,9 +767,14 @@ static int cube_smem(int k, size_t* bytes, const void* fn) {
 int compress_impl(mra_tree* t, int store_d, cudaStream_t st) {
     if (!store_d) {
         const int k = t->k;
+        MRA_CK(cudaMemsetAsync(t->dnorm, 0, t->n * sizeof(double), st));
+        if (k == 4 || k == 6 || k == 8) {
+            MRA_TRY(k == 4 ? compress_fast_t<4>(t, st) : (k == 6 ? compress_fast_t<6>(t, st) : compress_fast_t<8>(t, st)));
+            t->state = MRA_TREE_REDUNDANT;
+            return MRA_OK;
+        }
         const size_t smem = (4 * (size_t)k * k + 15 * (size_t)k * k * k) * sizeof(double);
         MRA_CK(cudaFuncSetAttribute(k_compress_fast_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MRA_CK(cudaMemsetAsync(t->dnorm, 0, t->n * sizeof(double), st));
         for (int j = t->nlev - 2; j >= 0; --j) {
             int lo = t->off[j], hi = t->off[j + 1];
             if (hi <= lo) continue;
@@ -696,6 +817,11 @@ int inverse_impl(mra_tree* t, cudaStream_t st) {
 
 int assemble_impl(mra_tree* t, cudaStream_t st) {
     const int k = t->k;
+    if (k == 4 || k == 6 || k == 8) {
+        MRA_TRY(k == 4 ? assemble_t<4>(t, st) : (k == 6 ? assemble_t<6>(t, st) : assemble_t<8>(t, st)));
+        t->state = MRA_TREE_LEAVES;
+        return MRA_OK;
+    }
     const size_t smem = (4 * (size_t)k * k + 7 * (size_t)k * k * k) * sizeof(double);
     MRA_CK(cudaFuncSetAttribute(k_up_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int j = 0; j + 1 < t->nlev; ++j) {
