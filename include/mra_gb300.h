@@ -367,7 +367,7 @@ int mra_screen_data(const mra_op* op, const mra_tree* f, float* inputs, float* t
  * must not be capturing.  Executes on one plan must not overlap.
  * mra_plan_autotune (synchronous) times the tensor-core kernel variants on
  * the plan's worklist, reps launches each: (terms per chunk, CTAs per SM) in
- * (8,3) (8,2) (4,3) (4,2) (8,1), node order as screened or heaviest first
+ * (8,3) (8,2) (4,3) (4,2) (4,4), node order as screened or heaviest first
  * (most pairs).  The fastest becomes the plan's variant (ms_variant[v],
  * v = pair index + 5 heavy_first); other precisions have one variant.
  * mra_plan_set_variant chooses one by hand.  Both drop a captured graph.

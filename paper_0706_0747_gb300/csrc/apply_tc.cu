@@ -166,7 +166,7 @@ __device__ __forceinline__ float pow2floor(double x) {
 }
 
 template <int MC, bool LADDER>
-__global__ void __launch_bounds__(TC_THREADS, 3) k_apply_tc(TcArgs T) {
+__global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs T) {
     using L = TcSmem<MC>;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint32_t s_tmem;
@@ -680,8 +680,8 @@ static int launch_mc(const TcArgs& T, int ctas_per_sm, cudaStream_t st) {
     return MRA_OK;
 }
 
-// variant: terms per chunk (4 or 8) and CTAs per SM (1 to 3); registers,
-// TMEM and shared memory allow 3 CTAs per SM for both chunk sizes.
+// variant: terms per chunk (4 or 8) and CTAs per SM (1 to 3 for 8 terms, 1 to 4
+// for 4 terms: registers, TMEM and shared memory allow that many).
 // tc_configure() first.
 int tc_launch(const TcArgs& T, int mc, int ctas_per_sm, cudaStream_t st) {
     MRA_CK(cudaMemsetAsync(T.counter, 0, sizeof(int), st));

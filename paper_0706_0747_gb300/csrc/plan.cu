@@ -354,7 +354,7 @@ int mra_plan_autotune(mra_plan* p, int reps, void* stream) {
     MRA_CK(cudaEventCreate(&e1));
     float best = 1e30f;
     // (terms per chunk, CTAs per SM)
-    static const int kMC[5] = {8, 8, 4, 4, 8}, kCTA[5] = {3, 2, 3, 2, 1};
+    static const int kMC[5] = {8, 8, 4, 4, 4}, kCTA[5] = {3, 2, 3, 2, 4};
     for (int v = 0; v < MRA_PLAN_VARIANTS; ++v) {
         const int mc = kMC[v % 5], ctas = kCTA[v % 5], ord = v / 5;
         MRA_TRY(plan_tc_launch(p, mc, ctas, ord, st));  // warm-up
@@ -381,8 +381,8 @@ int mra_plan_autotune(mra_plan* p, int reps, void* stream) {
 
 int mra_plan_set_variant(mra_plan* p, int mc, int ctas_per_sm, int heavy_first) {
     if (!plan_ok(p)) { set_error("invalid plan handle"); return MRA_EINVAL; }
-    if ((mc != 4 && mc != 8) || ctas_per_sm < 1 || ctas_per_sm > 3) {
-        set_error("variant: terms per chunk 4 or 8, 1 to 3 CTAs per SM");
+    if ((mc != 4 && mc != 8) || ctas_per_sm < 1 || ctas_per_sm > (mc == 4 ? 4 : 3)) {
+        set_error("variant: terms per chunk 8 with 1 to 3 CTAs per SM, or 4 with 1 to 4");
         return MRA_EINVAL;
     }
     plan_drop_graph(p);

@@ -164,9 +164,9 @@ def test_autotune_variants_agree(batch):
     info = plan.autotune(reps=2)
     assert info["tuned"] == 1
     assert all(ms > 0.0 for ms in info["ms_variant"])
-    assert info["terms_per_chunk"] in (4, 8) and info["ctas_per_sm"] in (1, 2, 3)
+    assert info["terms_per_chunk"] in (4, 8) and info["ctas_per_sm"] in (1, 2, 3, 4)
     for v in range(10):
-        mc, ctas = [(8, 3), (8, 2), (4, 3), (4, 2), (8, 1)][v % 5]
+        mc, ctas = [(8, 3), (8, 2), (4, 3), (4, 2), (4, 4)][v % 5]
         plan.set_variant(terms_per_chunk=mc, ctas_per_sm=ctas, heavy_first=v >= 5)
         plan.execute()
         outs = outputs(plan, len(tg))
