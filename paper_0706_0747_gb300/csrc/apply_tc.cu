@@ -488,10 +488,11 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                         // D_I -> stage II A: row (c1, i3), K column i2.  This thread holds
                         // D_I rows (i2, i3) = (2 quarter, lane/4) and (2 quarter + 1, lane/4):
                         // K neighbours, stored as one half2 per c1
+                        float vv[MC / 2][4];
+                        tc::tmem_ld16x256_rep<MC / 2>(tD1 + lane_off + mc_lo * 8, vv);
 #pragma unroll
                         for (int mc = mc_lo; mc < mc_hi; ++mc) {
-                            float v[4];
-                            tc::tmem_ld16x256(tD1 + lane_off + mc * 8, v);
+                            const float* v = vv[mc - mc_lo];
                             const int i3 = lane >> 2;
                             const float c2 = s_c2[mc];
 #pragma unroll
@@ -541,10 +542,11 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     if (aborted) break;
                     tc::fence_after();
                     // D_II rows (c1, i3) = (2 quarter + s, lane/4), columns c2 = cA + h
+                    float vv[MC / 2][4];
+                    tc::tmem_ld16x256_rep<MC / 2>(tD2 + lane_off + mc_lo * 8, vv);
 #pragma unroll
                     for (int mc = mc_lo; mc < mc_hi; ++mc) {
-                        float v[4];
-                        tc::tmem_ld16x256(tD2 + lane_off + mc * 8, v);
+                        const float* v = vv[mc - mc_lo];
                         const int i3 = lane >> 2;
                         const float c3 = s_c3[mc];
 #pragma unroll
@@ -581,10 +583,11 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     if (aborted) break;
                     tc::fence_after();
                     // ghat += w_m Y_m (FP64): row (c1, c2), column c3; D_I is free again after this
+                    float yv[MC / 2][4];
+                    tc::tmem_ld16x256_rep<MC / 2>(tD3 + lane_off + mc_lo * 8, yv);
 #pragma unroll
                     for (int mc = mc_lo; mc < mc_hi; ++mc) {
-                        float v[4];
-                        tc::tmem_ld16x256(tD3 + lane_off + mc * 8, v);
+                        const float* v = yv[mc - mc_lo];
                         const double fin = s_fin[mc];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) y[q] += fin * (double)v[q];

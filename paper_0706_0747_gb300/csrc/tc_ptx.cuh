@@ -90,6 +90,44 @@ __device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, float* v) {
     for (int q = 0; q < 4; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// NREP (2 or 4) repetitions of the 16x256b shape over consecutive 8-column
+// groups in one instruction and one wait: v[r][0..3] as in tmem_ld16x256 for
+// columns taddr + 8 r.  The wait names every destination register, so no use
+// can be scheduled before it.
+template <int NREP>
+__device__ __forceinline__ void tmem_ld16x256_rep(uint32_t taddr, float (*v)[4]);
+
+template <>
+__device__ __forceinline__ void tmem_ld16x256_rep<2>(uint32_t taddr, float (*v)[4]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q >> 2][q & 3] = __uint_as_float(r[q]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld16x256_rep<4>(uint32_t taddr, float (*v)[4]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q >> 2][q & 3] = __uint_as_float(r[q]);
+}
+
 // 16-byte asynchronous global -> shared copies (completion by wait_all)
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
