@@ -381,7 +381,9 @@ typedef struct mra_plan mra_plan;
 typedef struct {
     int precision;          /* MRA_PREC_*                                     */
     int use_graph;          /* 1: executes replay one captured CUDA graph      */
-    int reserved[6];
+    int screen_mode;        /* MRA_SCREEN_STATIC or MRA_SCREEN_PAIR (ranges    */
+                            /* narrowed at creation with the blocks then)     */
+    int reserved[5];
 } mra_plan_opts;
 
 typedef struct {

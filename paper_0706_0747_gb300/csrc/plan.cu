@@ -97,6 +97,7 @@ struct mra_plan {
     float ms_screen = 0.0f;
     // graph
     int use_graph = 1;
+    int screen_mode = MRA_SCREEN_STATIC;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -218,6 +219,11 @@ static int plan_build(mra_plan* p, cudaStream_t st) {
     cudaEventDestroy(e1);
 
     MRA_TRY(dalloc(A, &p->gblk, (size_t)(p->S.nghost + 1) * k3));
+    if (p->screen_mode == MRA_SCREEN_PAIR) {
+        // exact per-pair term ranges from the blocks at creation (Step 2 first)
+        MRA_TRY(ghost_refine_forest(F, p->S, p->gblk, st));
+        MRA_TRY(schedule_narrow(op, F, p->S, p->gblk, 1, nullptr, 0, nullptr, nullptr, nullptr, A, st));
+    }
     MRA_TRY(dalloc(A, &p->out, (size_t)n * k3));
     MRA_TRY(dalloc(A, &p->nitems, (size_t)nt + 1));
     MRA_CK(cudaMemsetAsync(p->nitems, 0, ((size_t)nt + 1) * sizeof(unsigned long long), st));
@@ -291,6 +297,12 @@ int mra_plan_create(const mra_op* op, mra_tree* const* trees, int ntrees, const 
     p->precision = prec;
     p->tc = tc;
     p->use_graph = opts ? (opts->use_graph != 0) : 1;
+    p->screen_mode = opts ? opts->screen_mode : MRA_SCREEN_STATIC;
+    if (p->screen_mode != MRA_SCREEN_STATIC && p->screen_mode != MRA_SCREEN_PAIR) {
+        set_error("the batched apply takes the static or the exact per-pair screen");
+        delete p;
+        return MRA_EINVAL;
+    }
     p->A = trees[0]->A;
     p->A.stream = st;
     p->trees.assign(trees, trees + ntrees);

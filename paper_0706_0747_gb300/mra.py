@@ -73,7 +73,8 @@ class ApplyStats(ctypes.Structure):
 
 
 class PlanOpts(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+    _fields_ = [("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("screen_mode", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -249,13 +250,19 @@ class Tree:
     def n(self):
         return self.info().n_nodes
 
-    def export(self, stream=None):
+    def export(self, stream=None, out=None):
+        """(coords, leaf, blocks, dnorm) as host arrays; ``out`` may give
+        arrays (e.g. in pinned memory) with room for them, filled in place."""
         inf = self.info()
         n, k = inf.n_nodes, inf.k
-        coords = np.zeros((n, 4), dtype=np.int32)
-        leaf = np.zeros(n, dtype=np.int32)
-        blocks = np.zeros((n, k, k, k))
-        dnorm = np.zeros(n)
+        if out is None:
+            coords = np.zeros((n, 4), dtype=np.int32)
+            leaf = np.zeros(n, dtype=np.int32)
+            blocks = np.zeros((n, k, k, k))
+            dnorm = np.zeros(n)
+        else:
+            coords, leaf, blocks, dnorm = (a.reshape(-1)[:m].reshape(shp) for a, m, shp in
+                                           zip(out, (4 * n, n, n * k ** 3, n), ((n, 4), (n,), (n, k, k, k), (n,))))
         _check(lib().mra_tree_export(self.h, _ip(coords), _ip(leaf), _dp(blocks), _dp(dnorm), _stream(stream)))
         return coords, leaf, blocks, dnorm
 
@@ -418,14 +425,15 @@ class Plan:
             pass
 
 
-def plan_create(op, trees, precision=None, use_graph=True, stream=None):
-    """mra_plan_create over compressed trees (all of op's order k)."""
+def plan_create(op, trees, precision=None, use_graph=True, stream=None, screen="static"):
+    """mra_plan_create over compressed trees (all of op's order k); screen
+    "static" or "pair" (exact per-pair ranges fixed at creation)."""
     arr = (_P * len(trees))(*[t.h for t in trees])
     opts = None
-    if precision is not None or not use_graph:
+    if precision is not None or not use_graph or screen != "static":
         k = op.info().k
         prec = PREC[precision] if precision is not None else (PREC["tc"] if k <= 8 else PREC["fp64"])
-        opts = ctypes.byref(PlanOpts(prec, int(use_graph)))
+        opts = ctypes.byref(PlanOpts(prec, int(use_graph), SCREEN[screen]))
     h = _P()
     _check(lib().mra_plan_create(op.h, arr, len(trees), opts, _stream(stream), ctypes.byref(h)))
     return Plan(h.value, op, trees)

@@ -251,3 +251,20 @@ def test_rhs256_sampled_against_oracle(rhs256):
         ref = OA.apply_ns(op_o, t_o, stats=st_o, nodes=nodes)
         assert abs(plan.tree_stats(b)["eta"] - st_o["eta"]) <= 1e-12 * st_o["eta"]
         assert rel_l2({key: got[key] for key in nodes}, ref) <= 10 * cfg.eps
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tc"])
+def test_batch_pair_screen_matches_oracle(batch, precision):
+    """The exact per-pair screen in a batch: per tree the items of the oracle's
+    pair_screen apply and its result (rounding for FP64, the gate for tc)."""
+    trees_o, op_o, op_g, _ = batch
+    tg = gpu_trees(trees_o)
+    plan = mra.plan_create(op_g, tg, precision=precision, screen="pair")
+    plan.execute()
+    outs = outputs(plan, len(tg))
+    for b, t in enumerate(trees_o):
+        st_o = {}
+        ref = OA.apply_ns(op_o, t, stats=st_o, pair_screen=True)
+        got = plan.tree_stats(b)["n_items"]
+        assert abs(got - st_o["n_items"]) <= max(2, st_o["n_items"] // 100000)
+        assert rel_l2(outs[b], ref) <= (1e-10 if precision == "fp64" else 10 * EPS)
