@@ -57,3 +57,25 @@ def test_invalid_arguments_rejected_without_gpu(lib):
 
 def test_version(lib):
     assert "sm_103a" in mra.version()
+
+
+def test_batched_and_schedule_entries_reject_invalid_arguments(lib):
+    """Argument checks of the batched, network and no-alloc entries that run
+    before any device work (so they need no GPU)."""
+    h = ctypes.c_void_p()
+    # a plan needs an operator and at least one tree
+    assert lib.mra_plan_create(None, None, 0, None, None, ctypes.byref(h)) == mra.EINVAL
+    assert h.value is None
+    for fn, args in [("mra_plan_execute", (None, None)), ("mra_plan_autotune", (None, 1, None)),
+                     ("mra_plan_set_variant", (None, 8, 2, 0)), ("mra_plan_get_info", (None, None, None)),
+                     ("mra_plan_tree_stats", (None, 0, None, None)), ("mra_screen_data", (None, None, None, None, None)),
+                     ("mra_mlp_forward", (None, None, 0, None, None)), ("mra_mlp_num_params", (None, None)),
+                     ("mra_apply_ns_noalloc", (None, None, 0, None, None, None))]:
+        assert getattr(lib, fn)(*args) == mra.EINVAL, fn
+    p = ctypes.c_void_p()
+    assert lib.mra_plan_output(None, 0, None, ctypes.byref(p)) == mra.EINVAL and p.value is None
+    # network shapes outside [1, 1024]
+    assert lib.mra_mlp_create(0, 12, None, 0, None, None, ctypes.byref(h)) == mra.EINVAL
+    assert lib.mra_mlp_create(16, 2000, None, 0, None, None, ctypes.byref(h)) == mra.EINVAL
+    assert h.value is None
+    assert lib.mra_free_plan(None) == mra.OK and lib.mra_mlp_free(None) == mra.OK
