@@ -800,18 +800,36 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         return MRA_EINVAL;
     }
     const Alloc& A = f->A;
-    cudaEvent_t ev[4];
+    // everything below is released on every return path; the output tree only
+    // when the call fails
+    struct Guard {
+        const Alloc& A;
+        ScreenOut S;
+        void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+        mra_tree* g = nullptr;
+        explicit Guard(const Alloc& a) : A(a) {}
+        ~Guard() {
+            screen_release(A, &S);
+            for (void* q : p) A.put(q);
+            for (cudaEvent_t e : ev)
+                if (e) cudaEventDestroy(e);
+            if (g) mra_free_tree(g);
+        }
+    } G(A);
+    cudaEvent_t* ev = G.ev;
     for (int e = 0; e < 4; ++e) MRA_CK(cudaEventCreate(&ev[e]));
     MRA_CK(cudaEventRecord(ev[0], st));
 
     const Forest F = forest_of_tree(f);
-    ScreenOut S;
+    ScreenOut& S = G.S;
     const int unscreened = o ? o->unscreened : 0;
-    int rc = screen_forest(op, F, unscreened, A, st, &S);
-    if (rc != MRA_OK) { screen_release(A, &S); return rc; }
+    int rc = MRA_OK;
+    MRA_TRY(screen_forest(op, F, unscreened, A, st, &S));
     MRA_CK(cudaEventRecord(ev[1], st));
     double* gblk;
     MRA_TRY(dalloc(A, &gblk, (size_t)(S.nghost + 1) * k3));
+    G.p[0] = gblk;
     MRA_TRY(ghost_refine_forest(F, S, gblk, st));
     // per-pair term ranges: the exact screen, or the learned one judged by it
     const int smode = o ? o->screen_mode : MRA_SCREEN_STATIC;
@@ -822,17 +840,19 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
             return MRA_EINVAL;
         }
         MRA_TRY(dalloc(A, &scounts, 2));
+        G.p[1] = scounts;
         MRA_CK(cudaMemsetAsync(scounts, 0, 2 * sizeof(unsigned long long), st));
         MRA_TRY(schedule_narrow(op, F, S, gblk, smode, o->schedule, std::max(0, o->margin), nullptr, nullptr,
                                 scounts, A, st));
     }
     MRA_CK(cudaEventRecord(ev[2], st));
 
-    mra_tree* g = nullptr;
-    MRA_TRY(tree_clone_skeleton(f, &g));
+    MRA_TRY(tree_clone_skeleton(f, &G.g));
+    mra_tree* g = G.g;
     g->state = MRA_TREE_NSFORM;
     unsigned long long* nitems;  // [0] items, [1] items with single FP16 operands
     MRA_TRY(dalloc(A, &nitems, 2));
+    G.p[2] = nitems;
     MRA_CK(cudaMemsetAsync(nitems, 0, 2 * sizeof(unsigned long long), st));
     double* lpb = nullptr;
 
@@ -853,6 +873,7 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         // single FP16 products for the terms the error budget allows
         if (prec == MRA_PREC_TC_LADDER) {
             MRA_TRY(dalloc(A, &lpb, 1));
+            G.p[3] = lpb;
             MRA_TRY(lp_budget(F, S, op->eps, lpb, st));
         }
         MRA_TRY(launch_apply_tc(aa, S.nghost, op, S.err + 1, lpb, nitems + 1, st));
@@ -904,9 +925,7 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         if (herr[1] == 4) { set_error("tensor-core apply: an MMA completion wait reached its limit"); rc = MRA_ETIMEOUT; }
         else if (herr[0] || herr[1]) { set_error("screen/ghost error code %d/%d", herr[0], herr[1]); rc = MRA_ECUDA; }
     }
-    screen_release(A, &S);
-    A.put(gblk); A.put(nitems); A.put(lpb); A.put(scounts);
-    for (int e = 0; e < 4; ++e) cudaEventDestroy(ev[e]);
+    G.g = nullptr;  // the caller owns the output from here
     *gout = g;
     return rc;
 }

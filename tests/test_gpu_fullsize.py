@@ -145,3 +145,28 @@ def test_helmholtz_slater_against_truncated_closed_form(helmholtz):
             num += ((bb - e) ** 2).sum()
             den += (e ** 2).sum()
     assert math.sqrt(num / den) <= 10 * cfg.eps
+
+
+def test_poisson_k8_learned_and_pair_screens_sampled(poisson_k8):
+    """The committed schedule network (trained on the learned-schedule seeds,
+    which do not include this input) and the exact pair screen on the full
+    k=8 tree: fewer items than the static screen, every passing item of the
+    exact test applied, and the sampled outputs within the 10 eps gate of the
+    oracle's static apply."""
+    from paper_0706_0747_gb300 import schedule as SCH
+    cfg, d, tree, hit, op_o, op_g = poisson_k8
+    c, l, b = oracle_to_arrays(tree, cfg.k)
+    tg = mra.tree_import(cfg.k, c, l, b)
+    mra.compress(tg)
+    _, st_s = mra.apply_ns(op_g, tg, precision="tc")
+    gp, st_p = mra.apply_ns(op_g, tg, precision="tc", screen="pair")
+    gl, st_l = mra.apply_ns(op_g, tg, precision="tc", screen="learned", schedule=SCH.load())
+    assert st_p["n_items"] <= st_l["n_items"] < st_s["n_items"]
+    tc = OT.copy_tree(tree)
+    OT.compress(tc, cfg.k)
+    nodes = sample_nodes(tc)
+    ref = OA.apply_ns(op_o, tc, nodes=nodes)
+    for g in (gp, gl):
+        cg, _, bg, _ = g.export()
+        got = arrays_to_dict(cg, bg)
+        assert rel_l2({key: got[key] for key in nodes}, ref) <= 10 * cfg.eps
