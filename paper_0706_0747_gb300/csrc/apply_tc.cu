@@ -75,9 +75,11 @@ __global__ void __launch_bounds__(32 * PREP_WARPS) k_tc_prep_blocks(int nb, int 
         __syncwarp();
         int e = 0;
         if (m > 0.0f) frexpf(m, &e);
-        // m * scale in [2^12, 2^13); blocks below 2^-100 keep the scale 2^113 (a
-        // finite float) and round to zero in FP16
-        const double scale = ldexp(1.0, 13 - max(e, -100));
+        // m * scale in [2^9, 2^13): the exponent is rounded up to a multiple of 4,
+        // so that neighbouring blocks mostly share a scale (and the stage-I B
+        // operand can be reused from line to line); blocks below 2^-100 keep the
+        // scale 2^113 (a finite float) and round to zero in FP16
+        const double scale = ldexp(1.0, 13 - ((max(e, -100) + 3) & ~3));
         for (int p = lane; p < 64; p += 32) {  // row (i2, i3) of the stage-I layout
             const int i2 = p >> 3, i3 = p & 7;
             uint4 h4, l4;
@@ -146,7 +148,8 @@ struct TcSmem {
     static constexpr int TLO = TIN + 864;           // 216 int16: term range
     static constexpr int THI = TLO + 432;
     static constexpr int TFL = THI + 432;           // 216 bytes: flags
-    static constexpr int MSK = TFL + 216;           // 36 x MC bytes
+    static constexpr int TG = (TFL + 216 + 15) / 16 * 16;  // 216 float: g = sx_node / sx_b per band position
+    static constexpr int MSK = TG + 864;            // 36 x MC bytes
     static constexpr int TOTAL = (MSK + 36 * MC + 127) / 128 * 128;
     // D_I and D_II (stage III's result reuses D_I's columns)
     static constexpr int TMEM_COLS = (16 * MC <= 64) ? 64 : ((16 * MC <= 128) ? 128 : 256);
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     int16_t* tlo = (int16_t*)(sm + L::TLO);
     int16_t* thi = (int16_t*)(sm + L::THI);
     unsigned char* tfl = sm + L::TFL;
+    float* tg = (float*)(sm + L::TG);
     unsigned char* msk = sm + L::MSK;
 
     // zero everything once: the K padding of stages II and III stays zero
@@ -275,6 +279,11 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
         const int mlo = s_mlo, mhi = s_mhi;
         const float xmax_node = __uint_as_float(s_xmax_bits);
         const float sx_node = ldexpf(1.0f, s_exp_min - 1);
+        // the power-of-two ratio between the node's scale and each input block's
+        for (int q = tid; q < 216; q += TC_THREADS) {
+            const int in = tin[q];
+            tg[q] = in == INT_MIN ? 0.0f : sx_node / T.sx[in >= 0 ? in : A.n + (-1 - in)];
+        }
         double y[4];  // (row rA + 8 s, column cA + h) at y[2 s + h]
 #pragma unroll
         for (int c = 0; c < 4; ++c) y[c] = 0.0;
@@ -408,6 +417,8 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     // B = [F^{t2}_hi ; F^{t2}_hi] (hi), [F^{t2}_lo ; 0] (lo); stage I B core
                     // (N group mc, K group q1) = mask ? g * F^{t1(q1)} : 0 with the power-of-two
                     // ratio g = sx_node / sx_b (exact in FP16)
+                    // masks and g exponents of the line B1 was last built for (per chunk)
+                    unsigned long long built_m = ~0ull, built_g = ~0ull;
                     auto build_B = [&](int q2b, int parb) {
                         const int lineb = q2b * 6 + q3, t2 = band_t(a2, q2b);
                         __half* B2H = (__half*)(sm + L::B2 + parb * (2 * MC * 256));
@@ -421,14 +432,23 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                             ((uint4*)(hl ? B2L : B2H))[mc * 16 + v] = src;
                             if (!hl) ((uint4*)B2H)[mc * 16 + 8 + v] = low ? make_uint4(0, 0, 0, 0) : src;
                         }
+                        // B1 depends on the line only through its masks and its g: when both
+                        // equal the last build's, B1 already holds this line's operand
+                        unsigned long long km = 0, kg = 0;
+#pragma unroll
+                        for (int mc = 0; mc < MC; ++mc) km |= (unsigned long long)msk[lineb * MC + mc] << (8 * mc);
+#pragma unroll
+                        for (int q1 = 0; q1 < 6; ++q1)
+                            kg |= (unsigned long long)((__float_as_uint(tg[q1 * 36 + lineb]) >> 23) & 0xffu) << (8 * q1);
+                        if (km == built_m && kg == built_g) return;
+                        built_m = km;
+                        built_g = kg;
                         for (int e = tid; e < 2 * MC * 6 * 8; e += TC_THREADS) {
                             const int hl = e / (MC * 48), mc = (e / 48) % MC, q1 = (e / 8) % 6, v = e % 8;
                             if (hl && all_low) continue;
                             uint4 out = make_uint4(0, 0, 0, 0);
                             if ((msk[lineb * MC + mc] >> q1) & 1u) {
-                                const int in = tin[q1 * 36 + lineb];
-                                const float sxb = T.sx[in >= 0 ? in : A.n + (-1 - in)];
-                                const float g = sx_node / sxb;
+                                const float g = tg[q1 * 36 + lineb];
                                 const uint4 fin4 = (hl ? FL : FH)[fbase + (mc * 7 + band_t(a1, q1) + 3) * 8 + v];
                                 const __half2 g2 = __float2half2_rn(g);
                                 const __half2* pi = (const __half2*)&fin4;

@@ -140,21 +140,22 @@ def test_graph_replay_and_rewritten_blocks(batch):
     again = outputs(plan, len(tg))
     for a, b in zip(first, again):
         assert all(np.array_equal(a[key], b[key]) for key in a)
-    # double every tree's coefficients: eta = eps sigma / ||f|| is unchanged,
-    # so the plan's screen still holds and every output doubles exactly
+    # scale every tree's coefficients by 16: eta = eps sigma / ||f|| is
+    # unchanged, so the plan's screen still holds; block scales are powers of
+    # 16, so the FP16 operands are the same bits and every output is exactly
+    # 16 times the first (blocks below the scale clamp aside)
     for t in tg:
         s_ptr, _ = t.device_arrays()
         n, k3 = t.n, K ** 3
         buf = torch.empty(n * k3, dtype=torch.float64, device="cuda")
         c, l, bl, _ = t.export()
-        buf.copy_(torch.from_numpy(2.0 * bl.reshape(-1)))
+        buf.copy_(torch.from_numpy(16.0 * bl.reshape(-1)))
         mra.tree_set_blocks(t, buf.data_ptr())
         torch.cuda.synchronize()
     plan.execute()
-    doubled = outputs(plan, len(tg))
-    for a, b in zip(first, doubled):
-        for key in a:
-            assert np.array_equal(2.0 * a[key], b[key])
+    scaled = outputs(plan, len(tg))
+    for a, b in zip(first, scaled):
+        assert rel_l2(b, {key: 16.0 * v for key, v in a.items()}) <= 1e-13
 
 
 def test_autotune_variants_agree(batch):
