@@ -207,13 +207,16 @@ int mra_op_export(const mra_op* op, double* w_host, double* tau_host, double* F_
  * The input tree must be MRA_TREE_REDUNDANT (mra_compress) and no deeper than
  * the operator's max_level.  Output: a new tree in state MRA_TREE_NSFORM.
  * Returns after the work is queued; stats (optional, host) are filled when the
- * call returns (the call synchronises once to size the worklist). */
+ * call returns (the call synchronises once to size the worklist).
+ * Errors found on the device are read back after the apply: MRA_ETIMEOUT when
+ * a tensor-core completion wait gave up, MRA_EINVAL when a tensor-core output
+ * scale w_m / (s_V s_F) falls outside FP32's range (use MRA_PREC_FP64). */
 
 #define MRA_PREC_FP64     0   /* FP64 SIMT contractions                        */
 #define MRA_PREC_FP32     1   /* FP32 SIMT contractions, FP64 accumulation     */
 #define MRA_PREC_TC_SPLIT 2   /* FP16 hi+lo split products on tcgen05 tensor   */
-                              /* cores, FP32 accumulation, FP64 accumulation   */
-                              /* into the output blocks                        */
+                              /* cores, FP32 accumulation, output blocks       */
+                              /* accumulated as float pairs (TwoSum)           */
 #define MRA_PREC_TC_LADDER 3  /* precision ladder on the tensor cores: per     */
                               /* output node and term, single FP16 products    */
                               /* (one MMA instead of three) when the term's    */

@@ -923,6 +923,7 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         cudaEventElapsedTime(&stats->ms_ghost, ev[1], ev[2]);
         cudaEventElapsedTime(&stats->ms_apply, ev[2], ev[3]);
         if (herr[1] == 4) { set_error("tensor-core apply: an MMA completion wait reached its limit"); rc = MRA_ETIMEOUT; }
+        else if (herr[1] == 5) { set_error("tensor-core apply: an output scale is outside the FP32 range (use fp64)"); rc = MRA_EINVAL; }
         else if (herr[0] || herr[1]) { set_error("screen/ghost error code %d/%d", herr[0], herr[1]); rc = MRA_ECUDA; }
     }
     G.g = nullptr;  // the caller owns the output from here

@@ -10,13 +10,14 @@
 //             MMA M=64, N=8, K=16 (i2, zero padded), accumulated over the plane's lines in TMEM
 //   stage III per plane and term: Y_m[(c1,c2)][c3] += sum_i3 V_m F^{t3}[c3][i3]
 //             MMA M=64, N=8, K=16 (i3, zero padded), accumulated over planes in TMEM
-//   ghat_a += w_m Y_m in FP64.
+//   ghat_a += w_m Y_m: per plane, an FP32 sum over the chunk's terms, added to ghat
+//             kept as a pair of floats (TwoSum), so no FP64 arithmetic runs per item.
 // Every operand is FP16 split into hi + lo (v ~= hi + lo to 2^-22), and each
 // product is hi*hi + hi*lo + lo*hi into an FP32 accumulator: three MMAs in
 // stage I; in stages II and III, whose contraction (8) fills half of an
 // MMA's K = 16, two: A = [A_hi | A_lo] against [B_hi ; B_hi] and [B_lo ; 0].
 // Power-of-two scales keep every operand in FP16's normal range: per input
-// block (x * sx in [2^12, 2^13)), per (j, m) operator block (F * sF), per node
+// block (x * sx in [2^9, 2^13), sx a power of 16), per (j, m) operator block (F * sF), per node
 // (sx_node = the smallest block scale of the neighbourhood), and per term for
 // W and V from bounds (|W| <= 48 max|F| max|x|, |V| <= 48 max|F| max|W|).
 //
@@ -28,6 +29,7 @@
 // next line's operands are staged.  CTAs are persistent and take nodes from
 // an atomic counter (optionally in a given order), so one launch can cover the
 // nodes of many trees.
+#include <cfloat>
 #include <climits>
 
 #include "apply_common.cuh"
@@ -141,10 +143,10 @@ struct TcSmem {
     static constexpr int B1H = 24576;               // MC terms x 6 K groups x 128 B: stage I B
     static constexpr int B1L = B1H + MC * 768;
     static constexpr int A2H = B1L + MC * 768;      // MC x 2048 B: stage II A (K: hi | lo); stage III A aliases it
-    static constexpr int B2 = A2H + MC * 2048;      // 2 buffers x {hi, lo} x MC x 256 B
-    static constexpr int B3H = B2 + MC * 1024;      // MC x 256 B: stage III B
-    static constexpr int B3L = B3H + MC * 256;
-    static constexpr int TIN = B3L + MC * 256;      // 216 int: input block per band position
+    static constexpr int FSH = A2H + MC * 2048;     // MC terms x 7 shifts x 128 B: the chunk's F (hi)
+    static constexpr int FSL = FSH + MC * 896;      // (lo)
+    static constexpr int FZ = FSL + MC * 896;       // one zero core matrix
+    static constexpr int TIN = FZ + 128;            // 216 int: input block per band position
     static constexpr int TLO = TIN + 864;           // 216 int16: term range
     static constexpr int THI = TLO + 432;
     static constexpr int TFL = THI + 432;           // 216 bytes: flags
@@ -158,16 +160,6 @@ struct TcSmem {
 static_assert(3 * (TcSmem<8>::TOTAL + 2048) <= 232448, "8 terms per chunk: three CTAs per SM");
 static_assert(3 * TcSmem<8>::TMEM_COLS <= 512, "three CTAs' tensor memory");
 
-__device__ __forceinline__ float pow2floor(double x) {
-    if (!(x > 0.0)) return 0.0f;
-    int e;
-    frexp(x, &e);
-    e -= 1;
-    if (e > 126) e = 126;
-    if (e < -126) return 0.0f;
-    return ldexpf(1.0f, e);
-}
-
 template <int MC, bool LADDER>
 __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs T) {
     using L = TcSmem<MC>;
@@ -179,7 +171,8 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     __shared__ unsigned long long s_items;
     __shared__ float s_c2[MC], s_c3[MC];
     __shared__ unsigned char s_lm[36], s_pm[6];
-    __shared__ double s_fin[MC];
+    __shared__ float s_fin[MC];
+    __shared__ int s_cnt[MC];
     __shared__ float s_B[MC];
     __shared__ unsigned char s_low[MC];
     __shared__ int s_all_low;
@@ -191,9 +184,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     __half* B1H = (__half*)(sm + L::B1H);
     __half* B1L = (__half*)(sm + L::B1L);
     __half* A2H = (__half*)(sm + L::A2H);
-    __half* B3H = (__half*)(sm + L::B3H);
-    __half* B3L = (__half*)(sm + L::B3L);
-    // the chunk's operator blocks are read from L1/L2: F (hi, lo) of term m0 + mc at shift t
+    // the operator blocks F (hi, lo) of term m at shift t: uint4 index ((j M + m) 7 + t + 3) 8
     const uint4* FH = (const uint4*)T.Fh;
     const uint4* FL = (const uint4*)T.Fl;
     int* tin = (int*)(sm + L::TIN);
@@ -211,7 +202,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = s_tmem;
-    const uint32_t tD1 = tbase, tD2 = tbase + 8 * MC, tD3 = tbase;  // stage III reuses D_I
+    // two TMEM blocks of 8 MC columns: D_I and D_II, swapping roles per plane (D_III reuses D_I)
     // warps w and w+4 share TMEM lane quarter w and split the terms of a chunk
     const int quarter = warp & 3, whalf = warp >> 2;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
@@ -222,6 +213,13 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     // 16 quarter + lane/4 and that + 8, columns cA and cA + 1 of each term
     const int rA = quarter * 16 + (lane >> 2), cA = 2 * (lane & 3);
     const uint32_t sbase = tc::smem_u32(sm);
+    // B operands of stages II and III read in place from the chunk's staged F: the hi operand
+    // [F_hi ; F_hi] has K-group offset 0 (both K groups are the same core matrix), the lo
+    // operand [F_lo ; 0] reaches the zero block; a single-FP16 term pairs F_hi with zeros
+    auto fdesc = [&](int mc, int t, bool hi, bool low) -> uint64_t {
+        const uint32_t o = (uint32_t)((hi ? L::FSH : L::FSL) + (mc * 7 + t + 3) * 128);
+        return tc::sdesc(sbase + o, (hi && !low) ? 0u : (uint32_t)L::FZ - o, 256);
+    };
 
     // the abort decision comes from __syncthreads_or, so it is uniform
     bool aborted = false;
@@ -284,13 +282,31 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
             const int in = tin[q];
             tg[q] = in == INT_MIN ? 0.0f : sx_node / T.sx[in >= 0 ? in : A.n + (-1 - in)];
         }
-        double y[4];  // (row rA + 8 s, column cA + h) at y[2 s + h]
+        // ghat: (row rA + 8 s, column cA + h) at [2 s + h], as the unevaluated sum yh + yl of
+        // two floats (FP64 arithmetic is scarce on this part)
+        float yh[4], yl[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) y[c] = 0.0;
+        for (int c = 0; c < 4; ++c) yh[c] = yl[c] = 0.0f;
+        unsigned my_items = 0;  // kept (item, term) pairs counted by this thread
         if (mhi >= mlo && xmax_node > 0.0f) {
             for (int m0 = mlo; m0 <= mhi && !aborted; m0 += MC) {
                 // the kept-t1 masks per line and the per-term scales of the chunk
                 const size_t fbase = ((size_t)j * A.M + m0) * 56;  // uint4 index of F(m0, t = -3)
+                // the chunk's F^{j;m,t} (hi, lo) into shared memory, overlapping the set-up below:
+                // stages II and III read their B operands there in place, and stage I's B is
+                // built from there (terms past mhi get zeros)
+                {
+                    const int nv = MC * 56, nvalid = min(MC, mhi - m0 + 1) * 56;
+                    for (int e = tid; e < 2 * nv; e += TC_THREADS) {
+                        const int hl = e >= nv, r = hl ? e - nv : e;
+                        uint4* dst = (uint4*)(sm + (hl ? L::FSL : L::FSH)) + r;
+                        if (r < nvalid)
+                            tc::cp_async16(dst, (hl ? FL : FH) + fbase + r);
+                        else
+                            *dst = make_uint4(0, 0, 0, 0);
+                    }
+                    tc::cp_async_commit();
+                }
                 for (int e = tid; e < 36 * MC; e += TC_THREADS) {
                     const int line = e / MC, mc = e % MC, m = m0 + mc;
                     unsigned char mk = 0;
@@ -305,20 +321,32 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                             }
                     }
                     msk[e] = mk;
+                    my_items += __popc(mk);
                 }
                 if (tid < MC) {
                     const int m = m0 + tid;
-                    float c2 = 0.0f, c3 = 0.0f;
-                    double fin = 0.0;
+                    float c2 = 0.0f, c3 = 0.0f, fin = 0.0f;
                     if (m <= mhi) {
-                        const double mf = T.maxF[(size_t)j * A.M + m], sf = T.sF[(size_t)j * A.M + m];
-                        if (mf > 0.0) {
-                            const double sW = pow2floor(8192.0 / (48.0 * mf * (double)xmax_node));
-                            const double sV = pow2floor(8192.0 / (48.0 * 48.0 * mf * mf * (double)xmax_node));
-                            if (sW > 0.0 && sV > 0.0) {
-                                c2 = (float)(sW / (sf * (double)sx_node));
-                                c3 = (float)(sV / (sW * sf));
-                                fin = A.w[m] / (sV * sf);
+                        const float mf = T.maxF[(size_t)j * A.M + m], sf = T.sF[(size_t)j * A.M + m];
+                        if (mf > 0.0f) {
+                            // power-of-two scales by exponent arithmetic (no FP64 on this path):
+                            // sW = 2^eW, the largest power of two <= 8192 / (48 mf xmax), and
+                            // sV = 2^eV <= 8192 / (48^2 mf^2 xmax); sf is a power of two
+                            int em, ex, ef, e1, e2;
+                            const float fm = frexpf(mf, &em), fx = frexpf(xmax_node, &ex);
+                            frexpf(sf, &ef);
+                            ef -= 1;
+                            frexpf(8192.0f / (48.0f * fm * fx), &e1);
+                            frexpf(8192.0f / (2304.0f * fm * fm * fx), &e2);
+                            const int eW = min(e1 - 1 - em - ex, 126), eV = min(e2 - 1 - 2 * em - ex, 126);
+                            if (eW >= -126 && eV >= -126) {
+                                c2 = ldexpf(1.0f, eW - ef - (s_exp_min - 1));  // sW / (sf sx_node)
+                                c3 = ldexpf(1.0f, eV - eW - ef);                // sV / (sW sf)
+                                fin = ldexpf((float)A.w[m], -(eV + ef));        // w_m / (sV sf)
+                                if (!(fin <= FLT_MAX)) {  // outputs beyond the FP32 range: refuse
+                                    atomicExch(T.err, 5);
+                                    fin = 0.0f;
+                                }
                             }
                         }
                     }
@@ -326,7 +354,9 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     s_c3[tid] = c3;
                     s_fin[tid] = fin;
                     s_B[tid] = 0.0f;
+                    s_cnt[tid] = 0;
                 }
+                tc::cp_async_wait_all();  // this thread's part of the chunk's F
                 __syncthreads();
                 // precision ladder: B_m = w_m sum over the term's kept items of
                 // N_F(t1) N_F(t2) N_F(t3) ||x_b|| bounds its contribution to this node
@@ -345,6 +375,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                         }
                         acc *= (float)(nf[band_t(a2, line / 6) + 3] * nf[band_t(a3, line % 6) + 3]);
                         atomicAdd(&s_B[mc], acc);
+                        atomicAdd(&s_cnt[mc], __popc(mk));
                     }
                 __syncthreads();
                 // per line: the union of its terms' kept-t1 masks; per plane: any line
@@ -369,250 +400,259 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                         int low = 1;
                         if (m <= mhi) low = T.lpb && LADDER_U * A.w[m] * (double)s_B[mc] <= per_term;
                         s_low[mc] = (unsigned char)low;
+                        if (low) s_lowi += s_cnt[mc];
                         all &= low;
                     }
                     s_all_low = all;
                 }
                 __syncthreads();
                 const int all_low = LADDER ? s_all_low : 0;
-                for (int q3 = 0; q3 < 6 && !aborted; ++q3) {
-                    if (!s_pm[q3]) continue;  // uniform
-                    const int t3 = band_t(a3, q3);
-                    // stage III B: hi = [F^{t3}_hi ; F^{t3}_hi] and lo = [F^{t3}_lo ; 0] in K, so
-                    // that A3 = [A_hi | A_lo] gives A_hi F_hi + A_lo F_hi and A_hi F_lo in two
-                    // MMAs (a single-FP16 term has a zero second K group in hi)
-                    for (int e = tid; e < 2 * MC * 8; e += TC_THREADS) {
-                        const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
-                        const bool low = LADDER && s_low[mc];
-                        if (hl && low) continue;
-                        const uint4 src = m0 + mc <= mhi ? (hl ? FL : FH)[fbase + (mc * 7 + t3 + 3) * 8 + v]
-                                                         : make_uint4(0, 0, 0, 0);
-                        ((uint4*)(hl ? B3L : B3H))[mc * 16 + v] = src;
-                        if (!hl) ((uint4*)B3H)[mc * 16 + 8 + v] = low ? make_uint4(0, 0, 0, 0) : src;
+                // masks and g exponents of the line stage I's B was last built for
+                unsigned long long built_m = ~0ull, built_g = ~0ull;
+                // lines of the chunk in (t3 plane, t2) order; a cursor c = q3 * 6 + q2 names line
+                // q2 * 6 + q3, and only lines with a kept item are visited
+                auto next_of = [&](int c) {
+                    for (++c; c < 36; ++c)
+                        if (s_lm[(c % 6) * 6 + c / 6]) break;
+                    return c;
+                };
+                auto line_of = [](int c) { return (c % 6) * 6 + c / 6; };
+                // stage I A (a line's six input blocks) is copied asynchronously into one of two
+                // buffers while earlier lines compute
+                auto fetch_line = [&](int c, int buf) {
+                    const int line = line_of(c);
+                    const unsigned lmx = s_lm[line];
+                    for (int e = tid; e < 6 * 64 * 2; e += TC_THREADS) {
+                        const int hl = e / 384, q1 = (e / 64) % 6, v = e % 64;  // 64 uint4 per 1 KB
+                        if (hl && all_low) continue;
+                        uint4* dst = (uint4*)(sm + (hl ? L::XL : L::XH) + buf * 6144) + q1 * 64 + v;
+                        if (lmx & (1u << q1)) {
+                            const int in = tin[q1 * 36 + line];
+                            const int b = in >= 0 ? in : A.n + (-1 - in);
+                            tc::cp_async16(dst, (const uint4*)((hl ? T.xl : T.xh) + (size_t)b * 512) + v);
+                        } else {
+                            *dst = make_uint4(0, 0, 0, 0);
+                        }
                     }
-                    // stage I A (a line's six input blocks) is copied asynchronously into one
-                    // of two buffers while the previous line computes
-                    auto next_line = [&](int q2) {
-                        for (++q2; q2 < 6; ++q2)
-                            if (s_lm[q2 * 6 + q3]) break;
-                        return q2;
-                    };
-                    auto fetch_line = [&](int line, int buf) {
-                        const unsigned lmx = s_lm[line];
-                        for (int e = tid; e < 6 * 64 * 2; e += TC_THREADS) {
-                            const int hl = e / 384, q1 = (e / 64) % 6, v = e % 64;  // 64 uint4 per 1 KB
-                            if (hl && all_low) continue;
-                            uint4* dst = (uint4*)(sm + (hl ? L::XL : L::XH) + buf * 6144) + q1 * 64 + v;
-                            if (lmx & (1u << q1)) {
-                                const int in = tin[q1 * 36 + line];
-                                const int b = in >= 0 ? in : A.n + (-1 - in);
-                                tc::cp_async16(dst, (const uint4*)((hl ? T.xl : T.xh) + (size_t)b * 512) + v);
-                            } else {
-                                *dst = make_uint4(0, 0, 0, 0);
-                            }
-                        }
-                        tc::cp_async_commit();
-                    };
-                    // stage II and I operands of line q2 into B2 buffer `par` and B1: stage II
-                    // B = [F^{t2}_hi ; F^{t2}_hi] (hi), [F^{t2}_lo ; 0] (lo); stage I B core
-                    // (N group mc, K group q1) = mask ? g * F^{t1(q1)} : 0 with the power-of-two
-                    // ratio g = sx_node / sx_b (exact in FP16)
-                    // masks and g exponents of the line B1 was last built for (per chunk)
-                    unsigned long long built_m = ~0ull, built_g = ~0ull;
-                    auto build_B = [&](int q2b, int parb) {
-                        const int lineb = q2b * 6 + q3, t2 = band_t(a2, q2b);
-                        __half* B2H = (__half*)(sm + L::B2 + parb * (2 * MC * 256));
-                        __half* B2L = B2H + MC * 128;
-                        for (int e = tid; e < 2 * MC * 8; e += TC_THREADS) {
-                            const int hl = e / (MC * 8), mc = (e / 8) % MC, v = e % 8;
-                            const bool low = LADDER && s_low[mc];
-                            if (hl && low) continue;
-                            const uint4 src = m0 + mc <= mhi ? (hl ? FL : FH)[fbase + (mc * 7 + t2 + 3) * 8 + v]
-                                                             : make_uint4(0, 0, 0, 0);
-                            ((uint4*)(hl ? B2L : B2H))[mc * 16 + v] = src;
-                            if (!hl) ((uint4*)B2H)[mc * 16 + 8 + v] = low ? make_uint4(0, 0, 0, 0) : src;
-                        }
-                        // B1 depends on the line only through its masks and its g: when both
-                        // equal the last build's, B1 already holds this line's operand
-                        unsigned long long km = 0, kg = 0;
+                    tc::cp_async_commit();
+                };
+                // stage I's B for a line: core (N group mc, K group q1) = mask ? g F^{t1(q1)} : 0
+                // with the power-of-two ratio g = sx_node / sx_b (exact in FP16)
+                auto build_B = [&](int c) {
+                    const int lineb = line_of(c);
+                    // B1 depends on the line only through its masks and its g: when both
+                    // equal the last build's, B1 already holds this line's operand
+                    unsigned long long km = 0, kg = 0;
 #pragma unroll
-                        for (int mc = 0; mc < MC; ++mc) km |= (unsigned long long)msk[lineb * MC + mc] << (8 * mc);
+                    for (int mc = 0; mc < MC; ++mc) km |= (unsigned long long)msk[lineb * MC + mc] << (8 * mc);
 #pragma unroll
-                        for (int q1 = 0; q1 < 6; ++q1)
-                            kg |= (unsigned long long)((__float_as_uint(tg[q1 * 36 + lineb]) >> 23) & 0xffu) << (8 * q1);
-                        if (km == built_m && kg == built_g) return;
-                        built_m = km;
-                        built_g = kg;
-                        for (int e = tid; e < 2 * MC * 6 * 8; e += TC_THREADS) {
-                            const int hl = e / (MC * 48), mc = (e / 48) % MC, q1 = (e / 8) % 6, v = e % 8;
-                            if (hl && all_low) continue;
-                            uint4 out = make_uint4(0, 0, 0, 0);
-                            if ((msk[lineb * MC + mc] >> q1) & 1u) {
-                                const float g = tg[q1 * 36 + lineb];
-                                const uint4 fin4 = (hl ? FL : FH)[fbase + (mc * 7 + band_t(a1, q1) + 3) * 8 + v];
-                                const __half2 g2 = __float2half2_rn(g);
-                                const __half2* pi = (const __half2*)&fin4;
-                                __half2* po = (__half2*)&out;
+                    for (int q1 = 0; q1 < 6; ++q1)
+                        kg |= (unsigned long long)((__float_as_uint(tg[q1 * 36 + lineb]) >> 23) & 0xffu) << (8 * q1);
+                    if (km == built_m && kg == built_g) return;
+                    built_m = km;
+                    built_g = kg;
+                    for (int e = tid; e < 2 * MC * 6 * 8; e += TC_THREADS) {
+                        const int hl = e / (MC * 48), mc = (e / 48) % MC, q1 = (e / 8) % 6, v = e % 8;
+                        if (hl && all_low) continue;
+                        uint4 out = make_uint4(0, 0, 0, 0);
+                        if ((msk[lineb * MC + mc] >> q1) & 1u) {
+                            const float g = tg[q1 * 36 + lineb];
+                            const uint4 fin4 =
+                                ((const uint4*)(sm + (hl ? L::FSL : L::FSH)))[(mc * 7 + band_t(a1, q1) + 3) * 8 + v];
+                            const __half2 g2 = __float2half2_rn(g);
+                            const __half2* pi = (const __half2*)&fin4;
+                            __half2* po = (__half2*)&out;
 #pragma unroll
-                                for (int h = 0; h < 4; ++h) po[h] = __hmul2(pi[h], g2);
-                            }
-                            ((uint4*)(hl ? B1L : B1H))[mc * 48 + q1 * 8 + v] = out;
+                            for (int h = 0; h < 4; ++h) po[h] = __hmul2(pi[h], g2);
                         }
-                    };
-                    // stage I of line q2 from X buffer parx (thread 0)
-                    auto issue_stage1 = [&](int q2i, int parx) {
-                        const int linei = q2i * 6 + q3;
+                        ((uint4*)(hl ? B1L : B1H))[mc * 48 + q1 * 8 + v] = out;
+                    }
+                };
+                // stage I from X buffer parx into the TMEM block d (thread 0)
+                auto issue_stage1 = [&](int parx, uint32_t d) {
 #pragma unroll
-                        for (int ks = 0; ks < 3; ++ks) {
-                            const uint64_t ah = tc::sdesc(sbase + L::XH + parx * 6144 + ks * 2048, 1024, 128);
-                            const uint64_t al = tc::sdesc(sbase + L::XL + parx * 6144 + ks * 2048, 1024, 128);
-                            const uint64_t bh = tc::sdesc(sbase + L::B1H + ks * 256, 128, 768);
-                            const uint64_t bl = tc::sdesc(sbase + L::B1L + ks * 256, 128, 768);
-                            tc::mma_f16(tD1, ah, bh, idI, ks > 0);
-                            if (!all_low) {
-                                tc::mma_f16(tD1, ah, bl, idI, 1);
-                                tc::mma_f16(tD1, al, bh, idI, 1);
-                            }
+                    for (int ks = 0; ks < 3; ++ks) {
+                        const uint64_t ah = tc::sdesc(sbase + L::XH + parx * 6144 + ks * 2048, 1024, 128);
+                        const uint64_t al = tc::sdesc(sbase + L::XL + parx * 6144 + ks * 2048, 1024, 128);
+                        const uint64_t bh = tc::sdesc(sbase + L::B1H + ks * 256, 128, 768);
+                        const uint64_t bl = tc::sdesc(sbase + L::B1L + ks * 256, 128, 768);
+                        tc::mma_f16(d, ah, bh, idI, ks > 0);
+                        if (!all_low) {
+                            tc::mma_f16(d, ah, bl, idI, 1);
+                            tc::mma_f16(d, al, bh, idI, 1);
                         }
-                        for (int mc = 0; mc < MC; ++mc) {
-                            const int c = __popc(msk[linei * MC + mc]);
-                            s_items += c;
-                            if (LADDER && s_low[mc]) s_lowi += c;
-                        }
-                    };
-                    // Software pipeline over the plane's lines: one wait and two block
-                    // barriers per line.  While line L's stage I runs, the previous line's
-                    // stage II runs too; after the wait the threads convert D_I(L), build
-                    // line L+1's B operands, and copy line L+2's input blocks; then one
-                    // thread issues stage II(L) and stage I(L+1) under a single commit.
-                    int q2 = next_line(-1);
-                    int q2n = next_line(q2);
-                    fetch_line(q2 * 6 + q3, 0);
-                    build_B(q2, 0);
+                    }
+                };
+                // ghat += w_m Y_m from the TMEM block d: row (c1, c2), column c3; per plane an FP32
+                // sum over this warp half's terms, joined to ghat with its rounding error (TwoSum)
+                auto accumulate_y = [&](uint32_t d) {
+                    float yv[MC / 2][4];
+                    tc::tmem_ld16x256_rep<MC / 2>(d + lane_off + mc_lo * 8, yv);
+                    float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                    for (int mc = mc_lo; mc < mc_hi; ++mc) {
+                        const float* v = yv[mc - mc_lo];
+                        const float fin = s_fin[mc];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) part[q] = fmaf(fin, v[q], part[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float sum = yh[q] + part[q], bv = sum - yh[q];
+                        yl[q] += (yh[q] - (sum - bv)) + (part[q] - bv);
+                        yh[q] = sum;
+                    }
+                };
+                // Software pipeline over the chunk's lines: one wait and two block barriers per
+                // line.  While line L's stage I runs, stage II of the line before runs too; after
+                // the wait the block converts D_I(L), builds line L+1's stage-I B and starts the
+                // copies of line L+2's input blocks, then one thread issues stage II(L) and stage
+                // I(L+1) under one commit.  After a plane's last line, stage III of the plane and
+                // stage I of the next plane's first line go out together: the two TMEM column
+                // blocks swap roles (D_I <-> D_II) from plane to plane, and stage III's result,
+                // left in the new D_II block, is read after the next wait.
+                int cur = next_of(-1);
+                if (cur < 36) {
+                    int nxt = next_of(cur);
+                    int xb = 0;  // X buffer of line L
+                    uint32_t dI = tbase, dII = tbase + 8 * MC;
+                    bool first = true, y_pending = false;
+                    fetch_line(cur, xb);
+                    build_B(cur);
                     tc::cp_async_wait_all();
-                    if (q2n < 6) fetch_line(q2n * 6 + q3, 1);
+                    if (nxt < 36) fetch_line(nxt, xb ^ 1);
                     tc::fence_async_smem();
                     __syncthreads();
                     if (tid == 0) {
                         tc::fence_after();
-                        issue_stage1(q2, 0);
+                        issue_stage1(xb, dI);
                         tc::commit(&s_mbar);
                     }
-                    for (int li = 0;; ++li) {
-                        const int par = li & 1;
-                        // stage I(L) and stage II(L-1) complete: D_I, B1, A2 and the buffers
-                        // of the other parity are free
+                    for (;;) {
+                        // stage I(L) and everything before it complete: D_I, B1, A2 and the X
+                        // buffer of line L are free
                         TC_WAIT_OR_ABORT();
                         if (aborted) break;
                         tc::fence_after();
+                        if (y_pending) {  // the previous plane's stage III
+                            accumulate_y(dII);
+                            y_pending = false;
+                        }
                         // D_I -> stage II A: row (c1, i3), K column i2.  This thread holds
                         // D_I rows (i2, i3) = (2 quarter, lane/4) and (2 quarter + 1, lane/4):
                         // K neighbours, stored as one half2 per c1
-                        float vv[MC / 2][4];
-                        tc::tmem_ld16x256_rep<MC / 2>(tD1 + lane_off + mc_lo * 8, vv);
+                        {
+                            float vv[MC / 2][4];
+                            tc::tmem_ld16x256_rep<MC / 2>(dI + lane_off + mc_lo * 8, vv);
 #pragma unroll
-                        for (int mc = mc_lo; mc < mc_hi; ++mc) {
-                            const float* v = vv[mc - mc_lo];
-                            const int i3 = lane >> 2;
-                            const float c2 = s_c2[mc];
+                            for (int mc = mc_lo; mc < mc_hi; ++mc) {
+                                const float* v = vv[mc - mc_lo];
+                                const int i3 = lane >> 2;
+                                const float c2 = s_c2[mc];
 #pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                const float x0 = v[h] * c2, x1 = v[2 + h] * c2;
-                                const int o = mc * 1024 + (cA + h) * 128 + i3 * 8 + 2 * quarter;
-                                const __half2 hi = __floats2half2_rn(x0, x1);
-                                *(__half2*)&A2H[o] = hi;
-                                if (!LADDER || !s_low[mc]) {
-                                    const float2 hf = __half22float2(hi);
-                                    *(__half2*)&A2H[o + 64] = __floats2half2_rn(x0 - hf.x, x1 - hf.y);  // K group 1
+                                for (int h = 0; h < 2; ++h) {
+                                    const float x0 = v[h] * c2, x1 = v[2 + h] * c2;
+                                    const int o = mc * 1024 + (cA + h) * 128 + i3 * 8 + 2 * quarter;
+                                    const __half2 hi = __floats2half2_rn(x0, x1);
+                                    *(__half2*)&A2H[o] = hi;
+                                    if (!LADDER || !s_low[mc]) {
+                                        const float2 hf = __half22float2(hi);
+                                        *(__half2*)&A2H[o + 64] = __floats2half2_rn(x0 - hf.x, x1 - hf.y);  // K group 1
+                                    }
                                 }
                             }
                         }
-                        const int q2nn = q2n < 6 ? next_line(q2n) : 6;
-                        if (q2n < 6) {
-                            build_B(q2n, par ^ 1);
+                        const int q3 = cur / 6;
+                        const bool last = nxt >= 36 || nxt / 6 != q3;  // L ends its plane
+                        const int nn = nxt < 36 ? next_of(nxt) : 36;
+                        if (nxt < 36) {
+                            build_B(nxt);
                             tc::cp_async_wait_all();  // line L+1's input blocks
-                            if (q2nn < 6) fetch_line(q2nn * 6 + q3, par);
+                            if (nn < 36) fetch_line(nn, xb);
                         }
                         tc::fence_before();
                         tc::fence_async_smem();
                         __syncthreads();
                         if (tid == 0) {
                             tc::fence_after();
-                            // stage II(L): per term, V += A2 (M=64 (c1,i3) x K=16) x B2 (N=8 c2)
-                            const uint32_t b2 = sbase + L::B2 + par * (2 * MC * 256);
+                            // stage II(L): per term, V += A2 (M=64 (c1,i3) x K=16) x F^{t2} (N=8 c2)
+                            const int t2 = band_t(a2, cur % 6);
                             for (int mc = 0; mc < MC; ++mc) {
+                                const bool low = LADDER && s_low[mc];
                                 const uint64_t a = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
-                                const uint64_t bh = tc::sdesc(b2 + mc * 256, 128, 256);
-                                const uint64_t bl = tc::sdesc(b2 + MC * 256 + mc * 256, 128, 256);
-                                tc::mma_f16(tD2 + mc * 8, a, bh, idS, li > 0);
-                                if (!LADDER || !s_low[mc]) tc::mma_f16(tD2 + mc * 8, a, bl, idS, 1);
+                                tc::mma_f16(dII + mc * 8, a, fdesc(mc, t2, true, low), idS, first ? 0u : 1u);
+                                if (!low) tc::mma_f16(dII + mc * 8, a, fdesc(mc, t2, false, false), idS, 1);
                             }
-                            if (q2n < 6) issue_stage1(q2n, par ^ 1);
+                            if (!last) issue_stage1(xb ^ 1, dI);
                             tc::commit(&s_mbar);
                         }
-                        if (q2n >= 6) break;
-                        q2 = q2n;
-                        q2n = q2nn;
-                    }
-                    tc::cp_async_wait_all();
-                    if (aborted) break;
-                    // wait for the plane's last stage II (committed with it), then
-                    // D_II -> stage III A (aliases stage II A)
-                    TC_WAIT_OR_ABORT();
-                    if (aborted) break;
-                    tc::fence_after();
-                    // D_II rows (c1, i3) = (2 quarter + s, lane/4), columns c2 = cA + h
-                    float vv[MC / 2][4];
-                    tc::tmem_ld16x256_rep<MC / 2>(tD2 + lane_off + mc_lo * 8, vv);
+                        if (last) {
+                            // the plane's last stage II complete: D_II -> stage III A (aliases
+                            // stage II A)
+                            TC_WAIT_OR_ABORT();
+                            if (aborted) break;
+                            tc::fence_after();
+                            // D_II rows (c1, i3) = (2 quarter + s, lane/4), columns c2 = cA + h
+                            {
+                                float vv[MC / 2][4];
+                                tc::tmem_ld16x256_rep<MC / 2>(dII + lane_off + mc_lo * 8, vv);
 #pragma unroll
-                    for (int mc = mc_lo; mc < mc_hi; ++mc) {
-                        const float* v = vv[mc - mc_lo];
-                        const int i3 = lane >> 2;
-                        const float c3 = s_c3[mc];
+                                for (int mc = mc_lo; mc < mc_hi; ++mc) {
+                                    const float* v = vv[mc - mc_lo];
+                                    const int i3 = lane >> 2;
+                                    const float c3 = s_c3[mc];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int c1 = 2 * quarter + (q >> 1), c2 = cA + (q & 1);
-                            const int o = mc * 1024 + c1 * 128 + c2 * 8 + i3;
-                            if (LADDER && s_low[mc]) {
-                                A2H[o] = __float2half_rn(v[q] * c3);
-                            } else {
-                                __half h, l;
-                                tc::split_h(v[q] * c3, h, l);
-                                A2H[o] = h;
-                                A2H[o + 64] = l;  // K group 1
+                                    for (int q = 0; q < 4; ++q) {
+                                        const int c1 = 2 * quarter + (q >> 1), c2 = cA + (q & 1);
+                                        const int o = mc * 1024 + c1 * 128 + c2 * 8 + i3;
+                                        if (LADDER && s_low[mc]) {
+                                            A2H[o] = __float2half_rn(v[q] * c3);
+                                        } else {
+                                            __half h, l;
+                                            tc::split_h(v[q] * c3, h, l);
+                                            A2H[o] = h;
+                                            A2H[o + 64] = l;  // K group 1
+                                        }
+                                    }
+                                }
+                            }
+                            tc::fence_before();
+                            tc::fence_async_smem();
+                            __syncthreads();
+                            // stage III: per term, Y += A3 (M=64 (c1,c2) x K=16) x F^{t3} (N=8 c3)
+                            // into the D_I block; the next plane's first stage I into D_II
+                            if (tid == 0) {
+                                tc::fence_after();
+                                const int t3 = band_t(a3, q3);
+                                for (int mc = 0; mc < MC; ++mc) {
+                                    const bool low = LADDER && s_low[mc];
+                                    const uint64_t a = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
+                                    tc::mma_f16(dI + mc * 8, a, fdesc(mc, t3, true, low), idS, 0);
+                                    if (!low) tc::mma_f16(dI + mc * 8, a, fdesc(mc, t3, false, false), idS, 1);
+                                }
+                                if (nxt < 36) issue_stage1(xb ^ 1, dII);
+                                tc::commit(&s_mbar);
+                            }
+                            const uint32_t d = dI;
+                            dI = dII;
+                            dII = d;
+                            y_pending = true;
+                            if (nxt >= 36) {  // the chunk's last plane
+                                TC_WAIT_OR_ABORT();
+                                if (aborted) break;
+                                tc::fence_after();
+                                accumulate_y(dII);
+                                y_pending = false;
+                                tc::fence_before();
+                                break;
                             }
                         }
+                        first = last;
+                        cur = nxt;
+                        nxt = nn;
+                        xb ^= 1;
                     }
-                    tc::fence_before();
-                    tc::fence_async_smem();
-                    __syncthreads();
-                    // stage III: per term, Y += A3 (M=64 (c1,c2) x K=16) x B3 (N=8 c3)
-                    if (tid == 0) {
-                        tc::fence_after();
-                        for (int mc = 0; mc < MC; ++mc) {
-                            const uint64_t a = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
-                            const uint64_t bh = tc::sdesc(sbase + L::B3H + mc * 256, 128, 256);
-                            const uint64_t bl = tc::sdesc(sbase + L::B3L + mc * 256, 128, 256);
-                            tc::mma_f16(tD3 + mc * 8, a, bh, idS, 0);
-                            if (!LADDER || !s_low[mc]) tc::mma_f16(tD3 + mc * 8, a, bl, idS, 1);
-                        }
-                        tc::commit(&s_mbar);
-                    }
-                    // B3 and the aliased A2/A3 are rewritten by the next plane
-                    TC_WAIT_OR_ABORT();
-                    if (aborted) break;
-                    tc::fence_after();
-                    // ghat += w_m Y_m (FP64): row (c1, c2), column c3; D_I is free again after this
-                    float yv[MC / 2][4];
-                    tc::tmem_ld16x256_rep<MC / 2>(tD3 + lane_off + mc_lo * 8, yv);
-#pragma unroll
-                    for (int mc = mc_lo; mc < mc_hi; ++mc) {
-                        const float* v = yv[mc - mc_lo];
-                        const double fin = s_fin[mc];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) y[q] += fin * (double)v[q];
-                    }
-                    tc::fence_before();
+                    tc::cp_async_wait_all();
                 }
                 if (aborted) break;
                 tc::fence_before();
@@ -623,14 +663,18 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
         double* ysm = (double*)(sm + L::XH);  // every copy into the X buffers is complete here
         if (whalf == 1)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) ysm[(rA + 8 * (q >> 1)) * 8 + cA + (q & 1)] = y[q];
+            for (int q = 0; q < 4; ++q) ysm[(rA + 8 * (q >> 1)) * 8 + cA + (q & 1)] = (double)yh[q] + (double)yl[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) my_items += __shfl_xor_sync(0xffffffffu, my_items, o);
+        if (lane == 0 && my_items) atomicAdd(&s_items, (unsigned long long)my_items);
         __syncthreads();
         if (whalf == 0)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int r = rA + 8 * (q >> 1), c1 = r >> 3, c2 = r & 7, c3 = cA + (q & 1);
                 if (c1 < kr && c2 < kr && c3 < kr)
-                    A.out[(size_t)node * kr * kr * kr + (c1 * kr + c2) * kr + c3] = y[q] + ysm[r * 8 + c3];
+                    A.out[(size_t)node * kr * kr * kr + (c1 * kr + c2) * kr + c3] =
+                        ((double)yh[q] + (double)yl[q]) + ysm[r * 8 + c3];
             }
         if (tid == 0 && A.n_items) atomicAdd(A.n_items + (A.node_tree ? A.node_tree[node] : 0), s_items);
         if (tid == 0 && T.n_lowp && s_lowi) atomicAdd(T.n_lowp, s_lowi);

@@ -451,6 +451,7 @@ int mra_plan_get_info(const mra_plan* p, mra_plan_info* info, void* stream) {
     info->graph_kernels = (int)p->graph_kernels;
     info->ms_screen = p->ms_screen;
     if (herr[1] == 4) { set_error("tensor-core apply: an MMA completion wait reached its limit"); return MRA_ETIMEOUT; }
+    if (herr[1] == 5) { set_error("tensor-core apply: an output scale is outside the FP32 range (use fp64)"); return MRA_EINVAL; }
     if (herr[0] || herr[1]) { set_error("screen/Step-2 error code %d/%d", herr[0], herr[1]); return MRA_ECUDA; }
     return MRA_OK;
 }
