@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     __shared__ unsigned long long s_items;
     __shared__ float s_c2[MC], s_c3[MC];
     __shared__ unsigned char s_lm[36], s_pm[6];
+    __shared__ unsigned long long s_km[36], s_kg[36];  // per line: masks, g exponents
     __shared__ float s_fin[MC];
     __shared__ int s_cnt[MC];
     __shared__ float s_B[MC];
@@ -216,10 +217,18 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     // B operands of stages II and III read in place from the chunk's staged F: the hi operand
     // [F_hi ; F_hi] has K-group offset 0 (both K groups are the same core matrix), the lo
     // operand [F_lo ; 0] reaches the zero block; a single-FP16 term pairs F_hi with zeros
+    // operand (mc, t) lies 128 (mc 7 + t + 3) bytes past the table's start: 8 (mc 7 + t + 3) in
+    // the descriptor's start-address field, and as much less in the K-group offset field when
+    // that offset reaches the zero block
     auto fdesc = [&](int mc, int t, bool hi, bool low) -> uint64_t {
-        const uint32_t o = (uint32_t)((hi ? L::FSH : L::FSL) + (mc * 7 + t + 3) * 128);
-        return tc::sdesc(sbase + o, (hi && !low) ? 0u : (uint32_t)L::FZ - o, 256);
+        const uint64_t k8 = (uint64_t)((mc * 7 + t + 3) * 8);
+        if (hi && !low) return tc::sdesc(sbase + L::FSH, 0u, 256) + k8;
+        const uint64_t base = hi ? tc::sdesc(sbase + L::FSH, L::FZ - L::FSH, 256)
+                                 : tc::sdesc(sbase + L::FSL, L::FZ - L::FSL, 256);
+        return base + k8 - (k8 << 16);
     };
+    // stage II/III A of term mc: 2048 bytes apart
+    auto adesc = [&](int mc) -> uint64_t { return tc::sdesc(sbase + L::A2H, 128, 256) + (uint64_t)(mc * 128); };
 
     // the abort decision comes from __syncthreads_or, so it is uniform
     bool aborted = false;
@@ -380,9 +389,18 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                 __syncthreads();
                 // per line: the union of its terms' kept-t1 masks; per plane: any line
                 if (tid < 36) {
+                    // stage I's B depends on the line only through its masks and g exponents
                     unsigned v = 0;
-                    for (int mc = 0; mc < MC; ++mc) v |= msk[tid * MC + mc];
+                    unsigned long long km = 0, kg = 0;
+                    for (int mc = 0; mc < MC; ++mc) {
+                        v |= msk[tid * MC + mc];
+                        km |= (unsigned long long)msk[tid * MC + mc] << (8 * mc);
+                    }
+                    for (int q1 = 0; q1 < 6; ++q1)
+                        kg |= (unsigned long long)((__float_as_uint(tg[q1 * 36 + tid]) >> 23) & 0xffu) << (8 * q1);
                     s_lm[tid] = (unsigned char)v;
+                    s_km[tid] = km;
+                    s_kg[tid] = kg;
                 }
                 __syncthreads();
                 if (tid < 6) {
@@ -422,14 +440,15 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                 auto fetch_line = [&](int c, int buf) {
                     const int line = line_of(c);
                     const unsigned lmx = s_lm[line];
-                    for (int e = tid; e < 6 * 64 * 2; e += TC_THREADS) {
-                        const int hl = e / 384, q1 = (e / 64) % 6, v = e % 64;  // 64 uint4 per 1 KB
-                        if (hl && all_low) continue;
-                        uint4* dst = (uint4*)(sm + (hl ? L::XL : L::XH) + buf * 6144) + q1 * 64 + v;
+                    // element e = (hl, q1, v): uint4 v (of 64) of block q1, hi then lo
+                    const int nfe = all_low ? 384 : 768;
+                    for (int e = tid; e < nfe; e += TC_THREADS) {
+                        const int hl = e >= 384, r = hl ? e - 384 : e, q1 = r >> 6;
+                        uint4* dst = (uint4*)(sm + L::XH + hl * (L::XL - L::XH) + buf * 6144) + r;
                         if (lmx & (1u << q1)) {
                             const int in = tin[q1 * 36 + line];
                             const int b = in >= 0 ? in : A.n + (-1 - in);
-                            tc::cp_async16(dst, (const uint4*)((hl ? T.xl : T.xh) + (size_t)b * 512) + v);
+                            tc::cp_async16(dst, (const uint4*)((hl ? T.xl : T.xh) + (size_t)b * 512) + (r & 63));
                         } else {
                             *dst = make_uint4(0, 0, 0, 0);
                         }
@@ -440,42 +459,38 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                 // with the power-of-two ratio g = sx_node / sx_b (exact in FP16)
                 auto build_B = [&](int c) {
                     const int lineb = line_of(c);
-                    // B1 depends on the line only through its masks and its g: when both
-                    // equal the last build's, B1 already holds this line's operand
-                    unsigned long long km = 0, kg = 0;
-#pragma unroll
-                    for (int mc = 0; mc < MC; ++mc) km |= (unsigned long long)msk[lineb * MC + mc] << (8 * mc);
-#pragma unroll
-                    for (int q1 = 0; q1 < 6; ++q1)
-                        kg |= (unsigned long long)((__float_as_uint(tg[q1 * 36 + lineb]) >> 23) & 0xffu) << (8 * q1);
+                    // when the line's masks and g equal the last build's, B1 already holds
+                    // this line's operand
+                    const unsigned long long km = s_km[lineb], kg = s_kg[lineb];
                     if (km == built_m && kg == built_g) return;
                     built_m = km;
                     built_g = kg;
-                    for (int e = tid; e < 2 * MC * 6 * 8; e += TC_THREADS) {
-                        const int hl = e / (MC * 48), mc = (e / 48) % MC, q1 = (e / 8) % 6, v = e % 8;
-                        if (hl && all_low) continue;
+                    // element e = (hl, mc, q1, v) of B1 (hi then lo, uint4 v of core (mc, q1)) is
+                    // uint4 e of B1H..B1L; its source F^{t1(q1)}_mc, t1 + 3 = q1 + (a1 & 1), is
+                    // uint4 e + 8 (e / 48 + (a1 & 1)) of the staged F (hi then lo)
+                    const int nb1 = all_low ? MC * 48 : 2 * MC * 48;
+                    for (int e = tid; e < nb1; e += TC_THREADS) {
+                        const int d48 = e / 48, q1 = (e - 48 * d48) >> 3, mc = d48 & (MC - 1);
                         uint4 out = make_uint4(0, 0, 0, 0);
                         if ((msk[lineb * MC + mc] >> q1) & 1u) {
-                            const float g = tg[q1 * 36 + lineb];
-                            const uint4 fin4 =
-                                ((const uint4*)(sm + (hl ? L::FSL : L::FSH)))[(mc * 7 + band_t(a1, q1) + 3) * 8 + v];
-                            const __half2 g2 = __float2half2_rn(g);
+                            const uint4 fin4 = ((const uint4*)(sm + L::FSH))[e + 8 * (d48 + (a1 & 1))];
+                            const __half2 g2 = __float2half2_rn(tg[q1 * 36 + lineb]);
                             const __half2* pi = (const __half2*)&fin4;
                             __half2* po = (__half2*)&out;
 #pragma unroll
                             for (int h = 0; h < 4; ++h) po[h] = __hmul2(pi[h], g2);
                         }
-                        ((uint4*)(hl ? B1L : B1H))[mc * 48 + q1 * 8 + v] = out;
+                        ((uint4*)B1H)[e] = out;
                     }
                 };
                 // stage I from X buffer parx into the TMEM block d (thread 0)
                 auto issue_stage1 = [&](int parx, uint32_t d) {
+                    const uint64_t a0 = tc::sdesc(sbase + L::XH + parx * 6144, 1024, 128);
+                    const uint64_t b0 = tc::sdesc(sbase + L::B1H, 128, 768);
 #pragma unroll
-                    for (int ks = 0; ks < 3; ++ks) {
-                        const uint64_t ah = tc::sdesc(sbase + L::XH + parx * 6144 + ks * 2048, 1024, 128);
-                        const uint64_t al = tc::sdesc(sbase + L::XL + parx * 6144 + ks * 2048, 1024, 128);
-                        const uint64_t bh = tc::sdesc(sbase + L::B1H + ks * 256, 128, 768);
-                        const uint64_t bl = tc::sdesc(sbase + L::B1L + ks * 256, 128, 768);
+                    for (int ks = 0; ks < 3; ++ks) {  // K step: 2048 bytes of X, 256 of B1
+                        const uint64_t ah = a0 + ks * 128, al = ah + (L::XL - L::XH) / 16;
+                        const uint64_t bh = b0 + ks * 16, bl = bh + (L::B1L - L::B1H) / 16;
                         tc::mma_f16(d, ah, bh, idI, ks > 0);
                         if (!all_low) {
                             tc::mma_f16(d, ah, bl, idI, 1);
@@ -579,7 +594,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                             const int t2 = band_t(a2, cur % 6);
                             for (int mc = 0; mc < MC; ++mc) {
                                 const bool low = LADDER && s_low[mc];
-                                const uint64_t a = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
+                                const uint64_t a = adesc(mc);
                                 tc::mma_f16(dII + mc * 8, a, fdesc(mc, t2, true, low), idS, first ? 0u : 1u);
                                 if (!low) tc::mma_f16(dII + mc * 8, a, fdesc(mc, t2, false, false), idS, 1);
                             }
@@ -626,7 +641,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                                 const int t3 = band_t(a3, q3);
                                 for (int mc = 0; mc < MC; ++mc) {
                                     const bool low = LADDER && s_low[mc];
-                                    const uint64_t a = tc::sdesc(sbase + L::A2H + mc * 2048, 128, 256);
+                                    const uint64_t a = adesc(mc);
                                     tc::mma_f16(dI + mc * 8, a, fdesc(mc, t3, true, low), idS, 0);
                                     if (!low) tc::mma_f16(dI + mc * 8, a, fdesc(mc, t3, false, false), idS, 1);
                                 }
