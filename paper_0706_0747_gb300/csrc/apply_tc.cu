@@ -21,8 +21,9 @@
 // (sx_node = the smallest block scale of the neighbourhood), and per term for
 // W and V from bounds (|W| <= 48 max|F| max|x|, |V| <= 48 max|F| max|W|).
 //
-// One elected thread issues the MMAs and commits them to an mbarrier; warp 0
-// polls it (bounded) and a block barrier releases the rest; the 256 threads
+// Three threads issue the MMAs (stage I; stages II/III for either half of the terms)
+// and commit them to one mbarrier; warp 0 polls it (bounded) and a block barrier
+// releases the rest; the 256 threads
 // read TMEM with tcgen05.ld and write the next stage's operand into shared
 // memory in the canonical no-swizzle K-major layout (8-row x 16-byte core
 // matrices).  Per line there is one wait: stage II of a line runs while the
@@ -39,6 +40,9 @@ namespace mra {
 
 #define TC_THREADS 256
 #define TC_WAIT_LIMIT (1u << 26)
+// MMA-issuing threads (lane 0 of warps 0..TC_ISSUERS-1): warps 0 and 1 issue stages II and III
+// for the two halves of a chunk's terms, warp 2 issues stage I; each commits to the mbarrier
+#define TC_ISSUERS 3
 // first-order bound on the relative error of one item done with single FP16
 // operands: six roundings to FP16 (x, W, V and the three F blocks, 2^-11
 // each) plus FP32 accumulation, rounded up to 8 * 2^-11
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     // zero everything once: the K padding of stages II and III stays zero
     for (int e = tid; e < L::TOTAL / 16; e += TC_THREADS) ((uint4*)sm)[e] = make_uint4(0, 0, 0, 0);
     if (warp == 0) tc::tmem_alloc(&s_tmem, L::TMEM_COLS);
-    if (tid == 0) tc::mbar_init(&s_mbar, 1);
+    if (tid == 0) tc::mbar_init(&s_mbar, TC_ISSUERS);
     tc::fence_async_smem();
     __syncthreads();
     tc::fence_after();
@@ -209,6 +213,10 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const int mc_lo = whalf * (MC / 2), mc_hi = mc_lo + MC / 2;
     const uint32_t idI = tc::idesc_f16(64, 8 * MC), idS = tc::idesc_f16(64, 8);
+    // a single-thread MMA costs the issuing thread tens of cycles, so three threads issue
+    // in parallel, each into its own accumulators (the results stay deterministic)
+    const bool issuer = lane == 0 && warp < TC_ISSUERS;
+    const int iss_lo = warp * (MC / 2), iss_hi = iss_lo + MC / 2;  // stage II/III terms of warps 0, 1
     uint32_t phase = 0;
     // accumulator rows of this thread in the M=64 layout (16x256b read-outs):
     // 16 quarter + lane/4 and that + 8, columns cA and cA + 1 of each term
@@ -538,9 +546,9 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     if (nxt < 36) fetch_line(nxt, xb ^ 1);
                     tc::fence_async_smem();
                     __syncthreads();
-                    if (tid == 0) {
+                    if (issuer) {
                         tc::fence_after();
-                        issue_stage1(xb, dI);
+                        if (warp == 2) issue_stage1(xb, dI);
                         tc::commit(&s_mbar);
                     }
                     for (;;) {
@@ -588,17 +596,20 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                         tc::fence_before();
                         tc::fence_async_smem();
                         __syncthreads();
-                        if (tid == 0) {
+                        if (issuer) {
                             tc::fence_after();
-                            // stage II(L): per term, V += A2 (M=64 (c1,i3) x K=16) x F^{t2} (N=8 c2)
-                            const int t2 = band_t(a2, cur % 6);
-                            for (int mc = 0; mc < MC; ++mc) {
-                                const bool low = LADDER && s_low[mc];
-                                const uint64_t a = adesc(mc);
-                                tc::mma_f16(dII + mc * 8, a, fdesc(mc, t2, true, low), idS, first ? 0u : 1u);
-                                if (!low) tc::mma_f16(dII + mc * 8, a, fdesc(mc, t2, false, false), idS, 1);
+                            if (warp < 2) {
+                                // stage II(L): per term, V += A2 (M=64 (c1,i3) x K=16) x F^{t2} (N=8 c2)
+                                const int t2 = band_t(a2, cur % 6);
+                                for (int mc = iss_lo; mc < iss_hi; ++mc) {
+                                    const bool low = LADDER && s_low[mc];
+                                    const uint64_t a = adesc(mc);
+                                    tc::mma_f16(dII + mc * 8, a, fdesc(mc, t2, true, low), idS, first ? 0u : 1u);
+                                    if (!low) tc::mma_f16(dII + mc * 8, a, fdesc(mc, t2, false, false), idS, 1);
+                                }
+                            } else if (!last) {
+                                issue_stage1(xb ^ 1, dI);
                             }
-                            if (!last) issue_stage1(xb ^ 1, dI);
                             tc::commit(&s_mbar);
                         }
                         if (last) {
@@ -636,16 +647,19 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                             __syncthreads();
                             // stage III: per term, Y += A3 (M=64 (c1,c2) x K=16) x F^{t3} (N=8 c3)
                             // into the D_I block; the next plane's first stage I into D_II
-                            if (tid == 0) {
+                            if (issuer) {
                                 tc::fence_after();
-                                const int t3 = band_t(a3, q3);
-                                for (int mc = 0; mc < MC; ++mc) {
-                                    const bool low = LADDER && s_low[mc];
-                                    const uint64_t a = adesc(mc);
-                                    tc::mma_f16(dI + mc * 8, a, fdesc(mc, t3, true, low), idS, 0);
-                                    if (!low) tc::mma_f16(dI + mc * 8, a, fdesc(mc, t3, false, false), idS, 1);
+                                if (warp < 2) {
+                                    const int t3 = band_t(a3, q3);
+                                    for (int mc = iss_lo; mc < iss_hi; ++mc) {
+                                        const bool low = LADDER && s_low[mc];
+                                        const uint64_t a = adesc(mc);
+                                        tc::mma_f16(dI + mc * 8, a, fdesc(mc, t3, true, low), idS, 0);
+                                        if (!low) tc::mma_f16(dI + mc * 8, a, fdesc(mc, t3, false, false), idS, 1);
+                                    }
+                                } else if (nxt < 36) {
+                                    issue_stage1(xb ^ 1, dII);
                                 }
-                                if (nxt < 36) issue_stage1(xb ^ 1, dII);
                                 tc::commit(&s_mbar);
                             }
                             const uint32_t d = dI;
