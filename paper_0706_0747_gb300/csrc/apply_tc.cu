@@ -21,7 +21,7 @@
 // (sx_node = the smallest block scale of the neighbourhood), and per term for
 // W and V from bounds (|W| <= 48 max|F| max|x|, |V| <= 48 max|F| max|W|).
 //
-// Three threads issue the MMAs (stage I; stages II/III for either half of the terms)
+// Five threads issue the MMAs (stage I; stages II/III for a quarter of the terms each)
 // and commit them to one mbarrier; warp 0 polls it (bounded) and a block barrier
 // releases the rest; the 256 threads
 // read TMEM with tcgen05.ld and write the next stage's operand into shared
@@ -40,9 +40,9 @@ namespace mra {
 
 #define TC_THREADS 256
 #define TC_WAIT_LIMIT (1u << 26)
-// MMA-issuing threads (lane 0 of warps 0..TC_ISSUERS-1): warps 0 and 1 issue stages II and III
-// for the two halves of a chunk's terms, warp 2 issues stage I; each commits to the mbarrier
-#define TC_ISSUERS 3
+// MMA-issuing threads (lane 0 of warps 0..TC_ISSUERS-1): warps 0-3 issue stages II and III
+// for a quarter of a chunk's terms each, warp 4 issues stage I; each commits to the mbarrier
+#define TC_ISSUERS 5
 // first-order bound on the relative error of one item done with single FP16
 // operands: six roundings to FP16 (x, W, V and the three F blocks, 2^-11
 // each) plus FP32 accumulation, rounded up to 8 * 2^-11
@@ -213,10 +213,10 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const int mc_lo = whalf * (MC / 2), mc_hi = mc_lo + MC / 2;
     const uint32_t idI = tc::idesc_f16(64, 8 * MC), idS = tc::idesc_f16(64, 8);
-    // a single-thread MMA costs the issuing thread tens of cycles, so three threads issue
-    // in parallel, each into its own accumulators (the results stay deterministic)
+    // an MMA costs the issuing thread tens of cycles, so five threads issue in parallel,
+    // each into its own accumulators (the results stay deterministic)
     const bool issuer = lane == 0 && warp < TC_ISSUERS;
-    const int iss_lo = warp * (MC / 2), iss_hi = iss_lo + MC / 2;  // stage II/III terms of warps 0, 1
+    const int iss_lo = warp * (MC / 4), iss_hi = iss_lo + MC / 4;  // stage II/III terms of warps 0-3
     uint32_t phase = 0;
     // accumulator rows of this thread in the M=64 layout (16x256b read-outs):
     // 16 quarter + lane/4 and that + 8, columns cA and cA + 1 of each term
@@ -528,9 +528,9 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                 };
                 // Software pipeline over the chunk's lines: one wait and two block barriers per
                 // line.  While line L's stage I runs, stage II of the line before runs too; after
-                // the wait the block converts D_I(L), builds line L+1's stage-I B and starts the
-                // copies of line L+2's input blocks, then one thread issues stage II(L) and stage
-                // I(L+1) under one commit.  After a plane's last line, stage III of the plane and
+                // the wait the block converts D_I(L) and builds line L+1's stage-I B, then the
+                // issuing threads send stage II(L) and stage I(L+1) under one commit while the
+                // others start the copies of line L+2's input blocks.  After a plane's last line, stage III of the plane and
                 // stage I of the next plane's first line go out together: the two TMEM column
                 // blocks swap roles (D_I <-> D_II) from plane to plane, and stage III's result,
                 // left in the new D_II block, is read after the next wait.
@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     __syncthreads();
                     if (issuer) {
                         tc::fence_after();
-                        if (warp == 2) issue_stage1(xb, dI);
+                        if (warp == 4) issue_stage1(xb, dI);
                         tc::commit(&s_mbar);
                     }
                     for (;;) {
@@ -591,14 +591,13 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                         if (nxt < 36) {
                             build_B(nxt);
                             tc::cp_async_wait_all();  // line L+1's input blocks
-                            if (nn < 36) fetch_line(nn, xb);
                         }
                         tc::fence_before();
                         tc::fence_async_smem();
                         __syncthreads();
                         if (issuer) {
                             tc::fence_after();
-                            if (warp < 2) {
+                            if (warp < 4) {
                                 // stage II(L): per term, V += A2 (M=64 (c1,i3) x K=16) x F^{t2} (N=8 c2)
                                 const int t2 = band_t(a2, cur % 6);
                                 for (int mc = iss_lo; mc < iss_hi; ++mc) {
@@ -612,6 +611,8 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                             }
                             tc::commit(&s_mbar);
                         }
+                        // line L+2's input blocks into line L's buffer, while the MMAs run
+                        if (nn < 36) fetch_line(nn, xb);
                         if (last) {
                             // the plane's last stage II complete: D_II -> stage III A (aliases
                             // stage II A)
@@ -649,7 +650,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                             // into the D_I block; the next plane's first stage I into D_II
                             if (issuer) {
                                 tc::fence_after();
-                                if (warp < 2) {
+                                if (warp < 4) {
                                     const int t3 = band_t(a3, q3);
                                     for (int mc = iss_lo; mc < iss_hi; ++mc) {
                                         const bool low = LADDER && s_low[mc];
