@@ -174,8 +174,8 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     __shared__ unsigned int s_xmax_bits;
     __shared__ unsigned long long s_items;
     __shared__ float s_c2[MC], s_c3[MC];
-    __shared__ unsigned char s_lm[36], s_pm[6];
-    __shared__ unsigned long long s_km[36], s_kg[36];  // per line: masks, g exponents
+    __shared__ unsigned char s_lm[36];
+    __shared__ unsigned long long s_kg[36];  // per line: the g exponents of its six blocks
     __shared__ float s_fin[MC];
     __shared__ int s_cnt[MC];
     __shared__ float s_B[MC];
@@ -198,6 +198,11 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     unsigned char* tfl = sm + L::TFL;
     float* tg = (float*)(sm + L::TG);
     unsigned char* msk = sm + L::MSK;
+    // the MC mask bytes of a line as one word (byte mc = term mc's kept-t1 mask)
+    auto line_masks = [&](int line) -> unsigned long long {
+        if (MC == 8) return *(const unsigned long long*)(msk + line * 8);
+        return *(const unsigned int*)(msk + line * MC);
+    };
 
     // zero everything once: the K padding of stages II and III stays zero
     for (int e = tid; e < L::TOTAL / 16; e += TC_THREADS) ((uint4*)sm)[e] = make_uint4(0, 0, 0, 0);
@@ -217,6 +222,16 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     // each into its own accumulators (the results stay deterministic)
     const bool issuer = lane == 0 && warp < TC_ISSUERS;
     const int iss_lo = warp * (MC / 4), iss_hi = iss_lo + MC / 4;  // stage II/III terms of warps 0-3
+    // this thread's elements e = tid + k TC_THREADS of stage I's B (uint4 e of B1H..B1L, core
+    // (mc, q1) of hi or lo): the staged-F source index without the node's t1 offset, and mc, q1
+    constexpr int NB1 = (2 * MC * 48 + TC_THREADS - 1) / TC_THREADS;
+    int b1_src[NB1], b1_mq[NB1];
+#pragma unroll
+    for (int k = 0; k < NB1; ++k) {
+        const int e = tid + k * TC_THREADS, d48 = e / 48, q1 = (e - 48 * d48) >> 3;
+        b1_src[k] = e + 8 * d48;
+        b1_mq[k] = (d48 & (MC - 1)) | (q1 << 8);
+    }
     uint32_t phase = 0;
     // accumulator rows of this thread in the M=64 layout (16x256b read-outs):
     // 16 quarter + lane/4 and that + 8, columns cA and cA + 1 of each term
@@ -394,44 +409,39 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                         atomicAdd(&s_B[mc], acc);
                         atomicAdd(&s_cnt[mc], __popc(mk));
                     }
-                __syncthreads();
-                // per line: the union of its terms' kept-t1 masks; per plane: any line
                 if (tid < 36) {
-                    // stage I's B depends on the line only through its masks and g exponents
-                    unsigned v = 0;
-                    unsigned long long km = 0, kg = 0;
-                    for (int mc = 0; mc < MC; ++mc) {
-                        v |= msk[tid * MC + mc];
-                        km |= (unsigned long long)msk[tid * MC + mc] << (8 * mc);
+                    // per line: the union of its terms' kept-t1 masks
+                    unsigned long long km = line_masks(tid);
+                    km |= km >> 32;
+                    km |= km >> 16;
+                    km |= km >> 8;
+                    s_lm[tid] = (unsigned char)km;
+                    if (m0 == mlo) {  // once per node: stage I's B depends on g through these
+                        unsigned long long kg = 0;
+                        for (int q1 = 0; q1 < 6; ++q1)
+                            kg |= (unsigned long long)((__float_as_uint(tg[q1 * 36 + tid]) >> 23) & 0xffu) << (8 * q1);
+                        s_kg[tid] = kg;
                     }
-                    for (int q1 = 0; q1 < 6; ++q1)
-                        kg |= (unsigned long long)((__float_as_uint(tg[q1 * 36 + tid]) >> 23) & 0xffu) << (8 * q1);
-                    s_lm[tid] = (unsigned char)v;
-                    s_km[tid] = km;
-                    s_kg[tid] = kg;
                 }
                 __syncthreads();
-                if (tid < 6) {
-                    unsigned v = 0;
-                    for (int q2 = 0; q2 < 6; ++q2) v |= s_lm[q2 * 6 + tid];
-                    s_pm[tid] = (unsigned char)v;
-                }
-                if (LADDER && tid == 32) {
-                    // single FP16 products (hi only) for terms whose rounding error,
-                    // at most LADDER_U B_m, fits the node's share of the budget
-                    int all = 1;
-                    const double per_term = lp_node / (double)(mhi - mlo + 1);
-                    for (int mc = 0; mc < MC; ++mc) {
-                        const int m = m0 + mc;
-                        int low = 1;
-                        if (m <= mhi) low = T.lpb && LADDER_U * A.w[m] * (double)s_B[mc] <= per_term;
-                        s_low[mc] = (unsigned char)low;
-                        if (low) s_lowi += s_cnt[mc];
-                        all &= low;
+                if (LADDER) {
+                    if (tid == 32) {
+                        // single FP16 products (hi only) for terms whose rounding error,
+                        // at most LADDER_U B_m, fits the node's share of the budget
+                        int all = 1;
+                        const double per_term = lp_node / (double)(mhi - mlo + 1);
+                        for (int mc = 0; mc < MC; ++mc) {
+                            const int m = m0 + mc;
+                            int low = 1;
+                            if (m <= mhi) low = T.lpb && LADDER_U * A.w[m] * (double)s_B[mc] <= per_term;
+                            s_low[mc] = (unsigned char)low;
+                            if (low) s_lowi += s_cnt[mc];
+                            all &= low;
+                        }
+                        s_all_low = all;
                     }
-                    s_all_low = all;
+                    __syncthreads();
                 }
-                __syncthreads();
                 const int all_low = LADDER ? s_all_low : 0;
                 // masks and g exponents of the line stage I's B was last built for
                 unsigned long long built_m = ~0ull, built_g = ~0ull;
@@ -469,7 +479,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     const int lineb = line_of(c);
                     // when the line's masks and g equal the last build's, B1 already holds
                     // this line's operand
-                    const unsigned long long km = s_km[lineb], kg = s_kg[lineb];
+                    const unsigned long long km = line_masks(lineb), kg = s_kg[lineb];
                     if (km == built_m && kg == built_g) return;
                     built_m = km;
                     built_g = kg;
@@ -477,12 +487,18 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     // uint4 e of B1H..B1L; its source F^{t1(q1)}_mc, t1 + 3 = q1 + (a1 & 1), is
                     // uint4 e + 8 (e / 48 + (a1 & 1)) of the staged F (hi then lo)
                     const int nb1 = all_low ? MC * 48 : 2 * MC * 48;
-                    for (int e = tid; e < nb1; e += TC_THREADS) {
-                        const int d48 = e / 48, q1 = (e - 48 * d48) >> 3, mc = d48 & (MC - 1);
+                    const unsigned char* mline = msk + lineb * MC;
+                    const float* gline = tg + lineb;
+                    const uint4* fs = (const uint4*)(sm + L::FSH) + 8 * (a1 & 1);
+#pragma unroll
+                    for (int k = 0; k < NB1; ++k) {
+                        const int e = tid + k * TC_THREADS;
+                        if (e >= nb1) break;
+                        const int mc = b1_mq[k] & 0xff, q1 = b1_mq[k] >> 8;
                         uint4 out = make_uint4(0, 0, 0, 0);
-                        if ((msk[lineb * MC + mc] >> q1) & 1u) {
-                            const uint4 fin4 = ((const uint4*)(sm + L::FSH))[e + 8 * (d48 + (a1 & 1))];
-                            const __half2 g2 = __float2half2_rn(tg[q1 * 36 + lineb]);
+                        if ((mline[mc] >> q1) & 1u) {
+                            const uint4 fin4 = fs[b1_src[k]];
+                            const __half2 g2 = __float2half2_rn(gline[q1 * 36]);
                             const __half2* pi = (const __half2*)&fin4;
                             __half2* po = (__half2*)&out;
 #pragma unroll
