@@ -460,7 +460,10 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     const unsigned lmx = s_lm[line];
                     // element e = (hl, q1, v): uint4 v (of 64) of block q1, hi then lo
                     const int nfe = all_low ? 384 : 768;
-                    for (int e = tid; e < nfe; e += TC_THREADS) {
+#pragma unroll
+                    for (int k = 0; k < 768 / TC_THREADS; ++k) {
+                        const int e = tid + k * TC_THREADS;
+                        if (e >= nfe) continue;
                         const int hl = e >= 384, r = hl ? e - 384 : e, q1 = r >> 6;
                         uint4* dst = (uint4*)(sm + L::XH + hl * (L::XL - L::XH) + buf * 6144) + r;
                         if (lmx & (1u << q1)) {
@@ -490,13 +493,15 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     const unsigned char* mline = msk + lineb * MC;
                     const float* gline = tg + lineb;
                     const uint4* fs = (const uint4*)(sm + L::FSH) + 8 * (a1 & 1);
+                    // all of this thread's elements at once (predicated, no early exit), so that
+                    // their shared-memory loads are in flight together
 #pragma unroll
                     for (int k = 0; k < NB1; ++k) {
                         const int e = tid + k * TC_THREADS;
-                        if (e >= nb1) break;
                         const int mc = b1_mq[k] & 0xff, q1 = b1_mq[k] >> 8;
+                        const bool keep = e < nb1 && ((mline[mc] >> q1) & 1u);
                         uint4 out = make_uint4(0, 0, 0, 0);
-                        if ((mline[mc] >> q1) & 1u) {
+                        if (keep) {
                             const uint4 fin4 = fs[b1_src[k]];
                             const __half2 g2 = __float2half2_rn(gline[q1 * 36]);
                             const __half2* pi = (const __half2*)&fin4;
@@ -504,7 +509,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
 #pragma unroll
                             for (int h = 0; h < 4; ++h) po[h] = __hmul2(pi[h], g2);
                         }
-                        ((uint4*)B1H)[e] = out;
+                        if (e < nb1) ((uint4*)B1H)[e] = out;
                     }
                 };
                 // stage I from X buffer parx into the TMEM block d (thread 0)
