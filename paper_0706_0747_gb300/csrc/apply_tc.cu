@@ -4,7 +4,7 @@
 // Same nested sums as apply_fact.cu, per output node a and chunk of MC terms
 // m (w_m, F = F^{j;m,.}):
 //   stage I   per (t2,t3) line: W_m[c1][(i2,i3)] = sum_{t1 kept} sum_i1 F^{t1}[c1][i1] x_t[i1][i2][i3]
-//             MMA M=64 rows (i2,i3), N=8*MC (m,c1), K=48 (t1,i1); the kept-item
+//             MMA M=64 rows (i3,i2), N=8*MC (m,c1), K=48 (t1,i1); the kept-item
 //             mask zeroes whole F^{t1} blocks of the B operand
 //   stage II  per line and term: V_m[(c1,i3)][c2] += sum_i2 W_m[c1][i2][i3] F^{t2}[c2][i2]
 //             MMA M=64, N=8, K=16 (i2, zero padded), accumulated over the plane's lines in TMEM
@@ -23,10 +23,11 @@
 //
 // Five threads issue the MMAs (stage I; stages II/III for a quarter of the terms each)
 // and commit them to one mbarrier; warp 0 polls it (bounded) and a block barrier
-// releases the rest; the 256 threads
-// read TMEM with tcgen05.ld and write the next stage's operand into shared
-// memory in the canonical no-swizzle K-major layout (8-row x 16-byte core
-// matrices).  Per line there is one wait: stage II of a line runs while the
+// releases the rest; the 256 threads read TMEM with tcgen05.ld (16x256b) and
+// write the next stage's operand into shared memory in the no-swizzle K-major
+// layout (8-row x 16-byte core matrices) with transposing stmatrix stores: the
+// input blocks' rows are ordered (i3, i2), so that a warp's TMEM lane quarter
+// holds all eight K values of the rows it stores.  Per line there is one wait: stage II of a line runs while the
 // next line's operands are staged.  CTAs are persistent and take nodes from
 // an atomic counter (optionally in a given order), so one launch can cover the
 // nodes of many trees.
@@ -50,15 +51,15 @@ namespace mra {
 
 // ---------------------------------------------------------------- prep
 // Input blocks -> FP16 hi/lo in the stage-I A layout: element x[i1][i2][i3]
-// (zero for indices >= kr) at half index i2*64 + i3*8 + i1 (core matrix i2,
-// row i3, column i1), with a power-of-two scale per block.  Block b is node b
+// (zero for indices >= kr) at half index i3*64 + i2*8 + i1 (core matrix i3,
+// row i2, column i1), with a power-of-two scale per block.  Block b is node b
 // of s (b < n) or Step-2 block b - n.
 #define PREP_WARPS 8
 __global__ void __launch_bounds__(32 * PREP_WARPS) k_tc_prep_blocks(int nb, int kr, int n, const double* s,
                                                                   const double* gblk, __half* xh, __half* xl,
                                                                   float* sx, float* xmax, float* xnrm) {
     // warp per block: coalesced FP64 reads into shared memory, then each lane
-    // writes the 8 values (i1 = 0..7) of two (i2, i3) rows as one 16-byte hi
+    // writes the 8 values (i1 = 0..7) of two (i3, i2) rows as one 16-byte hi
     // and one 16-byte lo store
     __shared__ double xs[PREP_WARPS][512];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -86,8 +87,8 @@ __global__ void __launch_bounds__(32 * PREP_WARPS) k_tc_prep_blocks(int nb, int 
         // operand can be reused from line to line); blocks below 2^-100 keep the
         // scale 2^113 (a finite float) and round to zero in FP16
         const double scale = ldexp(1.0, 13 - ((max(e, -100) + 3) & ~3));
-        for (int p = lane; p < 64; p += 32) {  // row (i2, i3) of the stage-I layout
-            const int i2 = p >> 3, i3 = p & 7;
+        for (int p = lane; p < 64; p += 32) {  // row (i3, i2) of the stage-I layout
+            const int i3 = p >> 3, i2 = p & 7;
             uint4 h4, l4;
             __half* hh = (__half*)&h4;
             __half* ll = (__half*)&l4;
@@ -146,8 +147,12 @@ struct TcSmem {
     static constexpr int XL = 12288;                // (lo); buffer p at + p * 6144
     static constexpr int B1H = 24576;               // MC terms x 6 K groups x 128 B: stage I B
     static constexpr int B1L = B1H + MC * 768;
-    static constexpr int A2H = B1L + MC * 768;      // MC x 2048 B: stage II A (K: hi | lo); stage III A aliases it
-    static constexpr int FSH = A2H + MC * 2048;     // MC terms x 7 shifts x 128 B: the chunk's F (hi)
+    // stage II A (K: hi | lo; stage III A aliases it): per term 8 groups of 8 rows, A2_SBO
+    // bytes apart (272, not 256, so that the transposed stores of a group hit 32 banks)
+    static constexpr int A2_SBO = 272;
+    static constexpr int A2_TERM = 8 * A2_SBO;
+    static constexpr int A2H = B1L + MC * 768;
+    static constexpr int FSH = A2H + MC * A2_TERM;  // MC terms x 7 shifts x 128 B: the chunk's F (hi)
     static constexpr int FSL = FSH + MC * 896;      // (lo)
     static constexpr int FZ = FSL + MC * 896;       // one zero core matrix
     static constexpr int TIN = FZ + 128;            // 216 int: input block per band position
@@ -188,7 +193,6 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     const int kr = T.kr;
     __half* B1H = (__half*)(sm + L::B1H);
     __half* B1L = (__half*)(sm + L::B1L);
-    __half* A2H = (__half*)(sm + L::A2H);
     // the operator blocks F (hi, lo) of term m at shift t: uint4 index ((j M + m) 7 + t + 3) 8
     const uint4* FH = (const uint4*)T.Fh;
     const uint4* FL = (const uint4*)T.Fl;
@@ -251,7 +255,17 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
         return base + k8 - (k8 << 16);
     };
     // stage II/III A of term mc: 2048 bytes apart
-    auto adesc = [&](int mc) -> uint64_t { return tc::sdesc(sbase + L::A2H, 128, 256) + (uint64_t)(mc * 128); };
+    auto adesc = [&](int mc) -> uint64_t {
+        return tc::sdesc(sbase + L::A2H, 128, L::A2_SBO) + (uint64_t)(mc * (L::A2_TERM / 16));
+    };
+    // this thread's row of the transposed 8x8 stores into A2: matrix lane/8 = (row group
+    // 2 quarter + lane/16, K group (lane/8) & 1), row lane % 8 of it
+    //   D_I -> stage II A: group c1 = lane % 8 is the row, i3 = 2 quarter + lane/16
+    //   D_II -> stage III A: group c1 = 2 quarter + lane/16, row c2 = lane % 8
+    const uint32_t a2_row_I = sbase + L::A2H + (lane & 7) * L::A2_SBO + ((lane >> 3) & 1) * 128 +
+                              (2 * (warp & 3) + (lane >> 4)) * 16;
+    const uint32_t a2_row_II = sbase + L::A2H + (2 * (warp & 3) + (lane >> 4)) * L::A2_SBO +
+                               ((lane >> 3) & 1) * 128 + (lane & 7) * 16;
 
     // the abort decision comes from __syncthreads_or, so it is uniform
     bool aborted = false;
@@ -582,28 +596,21 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                             accumulate_y(dII);
                             y_pending = false;
                         }
-                        // D_I -> stage II A: row (c1, i3), K column i2.  This thread holds
-                        // D_I rows (i2, i3) = (2 quarter, lane/4) and (2 quarter + 1, lane/4):
-                        // K neighbours, stored as one half2 per c1
+                        // D_I -> stage II A (rows (c1, i3), K = i2 as hi | lo).  This thread holds D_I
+                        // rows (i3, i2) = (2 quarter, lane/4) and (2 quarter + 1, lane/4), columns
+                        // c1 = cA, cA + 1: per term, its fragments of the 8x8 matrices [i2][c1] of the
+                        // two i3, hi and lo, stored transposed (a memory row = the K values of a (c1, i3))
                         {
                             float vv[MC / 2][4];
                             tc::tmem_ld16x256_rep<MC / 2>(dI + lane_off + mc_lo * 8, vv);
 #pragma unroll
                             for (int mc = mc_lo; mc < mc_hi; ++mc) {
                                 const float* v = vv[mc - mc_lo];
-                                const int i3 = lane >> 2;
                                 const float c2 = s_c2[mc];
-#pragma unroll
-                                for (int h = 0; h < 2; ++h) {
-                                    const float x0 = v[h] * c2, x1 = v[2 + h] * c2;
-                                    const int o = mc * 1024 + (cA + h) * 128 + i3 * 8 + 2 * quarter;
-                                    const __half2 hi = __floats2half2_rn(x0, x1);
-                                    *(__half2*)&A2H[o] = hi;
-                                    if (!LADDER || !s_low[mc]) {
-                                        const float2 hf = __half22float2(hi);
-                                        *(__half2*)&A2H[o + 64] = __floats2half2_rn(x0 - hf.x, x1 - hf.y);  // K group 1
-                                    }
-                                }
+                                uint32_t h0, l0, h1, l1;
+                                tc::split_h2(v[0] * c2, v[1] * c2, h0, l0);
+                                tc::split_h2(v[2] * c2, v[3] * c2, h1, l1);
+                                tc::stmatrix_x4_trans(a2_row_I + mc * L::A2_TERM, h0, l0, h1, l1);
                             }
                         }
                         const int q3 = cur / 6;
@@ -640,28 +647,21 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                             TC_WAIT_OR_ABORT();
                             if (aborted) break;
                             tc::fence_after();
-                            // D_II rows (c1, i3) = (2 quarter + s, lane/4), columns c2 = cA + h
+                            // D_II -> stage III A (rows (c1, c2), K = i3 as hi | lo).  This thread holds
+                            // D_II rows (c1, i3) = (2 quarter, lane/4) and (2 quarter + 1, lane/4),
+                            // columns c2 = cA, cA + 1: per term, its fragments of the matrices [i3][c2]
+                            // of the two c1, hi and lo, stored transposed
                             {
                                 float vv[MC / 2][4];
                                 tc::tmem_ld16x256_rep<MC / 2>(dII + lane_off + mc_lo * 8, vv);
 #pragma unroll
                                 for (int mc = mc_lo; mc < mc_hi; ++mc) {
                                     const float* v = vv[mc - mc_lo];
-                                    const int i3 = lane >> 2;
                                     const float c3 = s_c3[mc];
-#pragma unroll
-                                    for (int q = 0; q < 4; ++q) {
-                                        const int c1 = 2 * quarter + (q >> 1), c2 = cA + (q & 1);
-                                        const int o = mc * 1024 + c1 * 128 + c2 * 8 + i3;
-                                        if (LADDER && s_low[mc]) {
-                                            A2H[o] = __float2half_rn(v[q] * c3);
-                                        } else {
-                                            __half h, l;
-                                            tc::split_h(v[q] * c3, h, l);
-                                            A2H[o] = h;
-                                            A2H[o + 64] = l;  // K group 1
-                                        }
-                                    }
+                                    uint32_t h0, l0, h1, l1;
+                                    tc::split_h2(v[0] * c3, v[1] * c3, h0, l0);
+                                    tc::split_h2(v[2] * c3, v[3] * c3, h1, l1);
+                                    tc::stmatrix_x4_trans(a2_row_II + mc * L::A2_TERM, h0, l0, h1, l1);
                                 }
                             }
                             tc::fence_before();

@@ -135,6 +135,24 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// four 8x8 b16 matrices from the warp's fragments (thread t holds row t/4, columns 2(t%4)
+// and 2(t%4)+1 of each, as one 32-bit register per matrix), stored transposed: memory row
+// r of matrix i (16 bytes at the address thread 8 i + r supplies) is column r of fragment i
+__device__ __forceinline__ void stmatrix_x4_trans(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(r0),
+                 "r"(r1), "r"(r2), "r"(r3)
+                 : "memory");
+}
+
+// FP32 pair -> FP16 hi + FP16 lo pairs (v ~= hi + lo to about 2^-22 relative), packed as half2
+__device__ __forceinline__ void split_h2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *(const uint32_t*)&h;
+    lo = *(const uint32_t*)&l;
+}
+
 // FP32 -> FP16 hi + FP16 lo with v ~= hi + lo to about 2^-22 relative
 __device__ __forceinline__ void split_h(float v, __half& hi, __half& lo) {
     hi = __float2half_rn(v);
