@@ -48,7 +48,7 @@ FP64_TFLOPS = 1.25
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # apply kernel on this workload, from one ncu capture of the current kernel
 # version; None where no capture of the current kernel exists.
-TRAFFIC_BYTES = {"tc": 140.22e6}
+TRAFFIC_BYTES = {"tc": 140.85e6}
 
 
 class Clocks:

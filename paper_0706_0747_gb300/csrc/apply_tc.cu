@@ -180,6 +180,8 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     __shared__ unsigned long long s_items;
     __shared__ float s_c2[MC], s_c3[MC];
     __shared__ unsigned char s_lm[36];
+    __shared__ unsigned char s_order[36];  // the chunk's lines with a kept item, as cursors
+    __shared__ int s_nl;
     __shared__ unsigned long long s_kg[36];  // per line: the g exponents of its six blocks
     __shared__ float s_fin[MC];
     __shared__ int s_cnt[MC];
@@ -202,6 +204,8 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     unsigned char* tfl = sm + L::TFL;
     float* tg = (float*)(sm + L::TG);
     unsigned char* msk = sm + L::MSK;
+    // lines in (t3 plane, t2) order: cursor c = q3 * 6 + q2 names line q2 * 6 + q3
+    auto line_of = [](int c) { return (c % 6) * 6 + c / 6; };
     // the MC mask bytes of a line as one word (byte mc = term mc's kept-t1 mask)
     auto line_masks = [&](int line) -> unsigned long long {
         if (MC == 8) return *(const unsigned long long*)(msk + line * 8);
@@ -437,6 +441,16 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                         s_kg[tid] = kg;
                     }
                 }
+                if (warp == 2) {
+                    // the visiting order: cursors of the lines with a kept item, ascending
+                    const bool h0 = line_masks(line_of(lane)) != 0;
+                    const bool h1 = lane < 4 && line_masks(line_of(32 + lane)) != 0;
+                    const unsigned b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
+                    const unsigned below = (1u << lane) - 1u;
+                    if (h0) s_order[__popc(b0 & below)] = (unsigned char)lane;
+                    if (h1) s_order[__popc(b0) + __popc(b1 & below)] = (unsigned char)(32 + lane);
+                    if (lane == 0) s_nl = __popc(b0) + __popc(b1);
+                }
                 __syncthreads();
                 if (LADDER) {
                     if (tid == 32) {
@@ -459,14 +473,6 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                 const int all_low = LADDER ? s_all_low : 0;
                 // masks and g exponents of the line stage I's B was last built for
                 unsigned long long built_m = ~0ull, built_g = ~0ull;
-                // lines of the chunk in (t3 plane, t2) order; a cursor c = q3 * 6 + q2 names line
-                // q2 * 6 + q3, and only lines with a kept item are visited
-                auto next_of = [&](int c) {
-                    for (++c; c < 36; ++c)
-                        if (s_lm[(c % 6) * 6 + c / 6]) break;
-                    return c;
-                };
-                auto line_of = [](int c) { return (c % 6) * 6 + c / 6; };
                 // stage I A (a line's six input blocks) is copied asynchronously into one of two
                 // buffers while earlier lines compute
                 auto fetch_line = [&](int c, int buf) {
@@ -569,9 +575,11 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                 // stage I of the next plane's first line go out together: the two TMEM column
                 // blocks swap roles (D_I <-> D_II) from plane to plane, and stage III's result,
                 // left in the new D_II block, is read after the next wait.
-                int cur = next_of(-1);
-                if (cur < 36) {
-                    int nxt = next_of(cur);
+                const int nl = s_nl;  // only lines with a kept item are visited
+                if (nl > 0) {
+                    int li = 0;
+                    int cur = s_order[0];
+                    int nxt = nl > 1 ? s_order[1] : 36;
                     int xb = 0;  // X buffer of line L
                     uint32_t dI = tbase, dII = tbase + 8 * MC;
                     bool first = true, y_pending = false;
@@ -615,7 +623,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                         }
                         const int q3 = cur / 6;
                         const bool last = nxt >= 36 || nxt / 6 != q3;  // L ends its plane
-                        const int nn = nxt < 36 ? next_of(nxt) : 36;
+                        const int nn = li + 2 < nl ? s_order[li + 2] : 36;
                         if (nxt < 36) {
                             build_B(nxt);
                             tc::cp_async_wait_all();  // line L+1's input blocks
@@ -699,6 +707,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                             }
                         }
                         first = last;
+                        ++li;
                         cur = nxt;
                         nxt = nn;
                         xb ^= 1;
