@@ -216,7 +216,10 @@ int mra_op_export(const mra_op* op, double* w_host, double* tau_host, double* F_
 #define MRA_PREC_FP32     1   /* FP32 SIMT contractions, FP64 accumulation     */
 #define MRA_PREC_TC_SPLIT 2   /* FP16 hi+lo split products on tcgen05 tensor   */
                               /* cores, FP32 accumulation, output blocks       */
-                              /* accumulated as float pairs (TwoSum)           */
+                              /* accumulated as float pairs (TwoSum); under    */
+                              /* the static screen the Step-2 blocks, which    */
+                              /* only become FP16 hi/lo operands, are refined  */
+                              /* in FP32 (both tensor-core rungs)              */
 #define MRA_PREC_TC_LADDER 3  /* precision ladder on the tensor cores: per     */
                               /* output node and term, single FP16 products    */
                               /* (one MMA instead of three) when the term's    */

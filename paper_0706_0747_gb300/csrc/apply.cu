@@ -464,15 +464,15 @@ __global__ void k_ghost_reid(int ng, const uint64_t* gkeys, const uint64_t* tab,
 
 // out = Mat along dimension `dim` of the k^3 array x (Mat k x k, out[c] = sum_i Mat[c][i] x[i]);
 // KT > 0 fixes k at compile time.
-template <int KT>
-__device__ void mode_mul(int kdyn, const double* Mat, const double* x, double* out, int dim) {
+template <int KT, typename T>
+__device__ void mode_mul(int kdyn, const T* Mat, const T* x, T* out, int dim) {
     const int k = KT ? KT : kdyn, k3 = k * k * k, kk = k * k;
     for (int idx = threadIdx.x; idx < k3; idx += blockDim.x) {
         const int i1 = idx / kk, i2 = (idx / k) % k, i3 = idx % k;
         const int c = dim == 0 ? i1 : (dim == 1 ? i2 : i3);
         const int st = dim == 0 ? kk : (dim == 1 ? k : 1);
-        const double* src = x + idx - c * st;
-        double a = 0.0;
+        const T* src = x + idx - c * st;
+        T a = 0;
         for (int i = 0; i < k; ++i) a += Mat[c * k + i] * src[i * st];
         out[idx] = a;
     }
@@ -485,20 +485,22 @@ __device__ void mode_mul(int kdyn, const double* Mat, const double* x, double* o
 // multiplied first, then one three-mode product), then every child of the
 // group, sharing the direction-3 and direction-2 partial products among the
 // children (d = 0 half of eqs. recon_even / recon_odd).
-template <int KT>
+// T = double, or float where the blocks only feed FP16 hi/lo tensor-core operands
+template <int KT, typename T>
 __global__ void k_ghost_refine_groups(Forest F, int ng, const uint64_t* gkeys, double* gblk, int32_t* err) {
-    extern __shared__ double sm[];
+    extern __shared__ double sm_raw[];
+    T* sm = (T*)sm_raw;
     const int k = KT ? KT : F.k, k3 = k * k * k, kk = k * k;
     const int g0 = blockIdx.x;
     const uint64_t key0 = gkeys[g0];
     if (g0 > 0 && (gkeys[g0 - 1] >> 3) == (key0 >> 3)) return;  // not the first child of its group
-    double* HT = sm;           // 2 k x k: HT[p][a][i] = H^(p)[i][a]
-    double* P = HT + 2 * kk;   // 3 k x k: the path matrices per direction
-    double* Q = P + 3 * kk;    // 3 k x k: scratch
-    double* x = Q + 3 * kk;    // k^3: the parent
-    double* y = x + k3;        // 2 k^3: direction 3 by p3
-    double* z = y + 2 * k3;    // 4 k^3: direction 2 by (p2, p3)
-    double* w = z + 4 * k3;    // k^3
+    T* HT = sm;                // 2 k x k: HT[p][a][i] = H^(p)[i][a]
+    T* P = HT + 2 * kk;        // 3 k x k: the path matrices per direction
+    T* Q = P + 3 * kk;         // 3 k x k: scratch
+    T* x = Q + 3 * kk;         // k^3: the parent
+    T* y = x + k3;             // 2 k^3: direction 3 by p3
+    T* z = y + 2 * k3;         // 4 k^3: direction 2 by (p2, p3)
+    T* w = z + 4 * k3;         // k^3
     const int j = (int)(key0 >> 58);
     const int tree = (int)((key0 >> 36) & ((1ull << GH_TREE_BITS) - 1));
     const uint64_t mk = key0 & ((1ull << 36) - 1);
@@ -507,7 +509,7 @@ __global__ void k_ghost_refine_groups(Forest F, int ng, const uint64_t* gkeys, d
     const int32_t* off = F.off + tree * (F.lm + 1);
     for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) {
         int p = e / kk, r = e % kk, a = r / k, i = r % k;
-        HT[e] = F.filt[p * kk + i * k + a];
+        HT[e] = (T)F.filt[p * kk + i * k + a];
     }
     __shared__ int anc, jj, gn;
     if (threadIdx.x == 0) {
@@ -527,7 +529,7 @@ __global__ void k_ghost_refine_groups(Forest F, int ng, const uint64_t* gkeys, d
     }
     __syncthreads();
     if (anc < 0) return;
-    for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = F.s[(size_t)anc * k3 + e];
+    for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = (T)F.s[(size_t)anc * k3 + e];
     if (jj < jp) {
         // P_d = H^(p_last)T ... H^(p_first)T along the path ancestor -> parent
         const int bd[3] = {b1, b2, b3};
@@ -539,8 +541,8 @@ __global__ void k_ghost_refine_groups(Forest F, int ng, const uint64_t* gkeys, d
         for (int lv = jj + 1; lv < jp; ++lv) {
             for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
                 const int d = e / kk, a = (e % kk) / k, i = e % k;
-                const double* H = HT + ((bd[d] >> (jp - lv - 1)) & 1) * kk;
-                double acc = 0.0;
+                const T* H = HT + ((bd[d] >> (jp - lv - 1)) & 1) * kk;
+                T acc = 0;
                 for (int c = 0; c < k; ++c) acc += H[a * k + c] * P[d * kk + c * k + i];
                 Q[e] = acc;
             }
@@ -548,21 +550,21 @@ __global__ void k_ghost_refine_groups(Forest F, int ng, const uint64_t* gkeys, d
             for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) P[e] = Q[e];
             __syncthreads();
         }
-        mode_mul<KT>(k, P + 2 * kk, x, y, 2);
-        mode_mul<KT>(k, P + kk, y, z, 1);
-        mode_mul<KT>(k, P, z, x, 0);
+        mode_mul<KT, T>(k, P + 2 * kk, x, y, 2);
+        mode_mul<KT, T>(k, P + kk, y, z, 1);
+        mode_mul<KT, T>(k, P, z, x, 0);
     } else {
         __syncthreads();
     }
     // the children: direction 3 for p3 = 0, 1; direction 2 for (p2, p3); direction 1 per child
-    mode_mul<KT>(k, HT, x, y, 2);
-    mode_mul<KT>(k, HT + kk, x, y + k3, 2);
-    for (int q = 0; q < 4; ++q) mode_mul<KT>(k, HT + (q >> 1) * kk, y + (q & 1) * k3, z + q * k3, 1);
+    mode_mul<KT, T>(k, HT, x, y, 2);
+    mode_mul<KT, T>(k, HT + kk, x, y + k3, 2);
+    for (int q = 0; q < 4; ++q) mode_mul<KT, T>(k, HT + (q >> 1) * kk, y + (q & 1) * k3, z + q * k3, 1);
     for (int g = 0; g < gn; ++g) {
         const uint64_t cm = gkeys[g0 + g] & 7ull;  // octant (p1 p2 p3) of the child
         const int p1 = (int)(cm >> 2) & 1, p23 = (int)(cm & 3);
-        mode_mul<KT>(k, HT + p1 * kk, z + p23 * k3, w, 0);
-        for (int e = threadIdx.x; e < k3; e += blockDim.x) gblk[(size_t)(g0 + g) * k3 + e] = w[e];
+        mode_mul<KT, T>(k, HT + p1 * kk, z + p23 * k3, w, 0);
+        for (int e = threadIdx.x; e < k3; e += blockDim.x) gblk[(size_t)(g0 + g) * k3 + e] = (double)w[e];
         __syncthreads();
     }
 }
@@ -746,16 +748,21 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
     return MRA_OK;
 }
 
-int ghost_refine_forest(const Forest& F, const ScreenOut& S, double* gblk, cudaStream_t st) {
-    if (S.nghost <= 0) return MRA_OK;
+template <typename T>
+static int ghost_refine_launch(const Forest& F, const ScreenOut& S, double* gblk, cudaStream_t st) {
     const int k = F.k, k3 = k * k * k;
-    const size_t gsm = (8 * (size_t)k * k + 8 * (size_t)k3) * sizeof(double);
-    auto fn = k == 8 ? k_ghost_refine_groups<8> : (k == 6 ? k_ghost_refine_groups<6> :
-                                                 (k == 4 ? k_ghost_refine_groups<4> : k_ghost_refine_groups<0>));
+    const size_t gsm = (8 * (size_t)k * k + 8 * (size_t)k3) * sizeof(T);
+    auto fn = k == 8 ? k_ghost_refine_groups<8, T> : (k == 6 ? k_ghost_refine_groups<6, T> :
+                                                    (k == 4 ? k_ghost_refine_groups<4, T> : k_ghost_refine_groups<0, T>));
     MRA_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
     fn<<<S.nghost, 128, gsm, st>>>(F, S.nghost, S.gkeys, gblk, S.err + 1);
     MRA_CK_LAUNCH();
     return MRA_OK;
+}
+
+int ghost_refine_forest(const Forest& F, const ScreenOut& S, double* gblk, cudaStream_t st, bool fp32) {
+    if (S.nghost <= 0) return MRA_OK;
+    return fp32 ? ghost_refine_launch<float>(F, S, gblk, st) : ghost_refine_launch<double>(F, S, gblk, st);
 }
 
 // Precision ladder budget per tree: single-FP16 terms may add at most
@@ -830,9 +837,11 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     double* gblk;
     MRA_TRY(dalloc(A, &gblk, (size_t)(S.nghost + 1) * k3));
     G.p[0] = gblk;
-    MRA_TRY(ghost_refine_forest(F, S, gblk, st));
     // per-pair term ranges: the exact screen, or the learned one judged by it
     const int smode = o ? o->screen_mode : MRA_SCREEN_STATIC;
+    // Step 2: in FP32 when the blocks only become FP16 hi/lo tensor-core operands (their
+    // rounding, 2^-24, is below the operands' 2^-22) and no screen decision reads them
+    MRA_TRY(ghost_refine_forest(F, S, gblk, st, tc && smode == MRA_SCREEN_STATIC));
     unsigned long long* scounts = nullptr;
     if (smode != MRA_SCREEN_STATIC) {
         if (smode != MRA_SCREEN_PAIR && smode != MRA_SCREEN_LEARNED) {

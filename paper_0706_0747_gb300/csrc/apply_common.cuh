@@ -96,7 +96,9 @@ struct ScreenOut {
 
 int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc& A, cudaStream_t st, ScreenOut* S);
 void screen_release(const Alloc& A, ScreenOut* S);
-int ghost_refine_forest(const Forest& F, const ScreenOut& S, double* gblk, cudaStream_t st);
+// Step 2 for every missing input block of a forest; fp32: refine in FP32 (for blocks that
+// only feed FP16 hi/lo tensor-core operands), else FP64
+int ghost_refine_forest(const Forest& F, const ScreenOut& S, double* gblk, cudaStream_t st, bool fp32 = false);
 Forest forest_of_tree(const mra_tree* f);
 
 int tc_alloc(const mra_op* op, int nb, TcBuffers* B);            // nb: node + Step-2 blocks

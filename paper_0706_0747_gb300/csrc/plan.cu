@@ -135,7 +135,7 @@ static int plan_enqueue(const mra_plan* p, cudaStream_t st) {
     const int nb = (int)std::max<size_t>(1, std::min<size_t>(152 * 8, (total + 255) / 256));
     k_forest_blocks<<<nb, 256, 0, st>>>(p->n, k3, p->dbase, p->node_tree, p->tref, p->s);
     MRA_CK_LAUNCH();
-    MRA_TRY(ghost_refine_forest(p->F, p->S, p->gblk, st));
+    MRA_TRY(ghost_refine_forest(p->F, p->S, p->gblk, st, p->tc && p->screen_mode == MRA_SCREEN_STATIC));
     MRA_CK(cudaMemsetAsync(p->nitems, 0, ((size_t)p->ntrees + 1) * sizeof(unsigned long long), st));
     if (p->tc) {
         MRA_TRY(tc_prep_blocks(p->n + p->S.nghost, p->k, p->n, p->s, p->gblk, p->tcb, st));
@@ -359,7 +359,7 @@ int mra_plan_autotune(mra_plan* p, int reps, void* stream) {
     const int nb = (int)std::max<size_t>(1, std::min<size_t>(152 * 8, (total + 255) / 256));
     k_forest_blocks<<<nb, 256, 0, st>>>(p->n, k3, p->dbase, p->node_tree, p->tref, p->s);
     MRA_CK_LAUNCH();
-    MRA_TRY(ghost_refine_forest(p->F, p->S, p->gblk, st));
+    MRA_TRY(ghost_refine_forest(p->F, p->S, p->gblk, st, p->tc && p->screen_mode == MRA_SCREEN_STATIC));
     MRA_TRY(tc_prep_blocks(p->n + p->S.nghost, p->k, p->n, p->s, p->gblk, p->tcb, st));
     cudaEvent_t e0, e1;
     MRA_CK(cudaEventCreate(&e0));
