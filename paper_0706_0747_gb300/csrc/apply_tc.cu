@@ -7,9 +7,9 @@
 //             MMA M=64 rows (i3,i2), N=8*MC (m,c1), K=48 (t1,i1); the kept-item
 //             mask zeroes whole F^{t1} blocks of the B operand
 //   stage II  per line and term: V_m[(c1,i3)][c2] += sum_i2 W_m[c1][i2][i3] F^{t2}[c2][i2]
-//             MMA M=64, N=8, K=16 (i2, zero padded), accumulated over the plane's lines in TMEM
+//             MMA M=64, N=8, K=16 (i2 as hi | lo), accumulated over the plane's lines in TMEM
 //   stage III per plane and term: Y_m[(c1,c2)][c3] += sum_i3 V_m F^{t3}[c3][i3]
-//             MMA M=64, N=8, K=16 (i3, zero padded), accumulated over planes in TMEM
+//             MMA M=64, N=8, K=16 (i3 as hi | lo), read out after each plane
 //   ghat_a += w_m Y_m: per plane, an FP32 sum over the chunk's terms, added to ghat
 //             kept as a pair of floats (TwoSum), so no FP64 arithmetic runs per item.
 // Every operand is FP16 split into hi + lo (v ~= hi + lo to 2^-22), and each
@@ -27,10 +27,11 @@
 // write the next stage's operand into shared memory in the no-swizzle K-major
 // layout (8-row x 16-byte core matrices) with transposing stmatrix stores: the
 // input blocks' rows are ordered (i3, i2), so that a warp's TMEM lane quarter
-// holds all eight K values of the rows it stores.  Per line there is one wait: stage II of a line runs while the
-// next line's operands are staged.  CTAs are persistent and take nodes from
-// an atomic counter (optionally in a given order), so one launch can cover the
-// nodes of many trees.
+// holds all eight K values of the rows it stores.  The lines of a chunk form one
+// software pipeline with one wait per line: stage II of line L and stage I of
+// line L+1 go out under one commit, while line L+2's input blocks are copied.
+// CTAs are persistent and take nodes from an atomic counter (optionally in a
+// given order), so one launch can cover the nodes of many trees.
 #include <cfloat>
 #include <climits>
 
@@ -168,6 +169,7 @@ struct TcSmem {
 // three CTAs per SM (the register limit) for either chunk size
 static_assert(3 * (TcSmem<8>::TOTAL + 2048) <= 232448, "8 terms per chunk: three CTAs per SM");
 static_assert(3 * TcSmem<8>::TMEM_COLS <= 512, "three CTAs' tensor memory");
+static_assert(TcSmem<8>::MSK % 8 == 0 && TcSmem<4>::MSK % 4 == 0, "a line's masks are read as one word");
 
 template <int MC, bool LADDER>
 __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs T) {
@@ -212,7 +214,8 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
         return *(const unsigned int*)(msk + line * MC);
     };
 
-    // zero everything once: the K padding of stages II and III stays zero
+    // zero everything once: the zero core matrix FZ stays zero, and operand buffers that a
+    // line leaves unwritten hold finite values (they meet zero B rows)
     for (int e = tid; e < L::TOTAL / 16; e += TC_THREADS) ((uint4*)sm)[e] = make_uint4(0, 0, 0, 0);
     if (warp == 0) tc::tmem_alloc(&s_tmem, L::TMEM_COLS);
     if (tid == 0) tc::mbar_init(&s_mbar, TC_ISSUERS);
@@ -247,10 +250,10 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
     const uint32_t sbase = tc::smem_u32(sm);
     // B operands of stages II and III read in place from the chunk's staged F: the hi operand
     // [F_hi ; F_hi] has K-group offset 0 (both K groups are the same core matrix), the lo
-    // operand [F_lo ; 0] reaches the zero block; a single-FP16 term pairs F_hi with zeros
-    // operand (mc, t) lies 128 (mc 7 + t + 3) bytes past the table's start: 8 (mc 7 + t + 3) in
-    // the descriptor's start-address field, and as much less in the K-group offset field when
-    // that offset reaches the zero block
+    // operand [F_lo ; 0] reaches the zero block; a single-FP16 term pairs F_hi with zeros.
+    // Operand (mc, t) lies 128 (mc 7 + t + 3) bytes past its table's start: 8 (mc 7 + t + 3)
+    // more in the descriptor's start-address field, and as much less in the K-group offset
+    // field when that offset reaches the zero block
     auto fdesc = [&](int mc, int t, bool hi, bool low) -> uint64_t {
         const uint64_t k8 = (uint64_t)((mc * 7 + t + 3) * 8);
         if (hi && !low) return tc::sdesc(sbase + L::FSH, 0u, 256) + k8;
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                                  : tc::sdesc(sbase + L::FSL, L::FZ - L::FSL, 256);
         return base + k8 - (k8 << 16);
     };
-    // stage II/III A of term mc: 2048 bytes apart
+    // stage II/III A of term mc: A2_TERM bytes apart
     auto adesc = [&](int mc) -> uint64_t {
         return tc::sdesc(sbase + L::A2H, 128, L::A2_SBO) + (uint64_t)(mc * (L::A2_TERM / 16));
     };
@@ -571,10 +574,11 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                 // line.  While line L's stage I runs, stage II of the line before runs too; after
                 // the wait the block converts D_I(L) and builds line L+1's stage-I B, then the
                 // issuing threads send stage II(L) and stage I(L+1) under one commit while the
-                // others start the copies of line L+2's input blocks.  After a plane's last line, stage III of the plane and
-                // stage I of the next plane's first line go out together: the two TMEM column
-                // blocks swap roles (D_I <-> D_II) from plane to plane, and stage III's result,
-                // left in the new D_II block, is read after the next wait.
+                // others start the copies of line L+2's input blocks.  After a plane's last
+                // line, stage III of the plane and stage I of the next plane's first line go
+                // out together: the two TMEM column blocks swap roles (D_I <-> D_II) from plane
+                // to plane, and stage III's result, left in the new D_II block, is read after
+                // the next wait.
                 const int nl = s_nl;  // only lines with a kept item are visited
                 if (nl > 0) {
                     int li = 0;
