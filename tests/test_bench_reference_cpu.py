@@ -24,3 +24,16 @@ def test_reference_arm_json_line():
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert line["config"]["workload"] == "poisson_k8_eps1e-6_adaptive7"
+
+
+@pytest.mark.slow
+def test_oracle_on_all_cores_shares_one_sample():
+    """bench.py's all-cores oracle timing: single-threaded processes released
+    together, each on its own share of one random node order."""
+    sys.path.insert(0, ROOT)
+    import bench
+    one = bench.run_oracle_sample(2.0, 1)["steps"][0]
+    two = bench.run_oracle_parallel(2.0, 2)
+    assert two["n_nodes"] == 7737 and two["items"] > 0 and two["seconds"] >= 2.0
+    # two shares of the same order cover more nodes than one process in the same time
+    assert two["nodes"] > one["nodes"]
