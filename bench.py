@@ -199,7 +199,11 @@ def cpu_baseline(budget_s=15.0):
 
 
 def cpu_baseline_all_cores(budget_s=15.0):
-    nproc = max(1, min(64, os.cpu_count() or 1))
+    try:  # the cores this process may run on (a container's cpuset), not the host's count
+        ncpu = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        ncpu = os.cpu_count() or 1
+    nproc = max(1, min(64, ncpu))
     r = run_oracle_parallel(budget_s, nproc)
     return {"value": r["items"] / r["seconds"], "unit": UNIT, "cores": nproc, "kind": "oracle",
             "sample": (f"{r['nodes']} of {r['n_nodes']} output nodes (one random order, shared out in chunks "
