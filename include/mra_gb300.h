@@ -21,8 +21,10 @@
  *     device memory.  `stream` is a cudaStream_t passed as void* (NULL = the
  *     legacy default stream).  Work is queued on that stream; calls return when
  *     queued unless stated otherwise ("synchronous").
- *   - Handles (mra_tree*, mra_op*) are owned by the library, opaque, and freed
- *     exactly once with mra_free().  Output handles are set to NULL on failure.
+ *   - Handles (mra_tree*, mra_op*, mra_plan*, mra_mlp*) are owned by the
+ *     library, opaque, and freed exactly once with mra_free() (or the typed
+ *     free of their kind).  Output handles are set to NULL on failure, and a
+ *     failing call releases every device block it took before it returns.
  *   - Device memory comes from the optional allocator hook (mra_alloc); when the
  *     hook is NULL the library uses cudaMallocAsync / cudaFreeAsync on `stream`.
  *   - There is no CPU fallback: every arithmetic step runs in the library's
@@ -206,26 +208,32 @@ int mra_op_export(const mra_op* op, double* w_host, double* tau_host, double* F_
  * ancestor leaf (Step 2).
  * The input tree must be MRA_TREE_REDUNDANT (mra_compress) and no deeper than
  * the operator's max_level.  Output: a new tree in state MRA_TREE_NSFORM.
- * Returns after the work is queued; stats (optional, host) are filled when the
- * call returns (the call synchronises once to size the worklist).
- * Errors found on the device are read back after the apply: MRA_ETIMEOUT when
- * a tensor-core completion wait gave up, MRA_EINVAL when a tensor-core output
- * scale w_m / (s_V s_F) falls outside FP32's range (use MRA_PREC_FP64). */
+ * Returns after the work is queued (the call synchronises once to size the
+ * worklist).  When stats (host) is not NULL the call also waits for the apply,
+ * fills stats and reads back the errors found on the device: MRA_ETIMEOUT
+ * when a tensor-core completion wait gave up, MRA_EINVAL when a tensor-core
+ * output scale w_m / (s_V s_F) falls outside FP32's range (use
+ * MRA_PREC_FP64), MRA_ECUDA for a failed Step-2 lookup; with stats NULL these
+ * are not checked. */
 
 #define MRA_PREC_FP64     0   /* FP64 SIMT contractions                        */
 #define MRA_PREC_FP32     1   /* FP32 SIMT contractions, FP64 accumulation     */
 #define MRA_PREC_TC_SPLIT 2   /* FP16 hi+lo split products on tcgen05 tensor   */
-                              /* cores, FP32 accumulation, output blocks       */
-                              /* accumulated as float pairs (TwoSum); under    */
-                              /* the static screen the Step-2 blocks, which    */
-                              /* only become FP16 hi/lo operands, are refined  */
-                              /* in FP32 (both tensor-core rungs)              */
+                              /* cores with FP32 accumulation (TMEM), each    */
+                              /* chunk of terms added to the output block in  */
+                              /* FP64; Step-2 blocks refined in FP64          */
 #define MRA_PREC_TC_LADDER 3  /* precision ladder on the tensor cores: per     */
                               /* output node and term, single FP16 products    */
                               /* (one MMA instead of three) when the term's    */
                               /* bound w_m sum_items prod N_F ||f_b|| times    */
                               /* 2^-8 fits the node's share of the budget      */
                               /* eps ||T_0 f_0|| / (4 sqrt(N)), else FP16 hi+lo */
+                              /* (FP64 output accumulation and Step 2)         */
+#define MRA_PREC_TC_FAST   4  /* MRA_PREC_TC_SPLIT with the Step-2 blocks,     */
+                              /* which only become FP16 hi/lo operands,        */
+                              /* refined in FP32 under the static screen: a    */
+                              /* variant outside the FP64 contract, kept to    */
+                              /* measure what that contract costs              */
 
 /* Screens of the (output box, translation) pairs' term ranges.  The test of
  * an item is w_m N_F(t1) N_F(t2) N_F(t3) ||f_b|| > eta_blk with
@@ -247,9 +255,21 @@ typedef struct {
                             /* of Algorithm 3 (same items; for comparison)    */
     int screen_mode;        /* MRA_SCREEN_*                                   */
     int margin;             /* learned screen: terms added on each side        */
-    int reserved[2];
+    int wait_limit;         /* tensor-core apply: polls of one MMA completion  */
+                            /* wait before it gives up (MRA_ETIMEOUT); 0 means */
+                            /* the default 2^26                                */
+    int test_flags;         /* 0 in normal use; MRA_TEST_WITHHOLD_MMA for the  */
+                            /* test of the bounded wait                        */
     const mra_mlp* schedule;  /* learned screen: a 16 -> 12 network (mra_mlp_*) */
 } mra_apply_opts;
+
+/* Test hook of the bounded device waits: the tensor-core apply's issuing
+ * threads send neither the first group of MMAs of a node nor its commit, so
+ * the first completion wait of every CTA can only end by reaching
+ * wait_limit.  Nothing is in flight when it gives up: the kernel records
+ * MRA_ETIMEOUT, frees its tensor memory and returns, and the output is not
+ * valid. */
+#define MRA_TEST_WITHHOLD_MMA 1
 
 typedef struct {
     int64_t n_pairs;        /* (output node, translation) pairs                */
@@ -287,13 +307,16 @@ int mra_apply_ns(const mra_op* op, const mra_tree* f, const mra_apply_opts* opts
  *     MRA_TREE_NSFORM tree mra_apply_ns would return).
  *   - n_items_host (optional): the number of (node, translation, term) items.
  * Sizes beyond these limits return MRA_EINVAL with a message, before any work
- * is queued (nodes, k) or right after the screen (refined blocks).
+ * is queued (nodes, k) or right after the screen (refined blocks: then only
+ * the screen has run, and nothing past it is queued).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call shares the one array and leaves its contents behind; the call
- * clears what must start at zero.  Calls that overlap on the GPU (other
- * streams or threads) race on the array: serialise them.  The call
- * synchronises `stream` once to read the worklist sizes. */
+ * (cudaGetSymbolAddress).  Every call shares the one array and leaves its
+ * contents behind; the call clears what must start at zero.  Calls that
+ * overlap on the GPU (other streams or threads) race on the array: serialise
+ * them.  The call synchronises `stream` twice -- after the screen, to read the
+ * worklist sizes, and at the end, to read the device's error words (a failed
+ * Step-2 lookup returns MRA_ECUDA) -- so it cannot be called while `stream` is
+ * being captured into a CUDA graph. */
 int mra_apply_ns_noalloc(const mra_op* op, const mra_tree* f, int precision, double* ghat_out,
                          void* stream, int64_t* n_items_host);
 
@@ -439,7 +462,11 @@ int mra_free_plan(mra_plan* p);
 int mra_reconstruct(mra_tree* t, int mode, int truncate, double eps, void* stream,
                     double* truncation_l2_host);
 
-/* Free a tree or operator handle (exactly once; NULL is ignored). */
+/* Free any handle of this library -- a tree, operator, plan or network --
+ * exactly once (NULL is ignored).  The kind is read from the tag every handle
+ * starts with; a pointer that is not a live handle returns MRA_EINVAL.  The
+ * typed frees below do the same for one kind each. */
+int mra_free(void* handle);
 int mra_free_tree(mra_tree* t);
 int mra_free_op(mra_op* op);
 

@@ -686,16 +686,16 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
     MRA_TRY(dalloc(A, &S->err, 2));
     MRA_CK(cudaMemsetAsync(S->dv, 0, 4 * (size_t)F.ntrees * sizeof(double), st));
     MRA_CK(cudaMemsetAsync(S->err, 0, 2 * sizeof(int32_t), st));
-    const int nb_norm = (int)std::max<long>(1, std::min<long>(152 * 16, ((long)n * 32 + 255) / 256));
+    const int nb_norm = (int)std::max<long>(1, std::min<long>(num_sms() * 16, ((long)n * 32 + 255) / 256));
     k_forest_norm2<<<nb_norm, 256, 0, st>>>(F, S->dv);
     MRA_CK_LAUNCH();
+    Scratch tmp(A);
     double* ym;
-    MRA_TRY(dalloc(A, &ym, (size_t)F.ntrees * M * k3));
+    MRA_TRY(tmp.get(&ym, (size_t)F.ntrees * M * k3));
     k_pilot_terms<<<dim3(M, F.ntrees), 128, (3 * (size_t)k3 + F.k * F.k) * sizeof(double), st>>>(F, M, op->w, op->F, ym);
     MRA_CK_LAUNCH();
     k_pilot_reduce<<<F.ntrees, 256, 0, st>>>(k3, M, ym, S->dv);
     MRA_CK_LAUNCH();
-    A.put(ym);
     k_schedule<<<F.ntrees, 256, 0, st>>>(M, F.lm, F.nlev, unscreened, op->eps, op->w, op->nF, op->est, S->dv,
                                          S->sched, S->sl);
     MRA_CK_LAUNCH();
@@ -703,7 +703,7 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
     ScreenArgs sa;
     sa.F = F; sa.M = M; sa.sl = S->sl; sa.sched = S->sched;
     sa.count = S->count; sa.pair_off = S->pair_off; sa.pairs = nullptr; sa.err = S->err;
-    const int sblocks = (int)std::max<long>(1, std::min<long>(152 * 32, ((long)n * 32 + 255) / 256));
+    const int sblocks = (int)std::max<long>(1, std::min<long>(num_sms() * 32, ((long)n * 32 + 255) / 256));
     uint64_t cap = 1024;
     while (cap < (uint64_t)n * 64ull) cap <<= 1;
     int32_t h[2] = {0, 0}, herr[2] = {0, 0};
@@ -797,11 +797,16 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     if (nlev - 1 > op->J) { set_error("tree depth %d exceeds operator max_level %d", nlev - 1, op->J); return MRA_EINVAL; }
     if (f->state != MRA_TREE_REDUNDANT) { set_error("apply_ns needs a compressed (redundant) tree"); return MRA_ESTATE; }
     const int prec = o ? o->precision : MRA_PREC_FP64;
-    if (prec != MRA_PREC_FP64 && prec != MRA_PREC_FP32 && prec != MRA_PREC_TC_SPLIT && prec != MRA_PREC_TC_LADDER) {
+    if (prec != MRA_PREC_FP64 && prec != MRA_PREC_FP32 && prec != MRA_PREC_TC_SPLIT && prec != MRA_PREC_TC_LADDER &&
+        prec != MRA_PREC_TC_FAST) {
         set_error("precision %d is not available", prec);
         return MRA_EINVAL;
     }
-    const bool tc = prec == MRA_PREC_TC_SPLIT || prec == MRA_PREC_TC_LADDER;
+    const bool tc = prec == MRA_PREC_TC_SPLIT || prec == MRA_PREC_TC_LADDER || prec == MRA_PREC_TC_FAST;
+    if (o && (o->wait_limit < 0 || (o->test_flags & ~MRA_TEST_WITHHOLD_MMA))) {
+        set_error("wait_limit must be >= 0 and test_flags a set of MRA_TEST_* bits");
+        return MRA_EINVAL;
+    }
     if (tc && ((o && (o->block_screen || o->itemwise)) || k > 8)) {
         set_error("the tensor-core apply needs k <= 8 and the static screen");
         return MRA_EINVAL;
@@ -839,9 +844,10 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
     G.p[0] = gblk;
     // per-pair term ranges: the exact screen, or the learned one judged by it
     const int smode = o ? o->screen_mode : MRA_SCREEN_STATIC;
-    // Step 2: in FP32 when the blocks only become FP16 hi/lo tensor-core operands (their
-    // rounding, 2^-24, is below the operands' 2^-22) and no screen decision reads them
-    MRA_TRY(ghost_refine_forest(F, S, gblk, st, tc && smode == MRA_SCREEN_STATIC));
+    // Step 2 in FP64 (a two-scale transform); MRA_PREC_TC_FAST refines in FP32 when the
+    // blocks only become FP16 hi/lo operands (rounding 2^-24, below the operands' 2^-22)
+    // and no screen decision reads them
+    MRA_TRY(ghost_refine_forest(F, S, gblk, st, prec == MRA_PREC_TC_FAST && smode == MRA_SCREEN_STATIC));
     unsigned long long* scounts = nullptr;
     if (smode != MRA_SCREEN_STATIC) {
         if (smode != MRA_SCREEN_PAIR && smode != MRA_SCREEN_LEARNED) {
@@ -885,7 +891,8 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
             G.p[3] = lpb;
             MRA_TRY(lp_budget(F, S, op->eps, lpb, st));
         }
-        MRA_TRY(launch_apply_tc(aa, S.nghost, op, S.err + 1, lpb, nitems + 1, st));
+        MRA_TRY(launch_apply_tc(aa, S.nghost, op, S.err + 1, lpb, nitems + 1, o ? (unsigned)o->wait_limit : 0u,
+                                o ? (o->test_flags & MRA_TEST_WITHHOLD_MMA) : 0, st));
     } else if (!itemwise) {
         // Algorithm 3's nested sums, factorised (apply_fact.cu)
         aa.F = prec == MRA_PREC_FP64 ? (const void*)op->F : (const void*)op->F32;
@@ -894,13 +901,13 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         aa.F = op->F;
         size_t smem = (size_t)k3 * sizeof(double) + (4 * (size_t)k3 + 3 * k * k) * sizeof(double);
         MRA_CK(cudaFuncSetAttribute(k_apply_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_apply_simt<double><<<std::min(n, 152 * 16), 128, smem, st>>>(aa);
+        k_apply_simt<double><<<std::min(n, num_sms() * 16), 128, smem, st>>>(aa);
         MRA_CK_LAUNCH();
     } else {
         aa.F = op->F32;
         size_t smem = (size_t)k3 * sizeof(double) + (4 * (size_t)k3 + 3 * k * k) * sizeof(float);
         MRA_CK(cudaFuncSetAttribute(k_apply_simt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_apply_simt<float><<<std::min(n, 152 * 16), 128, smem, st>>>(aa);
+        k_apply_simt<float><<<std::min(n, num_sms() * 16), 128, smem, st>>>(aa);
         MRA_CK_LAUNCH();
     }
     MRA_CK(cudaEventRecord(ev[3], st));
@@ -935,9 +942,10 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
         else if (herr[1] == 5) { set_error("tensor-core apply: an output scale is outside the FP32 range (use fp64)"); rc = MRA_EINVAL; }
         else if (herr[0] || herr[1]) { set_error("screen/ghost error code %d/%d", herr[0], herr[1]); rc = MRA_ECUDA; }
     }
+    if (rc != MRA_OK) return rc;  // the guard frees the output tree: *gout stays NULL
     G.g = nullptr;  // the caller owns the output from here
     *gout = g;
-    return rc;
+    return MRA_OK;
 }
 
 }  // namespace mra
@@ -1090,22 +1098,23 @@ int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, doubl
     if (precision == MRA_PREC_FP64) {
         aa.F = op->F;
         size_t smem = (size_t)k3 * sizeof(double) + (4 * (size_t)k3 + 3 * k * k) * sizeof(double);
-        k_apply_simt<double><<<std::min(n, 152 * 16), 128, smem, st>>>(aa);
+        k_apply_simt<double><<<std::min(n, num_sms() * 16), 128, smem, st>>>(aa);
         MRA_CK_LAUNCH();
     } else {
         aa.F = op->F32;
         size_t smem = (size_t)k3 * sizeof(double) + (4 * (size_t)k3 + 3 * k * k) * sizeof(float);
-        k_apply_simt<float><<<std::min(n, 152 * 16), 128, smem, st>>>(aa);
+        k_apply_simt<float><<<std::min(n, num_sms() * 16), 128, smem, st>>>(aa);
         MRA_CK_LAUNCH();
     }
-    if (n_items_host) {
-        unsigned long long ni = 0;
-        MRA_CK(cudaMemcpyAsync(&ni, nitems, sizeof(ni), cudaMemcpyDeviceToHost, st));
-        MRA_CK(cudaMemcpyAsync(herr, err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        MRA_CK(cudaStreamSynchronize(st));
-        *n_items_host = (int64_t)ni;
-        if (herr[0] || herr[1]) { set_error("screen/ghost error code %d/%d", herr[0], herr[1]); return MRA_ECUDA; }
-    }
+    // the device error words are always read back (a missed Step-2 lookup or a
+    // refinement without an ancestor leaf leaves ghat wrong); the item count only
+    // when asked for
+    unsigned long long ni = 0;
+    MRA_CK(cudaMemcpyAsync(&ni, nitems, sizeof(ni), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaMemcpyAsync(herr, err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaStreamSynchronize(st));
+    if (herr[0] || herr[1]) { set_error("screen/ghost error code %d/%d", herr[0], herr[1]); return MRA_ECUDA; }
+    if (n_items_host) *n_items_host = (int64_t)ni;
     return MRA_OK;
 }
 

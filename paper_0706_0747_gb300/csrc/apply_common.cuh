@@ -48,6 +48,8 @@ struct TcArgs {
     const double* lpb;     // per-tree error budget of one node for single-FP16 terms (NULL: all hi+lo)
     unsigned long long* n_lowp;  // items done with single FP16 operands (may be NULL)
     int* err;              // set to 4 when a completion wait reaches its limit
+    unsigned wait_limit;   // polls of one completion wait
+    int withhold;          // test hook: the first MMA group and its commit are not sent
     int* counter;          // work counter (zeroed by tc_launch)
     const int* order;      // node order (NULL: 0..nwork-1)
     int nwork;
@@ -111,7 +113,7 @@ int tc_launch(const TcArgs& T, int mc, int ctas_per_sm, cudaStream_t st);
 
 int launch_apply_fact(const ApplyArgs& A, int precision, cudaStream_t st);
 int launch_apply_tc(const ApplyArgs& A, int nghost, const mra_op* op, int* err, const double* lpb,
-                    unsigned long long* n_lowp, cudaStream_t st);
+                    unsigned long long* n_lowp, unsigned wait_limit, int withhold, cudaStream_t st);
 int lp_budget(const Forest& F, const ScreenOut& S, double eps, double* lpb, cudaStream_t st);
 int schedule_narrow(const mra_op* op, const Forest& F, const ScreenOut& S, const double* gblk, int mode,
                     const void* model, int margin, float* X_out, float* T_out, unsigned long long* counts,

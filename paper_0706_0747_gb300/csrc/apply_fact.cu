@@ -183,7 +183,7 @@ static int launch_k(const ApplyArgs& A, cudaStream_t st) {
                         4 * 216 * sizeof(int) + 36 * MC;
     auto fn = k_apply_fact<T, K, MC, NT>;
     MRA_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int nb = std::min(A.n, 152 * 8);
+    int nb = std::min(A.n, num_sms() * 8);
     fn<<<nb, NT, smem, st>>>(A);
     MRA_CK_LAUNCH();
     return MRA_OK;

@@ -10,8 +10,9 @@
 //             MMA M=64, N=8, K=16 (i2 as hi | lo), accumulated over the plane's lines in TMEM
 //   stage III per plane and term: Y_m[(c1,c2)][c3] += sum_i3 V_m F^{t3}[c3][i3]
 //             MMA M=64, N=8, K=16 (i3 as hi | lo), read out after each plane
-//   ghat_a += w_m Y_m: per plane, an FP32 sum over the chunk's terms, added to ghat
-//             kept as a pair of floats (TwoSum), so no FP64 arithmetic runs per item.
+//   ghat_a += w_m Y_m: per plane, an FP32 sum over the chunk's terms, summed in FP32
+//             over the chunk's planes; each chunk's sum is added to ghat in FP64 (one
+//             FP64 add per chunk and output coefficient, none per item).
 // Every operand is FP16 split into hi + lo (v ~= hi + lo to 2^-22), and each
 // product is hi*hi + hi*lo + lo*hi into an FP32 accumulator: three MMAs in
 // stage I; in stages II and III, whose contraction (8) fills half of an
@@ -41,7 +42,10 @@
 namespace mra {
 
 #define TC_THREADS 256
+// polls of one completion wait: the default, and the smallest accepted (far above the
+// time one group of MMAs takes)
 #define TC_WAIT_LIMIT (1u << 26)
+#define TC_WAIT_MIN 4096u
 // MMA-issuing threads (lane 0 of warps 0..TC_ISSUERS-1): warps 0-3 issue stages II and III
 // for a quarter of a chunk's terms each, warp 4 issues stage I; each commits to the mbarrier
 #define TC_ISSUERS 5
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
 #define TC_WAIT_OR_ABORT()                                                          \
     {                                                                               \
         bool ok_ = true;                                                            \
-        if (warp == 0) ok_ = tc::mbar_wait(&s_mbar, phase, TC_WAIT_LIMIT);          \
+        if (warp == 0) ok_ = tc::mbar_wait(&s_mbar, phase, T.wait_limit);           \
         phase ^= 1u;                                                                \
         if (__syncthreads_or(!ok_)) {                                               \
             aborted = true;                                                         \
@@ -335,11 +339,15 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
             const int in = tin[q];
             tg[q] = in == INT_MIN ? 0.0f : sx_node / T.sx[in >= 0 ? in : A.n + (-1 - in)];
         }
-        // ghat: (row rA + 8 s, column cA + h) at [2 s + h], as the unevaluated sum yh + yl of
-        // two floats (FP64 arithmetic is scarce on this part)
-        float yh[4], yl[4];
+        // ghat: (row rA + 8 s, column cA + h) at [2 s + h]: yc sums one chunk in FP32, yd
+        // the chunks in FP64
+        float yc[4];
+        double yd[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) yh[c] = yl[c] = 0.0f;
+        for (int c = 0; c < 4; ++c) {
+            yc[c] = 0.0f;
+            yd[c] = 0.0;
+        }
         unsigned my_items = 0;  // kept (item, term) pairs counted by this thread
         if (mhi >= mlo && xmax_node > 0.0f) {
             for (int m0 = mlo; m0 <= mhi && !aborted; m0 += MC) {
@@ -551,7 +559,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     }
                 };
                 // ghat += w_m Y_m from the TMEM block d: row (c1, c2), column c3; per plane an FP32
-                // sum over this warp half's terms, joined to ghat with its rounding error (TwoSum)
+                // sum over this warp half's terms, added to the chunk's FP32 sum
                 auto accumulate_y = [&](uint32_t d) {
                     float yv[MC / 2][4];
                     tc::tmem_ld16x256_rep<MC / 2>(d + lane_off + mc_lo * 8, yv);
@@ -564,11 +572,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                         for (int q = 0; q < 4; ++q) part[q] = fmaf(fin, v[q], part[q]);
                     }
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float sum = yh[q] + part[q], bv = sum - yh[q];
-                        yl[q] += (yh[q] - (sum - bv)) + (part[q] - bv);
-                        yh[q] = sum;
-                    }
+                    for (int q = 0; q < 4; ++q) yc[q] += part[q];
                 };
                 // Software pipeline over the chunk's lines: one wait and two block barriers per
                 // line.  While line L's stage I runs, stage II of the line before runs too; after
@@ -593,7 +597,9 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     if (nxt < 36) fetch_line(nxt, xb ^ 1);
                     tc::fence_async_smem();
                     __syncthreads();
-                    if (issuer) {
+                    // (test hook: with T.withhold nothing is sent, so the first wait can
+                    // only end by its limit, with no MMA in flight)
+                    if (issuer && !T.withhold) {
                         tc::fence_after();
                         if (warp == 4) issue_stage1(xb, dI);
                         tc::commit(&s_mbar);
@@ -719,6 +725,12 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
                     tc::cp_async_wait_all();
                 }
                 if (aborted) break;
+                // the chunk's sum joins ghat in FP64
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    yd[q] += (double)yc[q];
+                    yc[q] = 0.0f;
+                }
                 tc::fence_before();
                 __syncthreads();
             }
@@ -727,7 +739,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
         double* ysm = (double*)(sm + L::XH);  // every copy into the X buffers is complete here
         if (whalf == 1)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) ysm[(rA + 8 * (q >> 1)) * 8 + cA + (q & 1)] = (double)yh[q] + (double)yl[q];
+            for (int q = 0; q < 4; ++q) ysm[(rA + 8 * (q >> 1)) * 8 + cA + (q & 1)] = yd[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) my_items += __shfl_xor_sync(0xffffffffu, my_items, o);
         if (lane == 0 && my_items) atomicAdd(&s_items, (unsigned long long)my_items);
@@ -737,8 +749,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
             for (int q = 0; q < 4; ++q) {
                 const int r = rA + 8 * (q >> 1), c1 = r >> 3, c2 = r & 7, c3 = cA + (q & 1);
                 if (c1 < kr && c2 < kr && c3 < kr)
-                    A.out[(size_t)node * kr * kr * kr + (c1 * kr + c2) * kr + c3] =
-                        ((double)yh[q] + (double)yl[q]) + ysm[r * 8 + c3];
+                    A.out[(size_t)node * kr * kr * kr + (c1 * kr + c2) * kr + c3] = yd[q] + ysm[r * 8 + c3];
             }
         if (tid == 0 && A.n_items) atomicAdd(A.n_items + (A.node_tree ? A.node_tree[node] : 0), s_items);
         if (tid == 0 && T.n_lowp && s_lowi) atomicAdd(T.n_lowp, s_lowi);
@@ -776,7 +787,7 @@ int tc_prep_F(const mra_op* op, const TcBuffers& B, cudaStream_t st) {
 
 int tc_prep_blocks(int nb, int kr, int n, const double* s, const double* gblk, const TcBuffers& B, cudaStream_t st) {
     if (nb <= 0) return MRA_OK;
-    const int grid = std::max(1, std::min(152 * 8, (nb + PREP_WARPS - 1) / PREP_WARPS));
+    const int grid = std::max(1, std::min(num_sms() * 8, (nb + PREP_WARPS - 1) / PREP_WARPS));
     k_tc_prep_blocks<<<grid, 32 * PREP_WARPS, 0, st>>>(nb, kr, n, s, gblk, B.xh, B.xl, B.sx, B.xmax, B.xnrm);
     MRA_CK_LAUNCH();
     return MRA_OK;
@@ -804,7 +815,7 @@ int tc_configure() {
 
 template <int MC>
 static int launch_mc(const TcArgs& T, int ctas_per_sm, cudaStream_t st) {
-    const int grid = std::max(1, std::min(T.nwork, 152 * ctas_per_sm));
+    const int grid = std::max(1, std::min(T.nwork, num_sms() * ctas_per_sm));
     if (T.lpb) k_apply_tc<MC, true><<<grid, TC_THREADS, TcSmem<MC>::TOTAL, st>>>(T);
     else k_apply_tc<MC, false><<<grid, TC_THREADS, TcSmem<MC>::TOTAL, st>>>(T);
     MRA_CK_LAUNCH();
@@ -828,6 +839,8 @@ TcArgs tc_args(const ApplyArgs& A, const TcBuffers& B, int* err) {
     T.n_lowp = nullptr;
     T.Fh = B.Fh; T.Fl = B.Fl; T.sF = B.sF; T.maxF = B.maxF;
     T.err = err;  // the apply's error word: a wait that reaches its limit writes 4
+    T.wait_limit = TC_WAIT_LIMIT;
+    T.withhold = 0;
     T.counter = B.counter;
     T.order = nullptr;
     T.nwork = A.n;
@@ -836,22 +849,27 @@ TcArgs tc_args(const ApplyArgs& A, const TcBuffers& B, int* err) {
 }
 
 int launch_apply_tc(const ApplyArgs& A, int nghost, const mra_op* op, int* err, const double* lpb,
-                    unsigned long long* n_lowp, cudaStream_t st) {
+                    unsigned long long* n_lowp, unsigned wait_limit, int withhold, cudaStream_t st) {
     if (A.k > 8) {
         set_error("the tensor-core apply supports k <= 8 (got k = %d)", A.k);
         return MRA_EINVAL;
     }
-    TcBuffers B;
-    MRA_TRY(tc_alloc(op, A.n + nghost, &B));
-    MRA_TRY(tc_prep_F(op, B, st));
-    MRA_TRY(tc_prep_blocks(A.n + nghost, A.k, A.n, A.s, A.gblk, B, st));
+    // the operand buffers are released (stream-ordered, after the kernel) on every return
+    struct Guard {
+        const mra_op* op;
+        TcBuffers B;
+        ~Guard() { tc_release(op, &B); }
+    } G{op, TcBuffers()};
+    MRA_TRY(tc_alloc(op, A.n + nghost, &G.B));
+    MRA_TRY(tc_prep_F(op, G.B, st));
+    MRA_TRY(tc_prep_blocks(A.n + nghost, A.k, A.n, A.s, A.gblk, G.B, st));
     MRA_TRY(tc_configure());
-    TcArgs T = tc_args(A, B, err);
+    TcArgs T = tc_args(A, G.B, err);
     T.lpb = lpb;
     T.n_lowp = n_lowp;
-    MRA_TRY(tc_launch(T, 8, 3, st));
-    tc_release(op, &B);  // stream-ordered frees: released after the kernel completes
-    return MRA_OK;
+    T.wait_limit = wait_limit ? std::max(wait_limit, TC_WAIT_MIN) : TC_WAIT_LIMIT;
+    T.withhold = withhold;
+    return tc_launch(T, 8, 3, st);
 }
 
 }  // namespace mra

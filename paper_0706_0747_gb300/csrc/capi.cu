@@ -12,6 +12,25 @@ namespace mra {
 static thread_local char g_err[512] = "";
 static std::atomic<unsigned long long> g_launches(0);
 
+int num_sms() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    std::atomic<int>& c = cache[dev & 63];
+    int v = c.load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 1;
+        }
+        c.store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launch_add(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
@@ -262,6 +281,19 @@ int mra_free_tree(mra_tree* t) {
     t->magic = 0;
     delete t;
     return MRA_OK;
+}
+
+int mra_free(void* handle) {
+    if (!handle) return MRA_OK;
+    uint32_t tag;
+    memcpy(&tag, handle, sizeof(tag));  // every handle type starts with its tag
+    switch (tag) {
+        case MRA_TREE_MAGIC: return mra_free_tree((mra_tree*)handle);
+        case MRA_OP_MAGIC: return mra_free_op((mra_op*)handle);
+        case MRA_PLAN_MAGIC: return mra_free_plan((mra_plan*)handle);
+        case MRA_MLP_MAGIC: return mra_mlp_free((mra_mlp*)handle);
+        default: set_error("mra_free: not a live handle of this library"); return MRA_EINVAL;
+    }
 }
 
 int mra_free_op(mra_op* op) {

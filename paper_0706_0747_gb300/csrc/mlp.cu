@@ -22,7 +22,6 @@
 
 #include "mra_internal.cuh"
 
-#define MRA_MLP_MAGIC 0x4d4c5030u  // "MLP0"
 #define MLP_H 128
 #define MLP_RB 32  // rows per block
 
@@ -174,7 +173,7 @@ static const __half* w_trans(const mra_mlp* M, int l) {
 }
 
 static int refresh16(const mra_mlp* M, cudaStream_t st) {
-    k_refresh16<<<152, 256, 0, st>>>(w16_layout(M), M->master, M->w16);
+    k_refresh16<<<num_sms(), 256, 0, st>>>(w16_layout(M), M->master, M->w16);
     MRA_CK_LAUNCH();
     return MRA_OK;
 }
@@ -183,6 +182,10 @@ static int ensure_cap(mra_mlp* M, int64_t n) {
     if (n <= M->cap) return MRA_OK;
     const Alloc& A = M->A;
     A.put(M->h1); A.put(M->h2); A.put(M->h3); A.put(M->y); A.put(M->d3); A.put(M->d2); A.put(M->d1); A.put(M->dy);
+    // a failure below leaves no stale buffer behind (capacity 0, the rest NULL)
+    M->h1 = M->h2 = M->h3 = nullptr;
+    M->y = M->d3 = M->d2 = M->d1 = M->dy = nullptr;
+    M->cap = 0;
     int64_t c = std::max<int64_t>(n, 4096);
     MRA_TRY(dalloc(A, &M->h1, c * MLP_H));
     MRA_TRY(dalloc(A, &M->h2, c * MLP_H));
@@ -257,13 +260,12 @@ const mra_mlp* mlp_checked(const void* h) {
     return mlp_ok(M) ? M : nullptr;
 }
 int mlp_forward(const mra_mlp* M, const float* x, int64_t n, float* y, const Alloc& A, cudaStream_t st) {
+    Scratch tmp(A);
     __half *h1, *h2, *h3;
-    MRA_TRY(dalloc(A, &h1, (size_t)std::max<int64_t>(n, 1) * MLP_H));
-    MRA_TRY(dalloc(A, &h2, (size_t)std::max<int64_t>(n, 1) * MLP_H));
-    MRA_TRY(dalloc(A, &h3, (size_t)std::max<int64_t>(n, 1) * MLP_H));
-    const int rc = mlp_forward_impl(M, x, n, y, h1, h2, h3, st);
-    A.put(h1); A.put(h2); A.put(h3);
-    return rc;
+    MRA_TRY(tmp.get(&h1, (size_t)std::max<int64_t>(n, 1) * MLP_H));
+    MRA_TRY(tmp.get(&h2, (size_t)std::max<int64_t>(n, 1) * MLP_H));
+    MRA_TRY(tmp.get(&h3, (size_t)std::max<int64_t>(n, 1) * MLP_H));
+    return mlp_forward_impl(M, x, n, y, h1, h2, h3, st);
 }
 int mlp_n_in(const mra_mlp* M) { return M->n_in; }
 int mlp_n_out(const mra_mlp* M) { return M->n_out; }
@@ -393,7 +395,7 @@ int mra_mlp_train_step(mra_mlp* M, const float* x, const float* target, int64_t 
     MRA_TRY(mlp_loss_grad_impl(M, x, target, n, st));
     M->step++;
     const float c1 = (float)(1.0 - pow(0.9, M->step)), c2 = (float)(1.0 - pow(0.999, M->step));
-    k_adam<<<152, 256, 0, st>>>(M->np, M->master, M->grad, M->m, M->v, lr, c1, c2);
+    k_adam<<<num_sms(), 256, 0, st>>>(M->np, M->master, M->grad, M->m, M->v, lr, c1, c2);
     MRA_CK_LAUNCH();
     MRA_TRY(refresh16(M, st));
     if (loss_host) {

@@ -5,10 +5,15 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <vector>
+
 #include "../../include/mra_gb300.h"
 
+// every handle starts with one of these 32-bit tags (mra_free dispatches on it)
 #define MRA_TREE_MAGIC 0x54524545u  // "TREE"
 #define MRA_OP_MAGIC 0x4f504552u    // "OPER"
+#define MRA_PLAN_MAGIC 0x504c414eu  // "PLAN"
+#define MRA_MLP_MAGIC 0x4d4c5030u   // "MLP0"
 
 namespace mra {
 
@@ -24,6 +29,10 @@ void set_error(const char* fmt, ...);
             return MRA_ECUDA;                                                     \
         }                                                                         \
     } while (0)
+
+// streaming multiprocessors of the current device (queried once per device;
+// grids of persistent and grid-stride kernels are sized in multiples of it)
+int num_sms();
 
 // every kernel launch is followed by MRA_CK_LAUNCH(), which also counts it
 void count_launch();
@@ -58,6 +67,26 @@ inline int dalloc(const Alloc& A, T** p, size_t count) {
     }
     return MRA_OK;
 }
+
+// Temporary device memory of one call: every block taken through it is
+// released (stream-ordered) when the Scratch goes out of scope, on success
+// and on every error return.
+struct Scratch {
+    const Alloc& A;
+    std::vector<void*> p;
+    explicit Scratch(const Alloc& a) : A(a) {}
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+    template <class T>
+    int get(T** out, size_t count) {
+        const int rc = dalloc(A, out, count);
+        if (rc == MRA_OK) p.push_back((void*)*out);
+        return rc;
+    }
+    ~Scratch() {
+        for (size_t i = p.size(); i-- > 0;) A.put(p[i]);
+    }
+};
 
 // ---------------------------------------------------------------- handles
 struct TreeArrays {

@@ -320,9 +320,11 @@ int build_operator(mra_op* op, cudaStream_t st) {
     const Alloc& A = op->A;
     MRA_TRY(dalloc(A, &op->filt, 6 * k * k));
     MRA_TRY(dalloc(A, &op->scratch_i, 4));
-    double *w_tmp, *tau_tmp;
-    MRA_TRY(dalloc(A, &w_tmp, MRA_MAX_TERMS));
-    MRA_TRY(dalloc(A, &tau_tmp, MRA_MAX_TERMS));
+    // w and tau are allocated at their largest size and owned by op from here on
+    // (mra_free_op releases them on every error return of the caller)
+    MRA_TRY(dalloc(A, &op->w, MRA_MAX_TERMS));
+    MRA_TRY(dalloc(A, &op->tau, MRA_MAX_TERMS));
+    double *w_tmp = op->w, *tau_tmp = op->tau;
     MRA_TRY(launch_filters(k, op->filt, st));
     const double delta = op->eps / 10.0, R = sqrt(3.0);
     k_gauss_sum<<<1, 256, 0, st>>>(op->mu, op->alpha, op->eps, delta, R, w_tmp, tau_tmp, op->scratch_i);
@@ -331,15 +333,11 @@ int build_operator(mra_op* op, cudaStream_t st) {
     MRA_CK(cudaMemcpyAsync(&M, op->scratch_i, sizeof(int), cudaMemcpyDeviceToHost, st));
     MRA_CK(cudaStreamSynchronize(st));
     if (M <= 0) {
-        A.put(w_tmp);
-        A.put(tau_tmp);
         set_error("Gaussian-sum construction failed (code %d): more than %d terms or no convergence", M,
                   MRA_MAX_TERMS);
         return MRA_ECUDA;
     }
     op->M = M;
-    op->w = w_tmp;
-    op->tau = tau_tmp;
     const size_t nF = (size_t)(J + 1) * M * 7 * k * k;
     MRA_TRY(dalloc(A, &op->F, nF));
     MRA_TRY(dalloc(A, &op->F32, nF));

@@ -18,7 +18,6 @@
 
 #include "apply_common.cuh"
 
-#define MRA_PLAN_MAGIC 0x504c414eu  // "PLAN"
 
 namespace mra {
 
@@ -132,10 +131,11 @@ static int plan_tc_launch(const mra_plan* p, int mc, int ctas, int ordered, cuda
 static int plan_enqueue(const mra_plan* p, cudaStream_t st) {
     const int k3 = p->k * p->k * p->k;
     const size_t total = (size_t)p->n * k3;
-    const int nb = (int)std::max<size_t>(1, std::min<size_t>(152 * 8, (total + 255) / 256));
+    const int nb = (int)std::max<size_t>(1, std::min<size_t>(num_sms() * 8, (total + 255) / 256));
     k_forest_blocks<<<nb, 256, 0, st>>>(p->n, k3, p->dbase, p->node_tree, p->tref, p->s);
     MRA_CK_LAUNCH();
-    MRA_TRY(ghost_refine_forest(p->F, p->S, p->gblk, st, p->tc && p->screen_mode == MRA_SCREEN_STATIC));
+    MRA_TRY(ghost_refine_forest(p->F, p->S, p->gblk, st,
+                                p->precision == MRA_PREC_TC_FAST && p->screen_mode == MRA_SCREEN_STATIC));
     MRA_CK(cudaMemsetAsync(p->nitems, 0, ((size_t)p->ntrees + 1) * sizeof(unsigned long long), st));
     if (p->tc) {
         MRA_TRY(tc_prep_blocks(p->n + p->S.nghost, p->k, p->n, p->s, p->gblk, p->tcb, st));
@@ -194,11 +194,11 @@ static int plan_build(mra_plan* p, cudaStream_t st) {
     MRA_CK(cudaMemcpyAsync(p->dbase, p->base.data(), (nt + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     MRA_CK(cudaMemcpyAsync(p->off, p->off_host.data(), p->off_host.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     MRA_CK(cudaMemcpyAsync(p->nlev, p->nlev_host.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    const int nb = std::max(1, std::min(152 * 8, (n + 255) / 256));
+    const int nb = std::max(1, std::min(num_sms() * 8, (n + 255) / 256));
     k_forest_struct<<<nb, 256, 0, st>>>(n, nt, p->dbase, p->tref, p->coord, p->leaf, p->key, p->node_tree);
     MRA_CK_LAUNCH();
     const size_t total = (size_t)n * k3;
-    const int nbs = (int)std::max<size_t>(1, std::min<size_t>(152 * 8, (total + 255) / 256));
+    const int nbs = (int)std::max<size_t>(1, std::min<size_t>(num_sms() * 8, (total + 255) / 256));
     k_forest_blocks<<<nbs, 256, 0, st>>>(n, k3, p->dbase, p->node_tree, p->tref, p->s);
     MRA_CK_LAUNCH();
 
@@ -207,16 +207,20 @@ static int plan_build(mra_plan* p, cudaStream_t st) {
     F.coord = p->coord; F.leaf = p->leaf; F.key = p->key; F.off = p->off;
     F.node_tree = p->node_tree; F.nlev = p->nlev; F.s = p->s; F.filt = p->trees[0]->filt;
 
-    cudaEvent_t e0, e1;
-    MRA_CK(cudaEventCreate(&e0));
-    MRA_CK(cudaEventCreate(&e1));
-    MRA_CK(cudaEventRecord(e0, st));
+    struct Events {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    MRA_CK(cudaEventCreate(&ev.e[0]));
+    MRA_CK(cudaEventCreate(&ev.e[1]));
+    MRA_CK(cudaEventRecord(ev.e[0], st));
     MRA_TRY(screen_forest(op, F, 0, A, st, &p->S));
-    MRA_CK(cudaEventRecord(e1, st));
-    MRA_CK(cudaEventSynchronize(e1));
-    cudaEventElapsedTime(&p->ms_screen, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    MRA_CK(cudaEventRecord(ev.e[1], st));
+    MRA_CK(cudaEventSynchronize(ev.e[1]));
+    cudaEventElapsedTime(&p->ms_screen, ev.e[0], ev.e[1]);
 
     MRA_TRY(dalloc(A, &p->gblk, (size_t)(p->S.nghost + 1) * k3));
     if (p->screen_mode == MRA_SCREEN_PAIR) {
@@ -268,11 +272,12 @@ int mra_plan_create(const mra_op* op, mra_tree* const* trees, int ntrees, const 
     if (!op || op->magic != MRA_OP_MAGIC) { set_error("invalid operator handle"); return MRA_EINVAL; }
     if (!trees || ntrees < 1 || ntrees >= (1 << 22)) { set_error("ntrees must lie in [1, 2^22)"); return MRA_EINVAL; }
     const int prec = opts ? opts->precision : (op->k <= 8 ? MRA_PREC_TC_SPLIT : MRA_PREC_FP64);
-    if (prec != MRA_PREC_FP64 && prec != MRA_PREC_FP32 && prec != MRA_PREC_TC_SPLIT && prec != MRA_PREC_TC_LADDER) {
+    if (prec != MRA_PREC_FP64 && prec != MRA_PREC_FP32 && prec != MRA_PREC_TC_SPLIT && prec != MRA_PREC_TC_LADDER &&
+        prec != MRA_PREC_TC_FAST) {
         set_error("precision %d is not available", prec);
         return MRA_EINVAL;
     }
-    const bool tc = prec == MRA_PREC_TC_SPLIT || prec == MRA_PREC_TC_LADDER;
+    const bool tc = prec == MRA_PREC_TC_SPLIT || prec == MRA_PREC_TC_LADDER || prec == MRA_PREC_TC_FAST;
     if (tc && op->k > 8) { set_error("the tensor-core apply needs k <= 8"); return MRA_EINVAL; }
     long long total = 0;
     int lm = 0;
@@ -356,10 +361,11 @@ int mra_plan_autotune(mra_plan* p, int reps, void* stream) {
     // operands of the current blocks, then each variant timed on its own
     const int k3 = p->k * p->k * p->k;
     const size_t total = (size_t)p->n * k3;
-    const int nb = (int)std::max<size_t>(1, std::min<size_t>(152 * 8, (total + 255) / 256));
+    const int nb = (int)std::max<size_t>(1, std::min<size_t>(num_sms() * 8, (total + 255) / 256));
     k_forest_blocks<<<nb, 256, 0, st>>>(p->n, k3, p->dbase, p->node_tree, p->tref, p->s);
     MRA_CK_LAUNCH();
-    MRA_TRY(ghost_refine_forest(p->F, p->S, p->gblk, st, p->tc && p->screen_mode == MRA_SCREEN_STATIC));
+    MRA_TRY(ghost_refine_forest(p->F, p->S, p->gblk, st,
+                                p->precision == MRA_PREC_TC_FAST && p->screen_mode == MRA_SCREEN_STATIC));
     MRA_TRY(tc_prep_blocks(p->n + p->S.nghost, p->k, p->n, p->s, p->gblk, p->tcb, st));
     cudaEvent_t e0, e1;
     MRA_CK(cudaEventCreate(&e0));

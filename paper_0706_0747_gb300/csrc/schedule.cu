@@ -189,28 +189,29 @@ int schedule_narrow(const mra_op* op, const Forest& F, const ScreenOut& S, const
         if (!M) { set_error("the learned screen needs a network handle"); return MRA_EINVAL; }
         if (mlp_n_in(M) != 16 || mlp_n_out(M) != 12) { set_error("the schedule network must map 16 inputs to 12 outputs"); return MRA_EINVAL; }
     }
+    Scratch tmp(A);
     double *bn, *etab;
-    MRA_TRY(dalloc(A, &bn, (size_t)nb));
-    MRA_TRY(dalloc(A, &etab, (size_t)F.ntrees));
-    k_block_norms<<<std::max(1, std::min(152 * 16, (nb * 32 + 255) / 256)), 256, 0, st>>>(nb, n, k3, F.s, gblk, bn);
+    MRA_TRY(tmp.get(&bn, (size_t)nb));
+    MRA_TRY(tmp.get(&etab, (size_t)F.ntrees));
+    k_block_norms<<<std::max(1, std::min(num_sms() * 16, (nb * 32 + 255) / 256)), 256, 0, st>>>(nb, n, k3, F.s, gblk, bn);
     MRA_CK_LAUNCH();
     k_eta_blk<<<(F.ntrees + 127) / 128, 128, 0, st>>>(F, S.dv, op->eps, op->M, etab);
     MRA_CK_LAUNCH();
     float* X = X_out;
     float* Y = nullptr;
-    if (mode == 2 && !X) MRA_TRY(dalloc(A, &X, (size_t)n * 16));
+    if (mode == 2 && !X) MRA_TRY(tmp.get(&X, (size_t)n * 16));
     if (X) {
         k_sched_features<<<(n + 127) / 128, 128, 0, st>>>(F, S.pair_off, S.pairs, bn, etab, op->J, op->mu, X);
         MRA_CK_LAUNCH();
     }
     if (mode == 2) {
-        MRA_TRY(dalloc(A, &Y, (size_t)n * 12));
+        MRA_TRY(tmp.get(&Y, (size_t)n * 12));
         MRA_TRY(mlp_forward(M, X, n, Y, A, st));
     }
     int32_t *tlo = nullptr, *thi = nullptr;
     if (T_out) {
-        MRA_TRY(dalloc(A, &tlo, (size_t)n * 4));
-        MRA_TRY(dalloc(A, &thi, (size_t)n * 4));
+        MRA_TRY(tmp.get(&tlo, (size_t)n * 4));
+        MRA_TRY(tmp.get(&thi, (size_t)n * 4));
         k_fill_i32v<<<(n * 4 + 255) / 256, 256, 0, st>>>(tlo, n * 4, EMPTY_LO);
         MRA_CK_LAUNCH();
         k_fill_i32v<<<(n * 4 + 255) / 256, 256, 0, st>>>(thi, n * 4, -1);
@@ -228,8 +229,6 @@ int schedule_narrow(const mra_op* op, const Forest& F, const ScreenOut& S, const
         k_targets<<<(n + 127) / 128, 128, 0, st>>>(n, op->M, tlo, thi, T_out);
         MRA_CK_LAUNCH();
     }
-    A.put(bn); A.put(etab); A.put(Y); A.put(tlo); A.put(thi);
-    if (X != X_out) A.put(X);
     return MRA_OK;
 }
 
@@ -241,9 +240,10 @@ int screen_data_impl(const mra_op* op, const mra_tree* f, float* X, float* T, cu
     const Alloc& A = f->A;
     const Forest F = forest_of_tree(f);
     ScreenOut S;
+    Scratch tmp(A);
     int rc = screen_forest(op, F, 0, A, st, &S);
     double* gblk = nullptr;
-    if (rc == MRA_OK) rc = dalloc(A, &gblk, (size_t)(S.nghost + 1) * k3);
+    if (rc == MRA_OK) rc = tmp.get(&gblk, (size_t)(S.nghost + 1) * k3);
     if (rc == MRA_OK) rc = ghost_refine_forest(F, S, gblk, st);
     if (rc == MRA_OK) rc = schedule_narrow(op, F, S, gblk, 1, nullptr, 0, X, T, nullptr, A, st);
     if (rc == MRA_OK) {
@@ -254,7 +254,6 @@ int screen_data_impl(const mra_op* op, const mra_tree* f, float* X, float* T, cu
         else if (herr[0] || herr[1]) { set_error("screen/Step-2 error code %d/%d", herr[0], herr[1]); rc = MRA_ECUDA; }
     }
     screen_release(A, &S);
-    A.put(gblk);
     return rc;
 }
 

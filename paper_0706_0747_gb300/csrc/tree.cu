@@ -362,8 +362,9 @@ int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int 
     cudaStream_t st = A.stream;
     const int k3 = k * k * k;
     const int ng = f->n;
+    Scratch tmp(A);  // everything but the tree itself
     double* dd;
-    MRA_TRY(dalloc(A, &dd, 6 * (size_t)ng + 1));
+    MRA_TRY(tmp.get(&dd, 6 * (size_t)ng + 1));
     {
         std::vector<double> h(6 * (size_t)ng + 1, 0.0);
         for (int g = 0; g < ng; ++g) {
@@ -378,8 +379,8 @@ int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int 
     DensDev D{ng, dd, dd + ng, dd + 2 * ng, dd + 3 * ng};
     double* tol;
     int32_t *flags;  // [0] depth_hit, [1] total
-    MRA_TRY(dalloc(A, &tol, 1));
-    MRA_TRY(dalloc(A, &flags, 4));
+    MRA_TRY(tmp.get(&tol, 1));
+    MRA_TRY(tmp.get(&flags, 4));
     MRA_CK(cudaMemsetAsync(flags, 0, 4 * sizeof(int32_t), st));
     k_dens_scale<<<1, 256, 0, st>>>(D, eps, tol);
     MRA_CK_LAUNCH();
@@ -391,7 +392,7 @@ int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int 
     };
     std::vector<Level> L;
     int32_t* boxes0;
-    MRA_TRY(dalloc(A, &boxes0, 3));
+    MRA_TRY(tmp.get(&boxes0, 3));
     MRA_CK(cudaMemsetAsync(boxes0, 0, 3 * sizeof(int32_t), st));
     int nb = 1;
     int32_t* cur = boxes0;
@@ -400,9 +401,9 @@ int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int 
     MRA_CK(cudaFuncSetAttribute(k_build_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int j = 0; j <= max_level; ++j) {
         Level lv{nb, cur, nullptr, nullptr, plocal_prev, nullptr};
-        MRA_TRY(dalloc(A, &lv.refine, nb));
-        MRA_TRY(dalloc(A, &lv.pos, nb));
-        MRA_TRY(dalloc(A, &lv.s, (size_t)nb * k3));
+        MRA_TRY(tmp.get(&lv.refine, nb));
+        MRA_TRY(tmp.get(&lv.pos, nb));
+        MRA_TRY(tmp.get(&lv.s, (size_t)nb * k3));
         int mode;
         if (uniform_level >= 0) mode = (j < uniform_level) ? 1 : 2;
         else mode = (j < init_level) ? 1 : 0;
@@ -416,8 +417,8 @@ int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int 
         L.push_back(lv);
         if (nref == 0) break;
         int32_t *next, *plocal;
-        MRA_TRY(dalloc(A, &next, 3 * 8 * (size_t)nref));
-        MRA_TRY(dalloc(A, &plocal, nref));
+        MRA_TRY(tmp.get(&next, 3 * 8 * (size_t)nref));
+        MRA_TRY(tmp.get(&plocal, nref));
         k_make_children<<<(nb + 255) / 256, 256, 0, st>>>(nb, cur, lv.refine, lv.pos, next, plocal);
         MRA_CK_LAUNCH();
         cur = next;
@@ -429,10 +430,16 @@ int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int 
     t->k = k;
     t->A = A;
     t->state = MRA_TREE_LEAVES;
+    // the new tree is freed on every error return below
+    struct TreeGuard {
+        mra_tree* t;
+        ~TreeGuard() {
+            if (t) mra_free_tree(t);
+        }
+    } tg{t};
     int n = 0;
     for (auto& lv : L) n += lv.n;
-    int rc = tree_alloc_arrays(t, n, true);
-    if (rc != MRA_OK) return rc;
+    MRA_TRY(tree_alloc_arrays(t, n, true));
     t->nlev = (int)L.size();
     int base = 0;
     for (int j = 0; j < MRA_MAX_LEVEL + 2; ++j) t->off[j] = n;
@@ -456,11 +463,7 @@ int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int 
     MRA_CK(cudaMemcpyAsync(&hit, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MRA_CK(cudaStreamSynchronize(st));
     t->depth_hit = hit;
-    for (auto& lv : L) {
-        A.put(lv.boxes); A.put(lv.refine); A.put(lv.pos); A.put(lv.s); A.put(lv.parent_local);
-    }
-    if (cur != L.back().boxes) A.put(cur);
-    A.put(dd); A.put(tol); A.put(flags);
+    tg.t = nullptr;
     *out = t;
     return hit ? MRA_EDEPTH : MRA_OK;
 }
@@ -897,12 +900,13 @@ __global__ void k_compact(int n, int k3, const int32_t* alive, const int32_t* ne
 
 int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host) {
     const int n = t->n, k3 = t->k * t->k * t->k;
+    Scratch tmpmem(t->A);
     double* dv;  // [0] ||g||^2, [1] thr^2, [2] removed^2
     int32_t *alive, *newidx, *total;
-    MRA_TRY(dalloc(t->A, &dv, 4));
-    MRA_TRY(dalloc(t->A, &alive, n));
-    MRA_TRY(dalloc(t->A, &newidx, n));
-    MRA_TRY(dalloc(t->A, &total, 1));
+    MRA_TRY(tmpmem.get(&dv, 4));
+    MRA_TRY(tmpmem.get(&alive, n));
+    MRA_TRY(tmpmem.get(&newidx, n));
+    MRA_TRY(tmpmem.get(&total, 1));
     MRA_CK(cudaMemsetAsync(dv, 0, 4 * sizeof(double), st));
     k_leaf_norm2<<<256, 256, 0, st>>>(n, k3, t->a.leaf, t->s, dv);
     MRA_CK_LAUNCH();
@@ -931,7 +935,11 @@ int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host
         tmp.k = t->k;
         tmp.A = t->A;
         tmp.filt = t->filt;
-        MRA_TRY(tree_alloc_arrays(&tmp, n2, true));
+        const int rc = tree_alloc_arrays(&tmp, n2, true);
+        if (rc != MRA_OK) {
+            tree_free_arrays(&tmp);
+            return rc;
+        }
         k_compact<<<n, 128, 0, st>>>(n, k3, alive, newidx, t->a, t->s, t->dnorm, tmp.a, tmp.s, tmp.dnorm);
         MRA_CK_LAUNCH();
         int off2[MRA_MAX_LEVEL + 2];
@@ -952,7 +960,6 @@ int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host
         tmp.filt = nullptr;
     }
     MRA_CK(cudaStreamSynchronize(st));
-    t->A.put(dv); t->A.put(alive); t->A.put(newidx); t->A.put(total);
     return MRA_OK;
 }
 

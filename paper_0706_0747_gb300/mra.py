@@ -15,7 +15,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmra_gb300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEPTH, ESTATE = 0, 1, 2, 3, 4, 5, 6
-PREC = {"fp64": 0, "fp32": 1, "tc": 2, "tc_ladder": 3}
+PREC = {"fp64": 0, "fp32": 1, "tc": 2, "tc_ladder": 3, "tc_fast": 4}
+TEST_WITHHOLD_MMA = 1
 TREE_LEAVES, TREE_REDUNDANT, TREE_NSFORM = 0, 1, 2
 MAX_LEVEL = 12
 
@@ -58,7 +59,8 @@ SCREEN = {"static": 0, "pair": 1, "learned": 2}
 class ApplyOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("block_screen", ctypes.c_int),
                 ("unscreened", ctypes.c_int), ("itemwise", ctypes.c_int), ("screen_mode", ctypes.c_int),
-                ("margin", ctypes.c_int), ("reserved", ctypes.c_int * 2), ("schedule", ctypes.c_void_p)]
+                ("margin", ctypes.c_int), ("wait_limit", ctypes.c_int), ("test_flags", ctypes.c_int),
+                ("schedule", ctypes.c_void_p)]
 
 
 class ApplyStats(ctypes.Structure):
@@ -132,6 +134,7 @@ SIGNATURES = {
     "mra_mlp_train_step": [_P, _P, _P, ctypes.c_int64, ctypes.c_float, _P, _DP],
     "mra_mlp_free": [_P],
     "mra_screen_data": [_P, _P, _P, _P, _P],
+    "mra_free": [_P],
     "mra_free_tree": [_P],
     "mra_free_op": [_P],
     "mra_last_error": [],
@@ -357,11 +360,13 @@ def make_operator(mu, alpha, eps, k, max_level, stream=None, allocator="torch"):
 
 
 def apply_ns(op, tree, precision="fp64", block_screen=False, unscreened=False, itemwise=False, stream=None,
-             stats=True, screen="static", schedule=None, margin=2):
+             stats=True, screen="static", schedule=None, margin=2, wait_limit=0, test_flags=0):
     """mra_apply_ns.  screen: "static" (Sec. 4's ranges), "pair" (exact
     per-pair ranges) or "learned" (the network ``schedule``'s cut-offs, judged
-    by the exact test)."""
-    o = ApplyOpts(PREC[precision], int(block_screen), int(unscreened), int(itemwise), SCREEN[screen], int(margin))
+    by the exact test).  wait_limit / test_flags: the tensor-core apply's
+    bounded completion waits (0 = defaults)."""
+    o = ApplyOpts(PREC[precision], int(block_screen), int(unscreened), int(itemwise), SCREEN[screen], int(margin),
+                  int(wait_limit), int(test_flags))
     if schedule is not None:
         o.schedule = schedule.h
     st = ApplyStats()
@@ -521,7 +526,13 @@ def reconstruct(tree, mode="assemble", truncate=False, eps=0.0, stream=None):
 
 
 def free(handle):
-    handle.free()
+    """mra_free on a handle object (Tree, Operator, Plan, Mlp) or a raw
+    handle pointer; the object forgets its handle."""
+    h = getattr(handle, "h", handle)
+    if h:
+        _check(lib().mra_free(h))
+    if hasattr(handle, "h"):
+        handle.h = None
 
 
 def kernel_launches():

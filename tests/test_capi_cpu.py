@@ -28,7 +28,7 @@ def declared():
 def test_header_declares_entry_points():
     names = declared()
     for n in ["mra_build_tree", "mra_compress", "mra_make_operator", "mra_apply_ns", "mra_reconstruct",
-              "mra_free_tree", "mra_free_op"]:
+              "mra_free", "mra_free_tree", "mra_free_op"]:
         assert n in names
 
 
@@ -79,3 +79,12 @@ def test_batched_and_schedule_entries_reject_invalid_arguments(lib):
     assert lib.mra_mlp_create(16, 2000, None, 0, None, None, ctypes.byref(h)) == mra.EINVAL
     assert h.value is None
     assert lib.mra_free_plan(None) == mra.OK and lib.mra_mlp_free(None) == mra.OK
+
+
+def test_mra_free_dispatch_rejects_non_handles(lib):
+    """mra_free(NULL) is a no-op; memory that does not start with a handle tag
+    is refused with MRA_EINVAL (no device call is made)."""
+    assert lib.mra_free(None) == mra.OK
+    junk = ctypes.create_string_buffer(b"\x00" * 64)
+    assert lib.mra_free(ctypes.cast(junk, ctypes.c_void_p)) == mra.EINVAL
+    assert "not a live handle" in mra.last_error()

@@ -71,3 +71,50 @@ def test_noalloc_rejects_oversize_tree():
     with pytest.raises(mra.MraError) as e:
         mra.apply_ns_noalloc(op, tg, out.data_ptr())
     assert e.value.code == mra.EINVAL and "1024" in str(e.value)
+
+
+def test_noalloc_without_item_count(case):
+    """n_items_host is optional: with NULL the call still checks the device's
+    error words and writes the same output."""
+    import ctypes
+    k, eps, tg, op = case
+    n = tg.n
+    g, _ = mra.apply_ns(op, tg, precision="fp64")
+    ref = g.export()[2]
+    g.free()
+    out = torch.empty(n * k ** 3, dtype=torch.float64, device="cuda")
+    out.fill_(float("nan"))
+    rc = mra.lib().mra_apply_ns_noalloc(op.h, tg.h, mra.PREC["fp64"], out.data_ptr(),
+                                        torch.cuda.current_stream().cuda_stream, None)
+    assert rc == mra.OK, mra.last_error()
+    got = out.cpu().numpy().reshape(n, k, k, k)
+    assert rel_l2(got, ref) <= 1e-12
+
+
+def test_noalloc_rejects_too_many_refined_blocks(case):
+    """A tree within the node limit (825 nodes) whose Step 2 needs more than
+    4096 refined input blocks (5,725: four narrow Gaussians refined to level 7)
+    is refused after the screen with MRA_EINVAL; a valid call right after it
+    still matches mra_apply_ns."""
+    kk, e2 = 5, 1e-3
+    cens = [[0.37, 0.52, 0.61], [0.18, 0.81, 0.47], [0.62, 0.37, 0.21], [0.83, 0.66, 0.77]]
+    tree, _ = OT.build_tree(OT.Density([1.0] * 4, [1e4] * 4, cens), kk, e2, 8, init_level=1)
+    c, l, b = oracle_to_arrays(tree, kk)
+    tb = mra.tree_import(kk, c, l, b)
+    mra.compress(tb)
+    assert tb.n <= 1024
+    opb = mra.make_operator(0.0, 1.0, e2, kk, 8)
+    _, st = mra.apply_ns(opb, tb, precision="fp64")
+    assert st["n_ghosts"] > 4096
+    out = torch.empty(tb.n * kk ** 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(mra.MraError) as e:
+        mra.apply_ns_noalloc(opb, tb, out.data_ptr())
+    assert e.value.code == mra.EINVAL and "4096" in str(e.value)
+    k, eps, tg, op = case
+    g, st2 = mra.apply_ns(op, tg, precision="fp64")
+    ref = g.export()[2]
+    g.free()
+    out2 = torch.empty(tg.n * k ** 3, dtype=torch.float64, device="cuda")
+    items = mra.apply_ns_noalloc(op, tg, out2.data_ptr())
+    assert items == st2["n_items"]
+    assert rel_l2(out2.cpu().numpy().reshape(tg.n, k, k, k), ref) <= 1e-12
