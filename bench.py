@@ -321,6 +321,84 @@ def batched_section(K, Wu, flush, stream, peak_tensor, prec):
                          "note": "k = 6 runs on 8 x 8 tiles padded with zeros"}}
 
 
+# ---------------------------------------------------------------- learned + mixed + batched
+def learned_batched_section(K, Wu, flush, stream, n_per_mu=8):
+    """The three deployment forms together: the learned schedule (the trained
+    network, every miss restored by the exact test) with the tensor cores in
+    one batched, graph-capturable launch, on held-out densities of the
+    learned-schedule family (k = 8, eps = 1e-6, 16-128 Gaussians, seeds
+    7000 + i; the first n_per_mu Poisson and n_per_mu Helmholtz ones), against
+    the plain FP64 GPU apply of the same batch (static screen) and the
+    tensor-core batch with the static and the exact per-pair screens.  A step
+    is a fresh plan (screen at creation) + execute: new right-hand sides every
+    step.  Values count the plain-FP64-screen items of the batch."""
+    import numpy as np
+    import torch
+    from paper_0706_0747_gb300 import mra, schedule as SCH, workloads as W
+    net = SCH.load()
+    ops = SCH.operators()
+    picked = {0.0: [], 1.5: []}
+    i = 0
+    while min(len(v) for v in picked.values()) < n_per_mu:
+        mu, d = W.schedule_set(1, 2000 + i)[0]
+        if len(picked[mu]) < n_per_mu:
+            picked[mu].append((i, d))
+        i += 1
+    out = {"densities": {str(mu): [ix for ix, _ in v] for mu, v in picked.items()}, "groups": {}}
+    tot = {}
+    for mu, lst in picked.items():
+        trees = []
+        for _, d in lst:
+            t, _ = mra.build_tree(d, SCH.K, SCH.EPS, SCH.MAX_LEVEL, init_level=SCH.INIT_LEVEL)
+            mra.compress(t)
+            trees.append(t)
+        op = ops[mu]
+        grp = {"trees": len(trees), "nodes": int(sum(t.n for t in trees))}
+        outs = {}
+        for name, prec, kw, reps in (("fp64_static", "fp64", {}, 1), ("tc_static", "tc", {}, K),
+                                     ("tc_pair", "tc", {"screen": "pair"}, K),
+                                     ("tc_learned", "tc", {"screen": "learned", "schedule": net}, K)):
+            times = []
+            for it in range(1 + reps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                p = mra.plan_create(op, trees, precision=prec, use_graph=False, **kw)
+                p.execute()
+                e1.record(stream)
+                e1.synchronize()
+                if it > 0:
+                    times.append(e0.elapsed_time(e1))
+                info = p.info()
+                if it == reps:
+                    outs[name] = np.concatenate([p.output(b).export()[2].ravel() for b in range(len(trees))])
+                p.free()
+            grp[name] = {"ms_screen_and_execute": sum(times) / len(times), "items": int(info["n_items"]),
+                         "misses": int(info["n_misses"])}
+        plain = grp["fp64_static"]["items"]
+        ref = outs["fp64_static"]
+        for name in ("fp64_static", "tc_static", "tc_pair", "tc_learned"):
+            g = grp[name]
+            g["value"] = plain / (g["ms_screen_and_execute"] / 1e3)
+            g["rel_l2_vs_fp64_static"] = float(np.linalg.norm(outs[name] - ref) / np.linalg.norm(ref))
+            t = tot.setdefault(name, {"ms": 0.0, "items": 0, "misses": 0})
+            t["ms"] += g["ms_screen_and_execute"]
+            t["items"] += g["items"]
+            t["misses"] += g["misses"]
+        tot.setdefault("plain_items", 0)
+        tot["plain_items"] += plain
+        out["groups"][f"mu={mu}"] = grp
+        for t in trees:
+            t.free()
+    plain = tot.pop("plain_items")
+    out["total"] = {name: {"value": plain / (v["ms"] / 1e3), "ms": v["ms"], "items": v["items"],
+                           "misses": v["misses"]} for name, v in tot.items()}
+    out["learned_tc_batched_vs_fp64"] = out["total"]["tc_learned"]["value"] / out["total"]["fp64_static"]["value"]
+    out["unit"] = "block-applies/s (plain-FP64 static-screen item count)"
+    return out
+
+
 # ---------------------------------------------------------------- configs 1 and 3
 def _step_timer(mra, tree, op, eps, flush, stream, K, Wu, prec):
     import torch
@@ -434,6 +512,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-input batched section")
     ap.add_argument("--no-screens", action="store_true", help="skip the pair / learned screen section")
     ap.add_argument("--no-configs", action="store_true", help="skip the small-Poisson / Helmholtz section")
+    ap.add_argument("--no-learned-batched", action="store_true",
+                    help="skip the learned + tensor-core + batched section")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -636,6 +716,8 @@ def main():
         if not args.no_configs:
             line["configs"] = configs_section(K, Wu, flush, stream,
                                               prec if prec in ("tc", "tc_ladder", "tc_fast") else "tc")
+        if not args.no_learned_batched:
+            line["learned_batched"] = learned_batched_section(K, Wu, flush, stream)
         if not args.no_batched:
             line["batched"] = batched_section(K, Wu, flush, stream, pk["bf16_tflops"],
                                               prec if prec in ("tc", "tc_ladder") else "tc")

@@ -410,9 +410,15 @@ typedef struct mra_plan mra_plan;
 typedef struct {
     int precision;          /* MRA_PREC_*                                     */
     int use_graph;          /* 1: executes replay one captured CUDA graph      */
-    int screen_mode;        /* MRA_SCREEN_STATIC or MRA_SCREEN_PAIR (ranges    */
-                            /* narrowed at creation with the blocks then)     */
-    int reserved[5];
+    int screen_mode;        /* MRA_SCREEN_STATIC, MRA_SCREEN_PAIR or           */
+                            /* MRA_SCREEN_LEARNED (per-pair ranges narrowed at */
+                            /* creation with the blocks then; the learned      */
+                            /* screen's misses are found and restored by the   */
+                            /* exact test, per tree, as in mra_apply_ns)       */
+    int margin;             /* learned screen: terms added on each side        */
+    int reserved[4];
+    const mra_mlp* schedule;  /* learned screen: a 16 -> 12 network; it must   */
+                              /* outlive mra_plan_create only                 */
 } mra_plan_opts;
 
 typedef struct {
@@ -431,6 +437,10 @@ typedef struct {
     int graph_kernels;      /* kernels in one execute's graph                  */
     float ms_screen;        /* device time of the screen at creation           */
     int64_t n_items_lowp;   /* items of the last execute done with single FP16 */
+    int screen_mode;        /* MRA_SCREEN_* of the plan                        */
+    int64_t n_misses;       /* learned screen: passing items outside the       */
+                            /* network's ranges, restored at creation          */
+    int64_t n_pairs_empty;  /* pair / learned screens: pairs left with no term */
 } mra_plan_info;
 
 int mra_plan_create(const mra_op* op, mra_tree* const* trees, int ntrees, const mra_plan_opts* opts,

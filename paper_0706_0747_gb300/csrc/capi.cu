@@ -301,7 +301,7 @@ int mra_free_op(mra_op* op) {
     if (op->magic != MRA_OP_MAGIC) { set_error("invalid operator handle"); return MRA_EINVAL; }
     const Alloc& A = op->A;
     A.put(op->w); A.put(op->tau); A.put(op->F); A.put(op->F32); A.put(op->nF); A.put(op->est);
-    A.put(op->filt); A.put(op->scratch_i);
+    A.put(op->filt); A.put(op->scratch_i); A.put(op->rmq);
     op->magic = 0;
     delete op;
     return MRA_OK;

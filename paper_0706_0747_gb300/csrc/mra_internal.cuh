@@ -124,6 +124,10 @@ struct mra_op {
     double* est = nullptr;    // (J+1) M
     double* filt = nullptr;   // H0, H1, W
     int* scratch_i = nullptr; // device ints (status, M)
+    // per-pair screen tables (built on first use by a pair or learned screen):
+    // sparse-table range maxima over m of w_m N_F(t1) N_F(t2) N_F(t3) per (j, t)
+    double* rmq = nullptr;
+    int rmq_L = 0;
     mra::Alloc A;
 };
 

@@ -97,6 +97,9 @@ struct mra_plan {
     // graph
     int use_graph = 1;
     int screen_mode = MRA_SCREEN_STATIC;
+    const mra_mlp* schedule = nullptr;  // learned screen (used at creation only)
+    int margin = 0;
+    long long n_misses = 0, n_pairs_empty = 0;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -223,10 +226,21 @@ static int plan_build(mra_plan* p, cudaStream_t st) {
     cudaEventElapsedTime(&p->ms_screen, ev.e[0], ev.e[1]);
 
     MRA_TRY(dalloc(A, &p->gblk, (size_t)(p->S.nghost + 1) * k3));
-    if (p->screen_mode == MRA_SCREEN_PAIR) {
-        // exact per-pair term ranges from the blocks at creation (Step 2 first)
+    if (p->screen_mode != MRA_SCREEN_STATIC) {
+        // per-pair term ranges from the blocks at creation (Step 2 first): the exact
+        // screen, or the network's per-box ranges with every miss restored
+        Scratch tmp(A);
+        unsigned long long* counts;
+        MRA_TRY(tmp.get(&counts, 2));
+        MRA_CK(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st));
         MRA_TRY(ghost_refine_forest(F, p->S, p->gblk, st));
-        MRA_TRY(schedule_narrow(op, F, p->S, p->gblk, 1, nullptr, 0, nullptr, nullptr, nullptr, A, st));
+        MRA_TRY(schedule_narrow(op, F, p->S, p->gblk, p->screen_mode == MRA_SCREEN_PAIR ? 1 : 2, p->schedule,
+                                p->margin, nullptr, nullptr, counts, A, st));
+        unsigned long long hc[2] = {0, 0};
+        MRA_CK(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        MRA_CK(cudaStreamSynchronize(st));
+        p->n_misses = (long long)hc[0];
+        p->n_pairs_empty = (long long)hc[1];
     }
     MRA_TRY(dalloc(A, &p->out, (size_t)n * k3));
     MRA_TRY(dalloc(A, &p->nitems, (size_t)nt + 1));
@@ -303,8 +317,16 @@ int mra_plan_create(const mra_op* op, mra_tree* const* trees, int ntrees, const 
     p->tc = tc;
     p->use_graph = opts ? (opts->use_graph != 0) : 1;
     p->screen_mode = opts ? opts->screen_mode : MRA_SCREEN_STATIC;
-    if (p->screen_mode != MRA_SCREEN_STATIC && p->screen_mode != MRA_SCREEN_PAIR) {
-        set_error("the batched apply takes the static or the exact per-pair screen");
+    p->schedule = opts ? opts->schedule : nullptr;
+    p->margin = opts ? std::max(0, opts->margin) : 0;
+    if (p->screen_mode != MRA_SCREEN_STATIC && p->screen_mode != MRA_SCREEN_PAIR &&
+        p->screen_mode != MRA_SCREEN_LEARNED) {
+        set_error("screen mode %d is not available", p->screen_mode);
+        delete p;
+        return MRA_EINVAL;
+    }
+    if (p->screen_mode == MRA_SCREEN_LEARNED && !p->schedule) {
+        set_error("the learned screen needs a network handle (mra_plan_opts.schedule)");
         delete p;
         return MRA_EINVAL;
     }
@@ -456,6 +478,9 @@ int mra_plan_get_info(const mra_plan* p, mra_plan_info* info, void* stream) {
     info->graph = p->gexec != nullptr;
     info->graph_kernels = (int)p->graph_kernels;
     info->ms_screen = p->ms_screen;
+    info->screen_mode = p->screen_mode;
+    info->n_misses = p->n_misses;
+    info->n_pairs_empty = p->n_pairs_empty;
     if (herr[1] == 4) { set_error("tensor-core apply: an MMA completion wait reached its limit"); return MRA_ETIMEOUT; }
     if (herr[1] == 5) { set_error("tensor-core apply: an output scale is outside the FP32 range (use fp64)"); return MRA_EINVAL; }
     if (herr[0] || herr[1]) { set_error("screen/Step-2 error code %d/%d", herr[0], herr[1]); return MRA_ECUDA; }

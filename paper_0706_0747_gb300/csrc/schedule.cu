@@ -16,6 +16,8 @@
 // Every term of the static schedule inside the final range is applied.
 #include <math.h>
 
+#include <mutex>
+
 #include "apply_common.cuh"
 
 namespace mra {
@@ -83,6 +85,83 @@ __global__ void k_sched_features(Forest F, const int32_t* pair_off, const Pair* 
     }
 }
 
+// ---------------------------------------------------------------- range maxima
+// The exact test of a pair's term m is P(m) ||x_b|| > eta_blk with the
+// operator-only profile P(m) = ((w_m N_F(j,m,t1)) N_F(j,m,t2)) N_F(j,m,t3)
+// (the same product, in the same order, as the per-term test, so every
+// decision is bitwise the same).  Because x -> fl(x ||x_b||) is monotone,
+// some term of an interval passes exactly when the interval's maximum of P
+// does: a sparse table of range maxima per (j, t) answers that in O(1), and
+// the first / last passing term of an interval by binary search.
+#define RMQ_T 343  // translations t in [-3, 3]^3
+
+__host__ __device__ inline int rmq_levels(int M) {
+    int L = 1;
+    while ((1 << L) <= M) ++L;
+    return L;  // floor(log2 M) + 1
+}
+
+// block per (t, j): level 0 is P, level l the maximum of P over [m, m + 2^l)
+__global__ void k_rmq_build(int M, int L, const double* w, const double* nF, double* rmq) {
+    const int tc = blockIdx.x, j = blockIdx.y;
+    const int t1 = tc / 49 - 3, t2 = (tc / 7) % 7 - 3, t3 = tc % 7 - 3;
+    double* st = rmq + ((size_t)j * RMQ_T + tc) * L * M;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const double* r = nF + ((size_t)j * M + m) * 7;
+        st[m] = w[m] * r[t1 + 3] * r[t2 + 3] * r[t3 + 3];
+    }
+    __syncthreads();
+    for (int l = 1; l < L; ++l) {
+        const int h = 1 << (l - 1);
+        for (int m = threadIdx.x; m + 2 * h <= M; m += blockDim.x)
+            st[(size_t)l * M + m] = fmax(st[(size_t)(l - 1) * M + m], st[(size_t)(l - 1) * M + m + h]);
+        __syncthreads();
+    }
+}
+
+// built once per operator, on the first call that needs them (thread-safe)
+static int rmq_tables(const mra_op* op, cudaStream_t st, const double** out) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!op->rmq) {
+        mra_op* w = const_cast<mra_op*>(op);  // a cache: the operator's meaning is unchanged
+        const int L = rmq_levels(op->M);
+        double* t = nullptr;
+        MRA_TRY(dalloc(op->A, &t, (size_t)(op->J + 1) * RMQ_T * L * op->M));
+        k_rmq_build<<<dim3(RMQ_T, op->J + 1), 128, 0, st>>>(op->M, L, op->w, op->nF, t);
+        const cudaError_t e = cudaGetLastError();
+        count_launch();
+        if (e != cudaSuccess) {
+            op->A.put(t);
+            set_error("range-maximum tables: %s", cudaGetErrorString(e));
+            return MRA_ECUDA;
+        }
+        w->rmq = t;
+        w->rmq_L = L;
+    }
+    *out = op->rmq;
+    return MRA_OK;
+}
+
+struct Rmq {
+    const double* st;  // this pair's (j, t) table
+    int M;
+    __device__ double max(int a, int b) const {  // a <= b
+        const int l = 31 - __clz(b - a + 1);
+        return fmax(st[(size_t)l * M + a], st[(size_t)l * M + b - (1 << l) + 1]);
+    }
+};
+
+// J_m non-decreasing in m, per tree (then a pair's candidate terms form an interval)
+__global__ void k_jm_monotone(int ntrees, int M, const int32_t* sched, int sl, int32_t* mono) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ntrees; b += gridDim.x * blockDim.x) {
+        const int32_t* Jm = sched + (size_t)b * sl;
+        int ok = 1;
+        for (int m = 1; m < M && ok; ++m) ok = Jm[m] >= Jm[m - 1];
+        mono[b] = ok;
+    }
+}
+
 struct RangeArgs {
     Forest F;
     int M, sl, npairs, margin;
@@ -96,6 +175,9 @@ struct RangeArgs {
     int32_t* tlo;                 // [n][4] first / last passing term per class (NULL: not kept)
     int32_t* thi;
     unsigned long long* counts;   // [0] misses (passing items outside the prediction), [1] empty pairs
+    const double* rmq;            // range-maximum tables (rmq_L levels)
+    int rmq_L;
+    const int32_t* mono;          // [ntrees] J_m non-decreasing
 };
 
 // thread per pair: narrow its term range in place
@@ -109,6 +191,7 @@ __global__ void k_pair_ranges(RangeArgs R) {
     const double xn = R.bn[p.in >= 0 ? p.in : R.F.n + (-1 - p.in)];
     const double eta = R.etab[tree];
     const int S = pair_class(p);
+    const bool core_int = (p.flags & 1) != 0;
     // the prediction for this box and class
     int plo = 0, phi = -1;
     if (R.pred) {
@@ -120,19 +203,78 @@ __global__ void k_pair_ranges(RangeArgs R) {
         plo = max(plo, (int)p.m_lo);
         phi = min(phi, (int)p.m_hi);
     }
+    auto candidate = [&](int m) {
+        const int jm = Jm[m];
+        return jm >= j && !(core_int && jm > j);
+    };
+    auto passes_m = [&](int m) {
+        const size_t fb = ((size_t)j * R.M + m) * 7;
+        return R.w[m] * R.nF[fb + p.t1 + 3] * R.nF[fb + p.t2 + 3] * R.nF[fb + p.t3 + 3] * xn > eta;
+    };
     int first = EMPTY_LO, last = -1;
     unsigned long long miss = 0;
-    for (int m = p.m_lo; m <= p.m_hi; ++m) {
-        const int jm = Jm[m];
-        if (jm < j) continue;
-        if ((p.flags & 1) && jm > j) continue;
-        const size_t fb = ((size_t)j * R.M + m) * 7;
-        const double est = R.w[m] * R.nF[fb + p.t1 + 3] * R.nF[fb + p.t2 + 3] * R.nF[fb + p.t3 + 3] * xn;
-        if (est > eta) {
-            first = min(first, m);
-            last = m;
-            if (R.pred && (m < plo || m > phi)) ++miss;
+    bool need_exact = !R.pred || R.tlo || phi < plo;
+    if (R.mono[tree] && p.m_lo <= p.m_hi) {
+        // candidates: the interval [A, B] (J_m non-decreasing)
+        int A = p.m_lo, B = p.m_hi;
+        {  // first m with J_m >= j
+            int lo = 0, hi = R.M;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (Jm[mid] >= j) hi = mid;
+                else lo = mid + 1;
+            }
+            A = max(A, lo);
         }
+        if (core_int) {  // last m with J_m <= j
+            int lo = -1, hi = R.M - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (Jm[mid] <= j) lo = mid;
+                else hi = mid - 1;
+            }
+            B = min(B, lo);
+        }
+        const Rmq Q{R.rmq + ((size_t)j * RMQ_T + (p.t1 + 3) * 49 + (p.t2 + 3) * 7 + (p.t3 + 3)) * R.rmq_L * R.M, R.M};
+        auto any = [&](int lo, int hi) { return lo <= hi && Q.max(lo, hi) * xn > eta; };
+        if (R.pred && phi >= plo) {
+            // the judge: a passing term outside the prediction is a miss
+            const bool left = any(A, min(B, plo - 1)), right = any(max(A, phi + 1), B);
+            if (left || right) {
+                need_exact = true;
+                for (int m = A; m <= min(B, plo - 1); ++m) miss += passes_m(m);
+                for (int m = max(A, phi + 1); m <= B; ++m) miss += passes_m(m);
+            }
+        } else if (R.pred && any(A, B)) {
+            // predicted empty: every passing term is a miss
+            for (int m = A; m <= B; ++m) miss += passes_m(m);
+        }
+        if (need_exact && any(A, B)) {
+            int lo = A, hi = B;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (any(A, mid)) hi = mid;
+                else lo = mid + 1;
+            }
+            first = lo;
+            lo = A, hi = B;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (any(mid, B)) lo = mid;
+                else hi = mid - 1;
+            }
+            last = lo;
+        }
+    } else {
+        for (int m = p.m_lo; m <= p.m_hi; ++m) {
+            if (!candidate(m)) continue;
+            if (passes_m(m)) {
+                first = min(first, m);
+                last = m;
+                if (R.pred && (m < plo || m > phi)) ++miss;
+            }
+        }
+        need_exact = true;
     }
     if (R.tlo && last >= 0) {
         atomicMin(&R.tlo[a * 4 + S], first);
@@ -140,8 +282,9 @@ __global__ void k_pair_ranges(RangeArgs R) {
     }
     int lo = first, hi = last;
     if (R.pred && phi >= plo) {
-        lo = min(lo, plo);
-        hi = max(hi, phi);
+        // the prediction, extended to every passing term (first..last when a miss was found)
+        lo = need_exact ? min(lo, plo) : plo;
+        hi = need_exact ? max(hi, phi) : phi;
     }
     if (hi < lo) {
         lo = EMPTY_LO;
@@ -217,10 +360,17 @@ int schedule_narrow(const mra_op* op, const Forest& F, const ScreenOut& S, const
         k_fill_i32v<<<(n * 4 + 255) / 256, 256, 0, st>>>(thi, n * 4, -1);
         MRA_CK_LAUNCH();
     }
+    const double* rmq = nullptr;
+    MRA_TRY(rmq_tables(op, st, &rmq));
+    int32_t* mono;
+    MRA_TRY(tmp.get(&mono, (size_t)F.ntrees));
+    k_jm_monotone<<<(F.ntrees + 127) / 128, 128, 0, st>>>(F.ntrees, op->M, S.sched, S.sl, mono);
+    MRA_CK_LAUNCH();
     RangeArgs R;
     R.F = F; R.M = op->M; R.sl = S.sl; R.npairs = S.npairs; R.margin = margin;
     R.pairs = S.pairs; R.sched = S.sched; R.w = op->w; R.nF = op->nF; R.bn = bn; R.etab = etab;
     R.pred = Y; R.tlo = tlo; R.thi = thi; R.counts = counts;
+    R.rmq = rmq; R.rmq_L = op->rmq_L; R.mono = mono;
     if (S.npairs > 0) {
         k_pair_ranges<<<(S.npairs + 255) / 256, 256, 0, st>>>(R);
         MRA_CK_LAUNCH();

@@ -76,7 +76,7 @@ class ApplyStats(ctypes.Structure):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("screen_mode", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("margin", ctypes.c_int), ("reserved", ctypes.c_int * 4), ("schedule", ctypes.c_void_p)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -85,7 +85,8 @@ class PlanInfo(ctypes.Structure):
                 ("terms_per_chunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("heavy_first", ctypes.c_int),
                 ("tuned", ctypes.c_int), ("ms_variant", ctypes.c_float * 10), ("graph", ctypes.c_int),
                 ("graph_kernels", ctypes.c_int), ("ms_screen", ctypes.c_float),
-                ("n_items_lowp", ctypes.c_int64)]
+                ("n_items_lowp", ctypes.c_int64), ("screen_mode", ctypes.c_int), ("n_misses", ctypes.c_int64),
+                ("n_pairs_empty", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -430,15 +431,19 @@ class Plan:
             pass
 
 
-def plan_create(op, trees, precision=None, use_graph=True, stream=None, screen="static"):
+def plan_create(op, trees, precision=None, use_graph=True, stream=None, screen="static", schedule=None, margin=2):
     """mra_plan_create over compressed trees (all of op's order k); screen
-    "static" or "pair" (exact per-pair ranges fixed at creation)."""
+    "static", "pair" (exact per-pair ranges fixed at creation) or "learned"
+    (the network ``schedule``'s ranges, every miss restored at creation)."""
     arr = (_P * len(trees))(*[t.h for t in trees])
     opts = None
     if precision is not None or not use_graph or screen != "static":
         k = op.info().k
         prec = PREC[precision] if precision is not None else (PREC["tc"] if k <= 8 else PREC["fp64"])
-        opts = ctypes.byref(PlanOpts(prec, int(use_graph), SCREEN[screen]))
+        po = PlanOpts(prec, int(use_graph), SCREEN[screen], int(margin))
+        if schedule is not None:
+            po.schedule = schedule.h
+        opts = ctypes.byref(po)
     h = _P()
     _check(lib().mra_plan_create(op.h, arr, len(trees), opts, _stream(stream), ctypes.byref(h)))
     return Plan(h.value, op, trees)

@@ -269,3 +269,55 @@ def test_batch_pair_screen_matches_oracle(batch, precision):
         got = plan.tree_stats(b)["n_items"]
         assert abs(got - st_o["n_items"]) <= max(2, st_o["n_items"] // 100000)
         assert rel_l2(outs[b], ref) <= (1e-10 if precision == "fp64" else 10 * EPS)
+
+
+def _net(theta_tail=None, seed=None):
+    """A schedule network: constant outputs (zero weights, the given output
+    biases) or seeded random weights."""
+    from oracle import mlp as OM
+    n = sum(int(np.prod(s)) for s in OM.param_shapes(16))
+    if seed is not None:
+        rng = np.random.default_rng(seed)
+        theta = rng.normal(0.0, 0.05, n).astype(np.float32)
+        return mra.mlp_create(params=theta)
+    theta = np.zeros(n, dtype=np.float32)
+    theta[-12:] = np.tile(theta_tail, 4)
+    return mra.mlp_create(params=theta)
+
+
+def test_batch_learned_screen(batch):
+    """The learned screen inside the batched plan (learned + tensor cores +
+    one persistent graph-captured launch): per tree the same items, misses
+    and blocks as the single-tree learned apply with the same network; a
+    network predicting "empty" everywhere gives back the exact per-pair
+    screen (every passing item a miss, restored), one predicting every term
+    the static schedule."""
+    trees_o, op_o, op_g, ref = batch
+    tg = gpu_trees(trees_o)
+    for net, margin in ((_net(seed=11), 2), (_net(seed=12), 0)):
+        plan = mra.plan_create(op_g, tg, precision="tc", screen="learned", schedule=net, margin=margin)
+        plan.execute()
+        info = plan.info()
+        assert info["screen_mode"] == mra.SCREEN["learned"]
+        outs = outputs(plan, len(tg))
+        misses = 0
+        for b, t in enumerate(tg):
+            g, st = mra.apply_ns(op_g, t, precision="tc", screen="learned", schedule=net, margin=margin)
+            c, _, bl, _ = g.export()
+            assert plan.tree_stats(b)["n_items"] == st["n_items"]
+            misses += st["n_misses"]
+            assert rel_l2(outs[b], arrays_to_dict(c, bl)) <= 1e-14
+            assert rel_l2(outs[b], ref[b][0]) <= 10 * EPS
+        assert info["n_misses"] == misses
+    empty = mra.plan_create(op_g, tg, precision="tc", screen="learned", schedule=_net([10.0, 0.0, 0.0]), margin=0)
+    pair = mra.plan_create(op_g, tg, precision="tc", screen="pair")
+    empty.execute()
+    pair.execute()
+    assert empty.info()["n_items"] == pair.info()["n_items"] and empty.info()["n_misses"] > 0
+    for a, b in zip(outputs(empty, len(tg)), outputs(pair, len(tg))):
+        assert rel_l2(a, b) == 0.0
+    full = mra.plan_create(op_g, tg, precision="tc", screen="learned", schedule=_net([-10.0, 0.0, 1.0]), margin=0)
+    full.execute()
+    assert full.info()["n_items"] == sum(st["n_items"] for _, st in ref) and full.info()["n_misses"] == 0
+    with pytest.raises(mra.MraError):
+        mra.plan_create(op_g, tg, precision="tc", screen="learned")
