@@ -462,11 +462,11 @@ __global__ void k_ghost_reid(int ng, const uint64_t* gkeys, const uint64_t* tab,
     }
 }
 
-// out = Mat along dimension `dim` of the k^3 array x (Mat k x k, out[c] = sum_i Mat[c][i] x[i]);
-// KT > 0 fixes k at compile time.
-template <int KT, typename T>
-__device__ void mode_mul(int kdyn, const T* Mat, const T* x, T* out, int dim) {
-    const int k = KT ? KT : kdyn, k3 = k * k * k, kk = k * k;
+// out = Mat along dimension `dim` of the k^3 array x (Mat k x k, out[c] = sum_i Mat[c][i] x[i]),
+// generic k (row-major k^3 arrays, one output element per thread)
+template <typename T>
+__device__ void mode_mul(int k, const T* Mat, const T* x, T* out, int dim) {
+    const int k3 = k * k * k, kk = k * k;
     for (int idx = threadIdx.x; idx < k3; idx += blockDim.x) {
         const int i1 = idx / kk, i2 = (idx / k) % k, i3 = idx % k;
         const int c = dim == 0 ? i1 : (dim == 1 ? i2 : i3);
@@ -479,28 +479,63 @@ __device__ void mode_mul(int kdyn, const T* Mat, const T* x, T* out, int dim) {
     __syncthreads();
 }
 
+// The same for k = K fixed at compile time on (K, K, K) arrays whose innermost
+// extent is padded to K + 1 (so that fibers along it, one per thread, hit
+// distinct banks), for upper-triangular Mat: the refinement matrices H^(p)T and
+// their products vanish below the diagonal (H^(p)_{ia} = 0 for a > i, since
+// phi_i((u + p)/2) is a polynomial of degree i), so out[c] sums i >= c only.
+template <int K, typename T>
+__device__ __forceinline__ void mode_mul_tri(const T* Mat, const T* x, T* out, int dim) {
+    constexpr int P1 = K + 1, S0 = K * P1;
+    const int sf = dim == 0 ? S0 : (dim == 1 ? P1 : 1);             // along the fiber
+    const int sa = dim == 0 ? P1 : S0, sb = dim == 2 ? P1 : 1;        // the other two coordinates
+    for (int f = threadIdx.x; f < K * K; f += blockDim.x) {
+        const int a = f / K, b = f - a * K;
+        const T* src = x + a * sa + b * sb;
+        T v[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] = src[i * sf];
+        T* dst = out + a * sa + b * sb;
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            T acc = 0;
+#pragma unroll
+            for (int i = c; i < K; ++i) acc += Mat[c * K + i] * v[i];
+            dst[c * sf] = acc;
+        }
+    }
+    __syncthreads();
+}
+
 // Step 2 by sibling groups.  The ghost keys are sorted, so the children of one
 // parent box are consecutive; the block of a group's first ghost refines the
 // ancestor leaf to the parent (the path's per-direction two-scale matrices
 // multiplied first, then one three-mode product), then every child of the
 // group, sharing the direction-3 and direction-2 partial products among the
 // children (d = 0 half of eqs. recon_even / recon_odd).
-// T = double, or float where the blocks only feed FP16 hi/lo tensor-core operands
+// T = double, or float where the blocks only feed FP16 hi/lo tensor-core operands.
+// KT > 0: k fixed at compile time, padded arrays and triangular contractions.
 template <int KT, typename T>
 __global__ void k_ghost_refine_groups(Forest F, int ng, const uint64_t* gkeys, double* gblk, int32_t* err) {
     extern __shared__ double sm_raw[];
     T* sm = (T*)sm_raw;
     const int k = KT ? KT : F.k, k3 = k * k * k, kk = k * k;
+    const int bs = KT ? KT * KT * (KT + 1) : k3;  // one block's footprint in shared memory
     const int g0 = blockIdx.x;
     const uint64_t key0 = gkeys[g0];
     if (g0 > 0 && (gkeys[g0 - 1] >> 3) == (key0 >> 3)) return;  // not the first child of its group
     T* HT = sm;                // 2 k x k: HT[p][a][i] = H^(p)[i][a]
     T* P = HT + 2 * kk;        // 3 k x k: the path matrices per direction
     T* Q = P + 3 * kk;         // 3 k x k: scratch
-    T* x = Q + 3 * kk;         // k^3: the parent
-    T* y = x + k3;             // 2 k^3: direction 3 by p3
-    T* z = y + 2 * k3;         // 4 k^3: direction 2 by (p2, p3)
-    T* w = z + 4 * k3;         // k^3
+    T* x = Q + 3 * kk;         // 1 block: the parent
+    T* y = x + bs;             // 2 blocks: direction 3 by p3
+    T* z = y + 2 * bs;         // 4 blocks: direction 2 by (p2, p3)
+    T* w = z + 4 * bs;         // 1 block
+    auto at = [&](int e) { return KT ? (e / KT) * (KT + 1) + e % KT : e; };  // element e of a block
+    auto mm = [&](const T* Mat, const T* in, T* out, int dim) {
+        if (KT) mode_mul_tri<KT ? KT : 1, T>(Mat, in, out, dim);
+        else mode_mul<T>(k, Mat, in, out, dim);
+    };
     const int j = (int)(key0 >> 58);
     const int tree = (int)((key0 >> 36) & ((1ull << GH_TREE_BITS) - 1));
     const uint64_t mk = key0 & ((1ull << 36) - 1);
@@ -529,7 +564,7 @@ __global__ void k_ghost_refine_groups(Forest F, int ng, const uint64_t* gkeys, d
     }
     __syncthreads();
     if (anc < 0) return;
-    for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = (T)F.s[(size_t)anc * k3 + e];
+    for (int e = threadIdx.x; e < k3; e += blockDim.x) x[at(e)] = (T)F.s[(size_t)anc * k3 + e];
     if (jj < jp) {
         // P_d = H^(p_last)T ... H^(p_first)T along the path ancestor -> parent
         const int bd[3] = {b1, b2, b3};
@@ -550,21 +585,21 @@ __global__ void k_ghost_refine_groups(Forest F, int ng, const uint64_t* gkeys, d
             for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) P[e] = Q[e];
             __syncthreads();
         }
-        mode_mul<KT, T>(k, P + 2 * kk, x, y, 2);
-        mode_mul<KT, T>(k, P + kk, y, z, 1);
-        mode_mul<KT, T>(k, P, z, x, 0);
+        mm(P + 2 * kk, x, y, 2);
+        mm(P + kk, y, z, 1);
+        mm(P, z, x, 0);
     } else {
         __syncthreads();
     }
     // the children: direction 3 for p3 = 0, 1; direction 2 for (p2, p3); direction 1 per child
-    mode_mul<KT, T>(k, HT, x, y, 2);
-    mode_mul<KT, T>(k, HT + kk, x, y + k3, 2);
-    for (int q = 0; q < 4; ++q) mode_mul<KT, T>(k, HT + (q >> 1) * kk, y + (q & 1) * k3, z + q * k3, 1);
+    mm(HT, x, y, 2);
+    mm(HT + kk, x, y + bs, 2);
+    for (int q = 0; q < 4; ++q) mm(HT + (q >> 1) * kk, y + (q & 1) * bs, z + q * bs, 1);
     for (int g = 0; g < gn; ++g) {
         const uint64_t cm = gkeys[g0 + g] & 7ull;  // octant (p1 p2 p3) of the child
         const int p1 = (int)(cm >> 2) & 1, p23 = (int)(cm & 3);
-        mode_mul<KT, T>(k, HT + p1 * kk, z + p23 * k3, w, 0);
-        for (int e = threadIdx.x; e < k3; e += blockDim.x) gblk[(size_t)(g0 + g) * k3 + e] = (double)w[e];
+        mm(HT + p1 * kk, z + p23 * bs, w, 0);
+        for (int e = threadIdx.x; e < k3; e += blockDim.x) gblk[(size_t)(g0 + g) * k3 + e] = (double)w[at(e)];
         __syncthreads();
     }
 }
@@ -751,7 +786,7 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
 template <typename T>
 static int ghost_refine_launch(const Forest& F, const ScreenOut& S, double* gblk, cudaStream_t st) {
     const int k = F.k, k3 = k * k * k;
-    const size_t gsm = (8 * (size_t)k * k + 8 * (size_t)k3) * sizeof(T);
+    const size_t gsm = (8 * (size_t)k * k + 8 * (size_t)k * k * (k + 1)) * sizeof(T);  // padded blocks
     auto fn = k == 8 ? k_ghost_refine_groups<8, T> : (k == 6 ? k_ghost_refine_groups<6, T> :
                                                     (k == 4 ? k_ghost_refine_groups<4, T> : k_ghost_refine_groups<0, T>));
     MRA_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));

@@ -645,57 +645,113 @@ __global__ void k_compress_fast_level(int k, int lo, int hi, const int32_t* chil
     if (threadIdx.x == 0) dnorm[i] = sqrt(acc);
 }
 
-// The same two kernels with the order k fixed at compile time (the shapes of
-// every stage known, so the index arithmetic is by constants).
-template <int N0, int N1, int N2, int DIM, int NOUT>
-__device__ __forceinline__ void stage_t(const double* in, double* out, const double* Mat) {
-    constexpr int E0 = DIM == 0 ? NOUT : N0, E1 = DIM == 1 ? NOUT : N1, E2 = DIM == 2 ? NOUT : N2;
+// ---- triangular two-scale filters, one fiber per thread
+// H^(p)_{ia} = (1/sqrt 2) int_0^1 phi_i((u + p)/2) phi_a(u) du vanishes for a > i:
+// phi_i((u + p)/2) is a polynomial of degree i in u, and phi_a is orthogonal to
+// every polynomial of lower degree.  So D = [H0 | H1] (k x 2k, parent from
+// children) has in row i the columns a <= i of each half, and U = D^T (2k x k,
+// child from parent) has in row p k + a the columns i >= a: the mode products
+// below skip the structural zeros (k(k+1) multiply-adds per fiber instead of
+// 2k^2).  Each thread takes whole fibers along the contracted direction: it
+// loads the fiber's inputs into registers and writes all its outputs, so the
+// triangular loop bounds are compile-time constants and no warp diverges.
+// Shared-memory arrays keep their innermost extent padded to an odd number of
+// doubles, so that fibers along it (one per thread) hit distinct banks.
+enum { TRI_DENSE = 0, TRI_D = 1, TRI_U = 2 };
+
+// in: extents (N0, N1, N2), strides (IS0, IS1, 1); out: the same with NOUT along DIM,
+// strides (OS0, OS1, 1); Mat: NOUT x NIN row-major with structure TRI (KT = k)
+template <int N0, int N1, int N2, int IS0, int IS1, int DIM, int NOUT, int OS0, int OS1, int TRI, int KT>
+__device__ __forceinline__ void fiber_stage(const double* in, double* out, const double* Mat) {
     constexpr int NIN = DIM == 0 ? N0 : (DIM == 1 ? N1 : N2);
-    constexpr int S0 = N1 * N2, S1 = N2, ST = DIM == 0 ? S0 : (DIM == 1 ? S1 : 1);
-    for (int idx = threadIdx.x; idx < E0 * E1 * E2; idx += blockDim.x) {
-        const int x0 = idx / (E1 * E2), x1 = (idx / E2) % E1, x2 = idx % E2;
-        const int r = DIM == 0 ? x0 : (DIM == 1 ? x1 : x2);
-        const double* src = in + (DIM == 0 ? 0 : x0 * S0) + (DIM == 1 ? 0 : x1 * S1) + (DIM == 2 ? 0 : x2);
-        double acc = 0.0;
+    constexpr int IST = DIM == 0 ? IS0 : (DIM == 1 ? IS1 : 1);
+    constexpr int OST = DIM == 0 ? OS0 : (DIM == 1 ? OS1 : 1);
+    constexpr int FA = DIM == 0 ? N1 : N0, FB = DIM == 2 ? N1 : N2;  // the fiber's two other coordinates
+    constexpr int IA = DIM == 0 ? IS1 : IS0, IB = DIM == 2 ? IS1 : 1;
+    constexpr int OA = DIM == 0 ? OS1 : OS0, OB = DIM == 2 ? OS1 : 1;
+    for (int f = threadIdx.x; f < FA * FB; f += blockDim.x) {
+        const int a = f / FB, b = f - a * FB;
+        const double* src = in + a * IA + b * IB;
+        double v[NIN];
 #pragma unroll
-        for (int c = 0; c < NIN; ++c) acc += Mat[r * NIN + c] * src[c * ST];
-        out[idx] = acc;
+        for (int c = 0; c < NIN; ++c) v[c] = src[c * IST];
+        double* dst = out + a * OA + b * OB;
+#pragma unroll
+        for (int r = 0; r < NOUT; ++r) {
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < NIN; ++c) {
+                const bool nz = TRI == TRI_DENSE || (TRI == TRI_D && (c % KT) <= r) || (TRI == TRI_U && c >= r % KT);
+                if (nz) acc += Mat[r * NIN + c] * v[c];
+            }
+            dst[r * OST] = acc;
+        }
     }
     __syncthreads();
 }
 
 template <int K>
+struct TriSmem {
+    static constexpr int K2 = 2 * K, P2 = K2 + 1, P1 = K + 1;  // padded innermost extents
+    static constexpr int MATS = 4 * K * K;                   // U (2k x k) and D (k x 2k)
+    static constexpr int CUBE = K2 * K2 * P2;                // (2k, 2k, 2k)
+    static constexpr int RA = K * K2 * P2 > K2 * K * P1 ? K * K2 * P2 : K2 * K * P1;  // (k,2k,2k) | (2k,k,k)
+    static constexpr int RB = K * K * P2 > K2 * K2 * P1 ? K * K * P2 : K2 * K2 * P1;  // (k,k,2k) | (2k,2k,k)
+    static constexpr int SP = K * K * P1;                                            // (k, k, k)
+};
+
+// Assembly (eq. g_assemble) with d = 0: children += (U x U x U) s_parent.
+// Block per internal node of level j (nodes[lo..hi) of the level's list).
+template <int K>
 __global__ void k_up_level_t(int lo, int hi, const int32_t* child, double* s, const double* filt) {
-    constexpr int K2 = 2 * K, K3 = K * K * K;
+    using L = TriSmem<K>;
+    constexpr int K2 = 2 * K, K3 = K * K * K, P1 = L::P1;
     extern __shared__ double sm[];
     const int i = lo + blockIdx.x;
     if (i >= hi || child[i] < 0) return;
     const int c0 = child[i];
     double* U = sm;
     double* D = U + 2 * K * K;
-    double* x = D + 2 * K * K;  // K^3
-    double* t1 = x + K3;        // 2K^3
-    double* t2 = t1 + 2 * K3;   // 4K^3
+    double* x = D + 2 * K * K;  // (k, k, k), stride P1
+    double* t1 = x + L::SP;     // (2k, k, k)
+    double* t2 = t1 + L::RA;    // (2k, 2k, k)
     load_UD(K, filt, U, D);
-    for (int e = threadIdx.x; e < K3; e += blockDim.x) x[e] = s[(size_t)i * K3 + e];
+    for (int e = threadIdx.x; e < K3; e += blockDim.x) {
+        const int i1 = e / (K * K), i2 = (e / K) % K, i3 = e % K;
+        x[(i1 * K + i2) * P1 + i3] = s[(size_t)i * K3 + e];
+    }
     __syncthreads();
-    stage_t<K, K, K, 0, K2>(x, t1, U);
-    stage_t<K2, K, K, 1, K2>(t1, t2, U);
-    for (int idx = threadIdx.x; idx < 8 * K3; idx += blockDim.x) {
-        const int x1 = idx / (K2 * K2), x2 = (idx / K2) % K2, x3 = idx % K2;
-        const double* src = t2 + (x1 * K2 + x2) * K;
-        double acc = 0.0;
+    fiber_stage<K, K, K, K * P1, P1, 0, K2, K * P1, P1, TRI_U, K>(x, t1, U);
+    fiber_stage<K2, K, K, K * P1, P1, 1, K2, K2 * P1, P1, TRI_U, K>(t1, t2, U);
+    // direction 3 per fiber (x1, x2), added into the two children (p1 p2 0) and (p1 p2 1)
+    for (int f = threadIdx.x; f < K2 * K2; f += blockDim.x) {
+        const int x1 = f / K2, x2 = f % K2;
+        const double* src = t2 + (x1 * K2 + x2) * P1;
+        double v[K];
 #pragma unroll
-        for (int c = 0; c < K; ++c) acc += U[x3 * K + c] * src[c];
-        const int o = ((x1 / K) << 2) | ((x2 / K) << 1) | (x3 / K);
-        s[(size_t)(c0 + o) * K3 + ((x1 % K) * K + (x2 % K)) * K + (x3 % K)] += acc;
+        for (int c = 0; c < K; ++c) v[c] = src[c];
+        const int ob = ((x1 / K) << 2) | ((x2 / K) << 1);
+        const size_t base = ((size_t)(x1 % K) * K + (x2 % K)) * K;
+#pragma unroll
+        for (int r = 0; r < K2; ++r) {
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < K; ++c)
+                if (c >= r % K) acc += U[r * K + c] * v[c];
+            s[(size_t)(c0 + ob + r / K) * K3 + base + r % K] += acc;
+        }
     }
 }
 
+// Redundant tree without stored wavelet cubes: s_parent = (D x D x D) cube of the
+// children (eq. decomp_scaling), and the wavelet norm as ||cube - (U x U x U) s_parent||,
+// which equals ||d|| because the filter matrix is orthogonal (cube = W^T [s; d]).
+// Block per internal node of level j.
 template <int K>
 __global__ void k_compress_fast_level_t(int lo, int hi, const int32_t* child, double* s, double* dnorm,
                                         const double* filt) {
-    constexpr int K2 = 2 * K, K3 = K * K * K;
+    using L = TriSmem<K>;
+    constexpr int K2 = 2 * K, K3 = K * K * K, P1 = L::P1, P2 = L::P2;
     extern __shared__ double sm[];
     __shared__ double red[32];
     const int i = lo + blockIdx.x;
@@ -703,33 +759,44 @@ __global__ void k_compress_fast_level_t(int lo, int hi, const int32_t* child, do
     const int c0 = child[i];
     double* U = sm;
     double* D = U + 2 * K * K;
-    double* cube = D + 2 * K * K;  // 8K^3
-    double* r1 = cube + 8 * K3;    // 4K^3
-    double* r2 = r1 + 4 * K3;      // 2K^3
-    double* sp = r2 + 2 * K3;      // K^3
+    double* cube = D + 2 * K * K;  // (2k, 2k, 2k), stride P2
+    double* ra = cube + L::CUBE;
+    double* rb = ra + L::RA;
+    double* sp = rb + L::RB;       // (k, k, k), stride P1
     load_UD(K, filt, U, D);
     for (int e = threadIdx.x; e < 8 * K3; e += blockDim.x) {
         const int o = e / K3, r = e % K3;
         const int i1 = r / (K * K), i2 = (r / K) % K, i3 = r % K;
         const int x1 = ((o >> 2) & 1) * K + i1, x2 = ((o >> 1) & 1) * K + i2, x3 = (o & 1) * K + i3;
-        cube[(x1 * K2 + x2) * K2 + x3] = s[(size_t)(c0 + o) * K3 + r];
+        cube[(x1 * K2 + x2) * P2 + x3] = s[(size_t)(c0 + o) * K3 + r];
     }
     __syncthreads();
-    stage_t<K2, K2, K2, 0, K>(cube, r1, D);
-    stage_t<K, K2, K2, 1, K>(r1, r2, D);
-    stage_t<K, K, K2, 2, K>(r2, sp, D);
-    for (int e = threadIdx.x; e < K3; e += blockDim.x) s[(size_t)i * K3 + e] = sp[e];
-    stage_t<K, K, K, 0, K2>(sp, r2, U);
-    stage_t<K2, K, K, 1, K2>(r2, r1, U);
+    fiber_stage<K2, K2, K2, K2 * P2, P2, 0, K, K2 * P2, P2, TRI_D, K>(cube, ra, D);  // (k, 2k, 2k)
+    fiber_stage<K, K2, K2, K2 * P2, P2, 1, K, K * P2, P2, TRI_D, K>(ra, rb, D);      // (k, k, 2k)
+    fiber_stage<K, K, K2, K * P2, P2, 2, K, K * P1, P1, TRI_D, K>(rb, sp, D);        // (k, k, k)
+    for (int e = threadIdx.x; e < K3; e += blockDim.x) {
+        const int i1 = e / (K * K), i2 = (e / K) % K, i3 = e % K;
+        s[(size_t)i * K3 + e] = sp[(i1 * K + i2) * P1 + i3];
+    }
+    fiber_stage<K, K, K, K * P1, P1, 0, K2, K * P1, P1, TRI_U, K>(sp, ra, U);       // (2k, k, k)
+    fiber_stage<K2, K, K, K * P1, P1, 1, K2, K2 * P1, P1, TRI_U, K>(ra, rb, U);     // (2k, 2k, k)
     double acc = 0.0;
-    for (int idx = threadIdx.x; idx < 8 * K3; idx += blockDim.x) {
-        const int x1 = idx / (K2 * K2), x2 = (idx / K2) % K2, x3 = idx % K2;
-        const double* src = r1 + (x1 * K2 + x2) * K;
-        double up = 0.0;
+    for (int f = threadIdx.x; f < K2 * K2; f += blockDim.x) {
+        const int x1 = f / K2, x2 = f % K2;
+        const double* src = rb + (x1 * K2 + x2) * P1;
+        const double* cb = cube + (x1 * K2 + x2) * P2;
+        double v[K];
 #pragma unroll
-        for (int c = 0; c < K; ++c) up += U[x3 * K + c] * src[c];
-        const double dv = cube[idx] - up;
-        acc += dv * dv;
+        for (int c = 0; c < K; ++c) v[c] = src[c];
+#pragma unroll
+        for (int r = 0; r < K2; ++r) {
+            double up = 0.0;
+#pragma unroll
+            for (int c = 0; c < K; ++c)
+                if (c >= r % K) up += U[r * K + c] * v[c];
+            const double dv = cb[r] - up;
+            acc += dv * dv;
+        }
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) dnorm[i] = sqrt(acc);
@@ -737,7 +804,8 @@ __global__ void k_compress_fast_level_t(int lo, int hi, const int32_t* child, do
 
 template <int K>
 static int compress_fast_t(mra_tree* t, cudaStream_t st) {
-    const size_t smem = (4 * (size_t)K * K + 15 * (size_t)K * K * K) * sizeof(double);
+    using L = TriSmem<K>;
+    const size_t smem = (size_t)(L::MATS + L::CUBE + L::RA + L::RB + L::SP) * sizeof(double);
     MRA_CK(cudaFuncSetAttribute(k_compress_fast_level_t<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int j = t->nlev - 2; j >= 0; --j) {
         int lo = t->off[j], hi = t->off[j + 1];
@@ -750,7 +818,8 @@ static int compress_fast_t(mra_tree* t, cudaStream_t st) {
 
 template <int K>
 static int assemble_t(mra_tree* t, cudaStream_t st) {
-    const size_t smem = (4 * (size_t)K * K + 7 * (size_t)K * K * K) * sizeof(double);
+    using L = TriSmem<K>;
+    const size_t smem = (size_t)(L::MATS + L::SP + L::RA + L::RB) * sizeof(double);
     MRA_CK(cudaFuncSetAttribute(k_up_level_t<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int j = 0; j + 1 < t->nlev; ++j) {
         int lo = t->off[j], hi = t->off[j + 1];
