@@ -152,13 +152,35 @@ struct Rmq {
     }
 };
 
-// J_m non-decreasing in m, per tree (then a pair's candidate terms form an interval)
-__global__ void k_jm_monotone(int ntrees, int M, const int32_t* sched, int sl, int32_t* mono) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ntrees; b += gridDim.x * blockDim.x) {
-        const int32_t* Jm = sched + (size_t)b * sl;
-        int ok = 1;
-        for (int m = 1; m < M && ok; ++m) ok = Jm[m] >= Jm[m - 1];
-        mono[b] = ok;
+// A pair's candidate terms (those the static schedule keeps before the per-pair
+// test) are the terms m of its class range [m1, m2] with J_m >= j, or, for a core
+// translation at an internal node, J_m == j.  Per tree, level j and case ci the
+// set {m : J_m >= j} (ci = 0) or {m : J_m == j} (ci = 1) is written as at most
+// RUNS maximal runs of consecutive terms; a set with more runs is marked -1 and
+// its pairs fall back to testing every term.
+#define RUNS 4
+#define RUN_REC (1 + 2 * RUNS)  // count | (first, last) x RUNS
+
+__global__ void k_term_runs(int ntrees, int M, int lm, const int32_t* sched, int sl, int32_t* runs) {
+    const int b = blockIdx.x;
+    const int32_t* Jm = sched + (size_t)b * sl;
+    for (int e = threadIdx.x; e < lm * 2; e += blockDim.x) {
+        const int j = e >> 1, ci = e & 1;
+        int32_t* r = runs + ((size_t)b * lm * 2 + e) * RUN_REC;
+        int cnt = 0, start = -1;
+        for (int m = 0; m <= M; ++m) {
+            const bool in = m < M && (ci ? Jm[m] == j : Jm[m] >= j);
+            if (in && start < 0) start = m;
+            if (!in && start >= 0) {
+                if (cnt < RUNS) {
+                    r[1 + 2 * cnt] = start;
+                    r[2 + 2 * cnt] = m - 1;
+                }
+                ++cnt;
+                start = -1;
+            }
+        }
+        r[0] = cnt <= RUNS ? cnt : -1;
     }
 }
 
@@ -177,7 +199,7 @@ struct RangeArgs {
     unsigned long long* counts;   // [0] misses (passing items outside the prediction), [1] empty pairs
     const double* rmq;            // range-maximum tables (rmq_L levels)
     int rmq_L;
-    const int32_t* mono;          // [ntrees] J_m non-decreasing
+    const int32_t* runs;          // [ntrees][lm][2] candidate-term runs (k_term_runs)
 };
 
 // thread per pair: narrow its term range in place
@@ -214,57 +236,57 @@ __global__ void k_pair_ranges(RangeArgs R) {
     int first = EMPTY_LO, last = -1;
     unsigned long long miss = 0;
     bool need_exact = !R.pred || R.tlo || phi < plo;
-    if (R.mono[tree] && p.m_lo <= p.m_hi) {
-        // candidates: the interval [A, B] (J_m non-decreasing)
-        int A = p.m_lo, B = p.m_hi;
-        {  // first m with J_m >= j
-            int lo = 0, hi = R.M;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (Jm[mid] >= j) hi = mid;
-                else lo = mid + 1;
-            }
-            A = max(A, lo);
-        }
-        if (core_int) {  // last m with J_m <= j
-            int lo = -1, hi = R.M - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (Jm[mid] <= j) lo = mid;
-                else hi = mid - 1;
-            }
-            B = min(B, lo);
-        }
+    const int32_t* run = R.runs + (((size_t)tree * R.F.lm + j) * 2 + (core_int ? 1 : 0)) * RUN_REC;
+    const int nrun = run[0];
+    if (nrun >= 0) {
+        // candidates: the runs clipped to [m_lo, m_hi]; range maxima answer "does any pass"
         const Rmq Q{R.rmq + ((size_t)j * RMQ_T + (p.t1 + 3) * 49 + (p.t2 + 3) * 7 + (p.t3 + 3)) * R.rmq_L * R.M, R.M};
         auto any = [&](int lo, int hi) { return lo <= hi && Q.max(lo, hi) * xn > eta; };
-        if (R.pred && phi >= plo) {
-            // the judge: a passing term outside the prediction is a miss
-            const bool left = any(A, min(B, plo - 1)), right = any(max(A, phi + 1), B);
-            if (left || right) {
-                need_exact = true;
-                for (int m = A; m <= min(B, plo - 1); ++m) miss += passes_m(m);
-                for (int m = max(A, phi + 1); m <= B; ++m) miss += passes_m(m);
-            }
-        } else if (R.pred && any(A, B)) {
-            // predicted empty: every passing term is a miss
-            for (int m = A; m <= B; ++m) miss += passes_m(m);
-        }
-        if (need_exact && any(A, B)) {
+        // first / last passing term of [A, B] (one exists)
+        auto first_in = [&](int A, int B) {
             int lo = A, hi = B;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
                 if (any(A, mid)) hi = mid;
                 else lo = mid + 1;
             }
-            first = lo;
-            lo = A, hi = B;
+            return lo;
+        };
+        auto last_in = [&](int A, int B) {
+            int lo = A, hi = B;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (any(mid, B)) lo = mid;
                 else hi = mid - 1;
             }
-            last = lo;
+            return lo;
+        };
+        auto count_in = [&](int A, int B) {  // passing terms of [A, B] (only where a miss was found)
+            unsigned long long c = 0;
+            if (any(A, B))
+                for (int m = A; m <= B; ++m) c += passes_m(m);
+            return c;
+        };
+        const bool judged = R.pred && phi >= plo;
+        for (int q = 0; q < nrun; ++q) {
+            const int A = max((int)p.m_lo, run[1 + 2 * q]), B = min((int)p.m_hi, run[2 + 2 * q]);
+            if (A > B) continue;
+            if (judged) {
+                // the judge: a passing term outside the prediction is a miss
+                const unsigned long long ml = count_in(A, min(B, plo - 1)), mr = count_in(max(A, phi + 1), B);
+                if (ml + mr) need_exact = true;
+                miss += ml + mr;
+            } else if (R.pred) {
+                miss += count_in(A, B);  // predicted empty: every passing term is a miss
+            }
         }
+        if (need_exact)
+            for (int q = 0; q < nrun; ++q) {
+                const int A = max((int)p.m_lo, run[1 + 2 * q]), B = min((int)p.m_hi, run[2 + 2 * q]);
+                if (!any(A, B)) continue;
+                first = min(first, first_in(A, B));
+                last = max(last, last_in(A, B));
+            }
     } else {
         for (int m = p.m_lo; m <= p.m_hi; ++m) {
             if (!candidate(m)) continue;
@@ -362,15 +384,15 @@ int schedule_narrow(const mra_op* op, const Forest& F, const ScreenOut& S, const
     }
     const double* rmq = nullptr;
     MRA_TRY(rmq_tables(op, st, &rmq));
-    int32_t* mono;
-    MRA_TRY(tmp.get(&mono, (size_t)F.ntrees));
-    k_jm_monotone<<<(F.ntrees + 127) / 128, 128, 0, st>>>(F.ntrees, op->M, S.sched, S.sl, mono);
+    int32_t* runs;
+    MRA_TRY(tmp.get(&runs, (size_t)F.ntrees * F.lm * 2 * RUN_REC));
+    k_term_runs<<<F.ntrees, 64, 0, st>>>(F.ntrees, op->M, F.lm, S.sched, S.sl, runs);
     MRA_CK_LAUNCH();
     RangeArgs R;
     R.F = F; R.M = op->M; R.sl = S.sl; R.npairs = S.npairs; R.margin = margin;
     R.pairs = S.pairs; R.sched = S.sched; R.w = op->w; R.nF = op->nF; R.bn = bn; R.etab = etab;
     R.pred = Y; R.tlo = tlo; R.thi = thi; R.counts = counts;
-    R.rmq = rmq; R.rmq_L = op->rmq_L; R.mono = mono;
+    R.rmq = rmq; R.rmq_L = op->rmq_L; R.runs = runs;
     if (S.npairs > 0) {
         k_pair_ranges<<<(S.npairs + 255) / 256, 256, 0, st>>>(R);
         MRA_CK_LAUNCH();
