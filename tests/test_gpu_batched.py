@@ -166,14 +166,20 @@ def test_autotune_variants_agree(batch):
     assert info["tuned"] == 1
     assert all(ms > 0.0 for ms in info["ms_variant"])
     assert info["terms_per_chunk"] in (4, 8) and info["ctas_per_sm"] in (1, 2, 3, 4)
+    by_variant = {}
     for v in range(10):
         mc, ctas = [(8, 3), (8, 2), (4, 3), (4, 2), (4, 4)][v % 5]
         plan.set_variant(terms_per_chunk=mc, ctas_per_sm=ctas, heavy_first=v >= 5)
         plan.execute()
         outs = outputs(plan, len(tg))
+        by_variant[(mc, ctas, v >= 5)] = outs
         assert plan.info()["n_items"] == sum(st["n_items"] for _, st in ref)
         for b, (g_o, _) in enumerate(ref):
             assert rel_l2(outs[b], g_o) <= 10 * EPS
+    # the double-buffered pipeline (8 terms, two CTAs per SM) issues the same MMAs in the
+    # same order per accumulator as the single-buffered kernel: bit-identical blocks
+    for a, b in zip(by_variant[(8, 2, False)], by_variant[(8, 3, False)]):
+        assert all(np.array_equal(a[key], b[key]) for key in a)
 
 
 def test_plan_rejects_bad_inputs(batch):
