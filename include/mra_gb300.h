@@ -144,6 +144,28 @@ int mra_tree_device_arrays(const mra_tree* t, double** blocks, int32_t** leaf);
  * consistent with it. */
 int mra_tree_set_blocks(mra_tree* t, const double* blocks, void* stream);
 
+/* Output skeleton refinement.  The paper takes the output tree as a copy of
+ * the input's redundant tree and says the assumption will be removed later
+ * (Algorithm 2/3, Initialization); this entry removes it.  A potential is
+ * broader than its density, so the input tree, coarse wherever the density is
+ * negligible, is too coarse for the output near the sources.  One pass gives
+ * every leaf at level j < max_level whose 26-neighbourhood at level j holds an
+ * internal node its 8 children, filled with the exact two-scale refinement of
+ * the leaf's block (the d = 0 half of eqs. recon_even / recon_odd); `passes`
+ * passes are made (fewer if one splits nothing).  The function represented is
+ * unchanged: applying the operator to the refined tree gives the output on the
+ * graded skeleton, and the final truncation (mra_reconstruct) removes output
+ * blocks that are insignificant.
+ *   - f: a tree with leaf data (MRA_TREE_LEAVES or MRA_TREE_REDUNDANT); the
+ *     new tree has f's state (a split leaf keeps its block, which is the
+ *     projection its children refine, and a zero wavelet norm).
+ *   - n_split_host (optional): leaves split over all passes.
+ * Synchronous (the structure is built on the host).
+ * Errors: MRA_EINVAL for passes outside [0, 8] or max_level outside
+ * [0, MRA_MAX_LEVEL]; MRA_ESTATE for an ns-form tree. */
+int mra_tree_refine(const mra_tree* f, int passes, int max_level, void* stream, mra_tree** out,
+                    int* n_split_host);
+
 /* ------------------------------------------------------------------------ */
 /* Redundant tree (Sec. 2.2.1): bottom-up, each internal node receives
  * s^j = sum_p (H^(p1) x H^(p2) x H^(p3)) s^{j+1}_{child p} (eq. decomp_scaling)

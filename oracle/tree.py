@@ -280,3 +280,39 @@ def from_arrays(K, leaf, S):
     for row, lf, s in zip(np.asarray(K), np.asarray(leaf), np.asarray(S)):
         tree[tuple(int(v) for v in row)] = Node(bool(lf), np.array(s, dtype=np.float64))
     return tree
+
+
+def refine_graded(tree, k, passes=1, max_level=12):
+    """Output skeleton refinement (the paper copies the input skeleton for the
+    output and leaves the removal of that assumption for later, Algorithm 2/3,
+    Initialization).  Reading: one pass splits every leaf at level j <
+    max_level that has an internal node among the 26 boxes around it at level
+    j, each child receiving the exact refinement of the leaf's block
+    (``upsample``, the d = 0 half of eqs. recon_even / recon_odd); the split
+    leaf keeps its own block and a zero wavelet norm.  The function is
+    unchanged.  Returns (new tree, leaves split)."""
+    cur = copy_tree(tree)
+    total = 0
+    for _ in range(passes):
+        internal = {key for key, n in cur.items() if not n.leaf}
+        split = []
+        for key, n in cur.items():
+            j, a = key[0], key[1:]
+            if not n.leaf or j >= max_level:
+                continue
+            for dt in itertools.product((-1, 0, 1), repeat=3):
+                if dt == (0, 0, 0):
+                    continue
+                if (j,) + tuple(a[d] + dt[d] for d in range(3)) in internal:
+                    split.append(key)
+                    break
+        for key in split:
+            node = cur[key]
+            node.leaf = False
+            node.dnorm = 0.0
+            for p, ck in zip(OCTS, children(key)):
+                cur[ck] = Node(True, upsample(k, node.s, p))
+        total += len(split)
+        if not split:
+            break
+    return cur, total

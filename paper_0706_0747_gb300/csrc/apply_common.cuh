@@ -110,8 +110,8 @@ void tc_release(const mra_op* op, TcBuffers* B);
 int tc_configure();
 TcArgs tc_args(const ApplyArgs& A, const TcBuffers& B, int* err);
 int tc_launch(const TcArgs& T, int mc, int ctas_per_sm, cudaStream_t st);
-int tc2_configure();                               // apply_tc2.cu
-int tc2_launch(const TcArgs& T, cudaStream_t st);  // counter zeroed by the caller
+int tc3_configure();                               // apply_tc3.cu
+int tc3_launch(const TcArgs& T, cudaStream_t st);  // counter zeroed by the caller
 
 int launch_apply_fact(const ApplyArgs& A, int precision, cudaStream_t st);
 int launch_apply_tc(const ApplyArgs& A, int nghost, const mra_op* op, int* err, const double* lpb,

@@ -810,7 +810,7 @@ int tc_configure() {
     MRA_CK(cudaFuncSetAttribute(k_apply_tc<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<8>::TOTAL));
     MRA_CK(cudaFuncSetAttribute(k_apply_tc<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<4>::TOTAL));
     MRA_CK(cudaFuncSetAttribute(k_apply_tc<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<8>::TOTAL));
-    return tc2_configure();
+    return tc3_configure();
 }
 
 template <int MC>
@@ -824,13 +824,13 @@ static int launch_mc(const TcArgs& T, int ctas_per_sm, cudaStream_t st) {
 
 // variant: terms per chunk (4 or 8) and CTAs per SM (1 to 3 for 8 terms, 1 to 4
 // for 4 terms: registers, TMEM and shared memory allow that many); 8 terms at
-// two CTAs per SM is the double-buffered pipeline of apply_tc2.cu.
+// two CTAs per SM is the wide-MMA kernel of apply_tc3.cu.
 // tc_configure() first.
 int tc_launch(const TcArgs& T, int mc, int ctas_per_sm, cudaStream_t st) {
     MRA_CK(cudaMemsetAsync(T.counter, 0, sizeof(int), st));
     if (mc == 4) return launch_mc<4>(T, ctas_per_sm, st);
-    // 8 terms at two CTAs per SM: the double-buffered pipeline (apply_tc2.cu)
-    if (ctas_per_sm == 2) return tc2_launch(T, st);
+    // 8 terms at two CTAs per SM: the wide-MMA kernel (apply_tc3.cu)
+    if (ctas_per_sm == 2) return tc3_launch(T, st);
     return launch_mc<8>(T, ctas_per_sm, st);
 }
 

@@ -171,6 +171,17 @@ int mra_tree_set_blocks(mra_tree* t, const double* blocks, void* stream) {
     return MRA_OK;
 }
 
+int mra_tree_refine(const mra_tree* f, int passes, int max_level, void* stream, mra_tree** out,
+                    int* n_split_host) {
+    if (!out) { set_error("out is NULL"); return MRA_EINVAL; }
+    *out = nullptr;
+    if (!tree_ok(f)) { set_error("invalid tree handle"); return MRA_EINVAL; }
+    if (passes < 0 || passes > 8) { set_error("passes must lie in [0, 8]"); return MRA_EINVAL; }
+    if (max_level < 0 || max_level > MRA_MAX_LEVEL) { set_error("max_level outside [0, %d]", MRA_MAX_LEVEL); return MRA_EINVAL; }
+    if (f->state == MRA_TREE_NSFORM) { set_error("refine needs leaf data, not an ns-form tree"); return MRA_ESTATE; }
+    return refine_impl(f, passes, max_level, (cudaStream_t)stream, out, n_split_host);
+}
+
 int mra_compress(mra_tree* t, int store_d, void* stream) {
     if (!tree_ok(t)) { set_error("invalid tree handle"); return MRA_EINVAL; }
     if (t->state == MRA_TREE_NSFORM) { set_error("compress needs leaf data; assemble an ns-form tree first"); return MRA_ESTATE; }

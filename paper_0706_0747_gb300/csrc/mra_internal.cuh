@@ -149,6 +149,7 @@ int inverse_impl(mra_tree* t, cudaStream_t st);
 int assemble_impl(mra_tree* t, cudaStream_t st);
 int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host);
 int tree_clone_skeleton(const mra_tree* src, mra_tree** out);
+int refine_impl(const mra_tree* f, int passes, int max_level, cudaStream_t st, mra_tree** out, int* nsplit_total);
 
 // apply.cu
 int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cudaStream_t st,

@@ -39,17 +39,19 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
     asm volatile("fence.mbarrier_init.release.cluster;");
 }
 
-// Bounded wait for the given phase; returns false when the limit is reached.  Each
-// poll may suspend the thread for up to TC_POLL_NS nanoseconds (it resumes as soon
-// as the phase completes), so a waiting warp issues few instructions.
-#define TC_POLL_NS 1000u
+// Bounded wait for the given phase; returns false when the limit is reached.  A
+// poll that finds the phase incomplete puts the thread to sleep for TC_POLL_NS
+// nanoseconds before the next, so a waiting warp issues few instructions.
+#define TC_POLL_NS 32
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase, uint32_t limit) {
     uint32_t done = 0;
-    for (uint32_t it = 0; it < limit && !done; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(smem_u32(mbar)), "r"(phase), "r"(TC_POLL_NS));
+            : "r"(smem_u32(mbar)), "r"(phase));
+        if (done) break;
+        __nanosleep(TC_POLL_NS);
     }
     return done != 0;
 }

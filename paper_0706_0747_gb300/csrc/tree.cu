@@ -1033,3 +1033,193 @@ int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host
 }
 
 }  // namespace mra
+
+namespace mra {
+
+// ------------------------------------------------------------ output skeleton refinement
+// The paper takes the output tree as a copy of the input's redundant tree and
+// leaves the removal of that assumption for later (Algorithm 2/3,
+// Initialization).  A potential is broader than its density: Algorithm 1 keeps
+// the input tree coarse wherever the density is negligible, but there the
+// output still varies on the scale of its distance to the sources.  Refinement
+// pass (reading): every leaf at level j < max_level whose 26-neighbourhood at
+// level j holds an internal node gets its 8 children, with the exact
+// two-scale refinement of its block (the d = 0 half of eqs. recon_even /
+// recon_odd), so the function represented is unchanged and the split leaf
+// keeps its own block (its wavelet part is zero).  Applying the operator on
+// the refined tree gives the output on the graded skeleton; the final
+// truncation removes the output blocks that turn out to be insignificant.
+
+// block per node of the refined tree: copy of an old node's block, or the
+// refinement to octant (p1 p2 p3) of its parent's old block
+__global__ void k_refine_blocks(int k, int n, const int32_t* src, const int32_t* oct, const double* s_old,
+                                double* s_new, const double* filt) {
+    extern __shared__ double sm[];
+    const int k3 = k * k * k, kk = k * k;
+    double* HT = sm;          // 2 k x k: HT[p][a][i] = H^(p)[i][a]
+    double* x = HT + 2 * kk;  // k^3
+    double* y = x + k3;
+    for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) {
+        const int p = e / kk, r = e % kk, a = r / k, i = r % k;
+        HT[e] = filt[p * kk + i * k + a];
+    }
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const double* in = s_old + (size_t)src[i] * k3;
+        double* out = s_new + (size_t)i * k3;
+        const int o = oct[i];
+        if (o < 0) {
+            for (int e = threadIdx.x; e < k3; e += blockDim.x) out[e] = in[e];
+            continue;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = in[e];
+        __syncthreads();
+        // x <- (H^(p1)T x H^(p2)T x H^(p3)T) x, one direction at a time
+        for (int d = 2; d >= 0; --d) {
+            const int p = (o >> (2 - d)) & 1, st = d == 0 ? kk : (d == 1 ? k : 1);
+            const double* H = HT + p * kk;
+            for (int e = threadIdx.x; e < k3; e += blockDim.x) {
+                const int c = (e / st) % k;
+                const double* col = x + e - c * st;
+                double acc = 0.0;
+                for (int q = 0; q < k; ++q) acc += H[c * k + q] * col[q * st];
+                y[e] = acc;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = y[e];
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < k3; e += blockDim.x) out[e] = x[e];
+    }
+}
+
+// one refinement pass of t into a new tree (*out); *nsplit: leaves split
+static int refine_pass(const mra_tree* t, int max_level, cudaStream_t st, mra_tree** out, int* nsplit) {
+    *out = nullptr;
+    const int n = t->n, k = t->k, k3 = k * k * k;
+    std::vector<int32_t> coords(4 * (size_t)n), leaf(n);
+    MRA_CK(cudaMemcpyAsync(coords.data(), t->a.coord, coords.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaMemcpyAsync(leaf.data(), t->a.leaf, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaStreamSynchronize(st));
+    // internal boxes per level (keys sorted within a level, as the node order is)
+    std::vector<uint64_t> key(n);
+    for (int i = 0; i < n; ++i) key[i] = morton3(coords[4 * i + 1], coords[4 * i + 2], coords[4 * i + 3]);
+    auto internal_at = [&](int j, int b1, int b2, int b3) {
+        const int N = 1 << j;
+        if (b1 < 0 || b2 < 0 || b3 < 0 || b1 >= N || b2 >= N || b3 >= N) return false;
+        const uint64_t kk = morton3(b1, b2, b3);
+        const int lo = t->off[j], hi = t->off[j + 1];
+        const auto it = std::lower_bound(key.begin() + lo, key.begin() + hi, kk);
+        return it != key.begin() + hi && *it == kk && !leaf[it - key.begin()];
+    };
+    std::vector<char> split(n, 0);
+    int ns = 0;
+    for (int i = 0; i < n; ++i) {
+        const int j = coords[4 * i];
+        if (!leaf[i] || j >= max_level) continue;
+        bool found = false;
+        for (int d = 0; d < 27 && !found; ++d) {
+            if (d == 13) continue;
+            found = internal_at(j, coords[4 * i + 1] + d / 9 - 1, coords[4 * i + 2] + (d / 3) % 3 - 1,
+                                coords[4 * i + 3] + d % 3 - 1);
+        }
+        if (found) {
+            split[i] = 1;
+            ++ns;
+        }
+    }
+    *nsplit = ns;
+    // the new node list: every old node, and 8 children per split leaf; sorted by
+    // (level, Morton key) -- a child's key is its parent's key times 8 plus its octant
+    struct Rec {
+        int j;
+        uint64_t key;
+        int32_t src, oct, leaf;
+    };
+    std::vector<Rec> rec;
+    rec.reserve(n + 8 * (size_t)ns);
+    for (int i = 0; i < n; ++i) {
+        rec.push_back({coords[4 * i], key[i], i, -1, split[i] ? 0 : leaf[i]});
+        if (split[i])
+            for (int o = 0; o < 8; ++o) rec.push_back({coords[4 * i] + 1, (key[i] << 3) | (uint64_t)o, i, o, 1});
+    }
+    std::sort(rec.begin(), rec.end(), [](const Rec& a, const Rec& b) {
+        return a.j != b.j ? a.j < b.j : a.key < b.key;
+    });
+    const int n2 = (int)rec.size();
+    if (n2 >= (1 << 30) / 216) { set_error("refined tree too large (%d nodes)", n2); return MRA_EINVAL; }
+    std::vector<int32_t> c2(4 * (size_t)n2), l2(n2), src(n2), oct(n2);
+    for (int i = 0; i < n2; ++i) {
+        const Rec& r = rec[i];
+        c2[4 * i] = r.j;
+        if (r.oct < 0) {
+            for (int d = 1; d < 4; ++d) c2[4 * i + d] = coords[4 * r.src + d];
+        } else {
+            for (int d = 1; d < 4; ++d) c2[4 * i + d] = 2 * coords[4 * r.src + d] + ((r.oct >> (3 - d)) & 1);
+        }
+        l2[i] = r.leaf;
+        src[i] = r.src;
+        oct[i] = r.oct;
+    }
+    mra_tree* g = new mra_tree();
+    g->magic = MRA_TREE_MAGIC;
+    g->k = k;
+    g->A = t->A;
+    g->A.stream = st;
+    g->state = t->state;
+    g->depth_hit = t->depth_hit;
+    struct TreeGuard {
+        mra_tree* t;
+        ~TreeGuard() {
+            if (t) mra_free_tree(t);
+        }
+    } tg{g};
+    MRA_TRY(tree_alloc_arrays(g, n2, true));
+    MRA_TRY(tree_link_and_upload(g, c2.data(), l2.data()));
+    Scratch tmp(g->A);
+    int32_t *dsrc, *doct;
+    MRA_TRY(tmp.get(&dsrc, n2));
+    MRA_TRY(tmp.get(&doct, n2));
+    MRA_CK(cudaMemcpyAsync(dsrc, src.data(), n2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    MRA_CK(cudaMemcpyAsync(doct, oct.data(), n2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const size_t smem = (2 * (size_t)k * k + 2 * (size_t)k3) * sizeof(double);
+    k_refine_blocks<<<std::max(1, std::min(n2, num_sms() * 8)), 128, smem, st>>>(k, n2, dsrc, doct, t->s, g->s,
+                                                                                t->filt);
+    MRA_CK_LAUNCH();
+    // wavelet norms: old nodes keep theirs, split leaves have none (exact refinement)
+    std::vector<double> dn(n), dn2(n2, 0.0);
+    MRA_CK(cudaMemcpyAsync(dn.data(), t->dnorm, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < n2; ++i)
+        if (oct[i] < 0 && !split[src[i]]) dn2[i] = dn[src[i]];
+    MRA_CK(cudaMemcpyAsync(g->dnorm, dn2.data(), n2 * sizeof(double), cudaMemcpyHostToDevice, st));
+    MRA_CK(cudaStreamSynchronize(st));  // host vectors go out of scope
+    tg.t = nullptr;
+    *out = g;
+    return MRA_OK;
+}
+
+int refine_impl(const mra_tree* f, int passes, int max_level, cudaStream_t st, mra_tree** out, int* nsplit_total) {
+    *out = nullptr;
+    mra_tree* cur = nullptr;
+    int total = 0;
+    for (int p = 0; p < passes; ++p) {
+        mra_tree* next = nullptr;
+        int ns = 0;
+        const int rc = refine_pass(cur ? cur : f, max_level, st, &next, &ns);
+        if (cur) mra_free_tree(cur);
+        if (rc != MRA_OK) return rc;
+        cur = next;
+        total += ns;
+        if (ns == 0) break;
+    }
+    if (!cur) {  // no pass: a copy
+        int ns = 0;
+        MRA_TRY(refine_pass(f, -1, st, &cur, &ns));
+    }
+    if (nsplit_total) *nsplit_total = total;
+    *out = cur;
+    return MRA_OK;
+}
+
+}  // namespace mra

@@ -110,6 +110,7 @@ SIGNATURES = {
     "mra_tree_device_arrays": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)],
     "mra_tree_set_blocks": [_P, _P, _P],
     "mra_compress": [_P, ctypes.c_int, _P],
+    "mra_tree_refine": [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int)],
     "mra_make_operator": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                           ctypes.POINTER(Alloc), _P, ctypes.POINTER(_P)],
     "mra_op_get_info": [_P, ctypes.POINTER(OpInfo)],
@@ -347,6 +348,16 @@ def tree_import(k, coords, leaf, blocks, stream=None, allocator="torch"):
 def tree_set_blocks(tree, device_ptr, stream=None):
     """Overwrite the tree's blocks from device memory (n k^3 doubles)."""
     _check(lib().mra_tree_set_blocks(tree.h, device_ptr, _stream(stream)))
+
+
+def tree_refine(tree, passes=1, max_level=MAX_LEVEL, stream=None):
+    """mra_tree_refine: a new tree with the graded output skeleton (the same
+    function); returns (Tree, leaves split)."""
+    h = _P()
+    ns = ctypes.c_int(0)
+    _check(lib().mra_tree_refine(tree.h, int(passes), int(max_level), _stream(stream), ctypes.byref(h),
+                                 ctypes.byref(ns)))
+    return Tree(h.value), ns.value
 
 
 def compress(tree, store_d=False, stream=None):

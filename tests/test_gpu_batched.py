@@ -176,10 +176,11 @@ def test_autotune_variants_agree(batch):
         assert plan.info()["n_items"] == sum(st["n_items"] for _, st in ref)
         for b, (g_o, _) in enumerate(ref):
             assert rel_l2(outs[b], g_o) <= 10 * EPS
-    # the double-buffered pipeline (8 terms, two CTAs per SM) issues the same MMAs in the
-    # same order per accumulator as the single-buffered kernel: bit-identical blocks
+    # the wide-MMA kernel (8 terms, two CTAs per SM) sums the same split products in
+    # another order (and adds the lo*lo products of stages II and III): the same blocks
+    # to FP32 rounding
     for a, b in zip(by_variant[(8, 2, False)], by_variant[(8, 3, False)]):
-        assert all(np.array_equal(a[key], b[key]) for key in a)
+        assert rel_l2(a, b) <= 1e-6
 
 
 def test_plan_rejects_bad_inputs(batch):
