@@ -471,7 +471,68 @@ def configs_section(K, Wu, flush, stream, prec):
         out[name] = res
         tree.free()
         op.free()
+    out["poisson_k8_refined_skeleton"] = refined_skeleton_section(K, Wu, flush, stream, prec)
     return out
+
+
+def _eval_tree(coords, leaf, blocks, k, pts):
+    """The represented function at pts (host evaluation of the Legendre expansions
+    on the leaves containing them)."""
+    import numpy as np
+    from tests.closed_forms import legendre_scaled
+    index = {tuple(int(v) for v in c): i for i, c in enumerate(coords) if leaf[i]}
+    jmax = int(coords[:, 0].max())
+    out = np.zeros(len(pts))
+    for q, x in enumerate(pts):
+        for j in range(jmax + 1):
+            a = tuple(int(v) for v in np.minimum((x * 2 ** j).astype(int), 2 ** j - 1))
+            i = index.get((j,) + a)
+            if i is None:
+                continue
+            u = x * 2 ** j - np.array(a)
+            P = [legendre_scaled(k, u[d:d + 1])[:, 0] for d in range(3)]
+            out[q] = np.einsum("ijk,i,j,k->", blocks[i], P[0], P[1], P[2]) * 2.0 ** (1.5 * j)
+            break
+    return out
+
+
+def refined_skeleton_section(K, Wu, flush, stream, prec, n_pts=4000):
+    """The 3-D Poisson k = 8 workload with the output skeleton refined beyond the
+    input's (mra_tree_refine, one pass) against the paper's copied skeleton: output
+    tree sizes, the step time on each skeleton, and the output's error against the
+    closed-form potential sum_g erf(sqrt(a_g) r) / (4 pi r) at seeded sample points."""
+    import numpy as np
+    from scipy import special
+    from paper_0706_0747_gb300 import mra, workloads as W
+    cfg, dens = W.poisson_k8()
+    op = mra.make_operator(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
+    base, _ = mra.build_tree(dens, cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
+    pts = np.random.default_rng(2024).uniform(0.05, 0.95, (n_pts, 3))
+    exact = np.zeros(n_pts)
+    for a, c in zip(dens.expo, dens.centers):
+        r = np.linalg.norm(pts - c, axis=1)
+        exact += special.erf(np.sqrt(a) * r) / (4 * np.pi * r)
+    res = {"points": n_pts, "precision": prec}
+    for passes in (0, 1):
+        import time as _t
+        t0 = _t.perf_counter()
+        tree, nsplit = mra.tree_refine(base, passes=passes, max_level=cfg.max_level)
+        t_ref = _t.perf_counter() - t0
+        ms, ms_apply, st = _step_timer(mra, tree, op, cfg.eps, flush, stream, K, Wu, prec)
+        mra.compress(tree)
+        g, _ = mra.apply_ns(op, tree, precision=prec)
+        mra.reconstruct(g, mode="assemble", truncate=True, eps=cfg.eps)
+        c, l, b, _ = g.export()
+        got = _eval_tree(c, l, b, cfg.k, pts)
+        res[f"passes={passes}"] = {"input_nodes": tree.n, "leaves_split": nsplit, "output_nodes": g.n,
+                                  "ms_per_step": ms, "items": st["n_items"], "s_refine_host": t_ref,
+                                  "rel_l2_vs_closed_form": float(np.linalg.norm(got - exact) / np.linalg.norm(exact)),
+                                  "max_rel_err_vs_closed_form": float(np.max(np.abs(got - exact)) / np.max(np.abs(exact)))}
+        g.free()
+        tree.free()
+    base.free()
+    op.free()
+    return res
 
 
 # ---------------------------------------------------------------- replicas
@@ -623,9 +684,10 @@ def main():
         prec = args.precision
     ms, apl, st, nout, launches = runs[prec]
 
-    # the exact per-pair and the learned screens on the same input and path
-    # (reported beside the headline, which stays on the paper's static screen)
-    screens = {}
+    # the exact per-pair and the learned screens on the same input and path; the headline
+    # takes the faster exact screen (the paper's static one or the per-pair one) within the
+    # 10 eps gate, its value still counting the plain-FP64 static screen's items
+    screens, screen_runs = {}, {}
     if not args.no_screens and prec != "fp64":
         from paper_0706_0747_gb300 import schedule as SCH
         net = SCH.load()
@@ -636,6 +698,7 @@ def main():
             out = g.export()[2]
             g.free()
             r = timed(prec, K, Wu, **kw)
+            screen_runs[name] = r
             screens[name] = {"items": int(st_s["n_items"]), "misses": int(st_s["n_misses"]),
                              "ms_per_step": r[0] / K, "ms_apply_kernel": statistics.median(r[1]),
                              "value_plain_items": ws * items_plain * K / (r[0] / 1e3),
@@ -644,6 +707,13 @@ def main():
         screens["static"] = {"items": items_plain, "ms_per_step": ms / K,
                              "ms_apply_kernel": statistics.median(apl)}
         del ref64
+    screen = "static"
+    items_applied = st["n_items"]
+    if (args.precision == "auto" and "pair" in screens and screens["pair"]["rel_l2_vs_fp64_static"] <= 10 * cfg.eps
+            and screen_runs["pair"][0] < ms):
+        screen = "pair"
+        ms, apl, st, nout, launches = screen_runs["pair"]
+        items_applied = st["n_items"]
     table = {p: {"value": ws * items_plain * K / (r[0] / 1e3), "ms_per_step": r[0] / K,
                  "ms_apply_kernel": statistics.median(r[1]),
                  "rel_l2_vs_fp64": errs.get(p, 0.0), "items_single_fp16": lowp.get(p, 0)}
@@ -668,7 +738,7 @@ def main():
         t0 = time.perf_counter()
         t_in = mra.tree_import(k, coords, leaf, blocks)
         mra.compress(t_in)
-        g, _ = mra.apply_ns(op, t_in, precision=prec)
+        g, _ = mra.apply_ns(op, t_in, precision=prec, screen=screen)
         mra.reconstruct(g, mode="assemble", truncate=True, eps=cfg.eps)
         oc, ol, ob, od = g.export(out=outbuf)
         torch.cuda.synchronize()
@@ -683,7 +753,9 @@ def main():
     pk, pk_kind = peaks()
     flops_item = 6 * k ** 4
     ms_apply = statistics.median(apl)
-    achieved = items_plain * flops_item / (ms_apply / 1e3) / 1e12
+    # the kernel's own work: the items it applied (fewer than the plain count under the
+    # per-pair screen)
+    achieved = items_applied * flops_item / (ms_apply / 1e3) / 1e12
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     if prec in ("tc", "tc_ladder", "tc_fast"):
         # the kernel is timed inside a step of a few milliseconds: the burst peak
@@ -695,7 +767,8 @@ def main():
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": TRAFFIC_BYTES.get(prec), "traffic_unit": "bytes per launch (ncu)", "kernel": f"apply ({prec})", "peak_source": pk_kind if bound == "tensor" else
             "unit counts x 2070 MHz" if prec == "fp32" else "nominal FP64 rate of the part",
-            "flops_per_item": flops_item, "peak_kind": "burst" if bound == "tensor" else None}
+            "flops_per_item": flops_item, "items_per_launch": items_applied,
+            "peak_kind": "burst" if bound == "tensor" else None}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wu,
@@ -705,11 +778,15 @@ def main():
                           "tc_fast": "f16x2-split/f32acc/f64out, f32 Step 2"}[prec],
                 "data": "synthetic",
                 "config": {"workload": cfg.name, "k": k, "eps": cfg.eps, "M": op.info().M, "tree_nodes": n,
+                           "screen": screen,
                            "depth_hit": bool(hit), "precision": prec, "l2": "flushed (256 MB write) between steps",
                            "inputs": "64 unit-mass Gaussians, log10 a~U[2,5], centres~U[0.1,0.9]^3, seed 2000"},
                 "items_plain_fp64": items_plain, "pairs": st64["n_pairs"], "ghosts": st64["n_ghosts"],
                 "output_coeffs_per_s": coeffs, "fp64_value": value64, "speedup_vs_fp64_gpu": value / value64,
-                "ms_apply_kernel": ms_apply, "rel_l2_vs_fp64": errs.get(prec, 0.0), "precisions": table,
+                "ms_apply_kernel": ms_apply,
+                "rel_l2_vs_fp64": (screens[screen]["rel_l2_vs_fp64_static"] if screen != "static"
+                                   else errs.get(prec, 0.0)),
+                "items_applied": items_applied, "precisions": table,
                 "roofline": roof,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clocks, "screens": screens}
