@@ -68,6 +68,18 @@ def poisson_k8(instance=0, n_gauss=64):
     return cfg, unit_mass(expo, cen)
 
 
+def poisson_resolved(instance=0, n_gauss=16):
+    """3-D Poisson, k=8, eps=1e-6, adaptive to depth 7 with every density
+    resolved (no depth cap reached): 16 unit-mass Gaussians, log10 exponent
+    U[2, 3.5], centres U[0.2, 0.8]^3.  Used to compare the output on the input's
+    skeleton with the output on a refined one."""
+    rng = np.random.default_rng(1000 * 6 + instance)
+    expo = 10.0 ** rng.uniform(2.0, 3.5, n_gauss)
+    cen = rng.uniform(0.2, 0.8, (n_gauss, 3))
+    cfg = Config("poisson_resolved_k8_eps1e-6_adaptive7", 0.0, 1.0, 1e-6, 8, 7, init_level=2)
+    return cfg, unit_mass(expo, cen)
+
+
 def slater_fit(n_terms=5, zeta=2.0):
     """Least-squares fit of exp(-zeta r) by n_terms Gaussians (weights and
     exponents), on 400 log-spaced radii in [1e-3, 4]; exponents are kept as
