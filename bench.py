@@ -52,7 +52,7 @@ FP64_TFLOPS = 1.25
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # apply kernel on this workload, from one ncu capture of the current kernel
 # version; absent where no capture of the current kernel exists.
-TRAFFIC_BYTES = {}
+TRAFFIC_BYTES = {"tc/static": 140.571136e6, "tc/pair": 96.91648e6}
 
 
 class Clocks:
@@ -773,7 +773,7 @@ def main():
     else:
         peak, bound = FP64_TFLOPS, "alu"
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": TRAFFIC_BYTES.get(prec), "traffic_unit": "bytes per launch (ncu)", "kernel": f"apply ({prec})", "peak_source": pk_kind if bound == "tensor" else
+            "traffic": TRAFFIC_BYTES.get(f"{prec}/{screen}"), "traffic_unit": "bytes per launch (ncu)", "kernel": f"apply ({prec})", "peak_source": pk_kind if bound == "tensor" else
             "unit counts x 2070 MHz" if prec == "fp32" else "nominal FP64 rate of the part",
             "flops_per_item": flops_item, "items_per_launch": items_applied,
             "peak_kind": "burst" if bound == "tensor" else None}
