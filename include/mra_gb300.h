@@ -234,9 +234,9 @@ int mra_op_export(const mra_op* op, double* w_host, double* tau_host, double* F_
  * worklist).  When stats (host) is not NULL the call also waits for the apply,
  * fills stats and reads back the errors found on the device: MRA_ETIMEOUT
  * when a tensor-core completion wait gave up, MRA_EINVAL when a tensor-core
- * output scale w_m / (s_V s_F) falls outside FP32's range (use
- * MRA_PREC_FP64), MRA_ECUDA for a failed Step-2 lookup; with stats NULL these
- * are not checked. */
+ * output scale w_m / (s_V s_F) or an input value falls outside FP32's range
+ * (use MRA_PREC_FP64), MRA_ECUDA for a failed Step-2 lookup; with stats NULL
+ * these are not checked. */
 
 #define MRA_PREC_FP64     0   /* FP64 SIMT contractions                        */
 #define MRA_PREC_FP32     1   /* FP32 SIMT contractions, FP64 accumulation     */

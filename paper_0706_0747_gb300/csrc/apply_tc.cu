@@ -63,22 +63,22 @@ namespace mra {
 __global__ void __launch_bounds__(32 * PREP_WARPS) k_tc_prep_blocks(int nb, int kr, int n, const double* s,
                                                                   const double* gblk, __half* xh, __half* xl,
                                                                   float* sx, float* xmax, float* xnrm) {
-    // warp per block: coalesced FP64 reads into shared memory, then each lane
-    // writes the 8 values (i1 = 0..7) of two (i3, i2) rows as one 16-byte hi
-    // and one 16-byte lo store
-    __shared__ double xs[PREP_WARPS][512];
+    // warp per block: coalesced FP64 reads, each value rounded to FP32 once (the FP16
+    // hi/lo pair keeps 22 bits of it; FP32 keeps 24), then FP32 arithmetic only -- the
+    // part's FP64 rate is scarce; each lane writes the 8 values (i1 = 0..7) of two
+    // (i3, i2) rows as one 16-byte hi and one 16-byte lo store
+    __shared__ float xs[PREP_WARPS][512];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int k3 = kr * kr * kr;
-    double* x = xs[wl];
+    float* x = xs[wl];
     for (int b = blockIdx.x * PREP_WARPS + wl; b < nb; b += gridDim.x * PREP_WARPS) {
         const double* src = b < n ? s + (size_t)b * k3 : gblk + (size_t)(b - n) * k3;
-        double s2 = 0.0;
-        float m = 0.0f;
+        float s2 = 0.0f, m = 0.0f;
         for (int e = lane; e < k3; e += 32) {
-            const double v = src[e];
+            const float v = (float)src[e];
             x[e] = v;
-            m = fmaxf(m, (float)fabs(v));
-            s2 += v * v;
+            m = fmaxf(m, fabsf(v));
+            s2 = fmaf(v, v, s2);
         }
         for (int o = 16; o > 0; o >>= 1) {
             m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -90,8 +90,10 @@ __global__ void __launch_bounds__(32 * PREP_WARPS) k_tc_prep_blocks(int nb, int 
         // m * scale in [2^9, 2^13): the exponent is rounded up to a multiple of 4,
         // so that neighbouring blocks mostly share a scale (and the stage-I B
         // operand can be reused from line to line); blocks below 2^-100 keep the
-        // scale 2^113 (a finite float) and round to zero in FP16
-        const double scale = ldexp(1.0, 13 - ((max(e, -100) + 3) & ~3));
+        // scale 2^113 (a finite float) and round to zero in FP16.  Scaling by a
+        // power of two is exact.  (Values beyond FP32's range become infinite here;
+        // the apply refuses them as outside the FP32 range.)
+        const float scale = ldexpf(1.0f, 13 - ((max(e, -100) + 3) & ~3));
         for (int p = lane; p < 64; p += 32) {  // row (i3, i2) of the stage-I layout
             const int i3 = p >> 3, i2 = p & 7;
             uint4 h4, l4;
@@ -99,16 +101,16 @@ __global__ void __launch_bounds__(32 * PREP_WARPS) k_tc_prep_blocks(int nb, int 
             __half* ll = (__half*)&l4;
 #pragma unroll
             for (int i1 = 0; i1 < 8; ++i1) {
-                const double v = (i1 < kr && i2 < kr && i3 < kr) ? x[(i1 * kr + i2) * kr + i3] : 0.0;
-                tc::split_h((float)(v * scale), hh[i1], ll[i1]);
+                const float v = (i1 < kr && i2 < kr && i3 < kr) ? x[(i1 * kr + i2) * kr + i3] : 0.0f;
+                tc::split_h(v * scale, hh[i1], ll[i1]);
             }
             ((uint4*)(xh + (size_t)b * 512))[p] = h4;
             ((uint4*)(xl + (size_t)b * 512))[p] = l4;
         }
         if (lane == 0) {
-            sx[b] = (float)scale;
+            sx[b] = scale;
             xmax[b] = m;
-            xnrm[b] = (float)sqrt(s2);
+            xnrm[b] = sqrtf(s2);
         }
         __syncwarp();
     }
@@ -333,6 +335,8 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
         __syncthreads();
         const int mlo = s_mlo, mhi = s_mhi;
         const float xmax_node = __uint_as_float(s_xmax_bits);
+        // input values beyond FP32's range (infinite after the operand prep): refuse
+        if (!(xmax_node <= FLT_MAX) && tid == 0) atomicExch(T.err, 5);
         const float sx_node = ldexpf(1.0f, s_exp_min - 1);
         // the power-of-two ratio between the node's scale and each input block's
         for (int q = tid; q < 216; q += TC_THREADS) {
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(TC_THREADS, MC == 4 ? 4 : 3) k_apply_tc(TcArgs
             yd[c] = 0.0;
         }
         unsigned my_items = 0;  // kept (item, term) pairs counted by this thread
-        if (mhi >= mlo && xmax_node > 0.0f) {
+        if (mhi >= mlo && xmax_node > 0.0f && xmax_node <= FLT_MAX) {
             for (int m0 = mlo; m0 <= mhi && !aborted; m0 += MC) {
                 // the kept-t1 masks per line and the per-term scales of the chunk
                 const size_t fbase = ((size_t)j * A.M + m0) * 56;  // uint4 index of F(m0, t = -3)

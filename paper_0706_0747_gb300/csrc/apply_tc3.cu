@@ -218,6 +218,8 @@ __global__ void __launch_bounds__(TC3_THREADS, 2) k_apply_tc3(TcArgs T) {
         __syncthreads();
         const int mlo = s_mlo, mhi = s_mhi;
         const float xmax_node = __uint_as_float(s_xmax_bits);
+        // input values beyond FP32's range (infinite after the operand prep): refuse
+        if (!(xmax_node <= FLT_MAX) && tid == 0) atomicExch(T.err, 5);
         const float sx_node = ldexpf(1.0f, s_exp_min - 1);
         // the power-of-two ratio between the node's scale and each input block's
         for (int q = tid; q < 216; q += TC3_THREADS) {
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(TC3_THREADS, 2) k_apply_tc3(TcArgs T) {
             yd[c] = 0.0;
         }
         unsigned my_items = 0;  // kept (item, term) pairs counted by this thread
-        if (mhi >= mlo && xmax_node > 0.0f) {
+        if (mhi >= mlo && xmax_node > 0.0f && xmax_node <= FLT_MAX) {
             for (int m0 = mlo; m0 <= mhi && !aborted; m0 += MC) {
                 // the kept-t1 masks per line and the per-term scales of the chunk
                 const size_t fbase = ((size_t)j * A.M + m0) * 56;  // uint4 index of F(m0, t = -3)
