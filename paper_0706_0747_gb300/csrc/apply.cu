@@ -281,13 +281,18 @@ __device__ int ghost_find(const uint64_t* tab, uint32_t cap, uint64_t key) {
     return -1;
 }
 
+// The Step-2 set is keyed by the missing box's parent: slot -> parent key, an
+// 8-bit mask of the octants needed, and (after k_ghost_ids) the id of the
+// parent's first needed child.  A group's children get consecutive ids in
+// octant order, so no sort is needed to find siblings.
 struct ScreenArgs {
     Forest F;
     int M, sl;
     const int32_t* sched;  // per tree: Jm | m1 | m2 | cnt
     uint64_t* gtab;
     uint32_t gcap;
-    const int32_t* gid;    // slot -> ghost id (fill pass)
+    uint32_t* gmask;       // slot -> octants needed (count pass)
+    const int32_t* gid;    // slot -> id of its first needed child (fill pass)
     int32_t* count;        // per node pair count (count pass)
     const int32_t* pair_off;
     Pair* pairs;
@@ -330,12 +335,16 @@ __global__ void k_screen(ScreenArgs A) {
                         int idx = find_key_exact(A.F.key, off[j], off[j + 1], morton3(b1, b2, b3));
                         if (idx >= 0) in = idx;
                         else {
-                            uint64_t gk = ghost_key(j, b, b1, b2, b3);
+                            // keyed by the parent box (the child's level j is kept in the key)
+                            const uint64_t pk = ghost_key(j, b, b1 >> 1, b2 >> 1, b3 >> 1);
+                            const uint32_t oct = ((b1 & 1) << 2) | ((b2 & 1) << 1) | (b3 & 1);
                             if (!FILL) {
-                                if (ghost_insert(A.gtab, A.gcap, gk) < 0) atomicExch(A.err, 1);
+                                const int slot = ghost_insert(A.gtab, A.gcap, pk);
+                                if (slot < 0) atomicExch(A.err, 1);
+                                else atomicOr(&A.gmask[slot], 1u << oct);
                             } else {
-                                int slot = ghost_find(A.gtab, A.gcap, gk);
-                                in = slot >= 0 ? -1 - A.gid[slot] : 0;
+                                const int slot = ghost_find(A.gtab, A.gcap, pk);
+                                in = slot >= 0 ? -1 - (A.gid[slot] + __popc(A.gmask[slot] & ((1u << oct) - 1u))) : 0;
                                 if (slot < 0) atomicExch(A.err, 2);
                             }
                         }
@@ -367,14 +376,25 @@ __global__ void k_fill_u64(uint64_t* p, size_t n, uint64_t v) {
         p[i] = v;
 }
 
-__global__ void k_ghost_ids(const uint64_t* tab, uint32_t cap, int32_t* gid, uint64_t* gkeys, int32_t* ng) {
+// ids: each parent slot takes popc(mask) consecutive ids (the order of the slots is
+// whatever the atomic gives; every refined block is computed from its own key, so
+// the results do not depend on it)
+__global__ void k_ghost_ids(const uint64_t* tab, uint32_t cap, const uint32_t* gmask, int32_t* gid, int32_t* ng) {
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += gridDim.x * blockDim.x)
+        if (tab[s] != GH_EMPTY) gid[s] = atomicAdd(ng, __popc(gmask[s]));
+}
+
+// the children's keys (level | tree | Morton key of the child) at their ids
+__global__ void k_ghost_keys(const uint64_t* tab, uint32_t cap, const uint32_t* gmask, const int32_t* gid,
+                             uint64_t* gkeys) {
+    const uint64_t lo36 = (1ull << 36) - 1;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += gridDim.x * blockDim.x) {
-        uint64_t v = tab[s];
-        if (v != GH_EMPTY) {
-            int id = atomicAdd(ng, 1);
-            gid[s] = id;
-            gkeys[id] = v;
-        }
+        const uint64_t pk = tab[s];
+        if (pk == GH_EMPTY) continue;
+        const uint32_t mk = gmask[s];
+        int id = gid[s];
+        for (uint32_t o = 0; o < 8; ++o)
+            if ((mk >> o) & 1u) gkeys[id++] = (pk & ~lo36) | (((pk & lo36) << 3) | o);
     }
 }
 
@@ -452,15 +472,6 @@ __global__ void k_ghost_refine(Forest F, const uint64_t* gkeys, double* gblk, in
     for (int e = threadIdx.x; e < k3; e += blockDim.x) gblk[(size_t)blockIdx.x * k3 + e] = x[e];
 }
 
-// Ghost ids in sorted key order: gid[slot of key i] = i.
-__global__ void k_ghost_reid(int ng, const uint64_t* gkeys, const uint64_t* tab, uint32_t cap, int32_t* gid,
-                             int32_t* err) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
-        const int slot = ghost_find(tab, cap, gkeys[i]);
-        if (slot >= 0) gid[slot] = i;
-        else atomicExch(err, 2);
-    }
-}
 
 // out = Mat along dimension `dim` of the k^3 array x (Mat k x k, out[c] = sum_i Mat[c][i] x[i]),
 // generic k (row-major k^3 arrays, one output element per thread)
@@ -507,8 +518,8 @@ __device__ __forceinline__ void mode_mul_tri(const T* Mat, const T* x, T* out, i
     __syncthreads();
 }
 
-// Step 2 by sibling groups.  The ghost keys are sorted, so the children of one
-// parent box are consecutive; the block of a group's first ghost refines the
+// Step 2 by sibling groups.  The children of one parent box have consecutive ids
+// (k_ghost_ids / k_ghost_keys); the block of a group's first ghost refines the
 // ancestor leaf to the parent (the path's per-direction two-scale matrices
 // multiplied first, then one three-mode product), then every child of the
 // group, sharing the direction-3 and direction-2 partial products among the
@@ -701,7 +712,7 @@ __global__ void __launch_bounds__(128) k_apply_simt(ApplyArgs A) {
 // ------------------------------------------------------------------ driver
 void screen_release(const Alloc& A, ScreenOut* S) {
     A.put(S->dv); A.put(S->sched); A.put(S->count); A.put(S->pair_off); A.put(S->total); A.put(S->err);
-    A.put(S->gtab); A.put(S->gid); A.put(S->gkeys); A.put(S->pairs);
+    A.put(S->gtab); A.put(S->gid); A.put(S->gmask); A.put(S->gkeys); A.put(S->pairs);
     *S = ScreenOut();
 }
 
@@ -739,41 +750,44 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
     sa.F = F; sa.M = M; sa.sl = S->sl; sa.sched = S->sched;
     sa.count = S->count; sa.pair_off = S->pair_off; sa.pairs = nullptr; sa.err = S->err;
     const int sblocks = (int)std::max<long>(1, std::min<long>(num_sms() * 32, ((long)n * 32 + 255) / 256));
+    // parents of missing boxes: 16 slots per node to start (a box's band has at most
+    // 27 parent boxes, shared with its neighbours), regrown x4 on a probe overflow
     uint64_t cap = 1024;
-    while (cap < (uint64_t)n * 64ull) cap <<= 1;
+    while (cap < (uint64_t)n * 16ull) cap <<= 1;
     int32_t h[2] = {0, 0}, herr[2] = {0, 0};
     for (;;) {
         if (cap > (1ull << 30)) { set_error("ghost hash set overflow"); return MRA_ECUDA; }
         S->gcap = (uint32_t)cap;
         MRA_TRY(dalloc(A, &S->gtab, cap));
         MRA_TRY(dalloc(A, &S->gid, cap));
-        MRA_TRY(dalloc(A, &S->gkeys, cap));
+        MRA_TRY(dalloc(A, &S->gmask, cap));
         MRA_CK(cudaMemsetAsync(S->total, 0, 2 * sizeof(int32_t), st));
+        MRA_CK(cudaMemsetAsync(S->gmask, 0, cap * sizeof(uint32_t), st));
         k_fill_u64<<<1024, 256, 0, st>>>(S->gtab, cap, GH_EMPTY);
         MRA_CK_LAUNCH();
-        sa.gtab = S->gtab; sa.gcap = S->gcap; sa.gid = S->gid;
+        sa.gtab = S->gtab; sa.gcap = S->gcap; sa.gid = S->gid; sa.gmask = S->gmask;
         k_screen<false><<<sblocks, 256, 0, st>>>(sa);
         MRA_CK_LAUNCH();
         MRA_TRY(scan_exclusive(S->count, S->pair_off, n, S->total, st));
         MRA_CK(cudaMemcpyAsync(S->pair_off + n, S->total, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-        k_ghost_ids<<<1024, 256, 0, st>>>(S->gtab, S->gcap, S->gid, S->gkeys, S->total + 1);
+        k_ghost_ids<<<1024, 256, 0, st>>>(S->gtab, S->gcap, S->gmask, S->gid, S->total + 1);
         MRA_CK_LAUNCH();
         // the one host synchronisation: pair and ghost counts size the worklist
         MRA_CK(cudaMemcpyAsync(h, S->total, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         MRA_CK(cudaMemcpyAsync(herr, S->err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         MRA_CK(cudaStreamSynchronize(st));
         if (!herr[0]) break;
-        A.put(S->gtab); A.put(S->gid); A.put(S->gkeys);
-        S->gtab = nullptr; S->gid = nullptr; S->gkeys = nullptr;
+        A.put(S->gtab); A.put(S->gid); A.put(S->gmask);
+        S->gtab = nullptr; S->gid = nullptr; S->gmask = nullptr;
         MRA_CK(cudaMemsetAsync(S->err, 0, 2 * sizeof(int32_t), st));
         cap <<= 2;
     }
     S->npairs = h[0];
     S->nghost = h[1];
-    // ghost ids in key order: siblings (children of one parent box) become consecutive
-    if (S->nghost > 1) {
-        MRA_TRY(sort_keys_u64(A, S->gkeys, S->nghost, st));
-        k_ghost_reid<<<(S->nghost + 255) / 256, 256, 0, st>>>(S->nghost, S->gkeys, S->gtab, S->gcap, S->gid, S->err);
+    // the children's keys at their ids: siblings (children of one parent box) are consecutive
+    MRA_TRY(dalloc(A, &S->gkeys, (size_t)S->nghost + 1));
+    if (S->nghost > 0) {
+        k_ghost_keys<<<1024, 256, 0, st>>>(S->gtab, S->gcap, S->gmask, S->gid, S->gkeys);
         MRA_CK_LAUNCH();
     }
     MRA_TRY(dalloc(A, &S->pairs, (size_t)S->npairs + 1));
@@ -1002,7 +1016,7 @@ namespace mra {
 #define NA_HASH_CAP 16384u
 
 struct NaLayout {
-    size_t dv, sched, count, pair_off, total, err, gtab, gid, gkeys, pairs, gblk, nitems, bytes;
+    size_t dv, sched, count, pair_off, total, err, gtab, gid, gmask, gkeys, pairs, gblk, nitems, bytes;
 };
 
 static constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1018,7 +1032,8 @@ static NaLayout na_layout() {
     L.err = o;      o = na_align(o + 2 * sizeof(int32_t));
     L.gtab = o;     o = na_align(o + NA_HASH_CAP * sizeof(uint64_t));
     L.gid = o;      o = na_align(o + NA_HASH_CAP * sizeof(int32_t));
-    L.gkeys = o;    o = na_align(o + NA_HASH_CAP * sizeof(uint64_t));
+    L.gmask = o;    o = na_align(o + NA_HASH_CAP * sizeof(uint32_t));
+    L.gkeys = o;    o = na_align(o + NA_MAX_GHOSTS * sizeof(uint64_t));
     L.pairs = o;    o = na_align(o + (size_t)NA_MAX_NODES * 216 * sizeof(Pair));
     L.gblk = o;     o = na_align(o + (size_t)NA_MAX_GHOSTS * NA_MAX_K * NA_MAX_K * NA_MAX_K * sizeof(double));
     L.nitems = o;   o = na_align(o + sizeof(unsigned long long));
@@ -1078,6 +1093,7 @@ int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, doubl
     int32_t* err = (int32_t*)(base + L.err);
     uint64_t* gtab = (uint64_t*)(base + L.gtab);
     int32_t* gid = (int32_t*)(base + L.gid);
+    uint32_t* gmask = (uint32_t*)(base + L.gmask);
     uint64_t* gkeys = (uint64_t*)(base + L.gkeys);
     Pair* pairs = (Pair*)(base + L.pairs);
     double* gblk = (double*)(base + L.gblk);
@@ -1088,6 +1104,7 @@ int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, doubl
     MRA_CK(cudaMemsetAsync(total, 0, 2 * sizeof(int32_t), st));
     MRA_CK(cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), st));
     MRA_CK(cudaMemsetAsync(nitems, 0, sizeof(unsigned long long), st));
+    MRA_CK(cudaMemsetAsync(gmask, 0, NA_HASH_CAP * sizeof(uint32_t), st));
     k_fill_u64<<<64, 256, 0, st>>>(gtab, NA_HASH_CAP, GH_EMPTY);
     MRA_CK_LAUNCH();
     MRA_TRY(leaf_norm2(f, dv, st));
@@ -1100,14 +1117,14 @@ int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, doubl
     const Forest F = forest_of_tree(f);
     ScreenArgs sa;
     sa.F = F; sa.M = M; sa.sl = sl; sa.sched = sched;
-    sa.gtab = gtab; sa.gcap = NA_HASH_CAP; sa.gid = gid;
+    sa.gtab = gtab; sa.gcap = NA_HASH_CAP; sa.gid = gid; sa.gmask = gmask;
     sa.count = count; sa.pair_off = pair_off; sa.pairs = nullptr; sa.err = err;
     const int sblocks = (int)std::min<long>(4096, ((long)n * 32 + 255) / 256);
     k_screen<false><<<sblocks, 256, 0, st>>>(sa);
     MRA_CK_LAUNCH();
     MRA_TRY(scan_exclusive(count, pair_off, n, total, st));
     MRA_CK(cudaMemcpyAsync(pair_off + n, total, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-    k_ghost_ids<<<64, 256, 0, st>>>(gtab, NA_HASH_CAP, gid, gkeys, total + 1);
+    k_ghost_ids<<<64, 256, 0, st>>>(gtab, NA_HASH_CAP, gmask, gid, total + 1);
     MRA_CK_LAUNCH();
     int32_t h[2] = {0, 0}, herr[2] = {0, 0};
     MRA_CK(cudaMemcpyAsync(h, total, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -1119,6 +1136,8 @@ int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, doubl
     }
     const int nghost = h[1];
     if (nghost > 0) {
+        k_ghost_keys<<<64, 256, 0, st>>>(gtab, NA_HASH_CAP, gmask, gid, gkeys);
+        MRA_CK_LAUNCH();
         const size_t gsm = (2 * (size_t)k * k + 3 * (size_t)k3) * sizeof(double);
         k_ghost_refine<<<nghost, 128, gsm, st>>>(F, gkeys, gblk, err + 1);
         MRA_CK_LAUNCH();

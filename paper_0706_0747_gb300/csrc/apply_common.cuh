@@ -88,9 +88,10 @@ struct ScreenOut {
     int32_t* pair_off = nullptr;  // [n + 1]
     int32_t* total = nullptr;     // [2]: pairs, Step-2 blocks
     int32_t* err = nullptr;       // [0] screen, [1] Step 2 / apply
-    uint64_t* gtab = nullptr;     // ghost hash set
-    int32_t* gid = nullptr;
-    uint64_t* gkeys = nullptr;    // [nghost] level | tree | Morton key
+    uint64_t* gtab = nullptr;     // Step-2 set: parent keys of the missing boxes
+    int32_t* gid = nullptr;       // slot -> id of its first needed child
+    uint32_t* gmask = nullptr;    // slot -> octants needed
+    uint64_t* gkeys = nullptr;    // [nghost] level | tree | Morton key of each child, by id
     uint32_t gcap = 0;
     Pair* pairs = nullptr;        // [npairs], out and in are forest node indices
     int npairs = 0, nghost = 0;

@@ -156,8 +156,6 @@ int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cud
                mra_tree** g, mra_apply_stats* stats);
 int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, double* ghat, cudaStream_t st,
                        int64_t* n_items_host);
-// sort.cu
-int sort_keys_u64(const Alloc& A, uint64_t* keys, int n, cudaStream_t st);
 
 // schedule.cu
 int screen_data_impl(const mra_op* op, const mra_tree* f, float* X, float* T, cudaStream_t st);
