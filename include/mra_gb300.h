@@ -494,6 +494,87 @@ int mra_free_plan(mra_plan* p);
 int mra_reconstruct(mra_tree* t, int mode, int truncate, double eps, void* stream,
                     double* truncation_l2_host);
 
+/* ------------------------------------------------------------------------ */
+/* Products and inner products of trees, for the hydrogen ground-state
+ * iteration phi = -2 G_mu V phi of Sec. 6.2 (Steps 2 and 4).  The paper
+ * computes these by the method of its reference [A-B-G-V:2002], which it does
+ * not describe; the definitions below are this library's.
+ *
+ * A potential V(x) = sum_g (coef_g + r2coef_g |x - c_g|^2) exp(-expo_g |x - c_g|^2)
+ *                  + sum_n charge_n / |x - R_n|
+ * (host arrays, copied by the call; r2coef may be NULL).  expo_g >= 0, so a
+ * term with expo 0 is a polynomial; a nucleus of charge Z at R is the term
+ * charge -Z.  A quadrature point that coincides with some R_n takes 0 from
+ * that term. */
+typedef struct {
+    int n_gauss;
+    const double* coef_host;     /* n_gauss            */
+    const double* r2coef_host;   /* n_gauss or NULL     */
+    const double* expo_host;     /* n_gauss, >= 0       */
+    const double* center_host;   /* 3 n_gauss           */
+    int n_charge;
+    const double* charge_host;   /* n_charge            */
+    const double* position_host; /* 3 n_charge          */
+} mra_potential;
+
+/* out = scale * P(V f): a new tree on f's skeleton (state MRA_TREE_LEAVES,
+ * internal blocks zero) whose leaf (j, a) holds the coefficients of V f
+ * projected by the box's k-point Gauss-Legendre rule per direction,
+ *   s'_i = 2^{-3j/2} sum_q w_q phi_i(u_q) V(x_q) f(x_q),
+ * with f(x_q) from the leaf's block (eq. fvals2coefs and its inverse in
+ * tensor form).  Exact when V f restricted to the box is a polynomial of
+ * degree < 2k - 1 - (k - 1) = k per direction; otherwise the discrete
+ * projection of the product.  f: MRA_TREE_LEAVES or MRA_TREE_REDUNDANT.
+ * Synchronous.  Errors: MRA_EINVAL for an empty potential, a negative
+ * exponent, a NULL array or a non-finite value; MRA_ESTATE for an ns-form f. */
+int mra_tree_multiply(const mra_tree* f, const mra_potential* v, double scale, void* stream,
+                      mra_tree** out);
+
+/* <a, b> = sum over the leaves of sum_i a_i b_i: the L2 inner product over the
+ * unit cube of the two functions (the leaf blocks are coefficients in an
+ * orthonormal basis).  a and b must have the same skeleton (same k, node list
+ * and leaf flags) and leaf data (MRA_TREE_LEAVES or MRA_TREE_REDUNDANT).  FP64;
+ * the order of the partial sums is not fixed.  Synchronous (*out_host is
+ * written).  Errors: MRA_EINVAL for different skeletons; MRA_ESTATE for an
+ * ns-form tree. */
+int mra_tree_dot(const mra_tree* a, const mra_tree* b, void* stream, double* out_host);
+
+/* t *= alpha on every block (leaf and internal; stored wavelet cubes are
+ * dropped).  Stream-ordered; no synchronisation. */
+int mra_tree_scale(mra_tree* t, double alpha, void* stream);
+
+/* One pass of the ground-state iteration phi = -2 G_mu V phi (Sec. 6.2,
+ * eq. Kalos; Steps 2-5) on a cube of side `length` (physical units) mapped to
+ * the unit cube by x = length * u.  V is given in cube coordinates with
+ * physical values, V~(u) = V(length u): a nucleus of charge Z at the cube
+ * point u0 is the point charge -Z / length at u0.
+ *   2. P = V phi (mra_tree_multiply);
+ *   3. phi_new = -2 length^2 G~_{mu length} P: compress, mra_apply_ns with
+ *      the operator K_{mu length, 1} built for this call (eps, max_level,
+ *      opts as given; NULL opts = FP64 defaults), assembly without
+ *      truncation, so phi_new keeps phi's skeleton;
+ *   4. E_new = (-<P, phi_new> - mu^2/2 <phi_new, phi_new>
+ *               + <V phi_new, phi_new>) / <phi_new, phi_new>,
+ *      the paper's energy with (1/2)<grad phi_new, grad phi_new> replaced by
+ *      -<V phi, phi_new> - mu^2/2 ||phi_new||^2, which the equation
+ *      (-Laplacian + mu^2) phi_new = -2 V phi gives by integration by parts;
+ *   5. *phi_next = phi_new / ||phi_new|| (physical L2 norm), and the next mu.
+ * phi: leaf data (MRA_TREE_LEAVES or MRA_TREE_REDUNDANT); it is not changed.
+ * Synchronous.  Errors: those of the calls above; MRA_EINVAL for length or
+ * mu not positive and finite. */
+typedef struct {
+    double energy;     /* E_new                                                   */
+    double mu_next;    /* sqrt(-2 E_new), or mu when E_new >= 0                   */
+    double norm_new;   /* ||phi_new|| (physical units) before normalisation       */
+    int n_terms;       /* Gaussian terms M of the operator                        */
+    int64_t n_items;   /* items applied by Step 3                                 */
+    float ms_apply;    /* device time of Step 3's apply kernels (CUDA events)     */
+} mra_kalos_info;
+
+int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, double mu, double eps,
+                   int max_level, const mra_apply_opts* opts, void* stream, mra_tree** phi_next,
+                   mra_kalos_info* info);
+
 /* Free any handle of this library -- a tree, operator, plan or network --
  * exactly once (NULL is ignored).  The kind is read from the tag every handle
  * starts with; a pointer that is not a live handle returns MRA_EINVAL.  The

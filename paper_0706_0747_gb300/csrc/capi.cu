@@ -1,9 +1,10 @@
 // C ABI entry points (declared in include/mra_gb300.h): argument checks,
 // handle ownership, allocator hook and per-thread error messages.  All
-// arithmetic is done by the kernels in operator.cu, tree.cu and apply.cu.
+// arithmetic is done by the kernels in operator.cu, tree.cu, apply*.cu and product.cu.
 #include <stdarg.h>
 
 #include <atomic>
+#include <cmath>
 
 #include "mra_internal.cuh"
 
@@ -180,6 +181,113 @@ int mra_tree_refine(const mra_tree* f, int passes, int max_level, void* stream, 
     if (max_level < 0 || max_level > MRA_MAX_LEVEL) { set_error("max_level outside [0, %d]", MRA_MAX_LEVEL); return MRA_EINVAL; }
     if (f->state == MRA_TREE_NSFORM) { set_error("refine needs leaf data, not an ns-form tree"); return MRA_ESTATE; }
     return refine_impl(f, passes, max_level, (cudaStream_t)stream, out, n_split_host);
+}
+
+static bool all_finite(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+int mra_tree_multiply(const mra_tree* f, const mra_potential* v, double scale, void* stream, mra_tree** out) {
+    if (!out) { set_error("out is NULL"); return MRA_EINVAL; }
+    *out = nullptr;
+    if (!tree_ok(f)) { set_error("invalid tree handle"); return MRA_EINVAL; }
+    if (!v || v->n_gauss < 0 || v->n_charge < 0 || v->n_gauss + v->n_charge == 0) {
+        set_error("the potential has no terms");
+        return MRA_EINVAL;
+    }
+    if (v->n_gauss > 0 && (!v->coef_host || !v->expo_host || !v->center_host)) {
+        set_error("a Gaussian array of the potential is NULL");
+        return MRA_EINVAL;
+    }
+    if (v->n_charge > 0 && (!v->charge_host || !v->position_host)) {
+        set_error("a charge array of the potential is NULL");
+        return MRA_EINVAL;
+    }
+    const size_t ng = v->n_gauss, nc = v->n_charge;
+    if (!std::isfinite(scale) || (ng && !(all_finite(v->coef_host, ng) && all_finite(v->expo_host, ng) &&
+                                          all_finite(v->center_host, 3 * ng) &&
+                                          (!v->r2coef_host || all_finite(v->r2coef_host, ng)))) ||
+        (nc && !(all_finite(v->charge_host, nc) && all_finite(v->position_host, 3 * nc)))) {
+        set_error("non-finite potential parameter or scale");
+        return MRA_EINVAL;
+    }
+    for (size_t g = 0; g < ng; ++g)
+        if (v->expo_host[g] < 0.0) { set_error("exponent %zu is negative", g); return MRA_EINVAL; }
+    if (f->state == MRA_TREE_NSFORM) { set_error("multiply needs leaf data, not an ns-form tree"); return MRA_ESTATE; }
+    return tree_multiply_impl(f, v, scale, (cudaStream_t)stream, out);
+}
+
+int mra_tree_dot(const mra_tree* a, const mra_tree* b, void* stream, double* out_host) {
+    if (!out_host) { set_error("out_host is NULL"); return MRA_EINVAL; }
+    if (!tree_ok(a) || !tree_ok(b)) { set_error("invalid tree handle"); return MRA_EINVAL; }
+    if (a->k != b->k || a->n != b->n || memcmp(a->off, b->off, sizeof(a->off)) != 0) {
+        set_error("the two trees have different skeletons");
+        return MRA_EINVAL;
+    }
+    if (a->state == MRA_TREE_NSFORM || b->state == MRA_TREE_NSFORM) {
+        set_error("dot needs leaf data, not an ns-form tree");
+        return MRA_ESTATE;
+    }
+    return tree_dot_impl(a, b, out_host, (cudaStream_t)stream);
+}
+
+int mra_tree_scale(mra_tree* t, double alpha, void* stream) {
+    if (!tree_ok(t)) { set_error("invalid tree handle"); return MRA_EINVAL; }
+    if (!std::isfinite(alpha)) { set_error("alpha is not finite"); return MRA_EINVAL; }
+    return tree_scale_impl(t, alpha, (cudaStream_t)stream);
+}
+
+int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, double mu, double eps, int max_level,
+                   const mra_apply_opts* opts, void* stream, mra_tree** phi_next, mra_kalos_info* info) {
+    if (!phi_next) { set_error("phi_next is NULL"); return MRA_EINVAL; }
+    *phi_next = nullptr;
+    if (!tree_ok(phi)) { set_error("invalid tree handle"); return MRA_EINVAL; }
+    if (!(length > 0.0 && std::isfinite(length)) || !(mu > 0.0 && std::isfinite(mu))) {
+        set_error("length and mu must be positive and finite");
+        return MRA_EINVAL;
+    }
+    // every handle made here is freed on every return
+    struct Owned {
+        mra_tree *P = nullptr, *g = nullptr, *Q = nullptr;
+        mra_op* op = nullptr;
+        ~Owned() {
+            mra_free_tree(P);
+            mra_free_tree(g);
+            mra_free_tree(Q);
+            mra_free_op(op);
+        }
+    } o;
+    MRA_TRY(mra_tree_multiply(phi, v, 1.0, stream, &o.P));                          // Step 2
+    MRA_TRY(mra_make_operator(mu * length, 1.0, eps, phi->k, max_level, phi->A.has ? &phi->A.hook : nullptr,
+                              stream, &o.op));
+    MRA_TRY(mra_compress(o.P, 0, stream));                                          // Step 3
+    mra_apply_stats st{};
+    MRA_TRY(mra_apply_ns(o.op, o.P, opts, stream, &o.g, &st));
+    MRA_TRY(mra_reconstruct(o.g, MRA_RECON_ASSEMBLE, 0, 0.0, stream, nullptr));
+    MRA_TRY(mra_tree_scale(o.g, -2.0 * length * length, stream));
+    double nn = 0.0, pg = 0.0, qg = 0.0;                                            // Step 4
+    MRA_TRY(mra_tree_dot(o.g, o.g, stream, &nn));
+    MRA_TRY(mra_tree_dot(o.P, o.g, stream, &pg));
+    MRA_TRY(mra_tree_multiply(o.g, v, 1.0, stream, &o.Q));
+    MRA_TRY(mra_tree_dot(o.Q, o.g, stream, &qg));
+    if (!(nn > 0.0)) { set_error("phi_new vanishes"); return MRA_EINVAL; }
+    const double E = (-pg - 0.5 * mu * mu * nn + qg) / nn;
+    const double norm = std::sqrt(nn * length * length * length);
+    MRA_TRY(mra_tree_scale(o.g, 1.0 / norm, stream));                               // Step 5
+    MRA_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    if (info) {
+        info->energy = E;
+        info->mu_next = E < 0.0 ? std::sqrt(-2.0 * E) : mu;
+        info->norm_new = norm;
+        info->n_terms = o.op->M;
+        info->n_items = st.n_items;
+        info->ms_apply = st.ms_screen + st.ms_ghost + st.ms_apply;
+    }
+    *phi_next = o.g;
+    o.g = nullptr;
+    return MRA_OK;
 }
 
 int mra_compress(mra_tree* t, int store_d, void* stream) {

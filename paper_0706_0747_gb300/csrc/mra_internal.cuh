@@ -150,6 +150,10 @@ int assemble_impl(mra_tree* t, cudaStream_t st);
 int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host);
 int tree_clone_skeleton(const mra_tree* src, mra_tree** out);
 int refine_impl(const mra_tree* f, int passes, int max_level, cudaStream_t st, mra_tree** out, int* nsplit_total);
+// product.cu
+int tree_multiply_impl(const mra_tree* f, const mra_potential* v, double scale, cudaStream_t st, mra_tree** out);
+int tree_dot_impl(const mra_tree* a, const mra_tree* b, double* out_host, cudaStream_t st);
+int tree_scale_impl(mra_tree* t, double alpha, cudaStream_t st);
 
 // apply.cu
 int apply_impl(const mra_op* op, const mra_tree* f, const mra_apply_opts* o, cudaStream_t st,
@@ -204,40 +208,44 @@ __host__ __device__ inline void phi_all(int n, double u, double* out) {
     }
 }
 
-// Gauss-Legendre nodes/weights on [0,1], n <= 32, by Newton on P_n; the
-// nodes are returned in increasing order.  Called by one thread.
-__host__ __device__ inline void gauss_legendre01(int n, double* x, double* w) {
-    for (int i = 0; i < n; ++i) {
-        double z = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5));
-        double dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = z;
-            for (int q = 2; q <= n; ++q) {
-                double p2 = ((2.0 * q - 1.0) * z * p1 - (q - 1.0) * p0) / q;
-                p0 = p1;
-                p1 = p2;
-            }
-            double pn = (n == 1) ? z : p1, pm = (n == 1) ? 1.0 : p0;
-            dp = n * (z * pn - pm) / (z * z - 1.0);
-            double dz = pn / dp;
-            z -= dz;
-            if (fabs(dz) < 1e-16) {
-                // refresh derivative at the converged root
-                p0 = 1.0; p1 = z;
-                for (int q = 2; q <= n; ++q) {
-                    double p2 = ((2.0 * q - 1.0) * z * p1 - (q - 1.0) * p0) / q;
-                    p0 = p1;
-                    p1 = p2;
-                }
-                pn = (n == 1) ? z : p1; pm = (n == 1) ? 1.0 : p0;
-                dp = n * (z * pn - pm) / (z * z - 1.0);
-                break;
-            }
+// Root i of the n-point Gauss-Legendre rule on [0, 1] (n <= 32) by Newton on
+// P_n from the asymptotic start cos(pi (i + 3/4) / (n + 1/2)): stops once the
+// step is below 1e-15 (quadratic convergence leaves the root at rounding
+// level), then refreshes the derivative for the weight.  Node index
+// n - 1 - i (nodes increase with the index).
+__host__ __device__ inline void gauss_legendre01_root(int n, int i, double* x, double* w) {
+    double z = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5));
+    double pn = 0.0, pm = 0.0;
+    for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = z;
+        for (int q = 2; q <= n; ++q) {
+            double p2 = ((2.0 * q - 1.0) * z * p1 - (q - 1.0) * p0) / q;
+            p0 = p1;
+            p1 = p2;
         }
-        int idx = n - 1 - i;  // cos(.) decreases with i
-        x[idx] = 0.5 * (z + 1.0);
-        w[idx] = 1.0 / ((1.0 - z * z) * dp * dp);
+        pn = (n == 1) ? z : p1;
+        pm = (n == 1) ? 1.0 : p0;
+        const double dz = pn / (n * (z * pn - pm) / (z * z - 1.0));
+        z -= dz;
+        if (fabs(dz) < 1e-15) break;
     }
+    double p0 = 1.0, p1 = z;
+    for (int q = 2; q <= n; ++q) {
+        double p2 = ((2.0 * q - 1.0) * z * p1 - (q - 1.0) * p0) / q;
+        p0 = p1;
+        p1 = p2;
+    }
+    pn = (n == 1) ? z : p1;
+    pm = (n == 1) ? 1.0 : p0;
+    const double dp = n * (z * pn - pm) / (z * z - 1.0);
+    const int idx = n - 1 - i;  // cos(.) decreases with i
+    x[idx] = 0.5 * (z + 1.0);
+    w[idx] = 1.0 / ((1.0 - z * z) * dp * dp);
+}
+
+// all n nodes and weights, by one thread
+__host__ __device__ inline void gauss_legendre01(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) gauss_legendre01_root(n, i, x, w);
 }
 
 // parity band of the modified ns-form: t_d in [-3, 2] (even a_d) or [-2, 3] (odd)

@@ -271,7 +271,7 @@ __global__ void k_build_level(int k, int j, DensDev D, const int32_t* boxes, con
     __shared__ double red[32];
     const int b = blockIdx.x, tid = threadIdx.x;
     const int a1 = boxes[3 * b], a2 = boxes[3 * b + 1], a3 = boxes[3 * b + 2];
-    if (tid == 0) gauss_legendre01(k, g, gw);
+    if (tid < k) gauss_legendre01_root(k, tid, g, gw);
     __syncthreads();
     if (tid < k) {
         double tmp[MRA_MAX_K];

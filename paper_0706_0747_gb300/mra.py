@@ -34,6 +34,20 @@ class Density(ctypes.Structure):
                 ("center_host", ctypes.POINTER(ctypes.c_double))]
 
 
+class PotentialC(ctypes.Structure):
+    _fields_ = [("n_gauss", ctypes.c_int), ("coef_host", ctypes.POINTER(ctypes.c_double)),
+                ("r2coef_host", ctypes.POINTER(ctypes.c_double)),
+                ("expo_host", ctypes.POINTER(ctypes.c_double)),
+                ("center_host", ctypes.POINTER(ctypes.c_double)),
+                ("n_charge", ctypes.c_int), ("charge_host", ctypes.POINTER(ctypes.c_double)),
+                ("position_host", ctypes.POINTER(ctypes.c_double))]
+
+
+class KalosInfo(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("mu_next", ctypes.c_double), ("norm_new", ctypes.c_double),
+                ("n_terms", ctypes.c_int), ("n_items", ctypes.c_int64), ("ms_apply", ctypes.c_float)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -111,6 +125,11 @@ SIGNATURES = {
     "mra_tree_set_blocks": [_P, _P, _P],
     "mra_compress": [_P, ctypes.c_int, _P],
     "mra_tree_refine": [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int)],
+    "mra_tree_multiply": [_P, ctypes.POINTER(PotentialC), ctypes.c_double, _P, ctypes.POINTER(_P)],
+    "mra_tree_dot": [_P, _P, _P, _DP],
+    "mra_tree_scale": [_P, ctypes.c_double, _P],
+    "mra_kalos_step": [_P, ctypes.POINTER(PotentialC), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                       ctypes.c_int, ctypes.POINTER(ApplyOpts), _P, ctypes.POINTER(_P), ctypes.POINTER(KalosInfo)],
     "mra_make_operator": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                           ctypes.POINTER(Alloc), _P, ctypes.POINTER(_P)],
     "mra_op_get_info": [_P, ctypes.POINTER(OpInfo)],
@@ -360,6 +379,46 @@ def tree_refine(tree, passes=1, max_level=MAX_LEVEL, stream=None):
     return Tree(h.value), ns.value
 
 
+class Potential:
+    """V(x) = sum_g (coef_g + r2coef_g |x - c_g|^2) exp(-expo_g |x - c_g|^2)
+    + sum_n charges_n / |x - positions_n| (unit-cube coordinates)."""
+
+    def __init__(self, coef=(), expo=(), centers=(), r2coef=None, charges=(), positions=()):
+        self.coef = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(-1))
+        self.expo = np.ascontiguousarray(np.asarray(expo, dtype=np.float64).reshape(-1))
+        self.centers = np.ascontiguousarray(np.asarray(centers, dtype=np.float64).reshape(-1))
+        self.r2coef = (np.zeros_like(self.coef) if r2coef is None
+                       else np.ascontiguousarray(np.asarray(r2coef, dtype=np.float64).reshape(-1)))
+        self.charges = np.ascontiguousarray(np.asarray(charges, dtype=np.float64).reshape(-1))
+        self.positions = np.ascontiguousarray(np.asarray(positions, dtype=np.float64).reshape(-1))
+
+    def c_struct(self):
+        """The mra_potential view of the arrays (valid while self lives)."""
+        def p(a):
+            return _dp(a) if len(a) else None
+        return PotentialC(len(self.coef), p(self.coef), p(self.r2coef), p(self.expo), p(self.centers),
+                          len(self.charges), p(self.charges), p(self.positions))
+
+
+def tree_multiply(tree, potential, scale=1.0, stream=None):
+    """mra_tree_multiply: scale * (V f) projected leaf by leaf on f's skeleton."""
+    v = potential.c_struct()
+    h = _P()
+    _check(lib().mra_tree_multiply(tree.h, ctypes.byref(v), float(scale), _stream(stream), ctypes.byref(h)))
+    return Tree(h.value)
+
+
+def tree_dot(a, b, stream=None):
+    """mra_tree_dot: <a, b> over the unit cube (same skeleton)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().mra_tree_dot(a.h, b.h, _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def tree_scale(tree, alpha, stream=None):
+    _check(lib().mra_tree_scale(tree.h, float(alpha), _stream(stream)))
+
+
 def compress(tree, store_d=False, stream=None):
     _check(lib().mra_compress(tree.h, int(store_d), _stream(stream)))
 
@@ -386,6 +445,18 @@ def apply_ns(op, tree, precision="fp64", block_screen=False, unscreened=False, i
     _check(lib().mra_apply_ns(op.h, tree.h, ctypes.byref(o), _stream(stream), ctypes.byref(h),
                               ctypes.byref(st) if stats else None))
     return Tree(h.value), (st.as_dict() if stats else None)
+
+
+def kalos_step(phi, potential, length, mu, eps, max_level, precision="fp64", screen="static", stream=None):
+    """mra_kalos_step: one pass of phi = -2 G_mu V phi; returns (phi_next,
+    info dict with energy, mu_next, norm_new, n_terms, n_items, ms_apply)."""
+    v = potential.c_struct()
+    o = ApplyOpts(PREC[precision], 0, 0, 0, SCREEN[screen], 2, 0, 0)
+    info = KalosInfo()
+    h = _P()
+    _check(lib().mra_kalos_step(phi.h, ctypes.byref(v), float(length), float(mu), float(eps), int(max_level),
+                                ctypes.byref(o), _stream(stream), ctypes.byref(h), ctypes.byref(info)))
+    return Tree(h.value), {f: getattr(info, f) for f, _ in KalosInfo._fields_}
 
 
 def apply_ns_noalloc(op, tree, out_ptr, precision="fp64", stream=None):

@@ -144,3 +144,51 @@ def paper_poisson(a=300.0, k=8, eps=1e-6, max_level=6):
     r2 = np.full(3, -4.0 * a * a)
     cfg = Config(f"paper_poisson_a{a:g}_k{k}", 0.0, 1.0, eps, k, max_level, init_level=1)
     return cfg, Density(coef, np.full(3, a), cen, r2)
+
+
+def slater_expansion(zeta, h=0.4, r_min=1e-4):
+    """Gaussian expansion (c, a) of exp(-zeta r): the trapezoid rule with step
+    h in s on exp(-zeta r) = zeta / (2 sqrt(pi)) int exp(-s/2 - zeta^2 e^{-s}/4
+    - r^2 e^s) ds (the Laplace-transform identity of exp(-zeta sqrt(y)) with
+    y = r^2), over s in [ln(zeta^2 / 150), 2 ln(1 / r_min) + 2].  Absolute
+    error about 1e-10 for r >= r_min at h = 0.4 (66 terms at zeta = 1)."""
+    s = np.arange(math.log(zeta * zeta / 150.0), 2.0 * math.log(1.0 / r_min) + 2.0 + h, h)
+    c = zeta / (2.0 * math.sqrt(math.pi)) * h * np.exp(-s / 2.0 - zeta * zeta * np.exp(-s) / 4.0)
+    return c, np.exp(s)
+
+
+@dataclass
+class Hydrogen:
+    """The hydrogen ground-state iteration (Sec. 6.2): a cube of side L
+    (atomic units) with the nucleus at the cube point u0, the starting
+    function exp(-zeta0 r), the starting mu0, and the apply's k / eps /
+    max_level.  The starting tree is Algorithm 1 on the Gaussian expansion
+    of exp(-zeta0 r) in cube coordinates (exponents a L^2)."""
+    name: str
+    L: float
+    u0: tuple
+    zeta0: float
+    mu0: float
+    k: int
+    eps: float
+    max_level: int
+    init_level: int
+
+    def start_density(self):
+        c, a = slater_expansion(self.zeta0)
+        return Density(c, a * self.L * self.L, np.tile(np.asarray(self.u0, dtype=np.float64), (len(c), 1)),
+                       np.zeros_like(c))
+
+
+def hydrogen(k=8, eps=1e-6, max_level=12):
+    """Hydrogen ground state: L = 32, nucleus at the cube centre (a corner of
+    boxes at every level, so no GL node meets it), exp(-0.7 r) and mu0 = 0.8
+    to start."""
+    return Hydrogen(f"hydrogen_k{k}_eps{eps:g}_level{max_level}", 32.0, (0.5, 0.5, 0.5), 0.7, 0.8, k, eps,
+                    max_level, 3)
+
+
+def hydrogen_small():
+    """A small hydrogen case the oracle finishes in seconds: k = 5,
+    eps = 1e-3, depth 5."""
+    return Hydrogen("hydrogen_k5_eps1e-3_level5", 32.0, (0.5, 0.5, 0.5), 0.7, 0.8, 5, 1e-3, 5, 2)
