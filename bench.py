@@ -52,7 +52,7 @@ FP64_TFLOPS = 1.25
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # apply kernel on this workload, from one ncu capture of the current kernel
 # version; absent where no capture of the current kernel exists.
-TRAFFIC_BYTES = {"tc/static": 140.571136e6, "tc/pair": 96.91648e6}
+TRAFFIC_BYTES = {"tc/static": 141.334272e6, "tc/pair": 97.992448e6}
 
 
 class Clocks:
@@ -543,6 +543,52 @@ def _refined_one(workload, K, Wu, flush, stream, prec, n_pts):
     return res
 
 
+# ---------------------------------------------------------------- hydrogen
+def hydrogen_section(stream, max_iter=40):
+    """The hydrogen ground-state iteration of Sec. 6.2 (phi = -2 G_mu V phi,
+    mu = sqrt(-2E)) at k = 8, eps = 1e-6, depth 12 in a cube of 32 bohr, from
+    exp(-0.7 r) with mu0 = 0.8, on the FP64 and the tensor-core apply, until
+    |mu_{n+1} - mu_n| < 1e-7 and | ||phi_new|| - 1 | < 1e-6.  Each step is one
+    mra_kalos_step (product, operator re-weighted from the cache, compress,
+    apply, assembly, three inner products, normalisation), timed with CUDA
+    events on the stream.  The exact answer is E = -1/2."""
+    import math
+    import torch
+    from paper_0706_0747_gb300 import mra, workloads as W
+    hc = W.hydrogen()
+    out = {"workload": hc.name, "L_bohr": hc.L, "k": hc.k, "eps": hc.eps, "max_level": hc.max_level,
+           "start": "exp(-0.7 r), mu0 = 0.8", "exact_energy": -0.5}
+    pot = mra.Potential(charges=[-1.0 / hc.L], positions=[hc.u0])
+    for prec in ("fp64", "tc"):
+        phi, hit = mra.build_tree(hc.start_density(), hc.k, hc.eps, hc.max_level, init_level=hc.init_level)
+        out["tree_nodes"], out["depth_hit"] = phi.n, bool(hit)
+        mra.tree_scale(phi, 1.0 / math.sqrt(mra.tree_dot(phi, phi) * hc.L ** 3))
+        cache, mu, ms, hist = mra.OpCache(), hc.mu0, [], []
+        for it in range(max_iter):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            phi, info = mra.kalos_step(phi, pot, hc.L, mu, hc.eps, hc.max_level, precision=prec, op_cache=cache,
+                                       stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            hist.append(info)
+            dmu, mu = abs(info["mu_next"] - mu), info["mu_next"]
+            if dmu < 1e-7 and abs(info["norm_new"] - 1.0) < 1e-6:
+                break
+        steady = ms[1:] if len(ms) > 1 else ms
+        out[prec] = {"iterations": len(hist), "energy": hist[-1]["energy"],
+                     "abs_err_energy": abs(hist[-1]["energy"] + 0.5), "norm_new": hist[-1]["norm_new"],
+                     "ms_first_step": ms[0], "ms_per_step_median": statistics.median(steady),
+                     "ms_total": sum(ms), "steps_per_s": 1e3 / statistics.median(steady),
+                     "items_per_step": hist[-1]["n_items"], "ms_apply_median": statistics.median(
+                         [h["ms_apply"] for h in hist]), "operators_built": sum(h["op_rebuilt"] for h in hist),
+                     "energies": [h["energy"] for h in hist]}
+        cache.free()
+        phi.free()
+    return out
+
+
 # ---------------------------------------------------------------- replicas
 def slowest_ms(local_ms, ws, device):
     """The slowest replica's time: the maximum over the ranks of the
@@ -583,6 +629,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the small-Poisson / Helmholtz section")
     ap.add_argument("--no-learned-batched", action="store_true",
                     help="skip the learned + tensor-core + batched section")
+    ap.add_argument("--no-hydrogen", action="store_true", help="skip the hydrogen ground-state iteration")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -803,6 +850,8 @@ def main():
                                               prec if prec in ("tc", "tc_ladder", "tc_fast") else "tc")
         if not args.no_learned_batched:
             line["learned_batched"] = learned_batched_section(K, Wu, flush, stream)
+        if not args.no_hydrogen:
+            line["hydrogen"] = hydrogen_section(stream)
         if not args.no_batched:
             line["batched"] = batched_section(K, Wu, flush, stream, pk["bf16_tflops"],
                                               prec if prec in ("tc", "tc_ladder") else "tc")

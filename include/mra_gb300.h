@@ -206,6 +206,17 @@ typedef struct {
 } mra_op_info;
 int mra_op_get_info(const mra_op* op, mra_op_info* info);
 
+/* Re-weight op for another mu on its own term grid: tau_m = e^{2 s_m} and
+ * every table that depends only on tau (F, the block norms, the estimate)
+ * are kept, and w_m = h C_alpha exp(-mu^2 e^{-2 s_m}/4 + (3-2alpha) s_m) is
+ * recomputed (Sec. 3).  The new sum must pass the same sup-norm test as
+ * make_operator (|K_{mu,alpha} - sum| <= eps K_{0,alpha} on 4000 radii in
+ * [delta, R]); the grid was chosen for the construction's mu, so a new mu
+ * above it passes (its weights drop the broad terms faster) and one well
+ * below it may not.  Not concurrent with another call on op.  Synchronous.
+ * Errors: MRA_EINVAL (op unchanged) for mu < 0 or a grid that fails the test. */
+int mra_op_retune(mra_op* op, double mu, void* stream);
+
 /* Copy operator tables to host (any pointer may be NULL):
  * w_host, tau_host: M doubles; F_host: (max_level+1) * M * 7 * k * k doubles,
  * index [j][m][l+3][i][i']; nF_host: (max_level+1) * M * 7; est_host:
@@ -551,15 +562,22 @@ int mra_tree_scale(mra_tree* t, double alpha, void* stream);
  *   2. P = V phi (mra_tree_multiply);
  *   3. phi_new = -2 length^2 G~_{mu length} P: compress, mra_apply_ns with
  *      the operator K_{mu length, 1} built for this call (eps, max_level,
- *      opts as given; NULL opts = FP64 defaults), assembly without
- *      truncation, so phi_new keeps phi's skeleton;
+ *      opts as given; NULL opts = FP64 defaults), then eq. g_assemble
+ *      without truncation, so phi_new keeps phi's skeleton;
  *   4. E_new = (-<P, phi_new> - mu^2/2 <phi_new, phi_new>
  *               + <V phi_new, phi_new>) / <phi_new, phi_new>,
  *      the paper's energy with (1/2)<grad phi_new, grad phi_new> replaced by
  *      -<V phi, phi_new> - mu^2/2 ||phi_new||^2, which the equation
  *      (-Laplacian + mu^2) phi_new = -2 V phi gives by integration by parts;
- *   5. *phi_next = phi_new / ||phi_new|| (physical L2 norm), and the next mu.
+ *   5. *phi_next = phi_new / ||phi_new|| (physical L2 norm; state
+ *      MRA_TREE_LEAVES), and the next mu.
  * phi: leaf data (MRA_TREE_LEAVES or MRA_TREE_REDUNDANT); it is not changed.
+ * op_cache: NULL, or the address of an operator handle kept between steps.
+ * With NULL the step builds its operator and frees it.  Otherwise an
+ * operator in *op_cache with this k, eps and max_level (alpha 1) is
+ * re-weighted for mu * length (mra_op_retune); when that fails, or *op_cache
+ * is NULL or does not match, a new operator is built, the old one freed and
+ * the new one stored in *op_cache.  The caller frees it (mra_free).
  * Synchronous.  Errors: those of the calls above; MRA_EINVAL for length or
  * mu not positive and finite. */
 typedef struct {
@@ -567,13 +585,14 @@ typedef struct {
     double mu_next;    /* sqrt(-2 E_new), or mu when E_new >= 0                   */
     double norm_new;   /* ||phi_new|| (physical units) before normalisation       */
     int n_terms;       /* Gaussian terms M of the operator                        */
+    int op_rebuilt;    /* 1 when the step built its operator, 0 when it re-weighted */
     int64_t n_items;   /* items applied by Step 3                                 */
     float ms_apply;    /* device time of Step 3's apply kernels (CUDA events)     */
 } mra_kalos_info;
 
 int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, double mu, double eps,
-                   int max_level, const mra_apply_opts* opts, void* stream, mra_tree** phi_next,
-                   mra_kalos_info* info);
+                   int max_level, const mra_apply_opts* opts, mra_op** op_cache, void* stream,
+                   mra_tree** phi_next, mra_kalos_info* info);
 
 /* Free any handle of this library -- a tree, operator, plan or network --
  * exactly once (NULL is ignored).  The kind is read from the tag every handle

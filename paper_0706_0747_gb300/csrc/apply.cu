@@ -165,6 +165,13 @@ __global__ void k_schedule(int M, int lm, const int32_t* nlev_tab, int unscreene
     int32_t* m1 = Jm + M;
     int32_t* m2 = m1 + lm * 4;
     int32_t* cnt = m2 + lm * 4;
+    // shared copies of J_m, w_m and, per level, the core / off-core maxima of
+    // the 1-D block norms, so the serial range scans below read shared memory
+    extern __shared__ double sched_sm[];
+    double* ws = sched_sm;                        // M
+    double* cmax = ws + M;                        // lm * M: max over |l| <= 1
+    double* bmax = cmax + (size_t)lm * M;         // lm * M: max over |l| >= 2
+    int* Js = (int*)(bmax + (size_t)lm * M);      // M
     const double fn = sqrt(dv[4 * b]);
     const double eta = fn > 0.0 ? eps * dv[4 * b + 1] / fn : 0.0;
     if (threadIdx.x == 0) dv[4 * b + 2] = eta;
@@ -175,6 +182,13 @@ __global__ void k_schedule(int M, int lm, const int32_t* nlev_tab, int unscreene
             for (int j = 1; j < nlev; ++j)
                 if (w[m] * est[(size_t)j * M + m] > eta / M) jm = j;
         Jm[m] = jm;
+        Js[m] = jm;
+        ws[m] = w[m];
+    }
+    for (int e = threadIdx.x; e < nlev * M; e += blockDim.x) {
+        const double* r = nF + (size_t)e * 7;  // e = j * M + m
+        cmax[e] = fmax(fmax(r[2], r[3]), r[4]);
+        bmax[e] = fmax(fmax(r[0], r[1]), fmax(r[5], r[6]));
     }
     __syncthreads();
     const double budget = eta / (2.0 * 216.0);
@@ -188,17 +202,15 @@ __global__ void k_schedule(int M, int lm, const int32_t* nlev_tab, int unscreene
             // candidates: terms with J_m >= j, in increasing m
             int first = -1, last = -1, n = 0;
             for (int m = 0; m < M; ++m)
-                if (Jm[m] >= j) {
+                if (Js[m] >= j) {
                     if (first < 0) first = m;
                     last = m;
                     ++n;
                 }
             if (n > 0) {
                 auto e_of = [&](int m) {
-                    const double* r = nF + ((size_t)j * M + m) * 7;
-                    double c = fmax(fmax(r[2], r[3]), r[4]);
-                    double bb = fmax(fmax(r[0], r[1]), fmax(r[5], r[6]));
-                    double v = w[m];
+                    const double c = cmax[(size_t)j * M + m], bb = bmax[(size_t)j * M + m];
+                    double v = ws[m];
                     for (int q = 0; q < S; ++q) v *= c;
                     for (int q = S; q < 3; ++q) v *= bb;
                     return v;
@@ -206,7 +218,7 @@ __global__ void k_schedule(int M, int lm, const int32_t* nlev_tab, int unscreene
                 double acc = 0.0;
                 int lo = first;
                 for (; lo <= last; ++lo) {
-                    if (Jm[lo] < j) continue;
+                    if (Js[lo] < j) continue;
                     double e = e_of(lo);
                     if (acc + e <= budget) acc += e;
                     else break;
@@ -214,7 +226,7 @@ __global__ void k_schedule(int M, int lm, const int32_t* nlev_tab, int unscreene
                 acc = 0.0;
                 int hi = last;
                 for (; hi >= lo; --hi) {
-                    if (Jm[hi] < j) continue;
+                    if (Js[hi] < j) continue;
                     double e = e_of(hi);
                     if (acc + e <= budget) acc += e;
                     else break;
@@ -231,13 +243,20 @@ __global__ void k_schedule(int M, int lm, const int32_t* nlev_tab, int unscreene
         for (int ci = 0; ci < 2; ++ci) {
             int c = 0;
             for (int m = lo_m; m <= hi_m; ++m) {
-                if (Jm[m] < j) continue;
-                if (ci && S == 3 && Jm[m] > j) continue;
+                if (Js[m] < j) continue;
+                if (ci && S == 3 && Js[m] > j) continue;
                 ++c;
             }
             cnt[js * 2 + ci] = c;
         }
     }
+}
+
+static size_t schedule_smem(int M, int lm) { return ((size_t)M * (1 + 2 * (size_t)lm)) * sizeof(double) + M * sizeof(int); }
+
+static int schedule_smem_attr(int M, int lm) {
+    MRA_CK(cudaFuncSetAttribute(k_schedule, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schedule_smem(M, lm)));
+    return MRA_OK;
 }
 
 // ------------------------------------------------------------------ screen
@@ -742,8 +761,9 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
     MRA_CK_LAUNCH();
     k_pilot_reduce<<<F.ntrees, 256, 0, st>>>(k3, M, ym, S->dv);
     MRA_CK_LAUNCH();
-    k_schedule<<<F.ntrees, 256, 0, st>>>(M, F.lm, F.nlev, unscreened, op->eps, op->w, op->nF, op->est, S->dv,
-                                         S->sched, S->sl);
+    MRA_TRY(schedule_smem_attr(M, F.lm));
+    k_schedule<<<F.ntrees, 256, schedule_smem(M, F.lm), st>>>(M, F.lm, F.nlev, unscreened, op->eps, op->w, op->nF,
+                                                              op->est, S->dv, S->sched, S->sl);
     MRA_CK_LAUNCH();
 
     ScreenArgs sa;
@@ -1112,7 +1132,9 @@ int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, doubl
     k_pilot<<<1, 128, pilot_smem, st>>>(k, M, op->w, op->F, f->s, dv + 1);
     MRA_CK_LAUNCH();
     const int sl = M + 16 * nlev;
-    k_schedule<<<1, 256, 0, st>>>(M, nlev, nullptr, 0, op->eps, op->w, op->nF, op->est, dv, sched, sl);
+    MRA_TRY(schedule_smem_attr(M, nlev));
+    k_schedule<<<1, 256, schedule_smem(M, nlev), st>>>(M, nlev, nullptr, 0, op->eps, op->w, op->nF, op->est, dv,
+                                                       sched, sl);
     MRA_CK_LAUNCH();
     const Forest F = forest_of_tree(f);
     ScreenArgs sa;

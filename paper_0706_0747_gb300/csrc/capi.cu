@@ -239,8 +239,15 @@ int mra_tree_scale(mra_tree* t, double alpha, void* stream) {
     return tree_scale_impl(t, alpha, (cudaStream_t)stream);
 }
 
+int mra_op_retune(mra_op* op, double mu, void* stream) {
+    if (!op_ok(op)) { set_error("invalid operator handle"); return MRA_EINVAL; }
+    if (!(mu >= 0.0) || !std::isfinite(mu)) { set_error("mu must be finite and >= 0"); return MRA_EINVAL; }
+    return retune_operator(op, mu, (cudaStream_t)stream);
+}
+
 int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, double mu, double eps, int max_level,
-                   const mra_apply_opts* opts, void* stream, mra_tree** phi_next, mra_kalos_info* info) {
+                   const mra_apply_opts* opts, mra_op** op_cache, void* stream, mra_tree** phi_next,
+                   mra_kalos_info* info) {
     if (!phi_next) { set_error("phi_next is NULL"); return MRA_EINVAL; }
     *phi_next = nullptr;
     if (!tree_ok(phi)) { set_error("invalid tree handle"); return MRA_EINVAL; }
@@ -259,13 +266,27 @@ int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, d
             mra_free_op(op);
         }
     } o;
+    if (op_cache && *op_cache && !op_ok(*op_cache)) { set_error("op_cache holds no operator"); return MRA_EINVAL; }
     MRA_TRY(mra_tree_multiply(phi, v, 1.0, stream, &o.P));                          // Step 2
-    MRA_TRY(mra_make_operator(mu * length, 1.0, eps, phi->k, max_level, phi->A.has ? &phi->A.hook : nullptr,
-                              stream, &o.op));
+    mra_op* op = op_cache ? *op_cache : nullptr;
+    int rebuilt = 0;
+    if (!(op && op->k == phi->k && op->eps == eps && op->J == max_level && op->alpha == 1.0 &&
+          retune_operator(op, mu * length, (cudaStream_t)stream) == MRA_OK)) {
+        MRA_TRY(mra_make_operator(mu * length, 1.0, eps, phi->k, max_level, phi->A.has ? &phi->A.hook : nullptr,
+                                  stream, &o.op));
+        rebuilt = 1;
+        if (op_cache) {  // the cache takes the new operator
+            mra_free_op(*op_cache);
+            *op_cache = o.op;
+            o.op = nullptr;
+        }
+    }
+    if (!rebuilt) op = *op_cache;
+    else op = op_cache ? *op_cache : o.op;
     MRA_TRY(mra_compress(o.P, 0, stream));                                          // Step 3
     mra_apply_stats st{};
-    MRA_TRY(mra_apply_ns(o.op, o.P, opts, stream, &o.g, &st));
-    MRA_TRY(mra_reconstruct(o.g, MRA_RECON_ASSEMBLE, 0, 0.0, stream, nullptr));
+    MRA_TRY(mra_apply_ns(op, o.P, opts, stream, &o.g, &st));
+    MRA_TRY(assemble_impl(o.g, (cudaStream_t)stream));  // eq. g_assemble; leaf data only
     MRA_TRY(mra_tree_scale(o.g, -2.0 * length * length, stream));
     double nn = 0.0, pg = 0.0, qg = 0.0;                                            // Step 4
     MRA_TRY(mra_tree_dot(o.g, o.g, stream, &nn));
@@ -281,7 +302,8 @@ int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, d
         info->energy = E;
         info->mu_next = E < 0.0 ? std::sqrt(-2.0 * E) : mu;
         info->norm_new = norm;
-        info->n_terms = o.op->M;
+        info->n_terms = op->M;
+        info->op_rebuilt = rebuilt;
         info->n_items = st.n_items;
         info->ms_apply = st.ms_screen + st.ms_ghost + st.ms_apply;
     }

@@ -128,6 +128,7 @@ struct mra_op {
     // sparse-table range maxima over m of w_m N_F(t1) N_F(t2) N_F(t3) per (j, t)
     double* rmq = nullptr;
     int rmq_L = 0;
+    double gs_A = 0.0, gs_h = 0.0;  // the term grid: s_m = gs_A + (m + 1) gs_h
     mra::Alloc A;
 };
 
@@ -137,6 +138,7 @@ namespace mra {
 // operator.cu
 int launch_filters(int k, double* filt, cudaStream_t st);
 int build_operator(mra_op* op, cudaStream_t st);
+int retune_operator(mra_op* op, double mu, cudaStream_t st);
 
 // tree.cu
 int tree_alloc_arrays(mra_tree* t, int n, bool with_s);

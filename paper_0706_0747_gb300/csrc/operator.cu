@@ -108,7 +108,8 @@ __device__ double kernel_value(double mu, double alpha, double r) {
 // (c, chunk) evaluates candidate base + c on 256 of the 4000 radii, and the
 // per-candidate maxima meet in err_bits (non-negative doubles order like
 // their bit patterns).  k_gs_pick then takes the first candidate in sequence
-// order that passes -- the same choice the sequential search makes.
+// order that passes -- the same choice the sequential search makes.  Blocks of
+// 64 radii spread the FP64 work over many SMs.
 #define GS_CAND 16
 #define GS_NPTS 4000
 #define GS_ITERS 200
@@ -170,7 +171,8 @@ __global__ void __launch_bounds__(256) k_gs_check(double mu, double alpha, doubl
 // outM: M on success; -2 when more than MRA_MAX_TERMS terms are needed first;
 // -1 when no candidate of this batch passes (the host tries the next batch)
 __global__ void k_gs_pick(double mu, double alpha, double eps, const double* par, int base,
-                          const unsigned long long* err_bits, double* w, double* tau, int* outM) {
+                          const unsigned long long* err_bits, double* w, double* tau, int* outM,
+                          double* par_out_h) {
     __shared__ int pick, M;
     const int tid = threadIdx.x;
     const double A = par[0], B = par[1];
@@ -194,10 +196,51 @@ __global__ void k_gs_pick(double mu, double alpha, double eps, const double* par
     __syncthreads();
     if (pick < 0) return;
     const double h = gs_step(par[2], base + pick), Ca = c_alpha_dev(alpha);
+    if (tid == 0) par_out_h[0] = h;
     for (int m = tid; m < M; m += blockDim.x) {
         const double s = A + (m + 1) * h;
         tau[m] = exp(2.0 * s);
         w[m] = h * Ca * exp(-0.25 * mu * mu * exp(-2.0 * s) + (3.0 - 2.0 * alpha) * s);
+    }
+}
+
+// Weights of the term grid s_m = A + (m + 1) h for another mu (tau_m = e^{2 s_m}
+// does not depend on mu), and the sup-norm test of eq. KernelApproxByGaussians
+// for them on the same 4000 radii.
+__global__ void k_gs_weights(double mu, double alpha, double A, double h, int M, double* w) {
+    const double Ca = c_alpha_dev(alpha);
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        const double s = A + (m + 1) * h;
+        w[m] = h * Ca * exp(-0.25 * mu * mu * exp(-2.0 * s) + (3.0 - 2.0 * alpha) * s);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gs_check_grid(double mu, double alpha, double delta, double R, int M,
+                                                       const double* wg, const double* taug,
+                                                       unsigned long long* err_bits) {
+    __shared__ double w[MRA_MAX_TERMS], tau[MRA_MAX_TERMS], red[8];
+    const int tid = threadIdx.x;
+    for (int m = tid; m < M; m += blockDim.x) {
+        w[m] = wg[m];
+        tau[m] = taug[m];
+    }
+    __syncthreads();
+    const double lgd = log(delta), lgR = log(R);
+    double err = 0.0;
+    const int i = blockIdx.x * blockDim.x + tid;
+    if (i < GS_NPTS) {
+        const double r = exp(lgd + i * (lgR - lgd) / (GS_NPTS - 1.0));
+        double sum = 0.0;
+        for (int m = 0; m < M; ++m) sum += w[m] * exp(-tau[m] * r * r);
+        err = fabs(kernel_value(mu, alpha, r) - sum) / kernel_env(alpha, r);
+        if (!(err == err)) err = INFINITY;
+    }
+    for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
+    if ((tid & 31) == 0) red[tid >> 5] = err;
+    __syncthreads();
+    if (tid == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) err = fmax(err, red[q]);
+        atomicMax(err_bits, (unsigned long long)__double_as_longlong(err));
     }
 }
 
@@ -212,30 +255,39 @@ __global__ void k_gs_pick(double mu, double alpha, double eps, const double* par
 // and a block needs only the 2k Gaussian moments G+-_p, each integrated on
 // the Gaussian's own window |u| <= sqrt(46/c) by composite 16-point panels no
 // wider than min(1/4, 1/(2 sqrt c)), c = tau/4^j.
-__global__ void k_xcorr_coeffs(int k, double* C) {
+// grid k^2: block (i, i'); thread (q, g) < (2k, k) evaluates the inner rule's
+// term at x-node q and y-node g; the block then forms Phi+ at the 2k x-nodes
+// and their projections on phi_p.
+__global__ void __launch_bounds__(2 * MRA_MAX_K * MRA_MAX_K) k_xcorr_coeffs(int k, double* C) {
     __shared__ double xk[MRA_MAX_K], wk[MRA_MAX_K], x2[2 * MRA_MAX_K], w2[2 * MRA_MAX_K];
-    const int tid = threadIdx.x, n2 = 2 * k;
+    __shared__ double term[2 * MRA_MAX_K][MRA_MAX_K], phx[2 * MRA_MAX_K];
+    const int tid = threadIdx.x, n2 = 2 * k, e = blockIdx.x;
+    const int i = e / k, ip = e % k;
     if (tid < k) gauss_legendre01_root(k, tid, xk, wk);
     if (tid >= 32 && tid < 32 + n2) gauss_legendre01_root(n2, tid - 32, x2, w2);
     __syncthreads();
-    for (int e = tid; e < k * k; e += blockDim.x) {
-        const int i = e / k, ip = e % k;
-        double c[2 * MRA_MAX_K], pp[2 * MRA_MAX_K], ta[MRA_MAX_K], tb[MRA_MAX_K];
-        for (int p = 0; p < n2; ++p) c[p] = 0.0;
+    if (tid < n2 * k) {
+        const int q = tid / k, g = tid % k;
+        const double x = x2[q], y = (1.0 - x) * xk[g];
+        double ta[MRA_MAX_K], tb[MRA_MAX_K];
+        phi_all(k, x + y, ta);
+        phi_all(k, y, tb);
+        term[q][g] = wk[g] * ta[i] * tb[ip];
+    }
+    __syncthreads();
+    if (tid < n2) {
+        double phi = 0.0;
+        for (int g = 0; g < k; ++g) phi += term[tid][g];
+        phx[tid] = w2[tid] * phi * (1.0 - x2[tid]);
+    }
+    __syncthreads();
+    if (tid < n2) {  // thread p: sum over the x-nodes of phx_q phi_p(x_q)
+        double c = 0.0, pp[2 * MRA_MAX_K];
         for (int q = 0; q < n2; ++q) {
-            const double x = x2[q];
-            double phi = 0.0;
-            for (int g = 0; g < k; ++g) {
-                const double y = (1.0 - x) * xk[g];
-                phi_all(k, x + y, ta);
-                phi_all(k, y, tb);
-                phi += wk[g] * ta[i] * tb[ip];
-            }
-            phi *= 1.0 - x;
-            phi_all(n2, x, pp);
-            for (int p = 0; p < n2; ++p) c[p] += w2[q] * phi * pp[p];
+            phi_all(n2, x2[q], pp);
+            c += phx[q] * pp[tid];
         }
-        for (int p = 0; p < n2; ++p) C[(size_t)e * n2 + p] = c[p];
+        C[(size_t)e * n2 + tid] = c;
     }
 }
 
@@ -416,7 +468,7 @@ int build_operator(mra_op* op, cudaStream_t st) {
     MRA_TRY(tmp.get(&err_bits, GS_CAND));
     MRA_TRY(tmp.get(&C, (size_t)k * k * 2 * k));
     MRA_TRY(launch_filters(k, op->filt, st));
-    k_xcorr_coeffs<<<1, 256, 0, st>>>(k, C);
+    k_xcorr_coeffs<<<k * k, 2 * MRA_MAX_K * MRA_MAX_K, 0, st>>>(k, C);
     MRA_CK_LAUNCH();
     const double delta = op->eps / 10.0, R = sqrt(3.0);
     k_gs_setup<<<1, 32, 0, st>>>(op->mu, op->alpha, op->eps, delta, R, par);
@@ -424,14 +476,21 @@ int build_operator(mra_op* op, cudaStream_t st) {
     int M = -1;
     for (int base = 0; base < GS_ITERS && M == -1; base += GS_CAND) {
         MRA_CK(cudaMemsetAsync(err_bits, 0, GS_CAND * sizeof(unsigned long long), st));
-        k_gs_check<<<dim3(GS_CAND, (GS_NPTS + 255) / 256), 256, 0, st>>>(op->mu, op->alpha, delta, R, par, base,
-                                                                           err_bits);
+        k_gs_check<<<dim3(GS_CAND, (GS_NPTS + 63) / 64), 64, 0, st>>>(op->mu, op->alpha, delta, R, par, base,
+                                                                        err_bits);
         MRA_CK_LAUNCH();
         k_gs_pick<<<1, 256, 0, st>>>(op->mu, op->alpha, op->eps, par, base, err_bits, op->w, op->tau,
-                                     op->scratch_i);
+                                     op->scratch_i, par + 3);
         MRA_CK_LAUNCH();
         MRA_CK(cudaMemcpyAsync(&M, op->scratch_i, sizeof(int), cudaMemcpyDeviceToHost, st));
         MRA_CK(cudaStreamSynchronize(st));
+    }
+    double hpar[4] = {0, 0, 0, 0};
+    if (M > 0) {
+        MRA_CK(cudaMemcpyAsync(hpar, par, sizeof(hpar), cudaMemcpyDeviceToHost, st));
+        MRA_CK(cudaStreamSynchronize(st));
+        op->gs_A = hpar[0];
+        op->gs_h = hpar[3];
     }
     if (M <= 0) {
         set_error("Gaussian-sum construction failed (code %d): more than %d terms or no convergence", M,
@@ -451,6 +510,41 @@ int build_operator(mra_op* op, cudaStream_t st) {
     k_to_float<<<256, 256, 0, st>>>(op->F, op->F32, nF);
     MRA_CK_LAUNCH();
     // C is released with the Scratch (stream-ordered after the launches above)
+    return MRA_OK;
+}
+
+// New weights for mu on op's term grid; the tau-dependent tables (F, F32,
+// nF, est) are kept.  The grid must pass the sup-norm test for the new mu;
+// if it does not, op is left unchanged and MRA_EINVAL is returned.
+int retune_operator(mra_op* op, double mu, cudaStream_t st) {
+    Scratch tmp(op->A);
+    double* w;
+    unsigned long long* err_bits;
+    MRA_TRY(tmp.get(&w, op->M));
+    MRA_TRY(tmp.get(&err_bits, 1));
+    MRA_CK(cudaMemsetAsync(err_bits, 0, sizeof(unsigned long long), st));
+    k_gs_weights<<<(op->M + 127) / 128, 128, 0, st>>>(mu, op->alpha, op->gs_A, op->gs_h, op->M, w);
+    MRA_CK_LAUNCH();
+    const double delta = op->eps / 10.0, R = sqrt(3.0);
+    k_gs_check_grid<<<(GS_NPTS + 63) / 64, 64, 0, st>>>(mu, op->alpha, delta, R, op->M, w, op->tau, err_bits);
+    MRA_CK_LAUNCH();
+    unsigned long long bits = 0;
+    MRA_CK(cudaMemcpyAsync(&bits, err_bits, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaStreamSynchronize(st));
+    double err;
+    memcpy(&err, &bits, sizeof(err));
+    if (!(err <= op->eps)) {
+        set_error("the operator's term grid gives error %.3g > eps = %.3g for mu = %g", err, op->eps, mu);
+        return MRA_EINVAL;
+    }
+    MRA_CK(cudaMemcpyAsync(op->w, w, op->M * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (op->rmq) {  // the per-pair screen tables hold w_m: rebuilt on next use
+        op->A.put(op->rmq);
+        op->rmq = nullptr;
+        op->rmq_L = 0;
+    }
+    op->mu = mu;
+    MRA_CK(cudaStreamSynchronize(st));
     return MRA_OK;
 }
 

@@ -45,7 +45,8 @@ class PotentialC(ctypes.Structure):
 
 class KalosInfo(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("mu_next", ctypes.c_double), ("norm_new", ctypes.c_double),
-                ("n_terms", ctypes.c_int), ("n_items", ctypes.c_int64), ("ms_apply", ctypes.c_float)]
+                ("n_terms", ctypes.c_int), ("op_rebuilt", ctypes.c_int), ("n_items", ctypes.c_int64),
+                ("ms_apply", ctypes.c_float)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -129,7 +130,9 @@ SIGNATURES = {
     "mra_tree_dot": [_P, _P, _P, _DP],
     "mra_tree_scale": [_P, ctypes.c_double, _P],
     "mra_kalos_step": [_P, ctypes.POINTER(PotentialC), ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                       ctypes.c_int, ctypes.POINTER(ApplyOpts), _P, ctypes.POINTER(_P), ctypes.POINTER(KalosInfo)],
+                       ctypes.c_int, ctypes.POINTER(ApplyOpts), ctypes.POINTER(_P), _P, ctypes.POINTER(_P),
+                       ctypes.POINTER(KalosInfo)],
+    "mra_op_retune": [_P, ctypes.c_double, _P],
     "mra_make_operator": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                           ctypes.POINTER(Alloc), _P, ctypes.POINTER(_P)],
     "mra_op_get_info": [_P, ctypes.POINTER(OpInfo)],
@@ -447,15 +450,42 @@ def apply_ns(op, tree, precision="fp64", block_screen=False, unscreened=False, i
     return Tree(h.value), (st.as_dict() if stats else None)
 
 
-def kalos_step(phi, potential, length, mu, eps, max_level, precision="fp64", screen="static", stream=None):
+class OpCache:
+    """An operator handle kept between Kalos steps (mra_kalos_step's
+    op_cache); freed with the object."""
+
+    def __init__(self):
+        self.h = _P()
+
+    def free(self):
+        if self.h.value:
+            lib().mra_free(self.h)
+            self.h = _P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def op_retune(op, mu, stream=None):
+    """mra_op_retune: new weights for mu on op's term grid."""
+    _check(lib().mra_op_retune(op.h, float(mu), _stream(stream)))
+
+
+def kalos_step(phi, potential, length, mu, eps, max_level, precision="fp64", screen="static", op_cache=None,
+               stream=None):
     """mra_kalos_step: one pass of phi = -2 G_mu V phi; returns (phi_next,
-    info dict with energy, mu_next, norm_new, n_terms, n_items, ms_apply)."""
+    info dict with energy, mu_next, norm_new, n_terms, op_rebuilt, n_items,
+    ms_apply).  op_cache: an OpCache reused across steps, or None."""
     v = potential.c_struct()
     o = ApplyOpts(PREC[precision], 0, 0, 0, SCREEN[screen], 2, 0, 0)
     info = KalosInfo()
     h = _P()
     _check(lib().mra_kalos_step(phi.h, ctypes.byref(v), float(length), float(mu), float(eps), int(max_level),
-                                ctypes.byref(o), _stream(stream), ctypes.byref(h), ctypes.byref(info)))
+                                ctypes.byref(o), ctypes.byref(op_cache.h) if op_cache is not None else None,
+                                _stream(stream), ctypes.byref(h), ctypes.byref(info)))
     return Tree(h.value), {f: getattr(info, f) for f, _ in KalosInfo._fields_}
 
 

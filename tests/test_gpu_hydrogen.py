@@ -11,6 +11,7 @@ import math
 import numpy as np
 import pytest
 
+from oracle import gauss_sum as OG
 from oracle import hydrogen as OH
 from oracle import product as OP
 from oracle import tree as OT
@@ -101,6 +102,22 @@ def test_multiply_rejects_bad_potentials():
         assert e.value.code == mra.EINVAL
 
 
+def test_kalos_step_with_cached_operator_matches_fresh():
+    """A step whose operator comes from the cache (re-weighted) against one
+    that builds its own: the same kernel to eps, so the energies agree to
+    about eps."""
+    hc, phi = small_start()
+    g = import_tree(phi, hc.k)
+    pot = mra.Potential(charges=[-1.0 / hc.L], positions=[hc.u0])
+    cache = mra.OpCache()
+    _, i1 = mra.kalos_step(g, pot, hc.L, 0.9 * hc.mu0, hc.eps, hc.max_level, op_cache=cache)
+    _, i2 = mra.kalos_step(g, pot, hc.L, hc.mu0, hc.eps, hc.max_level, op_cache=cache)
+    _, i3 = mra.kalos_step(g, pot, hc.L, hc.mu0, hc.eps, hc.max_level)
+    assert (i1["op_rebuilt"], i2["op_rebuilt"], i3["op_rebuilt"]) == (1, 0, 1)
+    assert abs(i2["energy"] - i3["energy"]) <= 10 * hc.eps * abs(i3["energy"])
+    cache.free()
+
+
 def test_kalos_step_parity_small():
     """One pass of Steps 2-5 on the small case: energy, norm and the next
     iterate against the oracle's kalos_step on the same tree."""
@@ -115,6 +132,47 @@ def test_kalos_step_parity_small():
     assert rel_l2(leaf_blocks(nxt), oracle_leaf_blocks(onxt)) <= 1e-10
 
 
+def test_op_retune_keeps_grid_and_reweights():
+    """mra_op_retune: tau and the tau-only tables are kept bit for bit; w
+    becomes the weights of eq. KernelApproxByGaussians for the new mu on the
+    same grid (the oracle's term formula); the retuned operator applies the
+    same kernel as one built for the new mu (both within eps of it); a mu
+    far below the construction's fails the sup-norm test and leaves op as it
+    was."""
+    eps, k, J = 1e-6, 6, 5
+    op = mra.make_operator(20.0, 1.0, eps, k, J)
+    before = op.export()
+    mra.op_retune(op, 24.0)
+    after = op.export()
+    assert np.array_equal(before["tau"], after["tau"])
+    for key in ("F", "nF", "est"):
+        assert np.array_equal(before[key], after[key]), key
+    s = 0.5 * np.log(after["tau"])
+    h = (s[-1] - s[0]) / (len(s) - 1)
+    w_ref, tau_ref = OG._terms(24.0, 1.0, s[0] - h, h, len(s))
+    assert np.allclose(after["w"], w_ref, rtol=1e-12, atol=0)
+    assert np.allclose(after["tau"], tau_ref, rtol=1e-12, atol=0)
+    assert op.info().mu == 24.0
+    # same kernel as a fresh operator for mu = 24
+    dens = W.Density(np.array([1.0, 0.5]), np.array([300.0, 80.0]), np.array([[0.5, 0.5, 0.5], [0.4, 0.6, 0.5]]),
+                     np.zeros(2))
+    t, _ = mra.build_tree(dens, k, eps, J)
+    mra.compress(t)
+    fresh = mra.make_operator(24.0, 1.0, eps, k, J)
+    outs = []
+    for o in (op, fresh):
+        g, _ = mra.apply_ns(o, t)
+        mra.reconstruct(g, truncate=False)
+        c, l, b, _ = g.export()
+        outs.append({tuple(int(v) for v in cc): bb for cc, ll, bb in zip(c, l, b) if ll})
+    assert rel_l2(outs[0], outs[1]) <= 10 * eps
+    # far below the construction's mu the broad terms are missing
+    with pytest.raises(mra.MraError) as e:
+        mra.op_retune(op, 0.0)
+    assert e.value.code == mra.EINVAL
+    assert np.array_equal(op.export()["w"], after["w"]) and op.info().mu == 24.0
+
+
 @pytest.mark.parametrize("precision", ["fp64", "tc"])
 def test_hydrogen_ground_state_full_size(precision):
     """The full iteration (k = 8, eps = 1e-6, depth 12, L = 32) from
@@ -127,13 +185,16 @@ def test_hydrogen_ground_state_full_size(precision):
     phi = t
     mra.tree_scale(phi, 1.0 / math.sqrt(mra.tree_dot(t, t) * hc.L ** 3))
     pot = mra.Potential(charges=[-1.0 / hc.L], positions=[hc.u0])
-    mu, hist = hc.mu0, []
+    mu, hist, cache, rebuilt = hc.mu0, [], mra.OpCache(), []
     for _ in range(30):
-        phi, info = mra.kalos_step(phi, pot, hc.L, mu, hc.eps, hc.max_level, precision=precision)
+        phi, info = mra.kalos_step(phi, pot, hc.L, mu, hc.eps, hc.max_level, precision=precision, op_cache=cache)
         hist.append((info["energy"], info["norm_new"]))
+        rebuilt.append(info["op_rebuilt"])
         dmu, mu = abs(info["mu_next"] - mu), info["mu_next"]
         if dmu < 1e-7 and abs(info["norm_new"] - 1.0) < 1e-6:
             break
     E, norm = hist[-1]
     assert abs(E + 0.5) <= hc.eps, hist
     assert abs(norm - 1.0) <= 1e-5, hist
+    # mu rises from mu0 toward 1, so the first operator's grid serves every step
+    assert rebuilt[0] == 1 and sum(rebuilt) == 1, rebuilt
