@@ -252,7 +252,72 @@ __global__ void k_dens_scale(DensDev D, double eps, double* tol) {
     for (int g = threadIdx.x; g < D.n; g += blockDim.x)
         m = fmax(m, fabs(dens_eval(D, D.cen[3 * g], D.cen[3 * g + 1], D.cen[3 * g + 2])));
     m = block_max(m, red);
-    if (threadIdx.x == 0) *tol = eps * m;
+    if (threadIdx.x == 0) {
+        tol[0] = eps * m;
+        tol[1] = 1e-18 * m;  // terms below this on a box are skipped (rounding level)
+    }
+}
+
+// Values of the density on the tensor grid X[0][q1] x X[1][q2] x X[2][q3]
+// (k increasing points per direction) added into v[(q1 k + q2) k + q3],
+// block-cooperatively.  Each term factors by direction,
+// exp(-a|x - c|^2) = prod_d exp(-a (x_d - c_d)^2) and |x - c|^2 = sum_d (x_d - c_d)^2,
+// so per term the block forms 3k one-dimensional factors (in shared memory,
+// DG_CHUNK terms at a time) and each grid point costs a few products instead
+// of an exponential.  A term whose bound on the grid's box,
+// (|c| + |b| dmax^2) exp(-a dmin^2), is below `cut` is skipped.
+#define DG_CHUNK 32
+__device__ void dens_grid(const DensDev& D, int k, const double* X, double* v, double* E, double* R,
+                          double* cb, int* act, double cut) {
+    const int k3 = k * k * k, kk = k * k, k3d = 3 * k;
+    __shared__ int nact;
+    for (int g0 = 0; g0 < D.n; g0 += DG_CHUNK) {
+        const int ng = min(DG_CHUNK, D.n - g0);
+        if (threadIdx.x < 32) {  // warp 0: which terms of the chunk reach the box
+            const int g = g0 + threadIdx.x;
+            bool on = false;
+            if ((int)threadIdx.x < ng) {
+                double dmin2 = 0.0, dmax2 = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    const double lo = X[d * k] - D.cen[3 * g + d], hi = X[d * k + k - 1] - D.cen[3 * g + d];
+                    const double dn = lo > 0.0 ? lo : (hi < 0.0 ? -hi : 0.0);
+                    const double dx = fmax(fabs(lo), fabs(hi));
+                    dmin2 += dn * dn;
+                    dmax2 += dx * dx;
+                }
+                on = (fabs(D.coef[g]) + fabs(D.r2[g]) * dmax2) * exp(-D.expo[g] * dmin2) >= cut;
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, on);
+            if (on) {
+                const int slot = __popc(mask & ((1u << threadIdx.x) - 1u));
+                act[slot] = g;
+                cb[2 * slot] = D.coef[g];
+                cb[2 * slot + 1] = D.r2[g];
+            }
+            if (threadIdx.x == 0) nact = __popc(mask);
+        }
+        __syncthreads();
+        const int na = nact;
+        for (int e = threadIdx.x; e < na * k3d; e += blockDim.x) {
+            const int a = e / k3d, d = (e / k) % 3, q = e % k, g = act[a];
+            const double dx = X[d * k + q] - D.cen[3 * g + d];
+            R[e] = dx * dx;
+            E[e] = exp(-D.expo[g] * dx * dx);
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < k3; idx += blockDim.x) {
+            const int q1 = idx / kk, q2 = (idx / k) % k, q3 = idx % k;
+            double acc = v[idx];
+            for (int g = 0; g < na; ++g) {
+                const double* Eg = E + g * k3d;
+                const double* Rg = R + g * k3d;
+                const double prod = Eg[q1] * Eg[k + q2] * Eg[2 * k + q3];
+                acc += (cb[2 * g] + cb[2 * g + 1] * (Rg[q1] + Rg[k + q2] + Rg[2 * k + q3])) * prod;
+            }
+            v[idx] = acc;
+        }
+        __syncthreads();
+    }
 }
 
 // One block per box of level j.  mode: 0 adaptive test, 1 refine, 2 leaf.
@@ -268,7 +333,13 @@ __global__ void k_build_level(int k, int j, DensDev D, const int32_t* boxes, con
     double* t1 = v + k3;
     double* t2 = t1 + k3;
     double* s = t2 + k3;
+    double* X = s + k3;          // 3k grid coordinates
+    double* E = X + 3 * k;       // DG_CHUNK * 3k factors
+    double* R = E + DG_CHUNK * 3 * k;
+    double* cb = R + DG_CHUNK * 3 * k;  // (coef, r2coef) per term of a chunk
     __shared__ double red[32];
+    __shared__ int act[DG_CHUNK];
+    const double cut = tolp[1];
     const int b = blockIdx.x, tid = threadIdx.x;
     const int a1 = boxes[3 * b], a2 = boxes[3 * b + 1], a3 = boxes[3 * b + 2];
     if (tid < k) gauss_legendre01_root(k, tid, g, gw);
@@ -283,11 +354,13 @@ __global__ void k_build_level(int k, int j, DensDev D, const int32_t* boxes, con
         }
     }
     const double h = exp2(-(double)j);
-    for (int idx = tid; idx < k3; idx += blockDim.x) {
-        int q3 = idx % k, q2 = (idx / k) % k, q1 = idx / kk;
-        v[idx] = dens_eval(D, (g[q1] + a1) * h, (g[q2] + a2) * h, (g[q3] + a3) * h);
+    for (int e = tid; e < 3 * k; e += blockDim.x) {
+        const int d = e / k, q = e % k;
+        X[e] = (g[q] + (d == 0 ? a1 : (d == 1 ? a2 : a3))) * h;
     }
+    for (int idx = tid; idx < k3; idx += blockDim.x) v[idx] = 0.0;
     __syncthreads();
+    dens_grid(D, k, X, v, E, R, cb, act, cut);
     // s = 2^{-3j/2} (P x P x P) v  (eq. fvals2coefs in tensor form)
     mode_product(v, t1, P, 2, k);
     mode_product(t1, t2, P, 1, k);
@@ -305,12 +378,15 @@ __global__ void k_build_level(int k, int j, DensDev D, const int32_t* boxes, con
             mode_product(s, t1, Q + p3 * kk, 2, k);
             mode_product(t1, t2, Q + p2 * kk, 1, k);
             mode_product(t2, t1, Q + p1 * kk, 0, k);
-            for (int idx = tid; idx < k3; idx += blockDim.x) {
-                int q3 = idx % k, q2 = (idx / k) % k, q1 = idx / kk;
-                double f = dens_eval(D, (g[q1] + 2 * a1 + p1) * hc, (g[q2] + 2 * a2 + p2) * hc,
-                                     (g[q3] + 2 * a3 + p3) * hc);
-                err = fmax(err, fabs(f - up * t1[idx]));
+            // the child's GL grid, its density values into v
+            for (int e = tid; e < 3 * k; e += blockDim.x) {
+                const int d = e / k, q = e % k;
+                X[e] = (g[q] + (d == 0 ? 2 * a1 + p1 : (d == 1 ? 2 * a2 + p2 : 2 * a3 + p3))) * hc;
             }
+            for (int idx = tid; idx < k3; idx += blockDim.x) v[idx] = 0.0;
+            __syncthreads();
+            dens_grid(D, k, X, v, E, R, cb, act, cut);
+            for (int idx = tid; idx < k3; idx += blockDim.x) err = fmax(err, fabs(v[idx] - up * t1[idx]));
             __syncthreads();
         }
         err = block_max(err, red);
@@ -379,7 +455,7 @@ int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int 
     DensDev D{ng, dd, dd + ng, dd + 2 * ng, dd + 3 * ng};
     double* tol;
     int32_t *flags;  // [0] depth_hit, [1] total
-    MRA_TRY(tmp.get(&tol, 1));
+    MRA_TRY(tmp.get(&tol, 2));
     MRA_TRY(tmp.get(&flags, 4));
     MRA_CK(cudaMemsetAsync(flags, 0, 4 * sizeof(int32_t), st));
     k_dens_scale<<<1, 256, 0, st>>>(D, eps, tol);
@@ -397,7 +473,8 @@ int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int 
     int nb = 1;
     int32_t* cur = boxes0;
     int32_t* plocal_prev = nullptr;
-    const size_t smem = (2 * k + 3 * k * k + 4 * (size_t)k3) * sizeof(double);
+    const size_t smem =
+        (2 * k + 3 * k * k + 4 * (size_t)k3 + 3 * k + 2 * DG_CHUNK * 3 * (size_t)k + 2 * DG_CHUNK) * sizeof(double);
     MRA_CK(cudaFuncSetAttribute(k_build_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int j = 0; j <= max_level; ++j) {
         Level lv{nb, cur, nullptr, nullptr, plocal_prev, nullptr};
