@@ -25,6 +25,9 @@ multiplicative under Kronecker products):
 * the symmetrised 18-term estimate of eq. NormEstimateUsing1DBlocks for a
   3-D coarse shift (L1, L2, L3): the mean over the 6 orderings sigma of
   Nd(s1) NF(s2) NF(s3) + NU(s1) Nd(s2) NF(s3) + NU(s1) NU(s2) Nd(s3).
+* d = 2 (the paper's d = 2 variant): the same telescoping of a product of two
+  factors, F1 F2 - G1 G2 = (F1 - G1) F2 + G1 (F2 - G2), symmetrised over the 2
+  orderings: the mean of Nd(s1) NF(s2) + NU(s1) Nd(s2) over sigma (4 terms).
 
 Parity pins (tests/test_oracle_operator.py): the erf closed form of F_00
 (Phi_00 = 1 - |x|), the transposition/reflection symmetries implied by
@@ -109,14 +112,16 @@ def f_block(pe, j, tau, l):
 class Operator:
     """Operator tables for K_{mu,alpha} at order k on levels 0..max_level."""
 
-    def __init__(self, mu, alpha, eps, k, max_level, delta=None):
+    def __init__(self, mu, alpha, eps, k, max_level, delta=None, d=3):
         if not (1 <= k <= 16):
             raise ValueError("k must be in [1, 16]")
         if max_level < 0:
             raise ValueError("max_level must be >= 0")
+        if d not in (2, 3):
+            raise ValueError("d must be 2 or 3")
         self.mu, self.alpha, self.eps, self.k = float(mu), float(alpha), float(eps), int(k)
-        self.max_level = int(max_level)
-        self.w, self.tau = gauss_sum.gaussian_sum(mu, alpha, eps, delta=delta)
+        self.max_level, self.d = int(max_level), int(d)
+        self.w, self.tau = gauss_sum.gaussian_sum(mu, alpha, eps, delta=delta, d=d)
         self.M = len(self.w)
         self.H0, self.H1 = basis.two_scale_H(k)
         self.U = np.vstack([self.H0.T, self.H1.T])          # 2k x k
@@ -143,12 +148,12 @@ class Operator:
                     self.NFF[j, m, L + 1] = np.linalg.norm(FF)
                     self.NUF[j, m, L + 1] = np.linalg.norm(Fc)
                     self.NdF[j, m, L + 1] = np.linalg.norm(FF - UP)
-        # max over the coarse core L in {-1,0,1}^3 of the 18-term estimate
+        # max over the coarse core L in {-1,0,1}^d of the estimate
         self.est_core = np.zeros((J + 1, self.M))
         for j in range(1, J + 1):
             for m in range(self.M):
                 best = 0.0
-                for Ls in itertools.product(range(3), repeat=3):
+                for Ls in itertools.product(range(3), repeat=self.d):
                     best = max(best, self.estimate(j, m, Ls))
                 self.est_core[j, m] = best
 
@@ -159,6 +164,10 @@ class Operator:
         NF = self.NFF[j, m]
         NU = self.NUF[j, m]
         tot = 0.0
+        if len(Lidx) == 2:   # d = 2: two factors, two orderings
+            for a, b in itertools.permutations(Lidx):
+                tot += Nd[a] * NF[b] + NU[a] * Nd[b]
+            return tot / 2.0
         for s in itertools.permutations(Lidx):
             a, b, c = s
             tot += (Nd[a] * NF[b] * NF[c] + NU[a] * Nd[b] * NF[c] + NU[a] * NU[b] * Nd[c])
