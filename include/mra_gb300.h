@@ -63,6 +63,7 @@ extern "C" {
 typedef struct mra_tree mra_tree;
 typedef struct mra_op mra_op;
 typedef struct mra_mlp mra_mlp;
+typedef struct mra_tree2 mra_tree2;
 
 /* Device allocator hook: alloc returns device memory of `bytes` usable on
  * `stream` (NULL on failure); free releases it.  ctx is passed through. */
@@ -593,6 +594,70 @@ typedef struct {
 int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, double mu, double eps,
                    int max_level, const mra_apply_opts* opts, mra_op** op_cache, void* stream,
                    mra_tree** phi_next, mra_kalos_info* info);
+
+/* ------------------------------------------------------------------------ */
+/* The d = 2 variant.  The paper implemented the apply for d = 2 and d = 3
+ * (Sec. 6) and illustrates Algorithm 3 for d = 2; in d = 2 the band
+ * translations fall into three subsets, Core / Boundary-1 / Boundary-2 (Sec. 4).
+ * Functions on the unit square: a mra_tree2 holds k x k blocks in the basis
+ * phi^j_{i1,a1}(x1) phi^j_{i2,a2}(x2), nodes sorted by level then 2-D Morton key
+ * (bit 2b+1 from a1, bit 2b from a2), the 4 children of an internal node
+ * contiguous in quadrant order (p1 p2) = 00, 01, 10, 11.  Handles are released
+ * with mra_free (or mra_free_tree2); the conventions of the d = 3 calls hold. */
+
+/* Algorithm 1 in d = 2.  f->center_host holds 2 numbers per term (x, y); the
+ * other fields as in mra_build_tree.  Errors as mra_build_tree. */
+int mra_build_tree2(const mra_density* f, int k, double eps, int max_level, int uniform_level,
+                    int init_level, const mra_alloc* alloc, void* stream, mra_tree2** out);
+
+/* A d = 2 tree from host arrays: coords_host 3n int32 rows (j, a1, a2) sorted
+ * by level then key, leaf_host n flags, blocks_host n k^2 doubles.  The node set
+ * must be a complete quadtree rooted at (0, 0, 0).  Synchronous. */
+int mra_tree2_import(int k, int n, const int32_t* coords_host, const int32_t* leaf_host,
+                     const double* blocks_host, const mra_alloc* alloc, void* stream, mra_tree2** out);
+
+/* Copy coords (3n), leaf flags (n), blocks (n k^2) and wavelet norms (n) to host
+ * (any pointer may be NULL).  Synchronous. */
+int mra_tree2_export(const mra_tree2* t, int32_t* coords_host, int32_t* leaf_host, double* blocks_host,
+                     double* dnorm_host, void* stream);
+int mra_tree2_get_info(const mra_tree2* t, mra_tree_info* info);
+
+/* Redundant tree in d = 2: every internal node receives s^j and the norm of its
+ * three wavelet blocks from the (2k)^2 square of its 4 children, W sq W^T
+ * (eqs. decomp_scaling / decomp_wavelet).  In place; state MRA_TREE_REDUNDANT. */
+int mra_compress2(mra_tree2* t, void* stream);
+
+/* The operator K_{mu,alpha} in R^2: the Gaussian sum of the integral
+ * representation (eq. IntegralRepr with pi^{-1} in C_alpha and exponent
+ * (2 - 2 alpha) s; sup test relative to K_{0,alpha}(r) = C_alpha Gamma(1 - alpha)
+ * / (2 r^{2 - 2 alpha}) on [delta, sqrt 2]); the 1-D blocks F^{j;m,l} and norms
+ * as in d = 3; the estimate of eq. NormEstimateUsing1DBlocks for two factors
+ * (the mean of N_dif N_F + N_upF N_dif over both orderings).  alpha = 1/2,
+ * mu = 0 gives 1/(2 pi r).  Errors: MRA_EINVAL for alpha outside (0, 1) and as
+ * mra_make_operator.  The operator is usable only with mra_apply_ns2. */
+int mra_make_operator2(double mu, double alpha, double eps, int k, int max_level, const mra_alloc* alloc,
+                       void* stream, mra_op** out);
+
+/* Algorithm 3 in d = 2 (FP64): for every node a of the compressed input (the
+ * output skeleton), every translation t of the parity band whose input box
+ * lies in [0, 2^j)^2 and every kept term m,
+ *     ghat^j_a += w_m F^{j;m,t1} f^j_{a-t} (F^{j;m,t2})^T,
+ * with J_m, the subsets S = number of |t_d| <= 1 (0, 1, 2) and their ranges
+ * trimmed while the cumulative w_m prod_d max N_F stays <= eta / 72; a missing
+ * input block is refined from its ancestor leaf (Step 2, d = 0).  f must be
+ * MRA_TREE_REDUNDANT; the result is a new MRA_TREE_NSFORM tree on f's
+ * skeleton.  stats (optional): n_pairs, n_items, n_ghosts (Step-2 refinements
+ * made), eta, sigma, fnorm, ms_apply.  Synchronous.  Errors: MRA_EINVAL for a
+ * d = 3 operator, k mismatch or a tree deeper than the operator. */
+int mra_apply_ns2(const mra_op* op, const mra_tree2* f, void* stream, mra_tree2** g_ns,
+                  mra_apply_stats* stats);
+
+/* eq. g_assemble, compress and (truncate != 0) the merge of leaf siblings whose
+ * parent has ||d|| < eps ||g|| / sqrt(N) (Algorithm 3, Step 4), as
+ * mra_reconstruct(MRA_RECON_ASSEMBLE) in d = 3.  t must be MRA_TREE_NSFORM. */
+int mra_reconstruct2(mra_tree2* t, int truncate, double eps, void* stream, double* truncation_l2_host);
+
+int mra_free_tree2(mra_tree2* t);
 
 /* Free any handle of this library -- a tree, operator, plan or network --
  * exactly once (NULL is ignored).  The kind is read from the tag every handle

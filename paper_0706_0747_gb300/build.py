@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmra_gb300.so")
-SOURCES = ["capi.cu", "operator.cu", "tree.cu", "apply.cu", "apply_fact.cu", "apply_tc.cu", "apply_tc3.cu", "plan.cu", "mlp.cu", "schedule.cu", "product.cu"]
+SOURCES = ["capi.cu", "operator.cu", "tree.cu", "apply.cu", "apply_fact.cu", "apply_tc.cu", "apply_tc3.cu", "plan.cu", "mlp.cu", "schedule.cu", "product.cu", "d2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(HERE, "..", "include")]

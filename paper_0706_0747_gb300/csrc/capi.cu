@@ -270,7 +270,7 @@ int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, d
     MRA_TRY(mra_tree_multiply(phi, v, 1.0, stream, &o.P));                          // Step 2
     mra_op* op = op_cache ? *op_cache : nullptr;
     int rebuilt = 0;
-    if (!(op && op->k == phi->k && op->eps == eps && op->J == max_level && op->alpha == 1.0 &&
+    if (!(op && op->d == 3 && op->k == phi->k && op->eps == eps && op->J == max_level && op->alpha == 1.0 &&
           retune_operator(op, mu * length, (cudaStream_t)stream) == MRA_OK)) {
         MRA_TRY(mra_make_operator(mu * length, 1.0, eps, phi->k, max_level, phi->A.has ? &phi->A.hook : nullptr,
                                   stream, &o.op));
@@ -318,12 +318,13 @@ int mra_compress(mra_tree* t, int store_d, void* stream) {
     return compress_impl(t, store_d, (cudaStream_t)stream);
 }
 
-int mra_make_operator(double mu, double alpha, double eps, int k, int max_level, const mra_alloc* alloc, void* stream,
-                      mra_op** out) {
+// the operator in R^d (d = 3; d = 2 for the two-dimensional variant)
+static int make_operator_d(int d, double mu, double alpha, double eps, int k, int max_level, const mra_alloc* alloc,
+                           void* stream, mra_op** out) {
     if (!out) { set_error("out is NULL"); return MRA_EINVAL; }
     *out = nullptr;
     if (!(mu >= 0.0)) { set_error("mu must be >= 0"); return MRA_EINVAL; }
-    if (!(alpha > 0.0 && alpha < 1.5)) { set_error("alpha must lie in (0, 3/2)"); return MRA_EINVAL; }
+    if (!(alpha > 0.0 && alpha < 0.5 * d)) { set_error("alpha must lie in (0, %d/2)", d); return MRA_EINVAL; }
     if (!(eps > 0.0 && eps <= 0.5)) { set_error("eps must lie in (0, 0.5]"); return MRA_EINVAL; }
     if (k < 1 || k > MRA_MAX_K) { set_error("k=%d outside [1, %d]", k, MRA_MAX_K); return MRA_EINVAL; }
     if (max_level < 0 || max_level > MRA_MAX_LEVEL) { set_error("max_level outside [0, %d]", MRA_MAX_LEVEL); return MRA_EINVAL; }
@@ -334,6 +335,7 @@ int mra_make_operator(double mu, double alpha, double eps, int k, int max_level,
     op->mu = mu;
     op->alpha = alpha;
     op->eps = eps;
+    op->d = d;
     op->A = make_alloc(alloc, stream);
     int rc = build_operator(op, (cudaStream_t)stream);
     if (rc == MRA_OK) {
@@ -346,6 +348,21 @@ int mra_make_operator(double mu, double alpha, double eps, int k, int max_level,
     }
     *out = op;
     return MRA_OK;
+}
+
+int mra_make_operator(double mu, double alpha, double eps, int k, int max_level, const mra_alloc* alloc, void* stream,
+                      mra_op** out) {
+    return make_operator_d(3, mu, alpha, eps, k, max_level, alloc, stream, out);
+}
+
+int mra_make_operator2(double mu, double alpha, double eps, int k, int max_level, const mra_alloc* alloc,
+                       void* stream, mra_op** out) {
+    if (!(alpha < 1.0)) {
+        if (out) *out = nullptr;
+        set_error("the d = 2 operator needs alpha in (0, 1)");
+        return MRA_EINVAL;
+    }
+    return make_operator_d(2, mu, alpha, eps, k, max_level, alloc, stream, out);
 }
 
 int mra_op_get_info(const mra_op* op, mra_op_info* info) {
@@ -378,17 +395,20 @@ int mra_apply_ns(const mra_op* op, const mra_tree* f, const mra_apply_opts* opts
     if (!g_ns) { set_error("g_ns is NULL"); return MRA_EINVAL; }
     *g_ns = nullptr;
     if (!op_ok(op) || !tree_ok(f)) { set_error("invalid operator or tree handle"); return MRA_EINVAL; }
+    if (op->d != 3) { set_error("the operator is for d = 2 (use the d = 2 entry points)"); return MRA_EINVAL; }
     return apply_impl(op, f, opts, (cudaStream_t)stream, g_ns, stats);
 }
 
 int mra_apply_ns_noalloc(const mra_op* op, const mra_tree* f, int precision, double* ghat_out, void* stream,
                          int64_t* n_items_host) {
     if (!op_ok(op) || !tree_ok(f)) { set_error("invalid operator or tree handle"); return MRA_EINVAL; }
+    if (op->d != 3) { set_error("the operator is for d = 2 (use the d = 2 entry points)"); return MRA_EINVAL; }
     return apply_noalloc_impl(op, f, precision, ghat_out, (cudaStream_t)stream, n_items_host);
 }
 
 int mra_screen_data(const mra_op* op, const mra_tree* f, float* inputs, float* targets, void* stream) {
     if (!op_ok(op) || !tree_ok(f)) { set_error("invalid operator or tree handle"); return MRA_EINVAL; }
+    if (op->d != 3) { set_error("the operator is for d = 2 (use the d = 2 entry points)"); return MRA_EINVAL; }
     return screen_data_impl(op, f, inputs, targets, (cudaStream_t)stream);
 }
 
@@ -430,6 +450,7 @@ int mra_free(void* handle) {
     memcpy(&tag, handle, sizeof(tag));  // every handle type starts with its tag
     switch (tag) {
         case MRA_TREE_MAGIC: return mra_free_tree((mra_tree*)handle);
+        case MRA_TREE2_MAGIC: return mra_free_tree2((mra_tree2*)handle);
         case MRA_OP_MAGIC: return mra_free_op((mra_op*)handle);
         case MRA_PLAN_MAGIC: return mra_free_plan((mra_plan*)handle);
         case MRA_MLP_MAGIC: return mra_mlp_free((mra_mlp*)handle);

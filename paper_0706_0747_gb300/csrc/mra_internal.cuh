@@ -14,6 +14,7 @@
 #define MRA_OP_MAGIC 0x4f504552u    // "OPER"
 #define MRA_PLAN_MAGIC 0x504c414eu  // "PLAN"
 #define MRA_MLP_MAGIC 0x4d4c5030u   // "MLP0"
+#define MRA_TREE2_MAGIC 0x54524532u // "TRE2"
 
 namespace mra {
 
@@ -112,9 +113,27 @@ struct mra_tree {
     mra::Alloc A;
 };
 
+// A tree of the d = 2 variant: nodes sorted by (level, 2-D Morton key), the 4
+// children of an internal node contiguous in quadrant order, blocks k x k.
+struct mra_tree2 {
+    uint32_t magic;
+    int k, n, nlev, state, depth_hit;
+    int off[MRA_MAX_LEVEL + 2];
+    uint64_t* key = nullptr;
+    int32_t* coord = nullptr;   // (j, a1, a2) per node
+    int32_t* leaf = nullptr;
+    int32_t* child = nullptr;   // first of the 4 children, or -1
+    int32_t* parent = nullptr;  // -1 for the root
+    double* s = nullptr;        // n * k^2
+    double* dnorm = nullptr;    // n
+    double* filt = nullptr;     // H0, H1, W
+    mra::Alloc A;
+};
+
 struct mra_op {
     uint32_t magic;
     int k, J, M;  // J = max_level
+    int d = 3;    // dimension of the kernel: 3, or 2 for the two-dimensional variant
     double mu, alpha, eps;
     double* w = nullptr;      // M
     double* tau = nullptr;    // M
@@ -147,6 +166,7 @@ int tree_link_and_upload(mra_tree* t, const int32_t* coords_host, const int32_t*
 int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int uniform_level,
                     int init_level, const Alloc& A, mra_tree** out);
 int compress_impl(mra_tree* t, int store_d, cudaStream_t st);
+int scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* total, cudaStream_t st);
 int inverse_impl(mra_tree* t, cudaStream_t st);
 int assemble_impl(mra_tree* t, cudaStream_t st);
 int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host);

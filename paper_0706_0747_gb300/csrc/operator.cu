@@ -78,28 +78,32 @@ int launch_filters(int k, double* filt, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------- Gaussian sum
-__device__ double c_alpha_dev(double alpha) {
-    return 2.0 * exp2(-2.0 * alpha) * pow(3.14159265358979323846, -1.5) / tgamma(alpha);
+// In R^d (d = 3, and d = 2 for the two-dimensional variant) the integral
+// representation has C_alpha = 2 * 2^{-2 alpha} pi^{-d/2} / Gamma(alpha) and the
+// exponent (d - 2 alpha) s; the mu = 0 kernel is C_alpha Gamma(d/2 - alpha) /
+// (2 r^{d - 2 alpha}).
+__device__ double c_alpha_dev(double alpha, int d) {
+    return 2.0 * exp2(-2.0 * alpha) * pow(3.14159265358979323846, -0.5 * d) / tgamma(alpha);
 }
 
-__device__ double kernel_env(double alpha, double r) {  // K_{0,alpha}(r)
-    return tgamma(1.5 - alpha) * c_alpha_dev(alpha) / (2.0 * pow(r, 3.0 - 2.0 * alpha));
+__device__ double kernel_env(double alpha, double r, int d) {  // K_{0,alpha}(r)
+    return tgamma(0.5 * d - alpha) * c_alpha_dev(alpha, d) / (2.0 * pow(r, d - 2.0 * alpha));
 }
 
-// K_{mu,alpha}(r): closed forms for mu = 0 and for alpha = 1; otherwise the
+// K_{mu,alpha}(r): closed forms for mu = 0 and (d = 3) alpha = 1; otherwise the
 // integral representation (eq. IntegralRepr) by a trapezoid of step 0.02 over
 // the window where the integrand exceeds e^-50 (its error decays like
 // exp(-pi^2 / (2 * 0.02))).
-__device__ double kernel_value(double mu, double alpha, double r) {
-    if (mu == 0.0) return kernel_env(alpha, r);
-    if (alpha == 1.0) return exp(-mu * r) / (4.0 * 3.14159265358979323846 * r);
+__device__ double kernel_value(double mu, double alpha, double r, int d) {
+    if (mu == 0.0) return kernel_env(alpha, r, d);
+    if (alpha == 1.0 && d == 3) return exp(-mu * r) / (4.0 * 3.14159265358979323846 * r);
     double s_hi = 0.5 * log(50.0 / (r * r)) + 1.0;
     double s_lo = 0.5 * log(mu * mu / 200.0) - 1.0;
     const double hq = 0.02;
     double acc = 0.0;
     for (double s = s_lo; s <= s_hi; s += hq)
-        acc += exp(-r * r * exp(2.0 * s) - 0.25 * mu * mu * exp(-2.0 * s) + (3.0 - 2.0 * alpha) * s);
-    return c_alpha_dev(alpha) * hq * acc;
+        acc += exp(-r * r * exp(2.0 * s) - 0.25 * mu * mu * exp(-2.0 * s) + (d - 2.0 * alpha) * s);
+    return c_alpha_dev(alpha, d) * hq * acc;
 }
 
 // The step h shrinks by 3 % until the sup-norm test passes (the sequence
@@ -115,10 +119,10 @@ __device__ double kernel_value(double mu, double alpha, double r) {
 #define GS_ITERS 200
 
 // par = {A, B, h0}
-__global__ void k_gs_setup(double mu, double alpha, double eps, double delta, double R, double* par) {
+__global__ void k_gs_setup(double mu, double alpha, double eps, double delta, double R, int d, double* par) {
     if (threadIdx.x != 0) return;
-    const double L = log(1.0 / eps), q = 3.0 - 2.0 * alpha;
-    double A = log(0.1 * eps * q * tgamma(1.5 - alpha) / (2.0 * pow(R, q))) / q;
+    const double L = log(1.0 / eps), q = d - 2.0 * alpha;
+    double A = log(0.1 * eps * q * tgamma(0.5 * q) / (2.0 * pow(R, q))) / q;
     if (mu > 0.0) A = fmax(A, -0.5 * log(4.0 * (L + 10.0) / (mu * mu)));
     par[0] = A;
     par[1] = 0.5 * log((L + 5.0) / (delta * delta));
@@ -131,8 +135,8 @@ __device__ inline double gs_step(double h0, int n) {
     return h;
 }
 
-__global__ void __launch_bounds__(256) k_gs_check(double mu, double alpha, double delta, double R, const double* par,
-                                                  int base, unsigned long long* err_bits) {
+__global__ void __launch_bounds__(256) k_gs_check(double mu, double alpha, double delta, double R, int d,
+                                                  const double* par, int base, unsigned long long* err_bits) {
     __shared__ double w[MRA_MAX_TERMS], tau[MRA_MAX_TERMS], red[8];
     const int c = blockIdx.x, tid = threadIdx.x;
     if (base + c >= GS_ITERS) return;
@@ -142,11 +146,11 @@ __global__ void __launch_bounds__(256) k_gs_check(double mu, double alpha, doubl
         if (tid == 0) atomicMax(&err_bits[c], (unsigned long long)__double_as_longlong(INFINITY));
         return;
     }
-    const double Ca = c_alpha_dev(alpha);
+    const double Ca = c_alpha_dev(alpha, d);
     for (int m = tid; m < M; m += blockDim.x) {
         const double s = A + (m + 1) * h;
         tau[m] = exp(2.0 * s);
-        w[m] = h * Ca * exp(-0.25 * mu * mu * exp(-2.0 * s) + (3.0 - 2.0 * alpha) * s);
+        w[m] = h * Ca * exp(-0.25 * mu * mu * exp(-2.0 * s) + (d - 2.0 * alpha) * s);
     }
     __syncthreads();
     const double lgd = log(delta), lgR = log(R);
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(256) k_gs_check(double mu, double alpha, doubl
         const double r = exp(lgd + i * (lgR - lgd) / (GS_NPTS - 1.0));
         double sum = 0.0;
         for (int m = 0; m < M; ++m) sum += w[m] * exp(-tau[m] * r * r);
-        err = fabs(kernel_value(mu, alpha, r) - sum) / kernel_env(alpha, r);
+        err = fabs(kernel_value(mu, alpha, r, d) - sum) / kernel_env(alpha, r, d);
         if (!(err == err)) err = INFINITY;  // a NaN fails the test
     }
     for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__(256) k_gs_check(double mu, double alpha, doubl
 
 // outM: M on success; -2 when more than MRA_MAX_TERMS terms are needed first;
 // -1 when no candidate of this batch passes (the host tries the next batch)
-__global__ void k_gs_pick(double mu, double alpha, double eps, const double* par, int base,
+__global__ void k_gs_pick(double mu, double alpha, double eps, int d, const double* par, int base,
                           const unsigned long long* err_bits, double* w, double* tau, int* outM,
                           double* par_out_h) {
     __shared__ int pick, M;
@@ -195,27 +199,27 @@ __global__ void k_gs_pick(double mu, double alpha, double eps, const double* par
     }
     __syncthreads();
     if (pick < 0) return;
-    const double h = gs_step(par[2], base + pick), Ca = c_alpha_dev(alpha);
+    const double h = gs_step(par[2], base + pick), Ca = c_alpha_dev(alpha, d);
     if (tid == 0) par_out_h[0] = h;
     for (int m = tid; m < M; m += blockDim.x) {
         const double s = A + (m + 1) * h;
         tau[m] = exp(2.0 * s);
-        w[m] = h * Ca * exp(-0.25 * mu * mu * exp(-2.0 * s) + (3.0 - 2.0 * alpha) * s);
+        w[m] = h * Ca * exp(-0.25 * mu * mu * exp(-2.0 * s) + (d - 2.0 * alpha) * s);
     }
 }
 
 // Weights of the term grid s_m = A + (m + 1) h for another mu (tau_m = e^{2 s_m}
 // does not depend on mu), and the sup-norm test of eq. KernelApproxByGaussians
 // for them on the same 4000 radii.
-__global__ void k_gs_weights(double mu, double alpha, double A, double h, int M, double* w) {
-    const double Ca = c_alpha_dev(alpha);
+__global__ void k_gs_weights(double mu, double alpha, int d, double A, double h, int M, double* w) {
+    const double Ca = c_alpha_dev(alpha, d);
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
         const double s = A + (m + 1) * h;
-        w[m] = h * Ca * exp(-0.25 * mu * mu * exp(-2.0 * s) + (3.0 - 2.0 * alpha) * s);
+        w[m] = h * Ca * exp(-0.25 * mu * mu * exp(-2.0 * s) + (d - 2.0 * alpha) * s);
     }
 }
 
-__global__ void __launch_bounds__(256) k_gs_check_grid(double mu, double alpha, double delta, double R, int M,
+__global__ void __launch_bounds__(256) k_gs_check_grid(double mu, double alpha, double delta, double R, int d, int M,
                                                        const double* wg, const double* taug,
                                                        unsigned long long* err_bits) {
     __shared__ double w[MRA_MAX_TERMS], tau[MRA_MAX_TERMS], red[8];
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(256) k_gs_check_grid(double mu, double alpha, 
         const double r = exp(lgd + i * (lgR - lgd) / (GS_NPTS - 1.0));
         double sum = 0.0;
         for (int m = 0; m < M; ++m) sum += w[m] * exp(-tau[m] * r * r);
-        err = fabs(kernel_value(mu, alpha, r) - sum) / kernel_env(alpha, r);
+        err = fabs(kernel_value(mu, alpha, r, d) - sum) / kernel_env(alpha, r, d);
         if (!(err == err)) err = INFINITY;
     }
     for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
@@ -386,7 +390,7 @@ __device__ inline double warp_sum(double v) {
     return v;
 }
 
-__global__ void k_norms(int k, int M, const double* F, const double* filt, double* nF, double* est) {
+__global__ void k_norms(int k, int M, int d, const double* F, const double* filt, double* nF, double* est) {
     __shared__ double R[2][MRA_MAX_K * MRA_MAX_K];  // F^{j-1;L} H^(q)
     const int m = blockIdx.x, j = blockIdx.y, lane = threadIdx.x;
     const int kk = k * k;
@@ -431,8 +435,17 @@ __global__ void k_norms(int k, int M, const double* F, const double* filt, doubl
         NU[L + 1] = sqrt(warp_sum(nu));
     }
     if (lane != 0) return;
-    const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
     double best = 0.0;
+    if (d == 2) {  // two factors: F1 F2 - G1 G2 = (F1 - G1) F2 + G1 (F2 - G2), both orderings
+        for (int L1 = 0; L1 < 3; ++L1)
+            for (int L2 = 0; L2 < 3; ++L2) {
+                const double tot = Nd[L1] * NF[L2] + NU[L1] * Nd[L2] + Nd[L2] * NF[L1] + NU[L2] * Nd[L1];
+                best = fmax(best, tot / 2.0);
+            }
+        est[(size_t)j * M + m] = best;
+        return;
+    }
+    const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
     for (int L1 = 0; L1 < 3; ++L1)
         for (int L2 = 0; L2 < 3; ++L2)
             for (int L3 = 0; L3 < 3; ++L3) {
@@ -470,16 +483,16 @@ int build_operator(mra_op* op, cudaStream_t st) {
     MRA_TRY(launch_filters(k, op->filt, st));
     k_xcorr_coeffs<<<k * k, 2 * MRA_MAX_K * MRA_MAX_K, 0, st>>>(k, C);
     MRA_CK_LAUNCH();
-    const double delta = op->eps / 10.0, R = sqrt(3.0);
-    k_gs_setup<<<1, 32, 0, st>>>(op->mu, op->alpha, op->eps, delta, R, par);
+    const double delta = op->eps / 10.0, R = sqrt((double)op->d);
+    k_gs_setup<<<1, 32, 0, st>>>(op->mu, op->alpha, op->eps, delta, R, op->d, par);
     MRA_CK_LAUNCH();
     int M = -1;
     for (int base = 0; base < GS_ITERS && M == -1; base += GS_CAND) {
         MRA_CK(cudaMemsetAsync(err_bits, 0, GS_CAND * sizeof(unsigned long long), st));
-        k_gs_check<<<dim3(GS_CAND, (GS_NPTS + 63) / 64), 64, 0, st>>>(op->mu, op->alpha, delta, R, par, base,
-                                                                        err_bits);
+        k_gs_check<<<dim3(GS_CAND, (GS_NPTS + 63) / 64), 64, 0, st>>>(op->mu, op->alpha, delta, R, op->d, par,
+                                                                        base, err_bits);
         MRA_CK_LAUNCH();
-        k_gs_pick<<<1, 256, 0, st>>>(op->mu, op->alpha, op->eps, par, base, err_bits, op->w, op->tau,
+        k_gs_pick<<<1, 256, 0, st>>>(op->mu, op->alpha, op->eps, op->d, par, base, err_bits, op->w, op->tau,
                                      op->scratch_i, par + 3);
         MRA_CK_LAUNCH();
         MRA_CK(cudaMemcpyAsync(&M, op->scratch_i, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -505,7 +518,7 @@ int build_operator(mra_op* op, cudaStream_t st) {
     MRA_TRY(dalloc(A, &op->est, (size_t)(J + 1) * M));
     k_ftable<<<dim3(7, M, J + 1), FT_THREADS, 0, st>>>(k, M, op->tau, C, op->F);
     MRA_CK_LAUNCH();
-    k_norms<<<dim3(M, J + 1), 32, 0, st>>>(k, M, op->F, op->filt, op->nF, op->est);
+    k_norms<<<dim3(M, J + 1), 32, 0, st>>>(k, M, op->d, op->F, op->filt, op->nF, op->est);
     MRA_CK_LAUNCH();
     k_to_float<<<256, 256, 0, st>>>(op->F, op->F32, nF);
     MRA_CK_LAUNCH();
@@ -523,10 +536,11 @@ int retune_operator(mra_op* op, double mu, cudaStream_t st) {
     MRA_TRY(tmp.get(&w, op->M));
     MRA_TRY(tmp.get(&err_bits, 1));
     MRA_CK(cudaMemsetAsync(err_bits, 0, sizeof(unsigned long long), st));
-    k_gs_weights<<<(op->M + 127) / 128, 128, 0, st>>>(mu, op->alpha, op->gs_A, op->gs_h, op->M, w);
+    k_gs_weights<<<(op->M + 127) / 128, 128, 0, st>>>(mu, op->alpha, op->d, op->gs_A, op->gs_h, op->M, w);
     MRA_CK_LAUNCH();
-    const double delta = op->eps / 10.0, R = sqrt(3.0);
-    k_gs_check_grid<<<(GS_NPTS + 63) / 64, 64, 0, st>>>(mu, op->alpha, delta, R, op->M, w, op->tau, err_bits);
+    const double delta = op->eps / 10.0, R = sqrt((double)op->d);
+    k_gs_check_grid<<<(GS_NPTS + 63) / 64, 64, 0, st>>>(mu, op->alpha, delta, R, op->d, op->M, w, op->tau,
+                                                         err_bits);
     MRA_CK_LAUNCH();
     unsigned long long bits = 0;
     MRA_CK(cudaMemcpyAsync(&bits, err_bits, sizeof(bits), cudaMemcpyDeviceToHost, st));

@@ -284,6 +284,7 @@ int mra_plan_create(const mra_op* op, mra_tree* const* trees, int ntrees, const 
     if (!out) { set_error("out is NULL"); return MRA_EINVAL; }
     *out = nullptr;
     if (!op || op->magic != MRA_OP_MAGIC) { set_error("invalid operator handle"); return MRA_EINVAL; }
+    if (op->d != 3) { set_error("the operator is for d = 2"); return MRA_EINVAL; }
     if (!trees || ntrees < 1 || ntrees >= (1 << 22)) { set_error("ntrees must lie in [1, 2^22)"); return MRA_EINVAL; }
     const int prec = opts ? opts->precision : (op->k <= 8 ? MRA_PREC_TC_SPLIT : MRA_PREC_FP64);
     if (prec != MRA_PREC_FP64 && prec != MRA_PREC_FP32 && prec != MRA_PREC_TC_SPLIT && prec != MRA_PREC_TC_LADDER &&

@@ -133,6 +133,18 @@ SIGNATURES = {
                        ctypes.c_int, ctypes.POINTER(ApplyOpts), ctypes.POINTER(_P), _P, ctypes.POINTER(_P),
                        ctypes.POINTER(KalosInfo)],
     "mra_op_retune": [_P, ctypes.c_double, _P],
+    "mra_build_tree2": [ctypes.POINTER(Density), ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                        ctypes.c_int, ctypes.POINTER(Alloc), _P, ctypes.POINTER(_P)],
+    "mra_tree2_import": [ctypes.c_int, ctypes.c_int, _I32P, _I32P, _DP, ctypes.POINTER(Alloc), _P,
+                         ctypes.POINTER(_P)],
+    "mra_tree2_export": [_P, _I32P, _I32P, _DP, _DP, _P],
+    "mra_tree2_get_info": [_P, ctypes.POINTER(TreeInfo)],
+    "mra_compress2": [_P, _P],
+    "mra_make_operator2": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                           ctypes.POINTER(Alloc), _P, ctypes.POINTER(_P)],
+    "mra_apply_ns2": [_P, _P, _P, ctypes.POINTER(_P), ctypes.POINTER(ApplyStats)],
+    "mra_reconstruct2": [_P, ctypes.c_int, ctypes.c_double, _P, _DP],
+    "mra_free_tree2": [_P],
     "mra_make_operator": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                           ctypes.POINTER(Alloc), _P, ctypes.POINTER(_P)],
     "mra_op_get_info": [_P, ctypes.POINTER(OpInfo)],
@@ -420,6 +432,95 @@ def tree_dot(a, b, stream=None):
 
 def tree_scale(tree, alpha, stream=None):
     _check(lib().mra_tree_scale(tree.h, float(alpha), _stream(stream)))
+
+
+class Tree2:
+    """A tree of the d = 2 variant (mra_tree2): k x k blocks on the unit square."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    def info(self):
+        inf = TreeInfo()
+        _check(lib().mra_tree2_get_info(self.h, ctypes.byref(inf)))
+        return inf
+
+    @property
+    def n(self):
+        return self.info().n_nodes
+
+    def export(self, stream=None):
+        """(coords (n, 3), leaf (n,), blocks (n, k, k), dnorm (n,)) on the host."""
+        inf = self.info()
+        n, k = inf.n_nodes, inf.k
+        coords = np.zeros((n, 3), dtype=np.int32)
+        leaf = np.zeros(n, dtype=np.int32)
+        blocks = np.zeros((n, k, k))
+        dnorm = np.zeros(n)
+        _check(lib().mra_tree2_export(self.h, _ip(coords), _ip(leaf), _dp(blocks), _dp(dnorm), _stream(stream)))
+        return coords, leaf, blocks, dnorm
+
+    def free(self):
+        if self.h:
+            lib().mra_free_tree2(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_tree2(density, k, eps, max_level, uniform_level=-1, init_level=0, stream=None, allocator="torch"):
+    """mra_build_tree2 (Algorithm 1 in d = 2); density.centers is (n, 2).
+    Returns (Tree2, depth_hit)."""
+    coef = np.ascontiguousarray(density.coef, dtype=np.float64)
+    expo = np.ascontiguousarray(density.expo, dtype=np.float64)
+    cen = np.ascontiguousarray(np.asarray(density.centers, dtype=np.float64).reshape(-1))
+    r2 = np.ascontiguousarray(getattr(density, "r2coef", np.zeros_like(coef)), dtype=np.float64)
+    d = Density(len(coef), _dp(coef), _dp(r2), _dp(expo), _dp(cen))
+    h = _P()
+    rc = lib().mra_build_tree2(ctypes.byref(d), k, eps, max_level, uniform_level, init_level,
+                               _alloc_ptr(allocator), _stream(stream), ctypes.byref(h))
+    _check(rc, allow=(EDEPTH,))
+    return Tree2(h.value), rc == EDEPTH
+
+
+def tree2_import(k, coords, leaf, blocks, stream=None, allocator="torch"):
+    coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 3)
+    leaf = np.ascontiguousarray(leaf, dtype=np.int32)
+    blocks = np.ascontiguousarray(blocks, dtype=np.float64)
+    h = _P()
+    _check(lib().mra_tree2_import(k, len(coords), _ip(coords), _ip(leaf), _dp(blocks), _alloc_ptr(allocator),
+                                  _stream(stream), ctypes.byref(h)))
+    return Tree2(h.value)
+
+
+def compress2(tree, stream=None):
+    _check(lib().mra_compress2(tree.h, _stream(stream)))
+
+
+def make_operator2(mu, alpha, eps, k, max_level, stream=None, allocator="torch"):
+    """mra_make_operator2: K_{mu,alpha} in R^2 (0 < alpha < 1)."""
+    h = _P()
+    _check(lib().mra_make_operator2(mu, alpha, eps, k, max_level, _alloc_ptr(allocator), _stream(stream),
+                                    ctypes.byref(h)))
+    return Operator(h.value)
+
+
+def apply_ns2(op, tree, stream=None):
+    """mra_apply_ns2 (Algorithm 3 in d = 2, FP64): (ns-form Tree2, stats)."""
+    st = ApplyStats()
+    h = _P()
+    _check(lib().mra_apply_ns2(op.h, tree.h, _stream(stream), ctypes.byref(h), ctypes.byref(st)))
+    return Tree2(h.value), st.as_dict()
+
+
+def reconstruct2(tree, truncate=False, eps=0.0, stream=None):
+    rem = ctypes.c_double(0.0)
+    _check(lib().mra_reconstruct2(tree.h, int(truncate), eps, _stream(stream), ctypes.byref(rem)))
+    return rem.value
 
 
 def compress(tree, store_d=False, stream=None):

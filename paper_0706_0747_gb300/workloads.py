@@ -192,3 +192,33 @@ def hydrogen_small():
     """A small hydrogen case the oracle finishes in seconds: k = 5,
     eps = 1e-3, depth 5."""
     return Hydrogen("hydrogen_k5_eps1e-3_level5", 32.0, (0.5, 0.5, 0.5), 0.7, 0.8, 5, 1e-3, 5, 2)
+
+
+def unit_mass2(expo, centers):
+    """Unit-mass Gaussians in R^2: (a/pi) exp(-a |x - x0|^2)."""
+    expo = np.asarray(expo, dtype=np.float64)
+    return Density(expo / math.pi, expo, np.asarray(centers, dtype=np.float64).reshape(-1, 2), np.zeros_like(expo))
+
+
+def poisson2d(instance=0, n_gauss=64):
+    """The d = 2 variant at full size: the kernel 1/(2 pi r) of
+    (-Laplacian)^{-1/2} in R^2 (alpha = 1/2, mu = 0), k = 8, eps = 1e-6,
+    adaptive to depth 12; 64 unit-mass Gaussians, log10 exponent U[2.5, 5],
+    centres U[0.2, 0.8]^2, so that each Gaussian's mass outside the square is
+    below 3e-7 of it and the output can be checked against the free-space
+    closed form."""
+    rng = np.random.default_rng(1000 * 8 + instance)
+    expo = 10.0 ** rng.uniform(2.5, 5.0, n_gauss)
+    cen = rng.uniform(0.2, 0.8, (n_gauss, 2))
+    cfg = Config("poisson2d_half_k8_eps1e-6_adaptive12", 0.0, 0.5, 1e-6, 8, 12, init_level=2)
+    return cfg, unit_mass2(expo, cen)
+
+
+def poisson2d_small(instance=0):
+    """A d = 2 case the oracle finishes in seconds: k = 5, eps = 1e-4, depth 6;
+    4 unit-mass Gaussians, log10 exponent U[1.5, 3], centres U[0.25, 0.75]^2."""
+    rng = np.random.default_rng(1000 * 9 + instance)
+    expo = 10.0 ** rng.uniform(1.5, 3.0, 4)
+    cen = rng.uniform(0.25, 0.75, (4, 2))
+    cfg = Config("poisson2d_half_k5_eps1e-4_adaptive6", 0.0, 0.5, 1e-4, 5, 6, init_level=1)
+    return cfg, unit_mass2(expo, cen)
