@@ -589,6 +589,72 @@ def hydrogen_section(stream, max_iter=40):
     return out
 
 
+# ---------------------------------------------------------------- d = 2 variant
+def d2_section(K, Wu, flush, stream, sample_nodes=120):
+    """The d = 2 variant (Sec. 6; Algorithm 3 as illustrated for d = 2) on
+    poisson2d: the kernel 1/(2 pi r) (alpha = 1/2, mu = 0), k = 8, eps = 1e-6,
+    64 unit-mass Gaussians; a step is compress2 -> apply_ns2 (FP64) ->
+    reconstruct2 with truncation; block-applies/s of the step, the apply
+    kernel's FP64 rate against the part's nominal FP64 rate, and the oracle's
+    rate on a random sample of output nodes (one thread)."""
+    import time as _t
+    import numpy as np
+    import torch
+    from oracle import d2 as OD
+    from paper_0706_0747_gb300 import mra, workloads as W
+    cfg, dens = W.poisson2d()
+    op = mra.make_operator2(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
+    t, hit = mra.build_tree2(dens, cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
+
+    def step():
+        mra.compress2(t, stream=stream)
+        g, st = mra.apply_ns2(op, t, stream=stream)
+        mra.reconstruct2(g, truncate=True, eps=cfg.eps, stream=stream)
+        g.free()
+        return st
+    for _ in range(Wu):
+        step()
+    ms, apl = [], []
+    for _ in range(K):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        apl.append(st["ms_apply"])
+    k = cfg.k
+    flops_item = 4 * k ** 3
+    ms_step, ms_apply = statistics.median(ms), statistics.median(apl)
+    achieved = st["n_items"] * flops_item / (ms_apply / 1e3) / 1e12
+    # the oracle on a random sample of the same tree's output nodes
+    c, l, b, _ = t.export()
+    to = {tuple(int(v) for v in cc): OD.Node(bool(ll), bb.copy() if ll else None) for cc, ll, bb in zip(c, l, b)}
+    OD.compress(to, k)
+    keys = sorted(to)
+    rng = np.random.default_rng(7)
+    sample = [keys[i] for i in rng.choice(len(keys), size=min(sample_nodes, len(keys)), replace=False)]
+    opo = OD.operator(cfg.mu, cfg.alpha, cfg.eps, k, cfg.max_level)
+    sto = {}
+    t0 = _t.perf_counter()
+    OD.apply_ns(opo, to, stats=sto, nodes=sample)
+    cpu_s = _t.perf_counter() - t0
+    out = {"workload": cfg.name, "k": k, "eps": cfg.eps, "alpha": cfg.alpha, "mu": cfg.mu, "M": op.info().M,
+           "tree_nodes": t.n, "depth_hit": bool(hit), "items": st["n_items"], "pairs": st["n_pairs"],
+           "step2_refinements": st["n_ghosts"], "ms_per_step": ms_step, "ms_apply_kernel": ms_apply,
+           "value": st["n_items"] / (ms_step / 1e3), "unit": "block-applies/s", "dtype": "f64",
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP64_TFLOPS, "flops_per_item": flops_item,
+                        "peak_source": "nominal FP64 rate of the part"},
+           "cpu_baseline": {"value": sto["n_items"] / cpu_s, "unit": "block-applies/s", "cores": 1, "kind": "oracle",
+                          "sample": f"{len(sample)} of {len(keys)} output nodes, {sto['n_items']} items in "
+                                    f"{cpu_s:.1f} s (operator tables and compress untimed)"}}
+    t.free()
+    op.free()
+    return out
+
+
 # ---------------------------------------------------------------- replicas
 def slowest_ms(local_ms, ws, device):
     """The slowest replica's time: the maximum over the ranks of the
@@ -630,6 +696,7 @@ def main():
     ap.add_argument("--no-learned-batched", action="store_true",
                     help="skip the learned + tensor-core + batched section")
     ap.add_argument("--no-hydrogen", action="store_true", help="skip the hydrogen ground-state iteration")
+    ap.add_argument("--no-d2", action="store_true", help="skip the d = 2 variant")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -852,6 +919,8 @@ def main():
             line["learned_batched"] = learned_batched_section(K, Wu, flush, stream)
         if not args.no_hydrogen:
             line["hydrogen"] = hydrogen_section(stream)
+        if not args.no_d2:
+            line["d2"] = d2_section(K, Wu, flush, stream)
         if not args.no_batched:
             line["batched"] = batched_section(K, Wu, flush, stream, pk["bf16_tflops"],
                                               prec if prec in ("tc", "tc_ladder") else "tc")
