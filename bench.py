@@ -53,6 +53,8 @@ FP64_TFLOPS = 1.25
 # apply kernel on this workload, from one ncu capture of the current kernel
 # version; absent where no capture of the current kernel exists.
 TRAFFIC_BYTES = {"tc/static": 141.334272e6, "tc/pair": 97.992448e6}
+# k_apply2 on poisson2d (ncu, one launch): DRAM read + write
+TRAFFIC_D2 = 2.183936e6
 
 
 class Clocks:
@@ -645,7 +647,8 @@ def d2_section(K, Wu, flush, stream, sample_nodes=120):
            "step2_refinements": st["n_ghosts"], "ms_per_step": ms_step, "ms_apply_kernel": ms_apply,
            "value": st["n_items"] / (ms_step / 1e3), "unit": "block-applies/s", "dtype": "f64",
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                        "frac": achieved / FP64_TFLOPS, "flops_per_item": flops_item,
+                        "frac": achieved / FP64_TFLOPS, "flops_per_item": flops_item, "traffic": TRAFFIC_D2,
+                        "traffic_unit": "bytes per launch (ncu)",
                         "peak_source": "nominal FP64 rate of the part"},
            "cpu_baseline": {"value": sto["n_items"] / cpu_s, "unit": "block-applies/s", "cores": 1, "kind": "oracle",
                           "sample": f"{len(sample)} of {len(keys)} output nodes, {sto['n_items']} items in "
