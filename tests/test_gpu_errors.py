@@ -16,6 +16,7 @@
 * mra_free on every handle kind.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -117,6 +118,9 @@ def _free_all(made):
 
 
 def test_enomem_on_every_allocation_leaks_nothing():
+    # handles left over from earlier tests are released first, so that the
+    # byte count below measures this test's calls only
+    gc.collect()
     torch.cuda.synchronize()
     base = torch.cuda.memory_allocated()
     probe = FailingAlloc(0)
@@ -136,6 +140,8 @@ def test_enomem_on_every_allocation_leaks_nothing():
         _free_all(made)
         torch.cuda.synchronize()
         assert not A.live, f"allocation {n} of {total}: {len(A.live)} blocks leaked"
+    gc.collect()
+    torch.cuda.synchronize()
     assert torch.cuda.memory_allocated() == base
 
 
