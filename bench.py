@@ -588,6 +588,34 @@ def hydrogen_section(stream, max_iter=40):
                      "energies": [h["energy"] for h in hist]}
         cache.free()
         phi.free()
+    # two nuclei: the hydrogen molecular ion at R = 2 bohr
+    m = W.h2plus()
+    q, pos = m.potential_charges()
+    pot2 = mra.Potential(charges=q, positions=pos)
+    mol = {"workload": m.name, "L_bohr": m.L, "nuclei": [list(u) for u in m.nuclei], "exact_energy": m.exact_energy}
+    for prec in ("fp64", "tc"):
+        phi, _ = mra.build_tree(m.start_density(), m.k, m.eps, m.max_level, init_level=m.init_level)
+        mol["tree_nodes"] = phi.n
+        mra.tree_scale(phi, 1.0 / math.sqrt(mra.tree_dot(phi, phi) * m.L ** 3))
+        cache, mu, ms, hist = mra.OpCache(), m.mu0, [], []
+        for it in range(max_iter):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            phi, info = mra.kalos_step(phi, pot2, m.L, mu, m.eps, m.max_level, precision=prec, op_cache=cache,
+                                       stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            hist.append(info)
+            dmu, mu = abs(info["mu_next"] - mu), info["mu_next"]
+            if dmu < 1e-7 and abs(info["norm_new"] - 1.0) < 1e-6:
+                break
+        mol[prec] = {"iterations": len(hist), "energy": hist[-1]["energy"],
+                     "abs_err_energy": abs(hist[-1]["energy"] - m.exact_energy),
+                     "ms_per_step_median": statistics.median(ms[1:] if len(ms) > 1 else ms), "ms_total": sum(ms)}
+        cache.free()
+        phi.free()
+    out["h2plus"] = mol
     return out
 
 

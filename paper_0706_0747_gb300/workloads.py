@@ -222,3 +222,44 @@ def poisson2d_small(instance=0):
     cen = rng.uniform(0.25, 0.75, (4, 2))
     cfg = Config("poisson2d_half_k5_eps1e-4_adaptive6", 0.0, 0.5, 1e-4, 5, 6, init_level=1)
     return cfg, unit_mass2(expo, cen)
+
+
+@dataclass
+class OneElectron:
+    """A one-electron system for the ground-state iteration of Sec. 6.2 with
+    several nuclei: charges Z_n at cube points (the potential is
+    sum_n -Z_n / |x - R_n|), the starting function sum_n exp(-zeta0 |x - R_n|),
+    mu0, the apply's k / eps / max_level, and the exact electronic energy the
+    iteration must reach."""
+    name: str
+    L: float
+    nuclei: tuple
+    charges: tuple
+    zeta0: float
+    mu0: float
+    k: int
+    eps: float
+    max_level: int
+    init_level: int
+    exact_energy: float
+
+    def start_density(self):
+        c, a = slater_expansion(self.zeta0)
+        cen = np.concatenate([np.tile(np.asarray(u, dtype=np.float64), (len(c), 1)) for u in self.nuclei])
+        coef = np.concatenate([c for _ in self.nuclei])
+        return Density(coef, np.concatenate([a * self.L * self.L for _ in self.nuclei]), cen, np.zeros_like(coef))
+
+    def potential_charges(self):
+        """(charges, positions) in cube coordinates: -Z_n / L at u_n."""
+        return [-z / self.L for z in self.charges], [list(u) for u in self.nuclei]
+
+
+def h2plus(k=8, eps=1e-6, max_level=12):
+    """The hydrogen molecular ion at the bond length R = 2 bohr: two protons
+    at the cube points (1/2 -+ 1/32, 1/2, 1/2) of a 32-bohr cube (corners of
+    boxes from level 5 on, so no GL node meets them); exact electronic energy
+    -1.10263421 hartree (the total, with the protons' repulsion 1/R = 1/2, is
+    -0.60263421)."""
+    return OneElectron(f"h2plus_R2_k{k}_eps{eps:g}_level{max_level}", 32.0,
+                       ((0.5 - 1.0 / 32.0, 0.5, 0.5), (0.5 + 1.0 / 32.0, 0.5, 0.5)), (1.0, 1.0), 0.7, 1.2,
+                       k, eps, max_level, 3, -1.10263421)
