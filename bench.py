@@ -922,6 +922,12 @@ def main():
             "unit counts x 2070 MHz" if prec == "fp32" else "nominal FP64 rate of the part",
             "flops_per_item": flops_item, "items_per_launch": items_applied,
             "peak_kind": "burst" if bound == "tensor" else None}
+    if screen != "static" and "static" in screens and bound == "tensor":
+        # the same kernel at the paper's static screen (more items per launch), for context
+        a_st = items_plain * flops_item / (screens["static"]["ms_apply_kernel"] / 1e3) / 1e12
+        roof["static_screen"] = {"achieved": a_st, "frac": a_st / peak, "items_per_launch": items_plain,
+                                 "ms_per_launch": screens["static"]["ms_apply_kernel"],
+                                 "traffic": TRAFFIC_BYTES.get(f"{prec}/static")}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wu,
