@@ -576,9 +576,11 @@ int mra_tree_scale(mra_tree* t, double alpha, void* stream);
  * op_cache: NULL, or the address of an operator handle kept between steps.
  * With NULL the step builds its operator and frees it.  Otherwise an
  * operator in *op_cache with this k, eps and max_level (alpha 1) is
- * re-weighted for mu * length (mra_op_retune); when that fails, or *op_cache
- * is NULL or does not match, a new operator is built, the old one freed and
- * the new one stored in *op_cache.  The caller frees it (mra_free).
+ * re-weighted for mu * length (mra_op_retune); when its grid fails the
+ * sup-norm test for that mu, or *op_cache is NULL or does not match, a new
+ * operator is built, the old one freed and the new one stored in *op_cache
+ * (other errors of the re-weighting are returned).  The caller frees it
+ * (mra_free).
  * Synchronous.  Errors: those of the calls above; MRA_EINVAL for length or
  * mu not positive and finite. */
 typedef struct {

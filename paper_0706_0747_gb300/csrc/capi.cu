@@ -269,9 +269,14 @@ int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, d
     if (op_cache && *op_cache && !op_ok(*op_cache)) { set_error("op_cache holds no operator"); return MRA_EINVAL; }
     MRA_TRY(mra_tree_multiply(phi, v, 1.0, stream, &o.P));                          // Step 2
     mra_op* op = op_cache ? *op_cache : nullptr;
-    int rebuilt = 0;
-    if (!(op && op->d == 3 && op->k == phi->k && op->eps == eps && op->J == max_level && op->alpha == 1.0 &&
-          retune_operator(op, mu * length, (cudaStream_t)stream) == MRA_OK)) {
+    int rebuilt = 0, reuse = 0;
+    if (op && op->d == 3 && op->k == phi->k && op->eps == eps && op->J == max_level && op->alpha == 1.0) {
+        // a grid that fails the sup-norm test for this mu is rebuilt; any other error is returned
+        const int rc = retune_operator(op, mu * length, (cudaStream_t)stream);
+        if (rc != MRA_OK && rc != MRA_EINVAL) return rc;
+        reuse = rc == MRA_OK;
+    }
+    if (!reuse) {
         MRA_TRY(mra_make_operator(mu * length, 1.0, eps, phi->k, max_level, phi->A.has ? &phi->A.hook : nullptr,
                                   stream, &o.op));
         rebuilt = 1;

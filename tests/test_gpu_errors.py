@@ -22,6 +22,7 @@ import numpy as np
 import pytest
 
 from oracle import tree as OT
+from paper_0706_0747_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -135,6 +136,107 @@ def test_enomem_on_every_allocation_leaks_nothing():
         A = FailingAlloc(n)
         made = []
         rc, out = _sequence(A, made)
+        assert rc == mra.ENOMEM, f"allocation {n} of {total}: status {rc} ({mra.last_error()})"
+        assert out is None, f"allocation {n}: output handle set on failure"
+        _free_all(made)
+        torch.cuda.synchronize()
+        assert not A.live, f"allocation {n} of {total}: {len(A.live)} blocks leaked"
+    gc.collect()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == base
+
+
+def _sequence_products_d2(A, made):
+    """The hydrogen step's calls (product, inner product, two Kalos steps with
+    an operator cache: a build, then a re-weighting) and the d = 2 variant
+    (build_tree2, compress2, make_operator2, apply_ns2, reconstruct2 with
+    truncation), with the allocator hook on every handle."""
+    L = mra.lib()
+    st = torch.cuda.current_stream().cuda_stream
+    hc = W.hydrogen_small()
+    dens = hc.start_density()
+    coef, expo = np.ascontiguousarray(dens.coef), np.ascontiguousarray(dens.expo)
+    cen, r2 = np.ascontiguousarray(dens.centers.reshape(-1)), np.zeros_like(coef)
+    d = mra.Density(len(coef), mra._dp(coef), mra._dp(r2), mra._dp(expo), mra._dp(cen))
+    h = ctypes.c_void_p()
+    rc = L.mra_build_tree(ctypes.byref(d), hc.k, hc.eps, hc.max_level, -1, hc.init_level, ctypes.byref(A.hook), st,
+                          ctypes.byref(h))
+    if rc not in (mra.OK, mra.EDEPTH):
+        return rc, h.value
+    made.append(h.value)
+    phi = h.value
+    pot = mra.Potential(charges=[-1.0 / hc.L], positions=[hc.u0])
+    pc = pot.c_struct()
+    h = ctypes.c_void_p()
+    rc = L.mra_tree_multiply(phi, ctypes.byref(pc), 1.0, st, ctypes.byref(h))
+    if rc != mra.OK:
+        return rc, h.value
+    made.append(h.value)
+    dot = ctypes.c_double(0.0)
+    rc = L.mra_tree_dot(h.value, phi, st, ctypes.byref(dot))
+    if rc != mra.OK:
+        return rc, None
+    cache = ctypes.c_void_p()
+    info = mra.KalosInfo()
+    for mu in (0.8, 0.9):
+        h = ctypes.c_void_p()
+        rc = L.mra_kalos_step(phi, ctypes.byref(pc), hc.L, mu, hc.eps, hc.max_level, None, ctypes.byref(cache), st,
+                              ctypes.byref(h), ctypes.byref(info))
+        if cache.value and cache.value not in made:
+            made.append(cache.value)
+        if rc != mra.OK:
+            return rc, h.value
+        made.append(h.value)
+    d2c = np.array([30.0, 12.0]), np.array([70.0, 150.0]), np.array([0.45, 0.52, 0.62, 0.41])
+    r22 = np.zeros(2)
+    dd = mra.Density(2, mra._dp(d2c[0]), mra._dp(r22), mra._dp(d2c[1]), mra._dp(d2c[2]))
+    h = ctypes.c_void_p()
+    rc = L.mra_build_tree2(ctypes.byref(dd), 4, 1e-4, 5, -1, 1, ctypes.byref(A.hook), st, ctypes.byref(h))
+    if rc not in (mra.OK, mra.EDEPTH):
+        return rc, h.value
+    made.append(h.value)
+    t2 = h.value
+    rc = L.mra_compress2(t2, st)
+    if rc != mra.OK:
+        return rc, None
+    h = ctypes.c_void_p()
+    rc = L.mra_make_operator2(0.0, 0.5, 1e-4, 4, 5, ctypes.byref(A.hook), st, ctypes.byref(h))
+    if rc != mra.OK:
+        return rc, h.value
+    made.append(h.value)
+    op2 = h.value
+    h = ctypes.c_void_p()
+    s = mra.ApplyStats()
+    rc = L.mra_apply_ns2(op2, t2, st, ctypes.byref(h), ctypes.byref(s))
+    if rc != mra.OK:
+        return rc, h.value
+    made.append(h.value)
+    rem = ctypes.c_double(0.0)
+    rc = L.mra_reconstruct2(h.value, 1, 1e-4, st, ctypes.byref(rem))
+    if rc != mra.OK:
+        return rc, None
+    return mra.OK, None
+
+
+def test_enomem_in_products_kalos_and_d2_leaks_nothing():
+    """The same contract for the hydrogen step's entries and the d = 2
+    variant: every failed allocation gives MRA_ENOMEM, no output handle, and
+    no block left allocated once the handles made are freed."""
+    gc.collect()
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    probe = FailingAlloc(0)
+    made = []
+    rc, _ = _sequence_products_d2(probe, made)
+    assert rc == mra.OK, mra.last_error()
+    _free_all(made)
+    torch.cuda.synchronize()
+    total = probe.calls
+    assert not probe.live and total > 20
+    for n in range(1, total + 1):
+        A = FailingAlloc(n)
+        made = []
+        rc, out = _sequence_products_d2(A, made)
         assert rc == mra.ENOMEM, f"allocation {n} of {total}: status {rc} ({mra.last_error()})"
         assert out is None, f"allocation {n}: output handle set on failure"
         _free_all(made)
