@@ -293,11 +293,16 @@ int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, d
     MRA_TRY(mra_apply_ns(op, o.P, opts, stream, &o.g, &st));
     MRA_TRY(assemble_impl(o.g, (cudaStream_t)stream));  // eq. g_assemble; leaf data only
     MRA_TRY(mra_tree_scale(o.g, -2.0 * length * length, stream));
-    double nn = 0.0, pg = 0.0, qg = 0.0;                                            // Step 4
-    MRA_TRY(mra_tree_dot(o.g, o.g, stream, &nn));
-    MRA_TRY(mra_tree_dot(o.P, o.g, stream, &pg));
-    MRA_TRY(mra_tree_multiply(o.g, v, 1.0, stream, &o.Q));
-    MRA_TRY(mra_tree_dot(o.Q, o.g, stream, &qg));
+    MRA_TRY(mra_tree_multiply(o.g, v, 1.0, stream, &o.Q));                          // Step 4
+    // <phi_new, phi_new>, <P, phi_new>, <V phi_new, phi_new>: one pass (the four trees share
+    // phi's skeleton by construction)
+    double d3[3] = {0.0, 0.0, 0.0};
+    {
+        const mra_tree* da[3] = {o.g, o.P, o.Q};
+        const mra_tree* db[3] = {o.g, o.g, o.g};
+        MRA_TRY(tree_dot3_impl(da, db, d3, (cudaStream_t)stream));
+    }
+    const double nn = d3[0], pg = d3[1], qg = d3[2];
     if (!(nn > 0.0)) { set_error("phi_new vanishes"); return MRA_EINVAL; }
     const double E = (-pg - 0.5 * mu * mu * nn + qg) / nn;
     const double norm = std::sqrt(nn * length * length * length);

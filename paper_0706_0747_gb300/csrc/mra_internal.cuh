@@ -175,6 +175,8 @@ int refine_impl(const mra_tree* f, int passes, int max_level, cudaStream_t st, m
 // product.cu
 int tree_multiply_impl(const mra_tree* f, const mra_potential* v, double scale, cudaStream_t st, mra_tree** out);
 int tree_dot_impl(const mra_tree* a, const mra_tree* b, double* out_host, cudaStream_t st);
+// <a[p], b[p]> for p = 0, 1, 2 in one pass; all six trees share a's skeleton (not checked)
+int tree_dot3_impl(const mra_tree* const* a, const mra_tree* const* b, double* out_host, cudaStream_t st);
 int tree_scale_impl(mra_tree* t, double alpha, cudaStream_t st);
 
 // apply.cu

@@ -28,14 +28,17 @@ __device__ double pot_eval(const PotDev& V, double x1, double x2, double x3) {
 }
 
 // One block per leaf (grid-stride over nodes).  In shared memory: the GL
-// nodes and weights of [0, 1], Phi[q][i] = phi_i(u_q), and two k^3 buffers.
-// Coefficients -> values at the box's GL points are three mode products with
-// Phi (the 2^{3j/2} of the values and the 2^{-3j/2} of the projection
-// cancel); the values are multiplied by w_q1 w_q2 w_q3 V(x_q) scale; three
-// mode products with Phi^T give the projected coefficients.
-__global__ void k_tree_multiply(int k, int n, const int32_t* coord, const int32_t* leaf, const double* s,
+// nodes and weights of [0, 1], Phi[q][i] = phi_i(u_q), and two k^3 buffers
+// used in turn.  Coefficients -> values at the box's GL points are three mode
+// products with Phi (the 2^{3j/2} of the values and the 2^{-3j/2} of the
+// projection cancel); the values are multiplied by w_q1 w_q2 w_q3 V(x_q) scale;
+// three mode products with Phi^T give the projected coefficients.  KT > 0
+// fixes k at compile time (the inner loops unroll); KT = 0 takes k at run time.
+template <int KT>
+__global__ void k_tree_multiply(int k_rt, int n, const int32_t* coord, const int32_t* leaf, const double* s,
                                 PotDev V, double scale, double* out) {
     extern __shared__ double sm[];
+    const int k = KT > 0 ? KT : k_rt;
     const int k3 = k * k * k, kk = k * k;
     double* xq = sm;
     double* wq = xq + MRA_MAX_K;
@@ -59,42 +62,50 @@ __global__ void k_tree_multiply(int k, int n, const int32_t* coord, const int32_
         const int j = coord[4 * node];
         const double h = ldexp(1.0, -j);
         const double o1 = coord[4 * node + 1] * h, o2 = coord[4 * node + 2] * h, o3 = coord[4 * node + 3] * h;
-        for (int e = threadIdx.x; e < k3; e += blockDim.x) a[e] = s[(size_t)node * k3 + e];
+        double* x = a;
+        double* y = b;
+        for (int e = threadIdx.x; e < k3; e += blockDim.x) x[e] = s[(size_t)node * k3 + e];
         __syncthreads();
         // direction d has stride kk, k, 1 for d = 0, 1, 2 (block index i1 i2 i3, C order)
         for (int d = 0; d < 3; ++d) {
             const int st = d == 0 ? kk : (d == 1 ? k : 1);
             for (int e = threadIdx.x; e < k3; e += blockDim.x) {
                 const int q = (e / st) % k;
-                const double* col = a + e - q * st;
+                const double* col = x + e - q * st;
                 double acc = 0.0;
-                for (int i = 0; i < k; ++i) acc += Phi[q * k + i] * col[i * st];
-                b[e] = acc;
+#pragma unroll
+                for (int i = 0; i < (KT > 0 ? KT : MRA_MAX_K); ++i)
+                    if (KT > 0 || i < k) acc += Phi[q * k + i] * col[i * st];
+                y[e] = acc;
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < k3; e += blockDim.x) a[e] = b[e];
-            __syncthreads();
+            double* t = x;
+            x = y;
+            y = t;
         }
         for (int e = threadIdx.x; e < k3; e += blockDim.x) {
             const int q1 = e / kk, q2 = (e / k) % k, q3 = e % k;
             const double v = pot_eval(V, o1 + h * xq[q1], o2 + h * xq[q2], o3 + h * xq[q3]);
-            a[e] *= wq[q1] * wq[q2] * wq[q3] * v * scale;
+            x[e] *= wq[q1] * wq[q2] * wq[q3] * v * scale;
         }
         __syncthreads();
         for (int d = 0; d < 3; ++d) {
             const int st = d == 0 ? kk : (d == 1 ? k : 1);
             for (int e = threadIdx.x; e < k3; e += blockDim.x) {
                 const int i = (e / st) % k;
-                const double* col = a + e - i * st;
+                const double* col = x + e - i * st;
                 double acc = 0.0;
-                for (int q = 0; q < k; ++q) acc += Phi[q * k + i] * col[q * st];
-                b[e] = acc;
+#pragma unroll
+                for (int q = 0; q < (KT > 0 ? KT : MRA_MAX_K); ++q)
+                    if (KT > 0 || q < k) acc += Phi[q * k + i] * col[q * st];
+                y[e] = acc;
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < k3; e += blockDim.x) a[e] = b[e];
-            __syncthreads();
+            double* t = x;
+            x = y;
+            y = t;
         }
-        for (int e = threadIdx.x; e < k3; e += blockDim.x) dst[e] = a[e];
+        for (int e = threadIdx.x; e < k3; e += blockDim.x) dst[e] = x[e];
         __syncthreads();
     }
 }
@@ -111,6 +122,31 @@ __global__ void k_tree_dot(int n, int k3, const int32_t* leaf, const double* sa,
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0 && acc != 0.0) atomicAdd(out, acc);
+}
+
+// three inner products on one skeleton in one pass: out[p] = <sa[p], sb[p]>
+struct Dot3 {
+    const double* a[3];
+    const double* b[3];
+};
+__global__ void k_tree_dot3(int n, int k3, const int32_t* leaf, Dot3 D, double* out) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = warp; i < n; i += nwarps) {
+        if (!leaf[i]) continue;
+        for (int e = lane; e < k3; e += 32) {
+            const size_t o = (size_t)i * k3 + e;
+#pragma unroll
+            for (int p = 0; p < 3; ++p) acc[p] += D.a[p][o] * D.b[p][o];
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        double v = acc[p];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && v != 0.0) atomicAdd(out + p, v);
+    }
 }
 
 // 1 in *diff when the two node lists or leaf flags differ anywhere
@@ -163,8 +199,10 @@ int tree_multiply_impl(const mra_tree* f, const mra_potential* v, double scale, 
     MRA_CK(cudaMemcpyAsync(dv, hv.data(), nv * sizeof(double), cudaMemcpyHostToDevice, st));
     PotDev P{ng, nc, dv, dv + ng, dv + 2 * ng, dv + 3 * ng, dv + 6 * ng, dv + 6 * ng + nc};
     const size_t smem = (2 * MRA_MAX_K + MRA_MAX_K * MRA_MAX_K + 2 * (size_t)k3) * sizeof(double);
-    MRA_CK(cudaFuncSetAttribute(k_tree_multiply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tree_multiply<<<grid_for(f->n, 1), 128, smem, st>>>(k, f->n, f->a.coord, f->a.leaf, f->s, P, scale, g->s);
+    auto kern = k == 8 ? k_tree_multiply<8> : (k == 6 ? k_tree_multiply<6> : (k == 4 ? k_tree_multiply<4>
+                                                                                     : k_tree_multiply<0>));
+    MRA_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid_for(f->n, 1), 128, smem, st>>>(k, f->n, f->a.coord, f->a.leaf, f->s, P, scale, g->s);
     MRA_CK_LAUNCH();
     MRA_CK(cudaMemsetAsync(g->dnorm, 0, f->n * sizeof(double), st));
     MRA_CK(cudaStreamSynchronize(st));  // hv goes out of scope
@@ -194,6 +232,25 @@ int tree_dot_impl(const mra_tree* a, const mra_tree* b, double* out_host, cudaSt
         set_error("the two trees have different skeletons");
         return MRA_EINVAL;
     }
+    return MRA_OK;
+}
+
+int tree_dot3_impl(const mra_tree* const* a, const mra_tree* const* b, double* out_host, cudaStream_t st) {
+    const mra_tree* t = a[0];
+    const int k3 = t->k * t->k * t->k;
+    Scratch tmp(t->A);
+    double* acc;
+    MRA_TRY(tmp.get(&acc, 3));
+    MRA_CK(cudaMemsetAsync(acc, 0, 3 * sizeof(double), st));
+    Dot3 D;
+    for (int p = 0; p < 3; ++p) {
+        D.a[p] = a[p]->s;
+        D.b[p] = b[p]->s;
+    }
+    k_tree_dot3<<<grid_for((size_t)t->n * 32, 256), 256, 0, st>>>(t->n, k3, t->a.leaf, D, acc);
+    MRA_CK_LAUNCH();
+    MRA_CK(cudaMemcpyAsync(out_host, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaStreamSynchronize(st));
     return MRA_OK;
 }
 
