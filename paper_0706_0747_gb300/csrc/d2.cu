@@ -325,7 +325,7 @@ __global__ void k_place_level2(int nb, int j, int base, int next_base, const int
     T.leaf[i] = refine[b] ? 0 : 1;
     T.child[i] = refine[b] ? next_base + 4 * pos[b] : -1;
     T.parent[i] = (j == 0) ? -1 : prev_base + parent_local[b / 4];
-    for (int e = 0; e < kk; ++e) T.s[(size_t)i * kk + e] = s_lvl[(size_t)b * kk + e];
+    // (the level's blocks are copied as one contiguous range by the caller)
 }
 
 static int build_tree2_impl(const mra_density* f, int k, double eps, int max_level, int uniform_level, int init_level,
@@ -410,6 +410,8 @@ static int build_tree2_impl(const mra_density* f, int k, double eps, int max_lev
         k_place_level2<<<(nbj + 127) / 128, 128, 0, st>>>(nbj, j, base, next_base, L[j].boxes, L[j].refine, L[j].pos,
                                                            L[j].parent_local, prev_base, kk, L[j].s, T);
         MRA_CK_LAUNCH();
+        MRA_CK(cudaMemcpyAsync(t->s + (size_t)base * kk, L[j].s, (size_t)nbj * kk * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
         base = next_base;
     }
     MRA_CK(cudaMemsetAsync(t->dnorm, 0, n * sizeof(double), st));

@@ -430,7 +430,7 @@ __global__ void k_place_level(int nb, int j, int base, int next_base, const int3
     a.leaf[i] = refine[b] ? 0 : 1;
     a.child[i] = refine[b] ? next_base + 8 * pos[b] : -1;
     a.parent[i] = (j == 0) ? -1 : prev_base + parent_local[b / 8];
-    for (int e = 0; e < k3; ++e) s[(size_t)i * k3 + e] = s_lvl[(size_t)b * k3 + e];
+    // (the level's blocks are copied as one contiguous range by the caller)
 }
 
 int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int uniform_level, int init_level,
@@ -532,6 +532,8 @@ int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int 
         k_place_level<<<(nbj + 127) / 128, 128, 0, st>>>(nbj, j, base, next_base, L[j].boxes, L[j].refine, L[j].pos,
                                                           L[j].parent_local, prev_base, k3, L[j].s, t->a, t->s);
         MRA_CK_LAUNCH();
+        MRA_CK(cudaMemcpyAsync(t->s + (size_t)base * k3, L[j].s, (size_t)nbj * k3 * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
         base = next_base;
     }
     MRA_CK(cudaMemcpyAsync(t->a.off, t->off, sizeof(t->off), cudaMemcpyHostToDevice, st));
