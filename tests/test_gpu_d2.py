@@ -147,6 +147,18 @@ def test_apply2_parity_adaptive_with_refined_inputs():
     assert rel_l2(blocks, ghat) <= 1e-12
 
 
+@pytest.mark.parametrize("mu,alpha", [(4.0, 0.75), (0.0, 0.25)])
+def test_apply2_parity_other_kernels(mu, alpha):
+    """Other members of the d = 2 family: a screened kernel (mu > 0) and a
+    weaker singularity (alpha = 1/4), on the oracle-sized tree."""
+    cfg, dens = W.poisson2d_small()
+    to, _ = D.build_tree(oracle_density(dens), cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
+    g, st, ghat, sto, *_ = apply_both(to, cfg.k, (mu, alpha, cfg.eps, cfg.k, cfg.max_level))
+    blocks, _, _ = as_dicts(g)
+    assert st["n_items"] == sto["n_items"] and st["n_pairs"] == sto["n_pairs"]
+    assert rel_l2(blocks, ghat) <= 1e-12
+
+
 def test_reconstruct2_and_truncation_parity():
     cfg, dens = W.poisson2d_small()
     od = oracle_density(dens)
