@@ -406,7 +406,7 @@ def _step_timer(mra, tree, op, eps, flush, stream, K, Wu, prec):
     import torch
 
     def step():
-        mra.compress(tree)
+        mra.compress(tree, norms=False)
         g, st = mra.apply_ns(op, tree, precision=prec)
         mra.reconstruct(g, mode="assemble", truncate=True, eps=eps)
         g.free()
@@ -444,7 +444,7 @@ def configs_section(K, Wu, flush, stream, prec):
                "tree_nodes": tree.n, "depth_hit": bool(hit)}
         outs = {}
         for p in ("fp64", prec):
-            mra.compress(tree)
+            mra.compress(tree, norms=False)
             g, st = mra.apply_ns(op, tree, precision=p)
             outs[p] = g.export()[2]
             if p == "fp64" and name == "poisson_small":
@@ -529,7 +529,7 @@ def _refined_one(workload, K, Wu, flush, stream, prec, n_pts):
         tree, nsplit = mra.tree_refine(base, passes=passes, max_level=cfg.max_level)
         t_ref = _t.perf_counter() - t0
         ms, ms_apply, st = _step_timer(mra, tree, op, cfg.eps, flush, stream, K, Wu, prec)
-        mra.compress(tree)
+        mra.compress(tree, norms=False)
         g, _ = mra.apply_ns(op, tree, precision=prec)
         mra.reconstruct(g, mode="assemble", truncate=True, eps=cfg.eps)
         c, l, b, _ = g.export()
@@ -768,7 +768,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step(p, **kw):
-        mra.compress(tree)
+        mra.compress(tree, norms=False)
         g, st = mra.apply_ns(op, tree, precision=p, **kw)
         rem = mra.reconstruct(g, mode="assemble", truncate=True, eps=cfg.eps)
         n_out = g.n
@@ -802,7 +802,7 @@ def main():
     # each precision's error against the FP64 GPU path on the same input (the
     # FP64 path matches the oracle to 1e-12 in the parity tests)
     def ghat(p):
-        mra.compress(tree)
+        mra.compress(tree, norms=False)
         g, st_ = mra.apply_ns(op, tree, precision=p)
         out = g.export()[2]
         g.free()
@@ -846,7 +846,7 @@ def main():
         net = SCH.load()
         ref64 = ghat("fp64")[0]
         for name, kw in (("pair", {"screen": "pair"}), ("learned", {"screen": "learned", "schedule": net})):
-            mra.compress(tree)
+            mra.compress(tree, norms=False)
             g, st_s = mra.apply_ns(op, tree, precision=prec, **kw)
             out = g.export()[2]
             g.free()
@@ -890,7 +890,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         t_in = mra.tree_import(k, coords, leaf, blocks)
-        mra.compress(t_in)
+        mra.compress(t_in, norms=False)
         g, _ = mra.apply_ns(op, t_in, precision=prec, screen=screen)
         mra.reconstruct(g, mode="assemble", truncate=True, eps=cfg.eps)
         oc, ol, ob, od = g.export(out=outbuf)

@@ -175,9 +175,19 @@ int mra_tree_refine(const mra_tree* f, int passes, int max_level, void* stream, 
  * cube of its children.  G is the orthonormal completion of [H0 H1] by
  * Gram-Schmidt of (e_i, -e_i)/sqrt(2) (the paper defers G to Alpert et al.;
  * wavelet norms do not depend on the completion).  In place; state becomes
- * MRA_TREE_REDUNDANT.  store_d != 0 also keeps the wavelet cubes so that
- * mra_reconstruct(MRA_RECON_INVERSE) can undo the transform. */
-int mra_compress(mra_tree* t, int store_d, void* stream);
+ * MRA_TREE_REDUNDANT.  mode:
+ *   MRA_COMPRESS_NORMS    the scaling blocks of every internal node and its
+ *                         wavelet norm ||d|| (what the final truncation reads);
+ *   MRA_COMPRESS_STORE_D  also keeps the wavelet cubes, so that
+ *                         mra_reconstruct(MRA_RECON_INVERSE) can undo the transform;
+ *   MRA_COMPRESS_SCALING  the scaling blocks only -- all that Algorithm 3 reads of
+ *                         its input (s^j at every level) -- with the wavelet norms
+ *                         left at zero; half of the arithmetic of MRA_COMPRESS_NORMS.
+ * Errors: MRA_EINVAL for another mode, MRA_ESTATE for an ns-form tree. */
+#define MRA_COMPRESS_NORMS   0
+#define MRA_COMPRESS_STORE_D 1
+#define MRA_COMPRESS_SCALING 2
+int mra_compress(mra_tree* t, int mode, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* make_operator: the Gaussian sum of K_{mu,alpha} (Sec. 3) and the operator
@@ -493,12 +503,12 @@ int mra_free_plan(mra_plan* p);
 /* Reconstruct.
  * MRA_RECON_ASSEMBLE: for an MRA_TREE_NSFORM tree, eq. g_assemble top-down
  * (each child adds the d = 0 upsampling of its parent, eqs. recon_even /
- * recon_odd), then mra_compress; if truncate != 0, leaf siblings whose
+ * recon_odd), then mra_compress (MRA_COMPRESS_NORMS); if truncate != 0, leaf siblings whose
  * parent has ||d|| < eps ||g|| / sqrt(N) are merged bottom-up (Algorithm 3,
  * Step 4, "discard unnecessary blocks").  State becomes MRA_TREE_REDUNDANT
  * (the tree may shrink).
  * MRA_RECON_INVERSE: for an MRA_TREE_REDUNDANT tree compressed with
- * store_d != 0, the inverse two-scale transform from the root down (the
+ * MRA_COMPRESS_STORE_D, the inverse two-scale transform from the root down (the
  * filter matrix is orthogonal; its transpose inverts it); state becomes
  * MRA_TREE_LEAVES with the leaves rebuilt. */
 #define MRA_RECON_ASSEMBLE 0

@@ -95,8 +95,8 @@ __global__ void k_forest_norm2(Forest F, double* dv) {
 }
 
 // Pilot ||T_0 f_0|| in two steps: block (m, b) writes w_m (F x F x F) s0_b
-// (F = F^{0;m,0}, s0_b the root block of tree b) to ym[b][m]; then one block
-// per tree sums the terms in a fixed order and takes the norm.
+// (F = F^{0;m,0}, s0_b the root block of tree b) to ym[b][m]; then the terms are
+// summed per coefficient and the squares per tree, in a fixed order, and the norm taken.
 __global__ void k_pilot_terms(Forest F, int M, const double* w, const double* Ftab, double* ym) {
     extern __shared__ double sm[];
     const int k = F.k, k3 = k * k * k, kk = k * k, m = blockIdx.x, b = blockIdx.y;
@@ -132,24 +132,34 @@ __global__ void k_pilot_terms(Forest F, int M, const double* w, const double* Ft
     }
 }
 
-__global__ void k_pilot_reduce(int k3, int M, const double* ym, double* dv) {
-    __shared__ double red[32];
-    const int b = blockIdx.x;
+// Block (b, q) sums the terms of the 32 coefficients e = 32 q + lane of tree b's
+// pilot, eight warps taking every eighth term, and writes the sum of their squares
+// to part[b][q]; k_pilot_reduce then adds a tree's parts in order (deterministic).
+__global__ void k_pilot_partial(int k3, int M, const double* ym, double* part) {
+    __shared__ double sl[8][33];
+    const int b = blockIdx.x, q = blockIdx.y, lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int e = q * 32 + lane;
     const double* yb = ym + (size_t)b * M * k3;
-    double acc = 0.0;
-    for (int e = threadIdx.x; e < k3; e += blockDim.x) {
-        double y = 0.0;
-        for (int m = 0; m < M; ++m) y += yb[(size_t)m * k3 + e];
-        acc += y * y;
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    double y = 0.0;
+    if (e < k3)
+        for (int m = wq; m < M; m += 8) y += yb[(size_t)m * k3 + e];
+    sl[wq][lane] = y;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-        dv[4 * b + 1] = sqrt(s);
+    if (wq == 0) {
+        double t = 0.0;
+        for (int w8 = 0; w8 < 8; ++w8) t += sl[w8][lane];
+        double acc = t * t;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) part[(size_t)b * gridDim.y + q] = acc;
     }
+}
+
+__global__ void k_pilot_reduce(int nq, const double* part, double* dv) {
+    const int b = blockIdx.x, lane = threadIdx.x;
+    double acc = 0.0;
+    for (int q = lane; q < nq; q += 32) acc += part[(size_t)b * nq + q];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) dv[4 * b + 1] = sqrt(acc);
 }
 
 // ------------------------------------------------------------------ schedule
@@ -171,7 +181,8 @@ __global__ void k_schedule(int M, int lm, const int32_t* nlev_tab, int unscreene
     double* ws = sched_sm;                        // M
     double* cmax = ws + M;                        // lm * M: max over |l| <= 1
     double* bmax = cmax + (size_t)lm * M;         // lm * M: max over |l| >= 2
-    int* Js = (int*)(bmax + (size_t)lm * M);      // M
+    double* ev = bmax + (size_t)lm * M;           // lm * 4 * M: the bound e_m per (j, S)
+    int* Js = (int*)(ev + (size_t)lm * 4 * M);    // M
     const double fn = sqrt(dv[4 * b]);
     const double eta = fn > 0.0 ? eps * dv[4 * b + 1] / fn : 0.0;
     if (threadIdx.x == 0) dv[4 * b + 2] = eta;
@@ -191,6 +202,21 @@ __global__ void k_schedule(int M, int lm, const int32_t* nlev_tab, int unscreene
         bmax[e] = fmax(fmax(r[0], r[1]), fmax(r[5], r[6]));
     }
     __syncthreads();
+    // the bounds e_m = w_m cmax^S bmax^(3-S) of every (j, S, m) at once (the serial
+    // scans below then only add); a term with J_m < j gets 0, which the scans pass over
+    // exactly as they skip it (acc + 0 <= budget holds while acc <= budget)
+    for (int e = threadIdx.x; e < lm * 4 * M; e += blockDim.x) {
+        const int js = e / M, m = e - js * M, j = js >> 2, S = js & 3;
+        double v = 0.0;
+        if (j < nlev && Js[m] >= j) {
+            const double c = cmax[(size_t)j * M + m], bb = bmax[(size_t)j * M + m];
+            v = ws[m];
+            for (int q = 0; q < S; ++q) v *= c;
+            for (int q = S; q < 3; ++q) v *= bb;
+        }
+        ev[e] = v;
+    }
+    __syncthreads();
     const double budget = eta / (2.0 * 216.0);
     for (int js = threadIdx.x; js < lm * 4; js += blockDim.x) {
         const int j = js / 4, S = js % 4;
@@ -208,26 +234,18 @@ __global__ void k_schedule(int M, int lm, const int32_t* nlev_tab, int unscreene
                     ++n;
                 }
             if (n > 0) {
-                auto e_of = [&](int m) {
-                    const double c = cmax[(size_t)j * M + m], bb = bmax[(size_t)j * M + m];
-                    double v = ws[m];
-                    for (int q = 0; q < S; ++q) v *= c;
-                    for (int q = S; q < 3; ++q) v *= bb;
-                    return v;
-                };
+                const double* e_js = ev + (size_t)js * M;
                 double acc = 0.0;
                 int lo = first;
                 for (; lo <= last; ++lo) {
-                    if (Js[lo] < j) continue;
-                    double e = e_of(lo);
+                    const double e = e_js[lo];
                     if (acc + e <= budget) acc += e;
                     else break;
                 }
                 acc = 0.0;
                 int hi = last;
                 for (; hi >= lo; --hi) {
-                    if (Js[hi] < j) continue;
-                    double e = e_of(hi);
+                    const double e = e_js[hi];
                     if (acc + e <= budget) acc += e;
                     else break;
                 }
@@ -252,7 +270,7 @@ __global__ void k_schedule(int M, int lm, const int32_t* nlev_tab, int unscreene
     }
 }
 
-static size_t schedule_smem(int M, int lm) { return ((size_t)M * (1 + 2 * (size_t)lm)) * sizeof(double) + M * sizeof(int); }
+static size_t schedule_smem(int M, int lm) { return ((size_t)M * (1 + 6 * (size_t)lm)) * sizeof(double) + M * sizeof(int); }
 
 static int schedule_smem_attr(int M, int lm) {
     MRA_CK(cudaFuncSetAttribute(k_schedule, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schedule_smem(M, lm)));
@@ -755,11 +773,15 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
     k_forest_norm2<<<nb_norm, 256, 0, st>>>(F, S->dv);
     MRA_CK_LAUNCH();
     Scratch tmp(A);
-    double* ym;
+    double *ym, *part;
+    const int nq = (k3 + 31) / 32;
     MRA_TRY(tmp.get(&ym, (size_t)F.ntrees * M * k3));
+    MRA_TRY(tmp.get(&part, (size_t)F.ntrees * nq));
     k_pilot_terms<<<dim3(M, F.ntrees), 128, (3 * (size_t)k3 + F.k * F.k) * sizeof(double), st>>>(F, M, op->w, op->F, ym);
     MRA_CK_LAUNCH();
-    k_pilot_reduce<<<F.ntrees, 256, 0, st>>>(k3, M, ym, S->dv);
+    k_pilot_partial<<<dim3(F.ntrees, nq), 256, 0, st>>>(k3, M, ym, part);
+    MRA_CK_LAUNCH();
+    k_pilot_reduce<<<F.ntrees, 32, 0, st>>>(nq, part, S->dv);
     MRA_CK_LAUNCH();
     MRA_TRY(schedule_smem_attr(M, F.lm));
     k_schedule<<<F.ntrees, 256, schedule_smem(M, F.lm), st>>>(M, F.lm, F.nlev, unscreened, op->eps, op->w, op->nF,

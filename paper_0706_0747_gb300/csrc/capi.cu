@@ -288,7 +288,7 @@ int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, d
     }
     if (!rebuilt) op = *op_cache;
     else op = op_cache ? *op_cache : o.op;
-    MRA_TRY(mra_compress(o.P, 0, stream));                                          // Step 3
+    MRA_TRY(mra_compress(o.P, MRA_COMPRESS_SCALING, stream));                       // Step 3
     mra_apply_stats st{};
     MRA_TRY(mra_apply_ns(op, o.P, opts, stream, &o.g, &st));
     MRA_TRY(assemble_impl(o.g, (cudaStream_t)stream));  // eq. g_assemble; leaf data only
@@ -322,10 +322,14 @@ int mra_kalos_step(const mra_tree* phi, const mra_potential* v, double length, d
     return MRA_OK;
 }
 
-int mra_compress(mra_tree* t, int store_d, void* stream) {
+int mra_compress(mra_tree* t, int mode, void* stream) {
     if (!tree_ok(t)) { set_error("invalid tree handle"); return MRA_EINVAL; }
     if (t->state == MRA_TREE_NSFORM) { set_error("compress needs leaf data; assemble an ns-form tree first"); return MRA_ESTATE; }
-    return compress_impl(t, store_d, (cudaStream_t)stream);
+    if (mode != MRA_COMPRESS_NORMS && mode != MRA_COMPRESS_STORE_D && mode != MRA_COMPRESS_SCALING) {
+        set_error("compress mode %d is not one of MRA_COMPRESS_NORMS, _STORE_D, _SCALING", mode);
+        return MRA_EINVAL;
+    }
+    return compress_impl(t, mode, (cudaStream_t)stream);
 }
 
 // the operator in R^d (d = 3; d = 2 for the two-dimensional variant)
@@ -429,7 +433,7 @@ int mra_reconstruct(mra_tree* t, int mode, int truncate, double eps, void* strea
     if (mode == MRA_RECON_ASSEMBLE) {
         if (t->state != MRA_TREE_NSFORM) { set_error("assemble needs an ns-form tree"); return MRA_ESTATE; }
         MRA_TRY(assemble_impl(t, st));
-        MRA_TRY(compress_impl(t, 0, st));
+        MRA_TRY(compress_impl(t, MRA_COMPRESS_NORMS, st));
         if (truncate) {
             if (!(eps > 0.0)) { set_error("truncation eps must be > 0"); return MRA_EINVAL; }
             MRA_TRY(truncate_impl(t, eps, st, truncation_l2_host));

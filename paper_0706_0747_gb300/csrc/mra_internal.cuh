@@ -108,6 +108,7 @@ struct mra_tree {
     mra::TreeArrays a;
     double* s = nullptr;      // n * k^3 blocks
     double* dnorm = nullptr;  // n
+    void* slab = nullptr;     // one allocation holding a's arrays, s and dnorm
     double* dcube = nullptr;  // n * (2k)^3 wavelet cubes (optional)
     double* filt = nullptr;   // H0, H1 (2 k^2) then W (4 k^2), row-major
     mra::Alloc A;
@@ -165,7 +166,7 @@ void tree_free_arrays(mra_tree* t);
 int tree_link_and_upload(mra_tree* t, const int32_t* coords_host, const int32_t* leaf_host);
 int build_tree_impl(const mra_density* f, int k, double eps, int max_level, int uniform_level,
                     int init_level, const Alloc& A, mra_tree** out);
-int compress_impl(mra_tree* t, int store_d, cudaStream_t st);
+int compress_impl(mra_tree* t, int mode, cudaStream_t st);  // mode: MRA_COMPRESS_*
 int scan_exclusive(const int32_t* in, int32_t* out, int n, int32_t* total, cudaStream_t st);
 int inverse_impl(mra_tree* t, cudaStream_t st);
 int assemble_impl(mra_tree* t, cudaStream_t st);

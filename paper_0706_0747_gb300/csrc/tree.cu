@@ -113,17 +113,45 @@ __device__ double block_max(double v, double* red) {
 }
 
 // ------------------------------------------------------------ arrays
+// A tree's node arrays, wavelet norms and blocks share one allocation (one call
+// into the allocator), each array on a 256-byte boundary; the node arrays come
+// first, in the order below, so that a skeleton is one contiguous copy.
+struct SlabLayout {
+    size_t key, coord, leaf, child, parent, off, nodes_end, dnorm, s, total;
+    SlabLayout(size_t n, size_t k3, bool with_s) {
+        size_t at = 0;
+        auto take = [&](size_t bytes) {
+            const size_t o = at;
+            at += (bytes + 255) / 256 * 256;
+            return o;
+        };
+        key = take(n * sizeof(uint64_t));
+        coord = take(4 * n * sizeof(int32_t));
+        leaf = take(n * sizeof(int32_t));
+        child = take(n * sizeof(int32_t));
+        parent = take(n * sizeof(int32_t));
+        off = take((MRA_MAX_LEVEL + 2) * sizeof(int32_t));
+        nodes_end = at;
+        dnorm = take(n * sizeof(double));
+        s = take(with_s ? n * k3 * sizeof(double) : 0);
+        total = at;
+    }
+};
+
 int tree_alloc_arrays(mra_tree* t, int n, bool with_s) {
     const Alloc& A = t->A;
-    const int k3 = t->k * t->k * t->k;
-    MRA_TRY(dalloc(A, &t->a.key, n));
-    MRA_TRY(dalloc(A, &t->a.coord, 4 * (size_t)n));
-    MRA_TRY(dalloc(A, &t->a.leaf, n));
-    MRA_TRY(dalloc(A, &t->a.child, n));
-    MRA_TRY(dalloc(A, &t->a.parent, n));
-    MRA_TRY(dalloc(A, &t->a.off, MRA_MAX_LEVEL + 2));
-    MRA_TRY(dalloc(A, &t->dnorm, n));
-    if (with_s) MRA_TRY(dalloc(A, &t->s, (size_t)n * k3));
+    const SlabLayout L((size_t)n, (size_t)t->k * t->k * t->k, with_s);
+    unsigned char* base;
+    MRA_TRY(dalloc(A, &base, L.total));
+    t->slab = base;
+    t->a.key = (uint64_t*)(base + L.key);
+    t->a.coord = (int32_t*)(base + L.coord);
+    t->a.leaf = (int32_t*)(base + L.leaf);
+    t->a.child = (int32_t*)(base + L.child);
+    t->a.parent = (int32_t*)(base + L.parent);
+    t->a.off = (int32_t*)(base + L.off);
+    t->dnorm = (double*)(base + L.dnorm);
+    t->s = with_s ? (double*)(base + L.s) : nullptr;
     if (!t->filt) {
         MRA_TRY(dalloc(A, &t->filt, 6 * t->k * t->k));
         MRA_TRY(launch_filters(t->k, t->filt, A.stream));
@@ -134,10 +162,10 @@ int tree_alloc_arrays(mra_tree* t, int n, bool with_s) {
 
 void tree_free_arrays(mra_tree* t) {
     const Alloc& A = t->A;
-    A.put(t->a.key); A.put(t->a.coord); A.put(t->a.leaf); A.put(t->a.child); A.put(t->a.parent);
-    A.put(t->a.off); A.put(t->dnorm); A.put(t->s); A.put(t->dcube);
+    A.put(t->slab);
+    A.put(t->dcube);
     t->a = TreeArrays();
-    t->dnorm = nullptr; t->s = nullptr; t->dcube = nullptr;
+    t->dnorm = nullptr; t->s = nullptr; t->dcube = nullptr; t->slab = nullptr;
 }
 
 // Host-side validation and linking of an imported node list; uploads key,
@@ -216,16 +244,9 @@ int tree_clone_skeleton(const mra_tree* src, mra_tree** out) {
     }
     if (rc == MRA_OK) rc = tree_alloc_arrays(t, src->n, true);
     if (rc != MRA_OK) { tree_free_arrays(t); t->A.put(t->filt); delete t; return rc; }
-    cudaStream_t st = t->A.stream;
-    const int n = src->n;
-#define CPY(dst, s_, cnt) MRA_CK(cudaMemcpyAsync(dst, s_, (cnt) * sizeof(*(dst)), cudaMemcpyDeviceToDevice, st))
-    CPY(t->a.key, src->a.key, n);
-    CPY(t->a.coord, src->a.coord, 4 * (size_t)n);
-    CPY(t->a.leaf, src->a.leaf, n);
-    CPY(t->a.child, src->a.child, n);
-    CPY(t->a.parent, src->a.parent, n);
-    CPY(t->a.off, src->a.off, MRA_MAX_LEVEL + 2);
-#undef CPY
+    // both slabs are laid out for the same node count: the skeleton is one copy
+    const SlabLayout L((size_t)src->n, (size_t)src->k * src->k * src->k, true);
+    MRA_CK(cudaMemcpyAsync(t->slab, src->slab, L.nodes_end, cudaMemcpyDeviceToDevice, t->A.stream));
     *out = t;
     return MRA_OK;
 }
@@ -680,7 +701,7 @@ __global__ void k_up_level(int k, int lo, int hi, const int32_t* child, double* 
 // as ||cube - (U x U x U) s_parent||, which equals ||d|| because the filter
 // matrix is orthogonal (cube = W^T [s; d]).  Block per node of level j.
 __global__ void k_compress_fast_level(int k, int lo, int hi, const int32_t* child, double* s, double* dnorm,
-                                      const double* filt) {
+                                      const double* filt, int norms) {
     extern __shared__ double sm[];
     __shared__ double red[32];
     const int i = lo + blockIdx.x;
@@ -707,6 +728,7 @@ __global__ void k_compress_fast_level(int k, int lo, int hi, const int32_t* chil
     int n2[3] = {k, k, k2};
     stage_mul(r2, sp, n2, 2, D, k);
     for (int e = threadIdx.x; e < k3; e += blockDim.x) s[(size_t)i * k3 + e] = sp[e];
+    if (!norms) return;
     int m0[3] = {k, k, k};
     stage_mul(sp, r2, m0, 0, U, k2);
     int m1[3] = {k2, k, k};
@@ -826,7 +848,7 @@ __global__ void k_up_level_t(int lo, int hi, const int32_t* child, double* s, co
 // children (eq. decomp_scaling), and the wavelet norm as ||cube - (U x U x U) s_parent||,
 // which equals ||d|| because the filter matrix is orthogonal (cube = W^T [s; d]).
 // Block per internal node of level j.
-template <int K>
+template <int K, bool NORMS>
 __global__ void k_compress_fast_level_t(int lo, int hi, const int32_t* child, double* s, double* dnorm,
                                         const double* filt) {
     using L = TriSmem<K>;
@@ -857,6 +879,7 @@ __global__ void k_compress_fast_level_t(int lo, int hi, const int32_t* child, do
         const int i1 = e / (K * K), i2 = (e / K) % K, i3 = e % K;
         s[(size_t)i * K3 + e] = sp[(i1 * K + i2) * P1 + i3];
     }
+    if (!NORMS) return;  // the scaling blocks only (half of the work)
     fiber_stage<K, K, K, K * P1, P1, 0, K2, K * P1, P1, TRI_U, K>(sp, ra, U);       // (2k, k, k)
     fiber_stage<K2, K, K, K * P1, P1, 1, K2, K2 * P1, P1, TRI_U, K>(ra, rb, U);     // (2k, 2k, k)
     double acc = 0.0;
@@ -882,14 +905,15 @@ __global__ void k_compress_fast_level_t(int lo, int hi, const int32_t* child, do
 }
 
 template <int K>
-static int compress_fast_t(mra_tree* t, cudaStream_t st) {
+static int compress_fast_t(mra_tree* t, bool norms, cudaStream_t st) {
     using L = TriSmem<K>;
     const size_t smem = (size_t)(L::MATS + L::CUBE + L::RA + L::RB + L::SP) * sizeof(double);
-    MRA_CK(cudaFuncSetAttribute(k_compress_fast_level_t<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto fn = norms ? k_compress_fast_level_t<K, true> : k_compress_fast_level_t<K, false>;
+    MRA_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int j = t->nlev - 2; j >= 0; --j) {
         int lo = t->off[j], hi = t->off[j + 1];
         if (hi <= lo) continue;
-        k_compress_fast_level_t<K><<<hi - lo, 256, smem, st>>>(lo, hi, t->a.child, t->s, t->dnorm, t->filt);
+        fn<<<hi - lo, 256, smem, st>>>(lo, hi, t->a.child, t->s, t->dnorm, t->filt);
         MRA_CK_LAUNCH();
     }
     return MRA_OK;
@@ -915,12 +939,18 @@ static int cube_smem(int k, size_t* bytes, const void* fn) {
     return MRA_OK;
 }
 
-int compress_impl(mra_tree* t, int store_d, cudaStream_t st) {
-    if (!store_d) {
+int compress_impl(mra_tree* t, int mode, cudaStream_t st) {
+    if (mode != MRA_COMPRESS_STORE_D) {
         const int k = t->k;
+        const bool norms = mode == MRA_COMPRESS_NORMS;
+        if (t->dcube) {  // wavelet cubes of an earlier compress no longer match the blocks
+            t->A.put(t->dcube);
+            t->dcube = nullptr;
+        }
         MRA_CK(cudaMemsetAsync(t->dnorm, 0, t->n * sizeof(double), st));
         if (k == 4 || k == 6 || k == 8) {
-            MRA_TRY(k == 4 ? compress_fast_t<4>(t, st) : (k == 6 ? compress_fast_t<6>(t, st) : compress_fast_t<8>(t, st)));
+            MRA_TRY(k == 4 ? compress_fast_t<4>(t, norms, st)
+                           : (k == 6 ? compress_fast_t<6>(t, norms, st) : compress_fast_t<8>(t, norms, st)));
             t->state = MRA_TREE_REDUNDANT;
             return MRA_OK;
         }
@@ -929,7 +959,8 @@ int compress_impl(mra_tree* t, int store_d, cudaStream_t st) {
         for (int j = t->nlev - 2; j >= 0; --j) {
             int lo = t->off[j], hi = t->off[j + 1];
             if (hi <= lo) continue;
-            k_compress_fast_level<<<hi - lo, 256, smem, st>>>(k, lo, hi, t->a.child, t->s, t->dnorm, t->filt);
+            k_compress_fast_level<<<hi - lo, 256, smem, st>>>(k, lo, hi, t->a.child, t->s, t->dnorm, t->filt,
+                                                              norms ? 1 : 0);
             MRA_CK_LAUNCH();
         }
         t->state = MRA_TREE_REDUNDANT;
@@ -937,13 +968,13 @@ int compress_impl(mra_tree* t, int store_d, cudaStream_t st) {
     }
     size_t smem;
     MRA_TRY(cube_smem(t->k, &smem, (const void*)k_compress_level));
-    if (store_d && !t->dcube) MRA_TRY(dalloc(t->A, &t->dcube, (size_t)t->n * 8 * t->k * t->k * t->k));
+    if (!t->dcube) MRA_TRY(dalloc(t->A, &t->dcube, (size_t)t->n * 8 * t->k * t->k * t->k));
     MRA_CK(cudaMemsetAsync(t->dnorm, 0, t->n * sizeof(double), st));
     for (int j = t->nlev - 2; j >= 0; --j) {
         int lo = t->off[j], hi = t->off[j + 1];
         if (hi <= lo) continue;
         k_compress_level<<<hi - lo, 256, smem, st>>>(t->k, lo, hi, t->a.child, t->s, t->dnorm,
-                                                     store_d ? t->dcube : nullptr, t->filt);
+                                                     t->dcube, t->filt);
         MRA_CK_LAUNCH();
     }
     t->state = MRA_TREE_REDUNDANT;
@@ -952,7 +983,7 @@ int compress_impl(mra_tree* t, int store_d, cudaStream_t st) {
 
 int inverse_impl(mra_tree* t, cudaStream_t st) {
     if (!t->dcube) {
-        set_error("inverse transform needs a tree compressed with store_d");
+        set_error("inverse transform needs a tree compressed with MRA_COMPRESS_STORE_D");
         return MRA_ESTATE;
     }
     size_t smem;
@@ -986,20 +1017,23 @@ int assemble_impl(mra_tree* t, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ truncation
+// sum over the leaves of ||s||^2; a block takes whole nodes (no per-element division)
 __global__ void k_leaf_norm2(int n, int k3, const int32_t* leaf, const double* s, double* out) {
     __shared__ double red[32];
     double acc = 0.0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * k3;
-         e += (size_t)gridDim.x * blockDim.x) {
-        size_t i = e / k3;
-        if (leaf[i]) acc += s[e] * s[e];
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        if (!leaf[i]) continue;
+        const double* x = s + (size_t)i * k3;
+        for (int e = threadIdx.x; e < k3; e += blockDim.x) acc += x[e] * x[e];
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) atomicAdd(out, acc);
 }
 
+static int leaf_norm2_grid(int n) { return std::max(1, std::min(n, num_sms() * 4)); }
+
 int leaf_norm2(const mra_tree* t, double* out, cudaStream_t st) {
-    k_leaf_norm2<<<256, 256, 0, st>>>(t->n, t->k * t->k * t->k, t->a.leaf, t->s, out);
+    k_leaf_norm2<<<leaf_norm2_grid(t->n), 256, 0, st>>>(t->n, t->k * t->k * t->k, t->a.leaf, t->s, out);
     MRA_CK_LAUNCH();
     return MRA_OK;
 }
@@ -1030,6 +1064,14 @@ __global__ void k_fill_i32(int32_t* p, int n, int32_t v) {
     if (i < n) p[i] = v;
 }
 
+// lev[j] = newidx[off[j]] (n2 for a level that starts at or past the end), lev[MAX+2] = n2
+__global__ void k_level_starts(int n, const int32_t* off, const int32_t* newidx, const int32_t* total, int32_t* lev) {
+    const int j = threadIdx.x;
+    const int32_t n2 = *total;
+    if (j < MRA_MAX_LEVEL + 2) lev[j] = off[j] < n ? newidx[off[j]] : n2;
+    if (j == 0) lev[MRA_MAX_LEVEL + 2] = n2;
+}
+
 __global__ void k_compact(int n, int k3, const int32_t* alive, const int32_t* newidx, mra::TreeArrays a,
                           const double* s, const double* dnorm, mra::TreeArrays b, double* s2, double* dn2) {
     int i = blockIdx.x;
@@ -1050,13 +1092,14 @@ int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host
     const int n = t->n, k3 = t->k * t->k * t->k;
     Scratch tmpmem(t->A);
     double* dv;  // [0] ||g||^2, [1] thr^2, [2] removed^2
-    int32_t *alive, *newidx, *total;
+    int32_t *alive, *newidx, *total, *lev;
     MRA_TRY(tmpmem.get(&dv, 4));
     MRA_TRY(tmpmem.get(&alive, n));
     MRA_TRY(tmpmem.get(&newidx, n));
     MRA_TRY(tmpmem.get(&total, 1));
+    MRA_TRY(tmpmem.get(&lev, MRA_MAX_LEVEL + 3));
     MRA_CK(cudaMemsetAsync(dv, 0, 4 * sizeof(double), st));
-    k_leaf_norm2<<<256, 256, 0, st>>>(n, k3, t->a.leaf, t->s, dv);
+    k_leaf_norm2<<<leaf_norm2_grid(n), 256, 0, st>>>(n, k3, t->a.leaf, t->s, dv);
     MRA_CK_LAUNCH();
     k_thr2<<<1, 1, 0, st>>>(dv, n, eps, dv + 1);
     MRA_CK_LAUNCH();
@@ -1070,13 +1113,16 @@ int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host
         MRA_CK_LAUNCH();
     }
     MRA_TRY(scan_exclusive(alive, newidx, n, total, st));
-    std::vector<int32_t> hidx(n);
-    int32_t n2 = 0;
+    // the new first index of every level (the exclusive scan at the level's old first
+    // index) and the new node count, gathered on the device: one small read-back
+    k_level_starts<<<1, 32, 0, st>>>(n, t->a.off, newidx, total, lev);
+    MRA_CK_LAUNCH();
+    int32_t hlev[MRA_MAX_LEVEL + 3];
     double rem2 = 0.0;
-    MRA_CK(cudaMemcpyAsync(hidx.data(), newidx, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    MRA_CK(cudaMemcpyAsync(&n2, total, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MRA_CK(cudaMemcpyAsync(hlev, lev, sizeof(hlev), cudaMemcpyDeviceToHost, st));
     MRA_CK(cudaMemcpyAsync(&rem2, dv + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
     MRA_CK(cudaStreamSynchronize(st));
+    const int32_t n2 = hlev[MRA_MAX_LEVEL + 2];
     if (removed_host) *removed_host = sqrt(rem2);
     if (n2 != n) {
         mra_tree tmp;
@@ -1093,7 +1139,7 @@ int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host
         int off2[MRA_MAX_LEVEL + 2];
         int nlev2 = 0;
         // exclusive scan at a level's old first index = its new first index
-        for (int j = 0; j < MRA_MAX_LEVEL + 2; ++j) off2[j] = (t->off[j] < n) ? hidx[t->off[j]] : n2;
+        for (int j = 0; j < MRA_MAX_LEVEL + 2; ++j) off2[j] = hlev[j];
         for (int j = 0; j < t->nlev; ++j)
             if (off2[j] < n2) nlev2 = j + 1;
         for (int j = nlev2; j < MRA_MAX_LEVEL + 2; ++j) off2[j] = n2;
@@ -1101,13 +1147,13 @@ int truncate_impl(mra_tree* t, double eps, cudaStream_t st, double* removed_host
         t->a = tmp.a;
         t->s = tmp.s;
         t->dnorm = tmp.dnorm;
+        t->slab = tmp.slab;
         t->n = n2;
         t->nlev = nlev2;
         memcpy(t->off, off2, sizeof(off2));
         MRA_CK(cudaMemcpyAsync(t->a.off, t->off, sizeof(t->off), cudaMemcpyHostToDevice, st));
         tmp.filt = nullptr;
     }
-    MRA_CK(cudaStreamSynchronize(st));
     return MRA_OK;
 }
 

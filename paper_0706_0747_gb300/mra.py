@@ -523,8 +523,15 @@ def reconstruct2(tree, truncate=False, eps=0.0, stream=None):
     return rem.value
 
 
-def compress(tree, store_d=False, stream=None):
-    _check(lib().mra_compress(tree.h, int(store_d), _stream(stream)))
+COMPRESS_NORMS, COMPRESS_STORE_D, COMPRESS_SCALING = 0, 1, 2
+
+
+def compress(tree, store_d=False, stream=None, norms=True):
+    """mra_compress: store_d keeps the wavelet cubes (mode MRA_COMPRESS_STORE_D);
+    norms=False computes the scaling blocks only (MRA_COMPRESS_SCALING), all that
+    apply_ns reads of its input."""
+    mode = COMPRESS_STORE_D if store_d else (COMPRESS_NORMS if norms else COMPRESS_SCALING)
+    _check(lib().mra_compress(tree.h, mode, _stream(stream)))
 
 
 def make_operator(mu, alpha, eps, k, max_level, stream=None, allocator="torch"):

@@ -15,7 +15,7 @@ def main(prec="tc", screen="static"):
     cfg, dens = W.poisson_k8()
     op = mra.make_operator(cfg.mu, cfg.alpha, cfg.eps, cfg.k, cfg.max_level)
     tree, _ = mra.build_tree(dens, cfg.k, cfg.eps, cfg.max_level, init_level=cfg.init_level)
-    mra.compress(tree)
+    mra.compress(tree, norms=False)
     st = None
     for _ in range(2):
         g, st = mra.apply_ns(op, tree, precision=prec, screen=screen)

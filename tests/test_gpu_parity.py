@@ -120,6 +120,35 @@ def test_compress_without_stored_cubes(k):
             assert abs(dn[key] - n.dnorm) <= 1e-12 * n.dnorm + 1e-14 * scale
 
 
+@pytest.mark.parametrize("k", [3, 8])
+def test_compress_scaling_only(k):
+    """MRA_COMPRESS_SCALING: the same scaling blocks as the full compress (bit
+    for bit: the same H stages run), wavelet norms left at zero, the same
+    apply output; an unknown mode is refused, and a recompress without cubes
+    drops the stored ones (the inverse transform then refuses)."""
+    to, _ = OT.build_tree(DENS2, k, 1e-5, 4, init_level=1)
+    ta = gpu_tree_from_oracle(to, k)
+    tb = gpu_tree_from_oracle(to, k)
+    mra.compress(ta)
+    mra.compress(tb, norms=False)
+    _, _, ba, dna = ta.export()
+    _, _, bb, dnb = tb.export()
+    assert np.array_equal(ba, bb)
+    assert not dnb.any() and dna.any()
+    op = mra.make_operator(0.0, 1.0, 1e-5, k, 4)
+    ga, _ = mra.apply_ns(op, ta)
+    gb, _ = mra.apply_ns(op, tb)
+    assert np.array_equal(ga.export()[2], gb.export()[2])
+    with pytest.raises(mra.MraError) as e:
+        mra._check(mra.lib().mra_compress(ta.h, 3, None))
+    assert e.value.code == mra.EINVAL
+    mra.compress(ta, store_d=True)
+    mra.compress(ta, norms=False)
+    with pytest.raises(mra.MraError) as e:
+        mra.reconstruct(ta, mode="inverse")
+    assert e.value.code == mra.ESTATE
+
+
 def run_both(tree_o, op_o, op_g, k, precision="fp64", **kw):
     tg = gpu_tree_from_oracle(tree_o, k)
     mra.compress(tg)
