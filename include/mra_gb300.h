@@ -27,6 +27,9 @@
  *     failing call releases every device block it took before it returns.
  *   - Device memory comes from the optional allocator hook (mra_alloc); when the
  *     hook is NULL the library uses cudaMallocAsync / cudaFreeAsync on `stream`.
+ *     Blocks the library frees are kept (up to 4 GiB) for reuse by later calls
+ *     with the same hook, stream and size, and go back to the hook only through
+ *     mra_release_cached(): a hook must stay valid until then.
  *   - There is no CPU fallback: every arithmetic step runs in the library's
  *     CUDA kernels on the current device.
  *
@@ -66,7 +69,10 @@ typedef struct mra_mlp mra_mlp;
 typedef struct mra_tree2 mra_tree2;
 
 /* Device allocator hook: alloc returns device memory of `bytes` usable on
- * `stream` (NULL on failure); free releases it.  ctx is passed through. */
+ * `stream` (NULL on failure); free releases it.  ctx is passed through.  The
+ * library keeps the blocks it frees in a stream-ordered cache keyed by
+ * (hook, stream, size) and reuses them for requests with the same key, so a
+ * repeated call reaches the hook only for sizes it has not seen. */
 typedef struct {
     void* (*alloc)(size_t bytes, void* stream, void* ctx);
     void  (*free)(void* ptr, void* stream, void* ctx);
@@ -688,6 +694,12 @@ const char* mra_version(void);
 /* Number of kernels this library has launched in this process (all
  * devices, all threads); differences bracket a region of interest. */
 unsigned long long mra_kernel_launches(void);
+
+/* Return every device block in the library's reuse cache to the hook (or
+ * cudaFreeAsync) it came from, on the stream it was used on; the number of
+ * bytes released.  Call it before an allocator hook goes away, or to give the
+ * memory back.  Thread-safe; blocks held by live handles are not affected. */
+size_t mra_release_cached(void);
 
 #ifdef __cplusplus
 }

@@ -5,6 +5,9 @@
 
 #include <atomic>
 #include <cmath>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
 
 #include "mra_internal.cuh"
 
@@ -42,8 +45,72 @@ void set_error(const char* fmt, ...) {
     va_end(ap);
 }
 
+// ---------------------------------------------------------------- block cache
+// Stream-ordered cache in front of the allocator hook (or cudaMallocAsync): a
+// block the library frees is kept under (hook, stream, size) and handed out
+// again to the next request with the same hook, stream and size.  Every use of
+// a block is ordered on its stream, so reuse on that stream needs no event, and
+// nothing is reused across streams or hooks.  A step of the method allocates the
+// same sizes every time, so after the first step no call reaches the hook (each
+// hook call can be a round trip into an interpreter).  At most kCacheLimit bytes
+// are kept; mra_release_cached() returns every cached block to its hook.
+namespace {
+struct CacheKey {
+    void* alloc_fn;
+    void* free_fn;
+    void* ctx;
+    void* stream;
+    size_t bytes;
+    bool operator==(const CacheKey& o) const {
+        return alloc_fn == o.alloc_fn && free_fn == o.free_fn && ctx == o.ctx && stream == o.stream &&
+               bytes == o.bytes;
+    }
+};
+struct CacheKeyHash {
+    size_t operator()(const CacheKey& k) const {
+        size_t h = std::hash<void*>()(k.alloc_fn);
+        for (const void* q : {k.free_fn, k.ctx, k.stream}) h = h * 1000003u ^ std::hash<const void*>()(q);
+        return h * 1000003u ^ std::hash<size_t>()(k.bytes);
+    }
+};
+struct BlockCache {
+    std::mutex mu;
+    std::unordered_map<CacheKey, std::vector<void*>, CacheKeyHash> free_blocks;
+    std::unordered_map<void*, CacheKey> live;  // blocks handed out: their key
+    size_t cached_bytes = 0;
+};
+constexpr size_t kCacheLimit = (size_t)4 << 30;
+BlockCache& block_cache() {
+    static BlockCache* c = new BlockCache();  // never destroyed: frees may run at exit
+    return *c;
+}
+void raw_free(const CacheKey& k, void* p) {
+    if (k.free_fn) {
+        auto fn = (void (*)(void*, void*, void*))k.free_fn;
+        fn(p, k.stream, k.ctx);
+    } else {
+        cudaFreeAsync(p, (cudaStream_t)k.stream);
+    }
+}
+}  // namespace
+
 void* Alloc::get(size_t bytes) const {
     if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) / 256 * 256;
+    const CacheKey key{has ? (void*)hook.alloc : nullptr, has ? (void*)hook.free : nullptr, has ? hook.ctx : nullptr,
+                       (void*)stream, bytes};
+    BlockCache& C = block_cache();
+    {
+        std::lock_guard<std::mutex> lk(C.mu);
+        auto it = C.free_blocks.find(key);
+        if (it != C.free_blocks.end() && !it->second.empty()) {
+            void* p = it->second.back();
+            it->second.pop_back();
+            C.cached_bytes -= bytes;
+            C.live.emplace(p, key);
+            return p;
+        }
+    }
     void* p = nullptr;
     if (has) {
         p = hook.alloc(bytes, (void*)stream, hook.ctx);
@@ -51,13 +118,52 @@ void* Alloc::get(size_t bytes) const {
         cudaGetLastError();
         p = nullptr;
     }
+    if (p) {
+        std::lock_guard<std::mutex> lk(C.mu);
+        C.live.emplace(p, key);
+    }
     return p;
 }
 
 void Alloc::put(void* p) const {
     if (!p) return;
-    if (has) hook.free(p, (void*)stream, hook.ctx);
-    else cudaFreeAsync(p, stream);
+    BlockCache& C = block_cache();
+    CacheKey key{};
+    {
+        std::lock_guard<std::mutex> lk(C.mu);
+        auto it = C.live.find(p);
+        if (it != C.live.end()) {
+            key = it->second;
+            C.live.erase(it);
+            if (C.cached_bytes + key.bytes <= kCacheLimit) {
+                C.free_blocks[key].push_back(p);
+                C.cached_bytes += key.bytes;
+                return;
+            }
+        } else {  // not from Alloc::get: straight back to the hook
+            key = CacheKey{has ? (void*)hook.alloc : nullptr, has ? (void*)hook.free : nullptr,
+                           has ? hook.ctx : nullptr, (void*)stream, 0};
+        }
+    }
+    raw_free(key, p);
+}
+
+size_t release_cached() {
+    BlockCache& C = block_cache();
+    std::vector<std::pair<CacheKey, void*>> out;
+    {
+        std::lock_guard<std::mutex> lk(C.mu);
+        for (auto& kv : C.free_blocks)
+            for (void* p : kv.second) out.emplace_back(kv.first, p);
+        C.free_blocks.clear();
+        C.cached_bytes = 0;
+    }
+    size_t bytes = 0;
+    for (auto& e : out) {
+        raw_free(e.first, e.second);
+        bytes += e.first.bytes;
+    }
+    return bytes;
 }
 
 Alloc make_alloc(const mra_alloc* a, void* stream) {
@@ -82,6 +188,7 @@ extern "C" {
 const char* mra_last_error(void) { return g_err; }
 const char* mra_version(void) { return "mra_gb300 0.1 (sm_103a)"; }
 unsigned long long mra_kernel_launches(void) { return g_launches.load(); }
+size_t mra_release_cached(void) { return release_cached(); }
 
 int mra_build_tree(const mra_density* f, int k, double eps, int max_level, int uniform_level, int init_level,
                    const mra_alloc* alloc, void* stream, mra_tree** out) {

@@ -176,6 +176,7 @@ SIGNATURES = {
     "mra_last_error": [],
     "mra_version": [],
     "mra_kernel_launches": [],
+    "mra_release_cached": [],
 }
 
 
@@ -194,6 +195,8 @@ def lib():
                 fn.restype = ctypes.c_char_p
             elif name == "mra_kernel_launches":
                 fn.restype = ctypes.c_ulonglong
+            elif name == "mra_release_cached":
+                fn.restype = ctypes.c_size_t
             else:
                 fn.restype = ctypes.c_int
         _lib = L
@@ -762,6 +765,12 @@ def free(handle):
 
 def kernel_launches():
     return int(lib().mra_kernel_launches())
+
+
+def release_cached():
+    """mra_release_cached: return the library's cached device blocks to their
+    allocator hooks; the number of bytes released."""
+    return int(lib().mra_release_cached())
 
 
 def version():

@@ -22,7 +22,7 @@ def lib():
 
 def declared():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*|unsigned long long)\s+(mra_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*|unsigned long long|size_t)\s+(mra_\w+)\s*\(", txt, re.M)))
 
 
 def test_header_declares_entry_points():

@@ -122,6 +122,7 @@ def test_enomem_on_every_allocation_leaks_nothing():
     # handles left over from earlier tests are released first, so that the
     # byte count below measures this test's calls only
     gc.collect()
+    mra.release_cached()
     torch.cuda.synchronize()
     base = torch.cuda.memory_allocated()
     probe = FailingAlloc(0)
@@ -129,6 +130,7 @@ def test_enomem_on_every_allocation_leaks_nothing():
     rc, _ = _sequence(probe, made)
     assert rc == mra.OK, mra.last_error()
     _free_all(made)
+    mra.release_cached()
     torch.cuda.synchronize()
     total = probe.calls
     assert not probe.live and total > 20
@@ -139,9 +141,11 @@ def test_enomem_on_every_allocation_leaks_nothing():
         assert rc == mra.ENOMEM, f"allocation {n} of {total}: status {rc} ({mra.last_error()})"
         assert out is None, f"allocation {n}: output handle set on failure"
         _free_all(made)
+        mra.release_cached()  # the reuse cache hands this hook's blocks back
         torch.cuda.synchronize()
         assert not A.live, f"allocation {n} of {total}: {len(A.live)} blocks leaked"
     gc.collect()
+    mra.release_cached()
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated() == base
 
@@ -223,6 +227,7 @@ def test_enomem_in_products_kalos_and_d2_leaks_nothing():
     variant: every failed allocation gives MRA_ENOMEM, no output handle, and
     no block left allocated once the handles made are freed."""
     gc.collect()
+    mra.release_cached()
     torch.cuda.synchronize()
     base = torch.cuda.memory_allocated()
     probe = FailingAlloc(0)
@@ -230,6 +235,7 @@ def test_enomem_in_products_kalos_and_d2_leaks_nothing():
     rc, _ = _sequence_products_d2(probe, made)
     assert rc == mra.OK, mra.last_error()
     _free_all(made)
+    mra.release_cached()
     torch.cuda.synchronize()
     total = probe.calls
     assert not probe.live and total > 20
@@ -240,9 +246,11 @@ def test_enomem_in_products_kalos_and_d2_leaks_nothing():
         assert rc == mra.ENOMEM, f"allocation {n} of {total}: status {rc} ({mra.last_error()})"
         assert out is None, f"allocation {n}: output handle set on failure"
         _free_all(made)
+        mra.release_cached()  # the reuse cache hands this hook's blocks back
         torch.cuda.synchronize()
         assert not A.live, f"allocation {n} of {total}: {len(A.live)} blocks leaked"
     gc.collect()
+    mra.release_cached()
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated() == base
 
