@@ -80,18 +80,33 @@ __global__ void k_pilot(int k, int M, const double* w, const double* F, const do
 // ------------------------------------------------------------------ forest
 __device__ inline int forest_tree(const Forest& F, int i) { return F.node_tree ? F.node_tree[i] : 0; }
 
-// ||f_b||^2 = sum over the leaves of tree b of ||s||^2 (Parseval); warp per node
+// ||f_b||^2 = sum over the leaves of tree b of ||s||^2 (Parseval).  A warp takes a
+// contiguous run of nodes (the trees of a forest are contiguous) and adds its sum to
+// its tree's total once per tree it meets, not once per node.
 __global__ void k_forest_norm2(Forest F, double* dv) {
     const int k3 = F.k * F.k * F.k, lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int i = warp; i < F.n; i += nwarps) {
+    const int per = (F.n + nwarps - 1) / nwarps;
+    const int i0 = min(F.n, warp * per), i1 = min(F.n, i0 + per);
+    // every branch below is uniform over the warp (all lanes walk the same nodes)
+    auto flush = [&](double& acc, int tree) {
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0 && acc != 0.0) atomicAdd(&dv[4 * tree], acc);
+        acc = 0.0;
+    };
+    double acc = 0.0;
+    int tree = i0 < i1 ? forest_tree(F, i0) : 0;
+    for (int i = i0; i < i1; ++i) {
+        const int b = forest_tree(F, i);
+        if (b != tree) {
+            flush(acc, tree);
+            tree = b;
+        }
         if (!F.leaf[i]) continue;
         const double* s = F.s + (size_t)i * k3;
-        double acc = 0.0;
-        for (int e = lane; e < k3; e += 32) acc += s[e] * s[e];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) atomicAdd(&dv[4 * forest_tree(F, i)], acc);
+        for (int e = lane; e < k3; e += 32) acc = fma(s[e], s[e], acc);
     }
+    flush(acc, tree);
 }
 
 // Pilot ||T_0 f_0|| in two steps: block (m, b) writes w_m (F x F x F) s0_b
@@ -334,6 +349,10 @@ struct ScreenArgs {
     const int32_t* pair_off;
     Pair* pairs;
     int32_t* err;          // [0] hash overflow
+    // [n][216] (optional): the count pass's lookup per band position -- the input node,
+    // or -1 - slot of the missing box's parent in the Step-2 set -- so that the fill
+    // pass searches nothing
+    int32_t* qin;
 };
 
 // warp per output node; lane q covers band positions q, q+32, ... < 216
@@ -369,20 +388,34 @@ __global__ void k_screen(ScreenArgs A) {
                     ci = (S == 3 && !leaf) ? 1 : 0;
                     if (cnt[(j * 4 + S) * 2 + ci] > 0) {
                         valid = true;
-                        int idx = find_key_exact(A.F.key, off[j], off[j + 1], morton3(b1, b2, b3));
-                        if (idx >= 0) in = idx;
-                        else {
-                            // keyed by the parent box (the child's level j is kept in the key)
-                            const uint64_t pk = ghost_key(j, b, b1 >> 1, b2 >> 1, b3 >> 1);
-                            const uint32_t oct = ((b1 & 1) << 2) | ((b2 & 1) << 1) | (b3 & 1);
-                            if (!FILL) {
-                                const int slot = ghost_insert(A.gtab, A.gcap, pk);
-                                if (slot < 0) atomicExch(A.err, 1);
-                                else atomicOr(&A.gmask[slot], 1u << oct);
+                        const uint32_t oct = ((b1 & 1) << 2) | ((b2 & 1) << 1) | (b3 & 1);
+                        int32_t* qc = A.qin ? A.qin + (size_t)i * 216 + q : nullptr;
+                        if (FILL && qc) {
+                            const int32_t c = *qc;
+                            if (c >= 0) in = c;
+                            else {
+                                const int slot = -1 - c;
+                                in = -1 - (A.gid[slot] + __popc(A.gmask[slot] & ((1u << oct) - 1u)));
+                            }
+                        } else {
+                            int idx = find_key_exact(A.F.key, off[j], off[j + 1], morton3(b1, b2, b3));
+                            if (idx >= 0) {
+                                in = idx;
+                                if (qc) *qc = idx;
                             } else {
-                                const int slot = ghost_find(A.gtab, A.gcap, pk);
-                                in = slot >= 0 ? -1 - (A.gid[slot] + __popc(A.gmask[slot] & ((1u << oct) - 1u))) : 0;
-                                if (slot < 0) atomicExch(A.err, 2);
+                                // keyed by the parent box (the child's level j is kept in the key)
+                                const uint64_t pk = ghost_key(j, b, b1 >> 1, b2 >> 1, b3 >> 1);
+                                if (!FILL) {
+                                    const int slot = ghost_insert(A.gtab, A.gcap, pk);
+                                    if (slot < 0) atomicExch(A.err, 1);
+                                    else atomicOr(&A.gmask[slot], 1u << oct);
+                                    if (qc) *qc = -1 - (slot < 0 ? 0 : slot);
+                                } else {
+                                    const int slot = ghost_find(A.gtab, A.gcap, pk);
+                                    in = slot >= 0 ? -1 - (A.gid[slot] + __popc(A.gmask[slot] & ((1u << oct) - 1u)))
+                                                   : 0;
+                                    if (slot < 0) atomicExch(A.err, 2);
+                                }
                             }
                         }
                     }
@@ -769,7 +802,8 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
     MRA_TRY(dalloc(A, &S->err, 2));
     MRA_CK(cudaMemsetAsync(S->dv, 0, 4 * (size_t)F.ntrees * sizeof(double), st));
     MRA_CK(cudaMemsetAsync(S->err, 0, 2 * sizeof(int32_t), st));
-    const int nb_norm = (int)std::max<long>(1, std::min<long>(num_sms() * 16, ((long)n * 32 + 255) / 256));
+    // about eight nodes per warp (eight warps per block), so that few atomics meet
+    const int nb_norm = (int)std::max<long>(1, std::min<long>(num_sms() * 16, ((long)n + 63) / 64));
     k_forest_norm2<<<nb_norm, 256, 0, st>>>(F, S->dv);
     MRA_CK_LAUNCH();
     Scratch tmp(A);
@@ -791,6 +825,9 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
     ScreenArgs sa;
     sa.F = F; sa.M = M; sa.sl = S->sl; sa.sched = S->sched;
     sa.count = S->count; sa.pair_off = S->pair_off; sa.pairs = nullptr; sa.err = S->err;
+    // the count pass's lookups, kept for the fill pass (when they take at most 1 GiB)
+    sa.qin = nullptr;
+    if ((size_t)n * 216 * sizeof(int32_t) <= ((size_t)1 << 30)) MRA_TRY(tmp.get(&sa.qin, (size_t)n * 216));
     const int sblocks = (int)std::max<long>(1, std::min<long>(num_sms() * 32, ((long)n * 32 + 255) / 256));
     // parents of missing boxes: 16 slots per node to start (a box's band has at most
     // 27 parent boxes, shared with its neighbours), regrown x4 on a probe overflow
@@ -1162,7 +1199,7 @@ int apply_noalloc_impl(const mra_op* op, const mra_tree* f, int precision, doubl
     ScreenArgs sa;
     sa.F = F; sa.M = M; sa.sl = sl; sa.sched = sched;
     sa.gtab = gtab; sa.gcap = NA_HASH_CAP; sa.gid = gid; sa.gmask = gmask;
-    sa.count = count; sa.pair_off = pair_off; sa.pairs = nullptr; sa.err = err;
+    sa.count = count; sa.pair_off = pair_off; sa.pairs = nullptr; sa.err = err; sa.qin = nullptr;
     const int sblocks = (int)std::min<long>(4096, ((long)n * 32 + 255) / 256);
     k_screen<false><<<sblocks, 256, 0, st>>>(sa);
     MRA_CK_LAUNCH();
