@@ -802,15 +802,16 @@ struct TriSmem {
 };
 
 // Assembly (eq. g_assemble) with d = 0: children += (U x U x U) s_parent.
-// Block per internal node of level j (nodes[lo..hi) of the level's list).
+// Block per internal node of level j: the children of level j's internal nodes are the
+// level-(j+1) nodes in groups of eight, in the order of their parents, so block b takes
+// the group at cbase + 8 b (cbase: level j+1's first node) and its parent.
 template <int K>
-__global__ void k_up_level_t(int lo, int hi, const int32_t* child, double* s, const double* filt) {
+__global__ void k_up_level_t(int cbase, const int32_t* parent, double* s, const double* filt) {
     using L = TriSmem<K>;
     constexpr int K2 = 2 * K, K3 = K * K * K, P1 = L::P1;
     extern __shared__ double sm[];
-    const int i = lo + blockIdx.x;
-    if (i >= hi || child[i] < 0) return;
-    const int c0 = child[i];
+    const int c0 = cbase + 8 * blockIdx.x;
+    const int i = parent[c0];
     double* U = sm;
     double* D = U + 2 * K * K;
     double* x = D + 2 * K * K;  // (k, k, k), stride P1
@@ -849,15 +850,14 @@ __global__ void k_up_level_t(int lo, int hi, const int32_t* child, double* s, co
 // which equals ||d|| because the filter matrix is orthogonal (cube = W^T [s; d]).
 // Block per internal node of level j.
 template <int K, bool NORMS>
-__global__ void k_compress_fast_level_t(int lo, int hi, const int32_t* child, double* s, double* dnorm,
+__global__ void k_compress_fast_level_t(int cbase, const int32_t* parent, double* s, double* dnorm,
                                         const double* filt) {
     using L = TriSmem<K>;
     constexpr int K2 = 2 * K, K3 = K * K * K, P1 = L::P1, P2 = L::P2;
     extern __shared__ double sm[];
     __shared__ double red[32];
-    const int i = lo + blockIdx.x;
-    if (i >= hi || child[i] < 0) return;
-    const int c0 = child[i];
+    const int c0 = cbase + 8 * blockIdx.x;  // block per internal node, as in k_up_level_t
+    const int i = parent[c0];
     double* U = sm;
     double* D = U + 2 * K * K;
     double* cube = D + 2 * K * K;  // (2k, 2k, 2k), stride P2
@@ -911,9 +911,9 @@ static int compress_fast_t(mra_tree* t, bool norms, cudaStream_t st) {
     auto fn = norms ? k_compress_fast_level_t<K, true> : k_compress_fast_level_t<K, false>;
     MRA_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int j = t->nlev - 2; j >= 0; --j) {
-        int lo = t->off[j], hi = t->off[j + 1];
-        if (hi <= lo) continue;
-        fn<<<hi - lo, 256, smem, st>>>(lo, hi, t->a.child, t->s, t->dnorm, t->filt);
+        const int nparents = (t->off[j + 2] - t->off[j + 1]) / 8;
+        if (nparents <= 0) continue;
+        fn<<<nparents, 256, smem, st>>>(t->off[j + 1], t->a.parent, t->s, t->dnorm, t->filt);
         MRA_CK_LAUNCH();
     }
     return MRA_OK;
@@ -925,9 +925,9 @@ static int assemble_t(mra_tree* t, cudaStream_t st) {
     const size_t smem = (size_t)(L::MATS + L::SP + L::RA + L::RB) * sizeof(double);
     MRA_CK(cudaFuncSetAttribute(k_up_level_t<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int j = 0; j + 1 < t->nlev; ++j) {
-        int lo = t->off[j], hi = t->off[j + 1];
-        if (hi <= lo) continue;
-        k_up_level_t<K><<<hi - lo, 256, smem, st>>>(lo, hi, t->a.child, t->s, t->filt);
+        const int nparents = (t->off[j + 2] - t->off[j + 1]) / 8;
+        if (nparents <= 0) continue;
+        k_up_level_t<K><<<nparents, 256, smem, st>>>(t->off[j + 1], t->a.parent, t->s, t->filt);
         MRA_CK_LAUNCH();
     }
     return MRA_OK;
