@@ -801,62 +801,17 @@ struct TriSmem {
     static constexpr int SP = K * K * P1;                                            // (k, k, k)
 };
 
-// Assembly (eq. g_assemble) with d = 0: children += (U x U x U) s_parent.
-// Block per internal node of level j: the children of level j's internal nodes are the
-// level-(j+1) nodes in groups of eight, in the order of their parents, so block b takes
-// the group at cbase + 8 b (cbase: level j+1's first node) and its parent.
+// Redundant tree, scaling part: s_parent = (D x D x D) cube of the children (eq.
+// decomp_scaling).  Block per internal node of level j: the children of level j's
+// internal nodes are the level-(j+1) nodes in groups of eight, in the order of their
+// parents, so block b takes the group at cbase + 8 b (cbase: level j+1's first node)
+// and its parent.  The wavelet norms follow for all levels at once (k_wnorm_all).
 template <int K>
-__global__ void k_up_level_t(int cbase, const int32_t* parent, double* s, const double* filt) {
-    using L = TriSmem<K>;
-    constexpr int K2 = 2 * K, K3 = K * K * K, P1 = L::P1;
-    extern __shared__ double sm[];
-    const int c0 = cbase + 8 * blockIdx.x;
-    const int i = parent[c0];
-    double* U = sm;
-    double* D = U + 2 * K * K;
-    double* x = D + 2 * K * K;  // (k, k, k), stride P1
-    double* t1 = x + L::SP;     // (2k, k, k)
-    double* t2 = t1 + L::RA;    // (2k, 2k, k)
-    load_UD(K, filt, U, D);
-    for (int e = threadIdx.x; e < K3; e += blockDim.x) {
-        const int i1 = e / (K * K), i2 = (e / K) % K, i3 = e % K;
-        x[(i1 * K + i2) * P1 + i3] = s[(size_t)i * K3 + e];
-    }
-    __syncthreads();
-    fiber_stage<K, K, K, K * P1, P1, 0, K2, K * P1, P1, TRI_U, K>(x, t1, U);
-    fiber_stage<K2, K, K, K * P1, P1, 1, K2, K2 * P1, P1, TRI_U, K>(t1, t2, U);
-    // direction 3 per fiber (x1, x2), added into the two children (p1 p2 0) and (p1 p2 1)
-    for (int f = threadIdx.x; f < K2 * K2; f += blockDim.x) {
-        const int x1 = f / K2, x2 = f % K2;
-        const double* src = t2 + (x1 * K2 + x2) * P1;
-        double v[K];
-#pragma unroll
-        for (int c = 0; c < K; ++c) v[c] = src[c];
-        const int ob = ((x1 / K) << 2) | ((x2 / K) << 1);
-        const size_t base = ((size_t)(x1 % K) * K + (x2 % K)) * K;
-#pragma unroll
-        for (int r = 0; r < K2; ++r) {
-            double acc = 0.0;
-#pragma unroll
-            for (int c = 0; c < K; ++c)
-                if (c >= r % K) acc += U[r * K + c] * v[c];
-            s[(size_t)(c0 + ob + r / K) * K3 + base + r % K] += acc;
-        }
-    }
-}
-
-// Redundant tree without stored wavelet cubes: s_parent = (D x D x D) cube of the
-// children (eq. decomp_scaling), and the wavelet norm as ||cube - (U x U x U) s_parent||,
-// which equals ||d|| because the filter matrix is orthogonal (cube = W^T [s; d]).
-// Block per internal node of level j.
-template <int K, bool NORMS>
-__global__ void k_compress_fast_level_t(int cbase, const int32_t* parent, double* s, double* dnorm,
-                                        const double* filt) {
+__global__ void k_compress_fast_level_t(int cbase, const int32_t* parent, double* s, const double* filt) {
     using L = TriSmem<K>;
     constexpr int K2 = 2 * K, K3 = K * K * K, P1 = L::P1, P2 = L::P2;
     extern __shared__ double sm[];
-    __shared__ double red[32];
-    const int c0 = cbase + 8 * blockIdx.x;  // block per internal node, as in k_up_level_t
+    const int c0 = cbase + 8 * blockIdx.x;
     const int i = parent[c0];
     double* U = sm;
     double* D = U + 2 * K * K;
@@ -879,7 +834,95 @@ __global__ void k_compress_fast_level_t(int cbase, const int32_t* parent, double
         const int i1 = e / (K * K), i2 = (e / K) % K, i3 = e % K;
         s[(size_t)i * K3 + e] = sp[(i1 * K + i2) * P1 + i3];
     }
-    if (!NORMS) return;  // the scaling blocks only (half of the work)
+}
+
+// ---- the assembly sliced: one parent over k/2 blocks
+// Each block takes four rows x1 of the children's cube, r, k-1-r, k+r and 2k-1-r (their
+// triangular loops then have equal length), and runs the three contractions for those
+// rows alone: the contractions along directions 2 and 3 never mix rows of direction 1.
+// A level's work thus spreads over k/2 times as many blocks, which balances the large
+// levels over the SMs and runs a small level's few parents on several SMs each.
+
+// Assembly (eq. g_assemble, d = 0): children += (U x U x U) s_parent, U = D^T (row
+// p K + r has the columns c >= r), rows x1 in {q, K-1-q, K+q, 2K-1-q} of the cube.
+template <int K>
+__global__ void __launch_bounds__(128) k_up_slice(int cbase, const int32_t* parent, double* s, const double* filt) {
+    constexpr int K2 = 2 * K, K3 = K * K * K, P1 = K + 1, RX = 4;
+    __shared__ double U[K2 * K];
+    __shared__ double sp[K * K * P1];    // (i1, i2, i3), i3 padded
+    __shared__ double t1[RX * K * P1];   // (rx, i2, i3)
+    __shared__ double t2[RX * K2 * P1];  // (rx, x2, i3)
+    const int c0 = cbase + 8 * blockIdx.x, i = parent[c0], q = blockIdx.y, tid = threadIdx.x;
+    for (int e = tid; e < 2 * K * K; e += blockDim.x) {
+        const int p = e / (K * K), ii = (e / K) % K, a = e % K;  // H^(p)[ii][a]
+        U[(p * K + a) * K + ii] = filt[p * K * K + ii * K + a];
+    }
+    for (int e = tid; e < K3; e += blockDim.x) {
+        const int i1 = e / (K * K), i2 = (e / K) % K, i3 = e % K;
+        sp[(i1 * K + i2) * P1 + i3] = s[(size_t)i * K3 + e];
+    }
+    __syncthreads();
+    auto row_x1 = [&](int rx) { return (rx & 2 ? K : 0) + (rx & 1 ? K - 1 - q : q); };
+    // direction 1
+    for (int e = tid; e < RX * K * K; e += blockDim.x) {
+        const int rx = e / (K * K), i2 = (e / K) % K, i3 = e % K, x1 = row_x1(rx);
+        const double* Ur = U + x1 * K;
+        double acc = 0.0;
+        for (int c = x1 % K; c < K; ++c) acc += Ur[c] * sp[(c * K + i2) * P1 + i3];
+        t1[(rx * K + i2) * P1 + i3] = acc;
+    }
+    __syncthreads();
+    // direction 2 (x2 slowest: a warp shares its loop bound)
+    for (int e = tid; e < RX * K2 * K; e += blockDim.x) {
+        const int x2 = e / (RX * K), rx = (e / K) % RX, i3 = e % K;
+        const double* Ur = U + x2 * K;
+        double acc = 0.0;
+        for (int c = x2 % K; c < K; ++c) acc += Ur[c] * t1[(rx * K + c) * P1 + i3];
+        t2[(rx * K2 + x2) * P1 + i3] = acc;
+    }
+    __syncthreads();
+    // direction 3, added into the children's blocks
+    for (int e = tid; e < RX * K2 * K2; e += blockDim.x) {
+        const int rx = e / (K2 * K2), x2 = (e / K2) % K2, x3 = e % K2, x1 = row_x1(rx);
+        const double* Ur = U + x3 * K;
+        const double* src = t2 + (rx * K2 + x2) * P1;
+        double acc = 0.0;
+        for (int c = x3 % K; c < K; ++c) acc += Ur[c] * src[c];
+        const int o = ((x1 / K) << 2) | ((x2 / K) << 1) | (x3 / K);
+        s[(size_t)(c0 + o) * K3 + ((x1 % K) * K + x2 % K) * K + x3 % K] += acc;
+    }
+}
+
+// Wavelet norms of every internal node at once (after the scaling blocks of all
+// levels are in place): ||cube - (U x U x U) s_parent|| = ||d|| (the filter matrix is
+// orthogonal).  Block g takes the sibling group at 1 + 8 g -- the groups of all
+// levels in turn -- and its parent.
+template <int K>
+__global__ void k_wnorm_all(const int32_t* parent, const double* s, double* dnorm, const double* filt) {
+    using L = TriSmem<K>;
+    constexpr int K2 = 2 * K, K3 = K * K * K, P1 = L::P1, P2 = L::P2;
+    extern __shared__ double sm[];
+    __shared__ double red[32];
+    const int c0 = 1 + 8 * blockIdx.x;
+    const int i = parent[c0];
+    double* U = sm;
+    double* D = U + 2 * K * K;
+    double* cube = D + 2 * K * K;  // (2k, 2k, 2k), stride P2
+    double* ra = cube + L::CUBE;
+    double* rb = ra + L::RA;
+    double* sp = rb + L::RB;       // (k, k, k), stride P1
+    load_UD(K, filt, U, D);
+    for (int e = threadIdx.x; e < 8 * K3; e += blockDim.x) {
+        const int o = e / K3, r = e % K3;
+        const int i1 = r / (K * K), i2 = (r / K) % K, i3 = r % K;
+        const int x1 = ((o >> 2) & 1) * K + i1, x2 = ((o >> 1) & 1) * K + i2, x3 = (o & 1) * K + i3;
+        cube[(x1 * K2 + x2) * P2 + x3] = s[(size_t)(c0 + o) * K3 + r];
+    }
+    for (int e = threadIdx.x; e < K3; e += blockDim.x) {
+        const int i1 = e / (K * K), i2 = (e / K) % K, i3 = e % K;
+        sp[(i1 * K + i2) * P1 + i3] = s[(size_t)i * K3 + e];
+    }
+    __syncthreads();
     fiber_stage<K, K, K, K * P1, P1, 0, K2, K * P1, P1, TRI_U, K>(sp, ra, U);       // (2k, k, k)
     fiber_stage<K2, K, K, K * P1, P1, 1, K2, K2 * P1, P1, TRI_U, K>(ra, rb, U);     // (2k, 2k, k)
     double acc = 0.0;
@@ -906,14 +949,20 @@ __global__ void k_compress_fast_level_t(int cbase, const int32_t* parent, double
 
 template <int K>
 static int compress_fast_t(mra_tree* t, bool norms, cudaStream_t st) {
+    // the scaling blocks level by level, then the wavelet norms of all internal nodes in
+    // one launch
     using L = TriSmem<K>;
     const size_t smem = (size_t)(L::MATS + L::CUBE + L::RA + L::RB + L::SP) * sizeof(double);
-    auto fn = norms ? k_compress_fast_level_t<K, true> : k_compress_fast_level_t<K, false>;
-    MRA_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MRA_CK(cudaFuncSetAttribute(k_compress_fast_level_t<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int j = t->nlev - 2; j >= 0; --j) {
         const int nparents = (t->off[j + 2] - t->off[j + 1]) / 8;
         if (nparents <= 0) continue;
-        fn<<<nparents, 256, smem, st>>>(t->off[j + 1], t->a.parent, t->s, t->dnorm, t->filt);
+        k_compress_fast_level_t<K><<<nparents, 256, smem, st>>>(t->off[j + 1], t->a.parent, t->s, t->filt);
+        MRA_CK_LAUNCH();
+    }
+    if (norms && t->n > 1) {
+        MRA_CK(cudaFuncSetAttribute(k_wnorm_all<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_wnorm_all<K><<<(t->n - 1) / 8, 256, smem, st>>>(t->a.parent, t->s, t->dnorm, t->filt);
         MRA_CK_LAUNCH();
     }
     return MRA_OK;
@@ -921,13 +970,10 @@ static int compress_fast_t(mra_tree* t, bool norms, cudaStream_t st) {
 
 template <int K>
 static int assemble_t(mra_tree* t, cudaStream_t st) {
-    using L = TriSmem<K>;
-    const size_t smem = (size_t)(L::MATS + L::SP + L::RA + L::RB) * sizeof(double);
-    MRA_CK(cudaFuncSetAttribute(k_up_level_t<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int j = 0; j + 1 < t->nlev; ++j) {
         const int nparents = (t->off[j + 2] - t->off[j + 1]) / 8;
         if (nparents <= 0) continue;
-        k_up_level_t<K><<<nparents, 256, smem, st>>>(t->off[j + 1], t->a.parent, t->s, t->filt);
+        k_up_slice<K><<<dim3(nparents, K / 2), 128, 0, st>>>(t->off[j + 1], t->a.parent, t->s, t->filt);
         MRA_CK_LAUNCH();
     }
     return MRA_OK;
