@@ -2,8 +2,9 @@
 
 A step is one pass of the hot path over the resident input tree of the
 3-D Poisson workload (k = 8, eps = 1e-6, adaptive tree to depth 7, 64 unit-mass
-Gaussians): compress (redundant tree) -> apply_ns (screen, Step-2 refinement,
-separated apply) -> reconstruct (eq. g_assemble, compress, truncation).  The
+Gaussians): compress (the redundant tree's scaling blocks, all that Algorithm 3
+reads) -> apply_ns (screen, Step-2 refinement, separated apply) -> reconstruct
+(eq. g_assemble, compress with wavelet norms, truncation).  The
 operator tables and the input tree are built before timing (inputs resident in
 HBM).  The metric is block-applies/s: items of the plain FP64 screen per
 second of device time (CUDA events on the library's stream), with output
