@@ -802,8 +802,7 @@ int screen_forest(const mra_op* op, const Forest& F, int unscreened, const Alloc
     MRA_TRY(dalloc(A, &S->err, 2));
     MRA_CK(cudaMemsetAsync(S->dv, 0, 4 * (size_t)F.ntrees * sizeof(double), st));
     MRA_CK(cudaMemsetAsync(S->err, 0, 2 * sizeof(int32_t), st));
-    // about eight nodes per warp (eight warps per block), so that few atomics meet
-    const int nb_norm = (int)std::max<long>(1, std::min<long>(num_sms() * 16, ((long)n + 63) / 64));
+    const int nb_norm = (int)std::max<long>(1, std::min<long>(num_sms() * 16, ((long)n * 32 + 255) / 256));
     k_forest_norm2<<<nb_norm, 256, 0, st>>>(F, S->dv);
     MRA_CK_LAUNCH();
     Scratch tmp(A);
