@@ -244,7 +244,8 @@ __global__ void k_pair_ranges(RangeArgs R) {
         auto any = [&](int lo, int hi) { return lo <= hi && Q.max(lo, hi) * xn > eta; };
         // first / last passing term of [A, B] (one exists)
         auto first_in = [&](int A, int B) {
-            int lo = A, hi = B;
+            if (any(A, A)) return A;  // the first candidate passes (no search)
+            int lo = A + 1, hi = B;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
                 if (any(A, mid)) hi = mid;
@@ -253,7 +254,8 @@ __global__ void k_pair_ranges(RangeArgs R) {
             return lo;
         };
         auto last_in = [&](int A, int B) {
-            int lo = A, hi = B;
+            if (any(B, B)) return B;  // the last candidate passes
+            int lo = A, hi = B - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (any(mid, B)) lo = mid;
