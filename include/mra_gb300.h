@@ -29,7 +29,10 @@
  *     hook is NULL the library uses cudaMallocAsync / cudaFreeAsync on `stream`.
  *     Blocks the library frees are kept (up to 4 GiB) for reuse by later calls
  *     with the same hook, stream and size, and go back to the hook only through
- *     mra_release_cached(): a hook must stay valid until then.
+ *     mra_release_cached(): a hook must stay valid until then.  A handle takes
+ *     and returns its blocks in the order of the stream it was created on: a
+ *     call that queues work on another stream must be ordered with that stream
+ *     by the caller (an event), since a freed block can be handed out again at once.
  *   - There is no CPU fallback: every arithmetic step runs in the library's
  *     CUDA kernels on the current device.
  *

@@ -296,3 +296,44 @@ def test_mra_free_every_handle_kind():
         mra.free(obj)
         assert obj.h is None
     torch.cuda.synchronize()
+
+
+def test_block_cache_reuses_and_releases():
+    """The library's reuse cache: a repeated apply takes its blocks from the cache
+    (no call reaches the hook) and gives the same output bit for bit; a tree made
+    on another stream gets fresh blocks; mra_release_cached hands every cached
+    block back (the hook then holds only the live handles' blocks)."""
+    A = FailingAlloc(0)
+    k, eps = 4, 1e-4
+    tree, _ = mra.build_tree(DENS, k, eps, 3, uniform_level=2, allocator=A.hook)
+    mra.compress(tree, norms=False)
+    op = mra.make_operator(0.0, 1.0, eps, k, 3, allocator=A.hook)
+    g1, _ = mra.apply_ns(op, tree, precision="tc")
+    out1 = g1.export()[2]
+    g1.free()
+    calls = A.calls
+    g2, _ = mra.apply_ns(op, tree, precision="tc")
+    assert A.calls == calls  # every block of the second apply came from the cache
+    assert np.array_equal(g2.export()[2], out1)
+    g2.free()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        t2, _ = mra.build_tree(DENS, k, eps, 3, uniform_level=2, allocator=A.hook, stream=side.cuda_stream)
+        mra.compress(t2, norms=False, stream=side.cuda_stream)
+        g3, _ = mra.apply_ns(op, t2, precision="tc", stream=side.cuda_stream)
+        side.synchronize()
+    assert A.calls > calls  # blocks keyed by another stream: fresh ones from the hook
+    assert np.array_equal(g3.export(stream=side.cuda_stream)[2], out1)
+    g3.free()
+    mra.free(t2)
+    side.synchronize()
+    live_handles = dict(A.live)
+    released = mra.release_cached()
+    torch.cuda.synchronize()
+    assert released > 0 and len(A.live) < len(live_handles)
+    mra.free(tree)
+    mra.free(op)
+    mra.release_cached()
+    torch.cuda.synchronize()
+    assert not A.live
