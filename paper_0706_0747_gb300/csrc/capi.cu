@@ -222,15 +222,18 @@ int mra_tree_import(int k, int n, const int32_t* coords_host, const int32_t* lea
     t->state = MRA_TREE_LEAVES;
     t->depth_hit = 0;
     int rc = tree_alloc_arrays(t, n, true);
-    if (rc == MRA_OK) rc = tree_link_and_upload(t, coords_host, leaf_host);
     if (rc == MRA_OK) {
+        // the blocks first: from pinned memory the copy runs while the host links the
+        // node list below (which ends with a synchronisation of the stream)
         const size_t bytes = (size_t)n * k * k * k * sizeof(double);
         cudaError_t e = cudaMemcpyAsync(t->s, blocks_host, bytes, cudaMemcpyHostToDevice, t->A.stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(t->dnorm, 0, n * sizeof(double), t->A.stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(t->A.stream);
         if (e != cudaSuccess) { set_error("import copy: %s", cudaGetErrorString(e)); rc = MRA_ECUDA; }
     }
+    if (rc == MRA_OK) rc = tree_link_and_upload(t, coords_host, leaf_host);
     if (rc != MRA_OK) {
+        cudaStreamSynchronize(t->A.stream);  // no copy still reads the caller's buffers
+        cudaGetLastError();
         tree_free_arrays(t);
         t->A.put(t->filt);
         t->magic = 0;

@@ -201,6 +201,7 @@ int tree_link_and_upload(mra_tree* t, const int32_t* coords, const int32_t* leaf
     for (int i = 0; i < n; ++i) {
         int j = coords[4 * i];
         if (lf[i]) continue;
+        if (j >= MRA_MAX_LEVEL) { set_error("internal node %d lacks children (deepest level)", i); return MRA_EINVAL; }
         uint64_t ck = key[i] << 3;
         int lo = off[j + 1], hi = off[j + 2];
         int pos = (int)(std::lower_bound(key.begin() + lo, key.begin() + hi, ck) - key.begin());
@@ -214,14 +215,18 @@ int tree_link_and_upload(mra_tree* t, const int32_t* coords, const int32_t* leaf
         if (parent[i] < 0) { set_error("node %d has no parent", i); return MRA_EINVAL; }
     t->nlev = nlev;
     memcpy(t->off, off, sizeof(off));
+    // the node arrays in the slab's layout on the host, then one copy
+    const SlabLayout L((size_t)n, (size_t)t->k * t->k * t->k, true);
+    std::vector<unsigned char> stage(L.nodes_end);
+    memcpy(stage.data() + L.key, key.data(), n * sizeof(uint64_t));
+    memcpy(stage.data() + L.coord, coords, 4 * (size_t)n * sizeof(int32_t));
+    memcpy(stage.data() + L.leaf, lf.data(), n * sizeof(int32_t));
+    memcpy(stage.data() + L.child, child.data(), n * sizeof(int32_t));
+    memcpy(stage.data() + L.parent, parent.data(), n * sizeof(int32_t));
+    memcpy(stage.data() + L.off, off, sizeof(off));
     cudaStream_t st = t->A.stream;
-    MRA_CK(cudaMemcpyAsync(t->a.key, key.data(), n * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-    MRA_CK(cudaMemcpyAsync(t->a.coord, coords, 4 * (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    MRA_CK(cudaMemcpyAsync(t->a.leaf, lf.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    MRA_CK(cudaMemcpyAsync(t->a.child, child.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    MRA_CK(cudaMemcpyAsync(t->a.parent, parent.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    MRA_CK(cudaMemcpyAsync(t->a.off, off, sizeof(off), cudaMemcpyHostToDevice, st));
-    MRA_CK(cudaStreamSynchronize(st));  // host vectors go out of scope
+    MRA_CK(cudaMemcpyAsync(t->slab, stage.data(), L.nodes_end, cudaMemcpyHostToDevice, st));
+    MRA_CK(cudaStreamSynchronize(st));  // the staging vector goes out of scope
     return MRA_OK;
 }
 

@@ -333,3 +333,26 @@ def test_rejects_deeper_tree_than_operator():
     with pytest.raises(mra.MraError) as e:
         mra.apply_ns(op_g, tg)
     assert e.value.code == mra.EINVAL
+
+
+def test_import_rejects_malformed_node_lists():
+    """mra_tree_import checks the node list and names the first bad node:
+    out-of-range levels and boxes, an unsorted list, a list without the root
+    first, an internal node without its children, a node without a parent."""
+    to, _ = OT.build_tree(DENS2, 3, 1e-3, 3, init_level=1)
+    c, l, b = oracle_to_arrays(to, 3)
+    tg = mra.tree_import(3, c, l, b)          # the valid list imports
+    assert tg.info().n_nodes == len(to)
+    cases = []
+    bad = c.copy(); bad[5, 0] = 99; cases.append((bad, l, "out of range"))
+    bad = c.copy(); bad[5, 1] = 1 << int(bad[5, 0]); cases.append((bad, l, "box index out of range"))
+    bad = c.copy(); bad[[3, 4]] = bad[[4, 3]]; cases.append((bad, l, "not sorted"))
+    bad = c[1:].copy(); cases.append((bad, l[1:].copy(), "root"))
+    li = l.copy(); li[int(np.nonzero(l)[0][-1])] = 0; cases.append((c, li, "lacks child"))
+    keep = np.ones(len(c), bool); keep[int(np.nonzero(c[:, 0] == 1)[0][0])] = False   # drop one level-1 box
+    cases.append((c[keep].copy(), l[keep].copy(), ""))
+    for cc, ll, msg in cases:
+        with pytest.raises(mra.MraError) as e:
+            mra.tree_import(3, np.ascontiguousarray(cc), np.ascontiguousarray(ll), b[:len(cc)].copy())
+        assert e.value.code == mra.EINVAL
+        assert msg in str(e.value)
