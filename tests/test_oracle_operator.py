@@ -127,3 +127,27 @@ def test_estimate_bounds_true_difference(op):
             B = np.kron(np.kron(UP[Ls[0]], UP[Ls[1]]), UP[Ls[2]])
             est = op.estimate(j, m, tuple(L + 1 for L in Ls))
             assert np.linalg.norm(A - B) <= est * (1 + 1e-12) + 1e-300
+
+
+def test_coarse_blocks_are_two_scale_projections(op):
+    """The level-(j-1) block of translation L equals the 2x2 fine block matrix
+    [[F^{2L}, F^{2L-1}], [F^{2L+1}, F^{2L}]] at level j (rows: output child, columns:
+    input child) projected by the two-scale filters, D FF D^T with D = [H0 | H1] --
+    an identity of the scaling spaces (V_{j-1} inside V_j) that holds for any
+    kernel.  The two levels' tables come from separate quadratures, so this pins
+    the fine-block layout the norm estimate uses; the transposed layout fails."""
+    D = op.U.T
+    worst_wrong = 0.0
+    for j in range(1, op.max_level + 1):
+        for m in range(0, op.M, 5):
+            F = op.F[j, m]
+            for L in (-1, 0, 1):
+                C = op.F[j - 1, m, L + 3]
+                FF = np.block([[F[2 * L + 3], F[2 * L + 2]], [F[2 * L + 4], F[2 * L + 3]]])
+                # quadrature and rounding errors are relative to the term's blocks (for a
+                # narrow Gaussian the off-diagonal blocks are tiny tails of them)
+                scale = max(np.abs(op.F[j - 1, m]).max(), np.abs(F).max(), 1e-300)
+                assert np.abs(D @ FF @ D.T - C).max() <= 1e-10 * scale
+                FT = np.block([[F[2 * L + 3], F[2 * L + 4]], [F[2 * L + 2], F[2 * L + 3]]])
+                worst_wrong = max(worst_wrong, np.abs(D @ FT @ D.T - C).max() / scale)
+    assert worst_wrong > 1e-4
