@@ -841,6 +841,62 @@ __global__ void k_compress_fast_level_t(int cbase, const int32_t* parent, double
     }
 }
 
+// ---- the scaling blocks of a small level: one parent over k/2 blocks
+// Block (b, q) computes rows i1 in {q, K-1-q} of the parent's block (the contractions
+// along directions 2 and 3 never mix rows of direction 1), one output element per
+// thread and step.  It pays where a level has fewer parents than SMs: each parent then
+// runs on k/2 SMs; on the large levels the per-parent kernel below is faster.
+template <int K>
+__global__ void __launch_bounds__(128) k_down_slice(int cbase, const int32_t* parent, double* s,
+                                                    const double* filt) {
+    constexpr int K2 = 2 * K, K3 = K * K * K, P2 = K2 + 1, R = 2;
+    __shared__ double D[K * K2];
+    __shared__ double cube[K2 * K2 * P2];  // (x1, x2, x3), x3 padded
+    __shared__ double o1[R * K2 * P2];     // (r, x2, x3)
+    __shared__ double o2[R * K * P2];      // (r, i2, x3)
+    const int c0 = cbase + 8 * blockIdx.x, i = parent[c0], q = blockIdx.y, tid = threadIdx.x;
+    for (int e = tid; e < 2 * K * K; e += blockDim.x) {
+        const int p = e / (K * K), ii = (e / K) % K, a = e % K;  // H^(p)[ii][a]
+        D[ii * K2 + p * K + a] = filt[p * K * K + ii * K + a];
+    }
+    for (int e = tid; e < 8 * K3; e += blockDim.x) {
+        const int o = e / K3, r = e % K3;
+        const int i1 = r / (K * K), i2 = (r / K) % K, i3 = r % K;
+        const int x1 = ((o >> 2) & 1) * K + i1, x2 = ((o >> 1) & 1) * K + i2, x3 = (o & 1) * K + i3;
+        cube[(x1 * K2 + x2) * P2 + x3] = s[(size_t)(c0 + o) * K3 + r];
+    }
+    __syncthreads();
+    // direction 1: D = [H0 | H1] has in row i the columns a <= i of each half
+    for (int e = tid; e < R * K2 * K2; e += blockDim.x) {
+        const int r = e / (K2 * K2), x2 = (e / K2) % K2, x3 = e % K2, i1 = r ? K - 1 - q : q;
+        const double* Dr = D + i1 * K2;
+        double acc = 0.0;
+        for (int a = 0; a <= i1; ++a)
+            acc += Dr[a] * cube[(a * K2 + x2) * P2 + x3] + Dr[K + a] * cube[((K + a) * K2 + x2) * P2 + x3];
+        o1[(r * K2 + x2) * P2 + x3] = acc;
+    }
+    __syncthreads();
+    // direction 2 (i2 slowest: a warp shares its loop bound)
+    for (int e = tid; e < R * K * K2; e += blockDim.x) {
+        const int i2 = e / (R * K2), r = (e / K2) % R, x3 = e % K2;
+        const double* Dr = D + i2 * K2;
+        double acc = 0.0;
+        for (int a = 0; a <= i2; ++a)
+            acc += Dr[a] * o1[(r * K2 + a) * P2 + x3] + Dr[K + a] * o1[(r * K2 + K + a) * P2 + x3];
+        o2[(r * K + i2) * P2 + x3] = acc;
+    }
+    __syncthreads();
+    // direction 3, into rows i1 of the parent's block
+    for (int e = tid; e < R * K * K; e += blockDim.x) {
+        const int i3 = e / (R * K), r = (e / K) % R, i2 = e % K, i1 = r ? K - 1 - q : q;
+        const double* Dr = D + i3 * K2;
+        const double* src = o2 + (r * K + i2) * P2;
+        double acc = 0.0;
+        for (int a = 0; a <= i3; ++a) acc += Dr[a] * src[a] + Dr[K + a] * src[K + a];
+        s[(size_t)i * K3 + (i1 * K + i2) * K + i3] = acc;
+    }
+}
+
 // ---- the assembly sliced: one parent over k/2 blocks
 // Each block takes four rows x1 of the children's cube, r, k-1-r, k+r and 2k-1-r (their
 // triangular loops then have equal length), and runs the three contractions for those
@@ -962,7 +1018,10 @@ static int compress_fast_t(mra_tree* t, bool norms, cudaStream_t st) {
     for (int j = t->nlev - 2; j >= 0; --j) {
         const int nparents = (t->off[j + 2] - t->off[j + 1]) / 8;
         if (nparents <= 0) continue;
-        k_compress_fast_level_t<K><<<nparents, 256, smem, st>>>(t->off[j + 1], t->a.parent, t->s, t->filt);
+        if (2 * nparents < num_sms())  // a small level: each parent over k/2 blocks
+            k_down_slice<K><<<dim3(nparents, K / 2), 128, 0, st>>>(t->off[j + 1], t->a.parent, t->s, t->filt);
+        else
+            k_compress_fast_level_t<K><<<nparents, 256, smem, st>>>(t->off[j + 1], t->a.parent, t->s, t->filt);
         MRA_CK_LAUNCH();
     }
     if (norms && t->n > 1) {
