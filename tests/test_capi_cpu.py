@@ -59,6 +59,16 @@ def test_version(lib):
     assert "sm_103a" in mra.version()
 
 
+def test_compress_modes_and_cache_without_gpu(lib):
+    # the compress modes are ABI constants; a bad handle is refused before any mode check
+    assert (mra.COMPRESS_NORMS, mra.COMPRESS_STORE_D, mra.COMPRESS_SCALING) == (0, 1, 2)
+    for mode in (0, 1, 2, 3):
+        assert lib.mra_compress(None, mode, None) == mra.EINVAL
+    assert "tree handle" in mra.last_error()
+    # nothing allocated yet in this process: the reuse cache is empty
+    assert mra.release_cached() == 0
+
+
 def test_batched_and_schedule_entries_reject_invalid_arguments(lib):
     """Argument checks of the batched, network and no-alloc entries that run
     before any device work (so they need no GPU)."""
